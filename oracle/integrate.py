@@ -1,0 +1,142 @@
+"""E_xc, V_xc and N_el by numerical quadrature, in two modes.
+
+Definitional mode (D) evaluates the integrands of Eqs. exc_vvar, vxc_exact and
+zvec_r at every grid point with every basis function:
+
+    rho_i      = sum_{mu nu} P_{mu nu} phi_mu(r_i) phi_nu(r_i)
+    grad rho_i = sum_{mu nu} P_{mu nu} (grad phi_mu phi_nu + phi_mu grad phi_nu)
+    E_xc = sum_i w_i f(rho_i, sigma_i),   N_el = sum_i w_i rho_i
+    V_{mu nu} = sum_i w_i [vrho_i phi_mu phi_nu
+                + 2 vsigma_i grad rho_i . (grad phi_mu phi_nu + phi_mu grad phi_nu)].
+
+Method-equivalent mode (M) follows the batched formulation of Sec. 2.2, batch
+by batch over the screened function list S_j of each (merged) batch:
+
+    X^j = P^j Phi^j                                   (Eq. x_mat, GEMM)
+    rho_i = sum_mu Phi_{mu i} X_{mu i}                 (Eq. eval_local_den)
+    grad rho_i = 2 sum_mu grad Phi_{mu i} X_{mu i}     (Eq. eval_local_den_grad)
+    eps^j_i = w_i f,  d/drho, d/dsigma likewise         (Eq. eval_xc_batch)
+    E += sum_i eps^j_i                                 (Eq. exc_batch)
+    Z_{mu i} = 1/2 w vrho Phi_{mu i} + 2 w vsigma grad rho_i . grad Phi_{mu i}   (Eq. z_mat)
+    V^j = Z^j Phi^{jT} + Phi^j Z^{jT}                  (Eq. vxc_batch, SYR2K)
+    V_xc[S_j, S_j] += V^j                              (Eq. vxc_inc)
+
+Arrays here are point-major (row i = grid point), i.e. the transposes of the
+paper's Phi_{mu i}; the sums are the same.  M differs from D only by the
+screening (functions outside S_j are dropped) and by rounding order.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import collocation, functionals, partition, planner, quadrature
+
+CHUNK = 8192
+
+
+@dataclass
+class Grid:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    wq: np.ndarray
+    w: np.ndarray
+    parent: np.ndarray
+
+
+@dataclass
+class Result:
+    E: float
+    N: float
+    V: np.ndarray
+    E_batch: np.ndarray | None = None
+    N_batch: np.ndarray | None = None
+
+
+def make_grid(xyz, spec, weights: bool = True) -> Grid:
+    """Total quadrature Q with partitioned weights w_i = p_A(r_i) w^q_i (Eq. num_int)."""
+    x, y, z, wq, par = quadrature.molecular_grid(xyz, spec.nrad, spec.ntheta, spec.nphi, spec.mk_alpha)
+    w = None
+    if weights:
+        w = np.empty_like(wq)
+        for s in range(0, len(x), 1 << 16):
+            e = s + (1 << 16)
+            w[s:e] = wq[s:e] * partition.partition_weights(x[s:e], y[s:e], z[s:e], par[s:e], xyz,
+                                                           spec.partition)
+    return Grid(x, y, z, wq, w, par)
+
+
+def make_plan(grid: Grid, xyz, basis, spec) -> planner.Plan:
+    return planner.make_plan(grid.x, grid.y, grid.z, grid.parent, xyz, basis, spec.max_batch, spec.eta)
+
+
+def integrate_definitional(grid: Grid, basis, P, functional: str) -> Result:
+    fn = functionals.FUNCTIONALS[functional]
+    nbf = basis.nbf
+    E = 0.0
+    N = 0.0
+    V = np.zeros((nbf, nbf))
+    for s in range(0, len(grid.x), CHUNK):
+        sl = slice(s, s + CHUNK)
+        pts = np.stack([grid.x[sl], grid.y[sl], grid.z[sl]], axis=1)
+        w = grid.w[sl]
+        phi, gx, gy, gz = collocation.collocate(pts, basis)
+        rho = np.einsum("iu,uv,iv->i", phi, P, phi)
+        grad = [np.einsum("iu,uv,iv->i", g, P, phi) + np.einsum("iu,uv,iv->i", phi, P, g)
+                for g in (gx, gy, gz)]
+        sigma = grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]
+        f, vr, vs = fn(rho, sigma)
+        E += float(np.sum(w * f))
+        N += float(np.sum(w * rho))
+        # G_{i mu} = grad rho_i . grad phi_mu(r_i)
+        G = grad[0][:, None] * gx + grad[1][:, None] * gy + grad[2][:, None] * gz
+        V += phi.T @ ((w * vr)[:, None] * phi)
+        c = (2.0 * w * vs)[:, None]
+        V += (c * G).T @ phi + phi.T @ (c * G)
+    return Result(E, N, V)
+
+
+def integrate_batch(pts, w, phi_args, Pj, fn):
+    """One batch of the method-equivalent mode; returns (E_j, N_j, V^j)."""
+    phi, gx, gy, gz = phi_args
+    X = phi @ Pj                                                    # Eq. x_mat
+    rho = np.sum(phi * X, axis=1)                                   # Eq. eval_local_den
+    grad = [2.0 * np.sum(g * X, axis=1) for g in (gx, gy, gz)]      # Eq. eval_local_den_grad
+    sigma = grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]
+    f, vr, vs = fn(rho, sigma)
+    eps_w = w * f                                                   # Eq. eval_xc_batch
+    a = 0.5 * w * vr
+    b = 2.0 * w * vs
+    Z = a[:, None] * phi + b[:, None] * (grad[0][:, None] * gx + grad[1][:, None] * gy
+                                         + grad[2][:, None] * gz)   # Eq. z_mat
+    Vj = Z.T @ phi + phi.T @ Z                                      # Eq. vxc_batch
+    return float(np.sum(eps_w)), float(np.sum(w * rho)), Vj
+
+
+def integrate_method(grid: Grid, basis, P, functional: str, plan: planner.Plan,
+                     batches=None) -> Result:
+    """Method-equivalent mode over the merged batches of ``plan`` (or a subset)."""
+    fn = functionals.FUNCTIONALS[functional]
+    nbf = basis.nbf
+    V = np.zeros((nbf, nbf))
+    nb = len(plan.batch_points)
+    sel = range(nb) if batches is None else batches
+    Eb = np.zeros(nb)
+    Nb = np.zeros(nb)
+    for j in sel:
+        idx = plan.batch_points[j]
+        F = plan.batch_funcs[j]
+        if len(F) == 0:
+            continue
+        Pj = P[np.ix_(F, F)]
+        for s in range(0, len(idx), CHUNK):
+            ii = idx[s:s + CHUNK]
+            pts = np.stack([grid.x[ii], grid.y[ii], grid.z[ii]], axis=1)
+            cols = collocation.collocate(pts, basis, plan.batch_shells[j])
+            e, n, Vj = integrate_batch(pts, grid.w[ii], cols, Pj, fn)
+            Eb[j] += e
+            Nb[j] += n
+            V[np.ix_(F, F)] += Vj                                   # Eq. vxc_inc
+    return Result(float(np.sum(Eb)), float(np.sum(Nb)), V, Eb, Nb)

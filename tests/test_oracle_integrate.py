@@ -1,0 +1,145 @@
+"""Pins for the oracle's E_xc / V_xc / N_el (Eqs. exc_vvar, vxc_exact, zvec_r and the batched
+Eqs. x_mat ... z_mat), against closed forms, identities and brute force."""
+import math
+
+import numpy as np
+import pytest
+
+import xcinputs as X
+from oracle import collocation as C
+from oracle import functionals as F
+from oracle import integrate as I
+
+
+def _setup(name, **kw):
+    w = X.make_workload(name, **kw)
+    g = I.make_grid(w.mol.xyz, w.grid)
+    pl = I.make_plan(g, w.mol.xyz, w.basis, w.grid)
+    return w, g, pl
+
+
+@pytest.fixture(scope="module")
+def water1():
+    return _setup("water1_slater")
+
+
+@pytest.fixture(scope="module")
+def water1_pbe():
+    return _setup("water1_pbe_small")
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.3])
+def test_slater_exchange_of_single_s_gaussian(alpha):
+    # rho = N^2 exp(-2 a r^2), N^2 = (2a/pi)^(3/2):
+    # E_x = C_x int rho^(4/3) = C_x (2a/pi)^2 (3 pi / (8 a))^(3/2); equals -0.38275159923863333 at a = 1
+    mol = X.single_atom(8)
+    b = X.make_basis(mol, single_shell=(0, [alpha], [1.0]))
+    spec = X.GridSpec(75, 16, 32, "becke", 512)
+    g = I.make_grid(mol.xyz, spec)
+    pl = I.make_plan(g, mol.xyz, b, spec)
+    exact = F.C_X * (2 * alpha / math.pi) ** 2 * (3 * math.pi / (8 * alpha)) ** 1.5
+    if alpha == 1.0:
+        assert abs(exact - (-0.38275159923863333)) < 1e-15
+    for occ in (1.0, 2.0):
+        r = I.integrate_method(g, b, np.array([[occ]]), "slater", pl)
+        assert abs(r.E - occ ** (4 / 3) * exact) < 1e-9
+        assert abs(r.N - occ) < 1e-10
+
+
+def test_electron_count_is_trace_PS(water1):
+    w, g, pl = water1
+    r = I.integrate_method(g, w.basis, w.P, "slater", pl)
+    assert abs(np.trace(w.P @ w.S) - 10.0) < 1e-12
+    assert abs(r.N - 10.0) < 1e-4       # quadrature-limited on 50 x 12 x 24
+
+
+def test_lda_trace_identity(water1):
+    # f = C_x rho^(4/3): Tr(P V) = sum_i w_i rho_i vrho_i = (4/3) E_x on the same grid
+    w, g, pl = water1
+    r = I.integrate_method(g, w.basis, w.P, "slater", pl)
+    assert abs(np.sum(w.P * r.V) - 4.0 / 3.0 * r.E) < 1e-12 * abs(r.E)
+
+
+def test_gga_trace_identity(water1_pbe):
+    # Tr(P V) = sum_i w_i (rho_i vrho_i + 2 sigma_i vsigma_i) for any GGA
+    w, g, pl = water1_pbe
+    r = I.integrate_method(g, w.basis, w.P, "pbe", pl)
+    pts = np.stack([g.x, g.y, g.z], 1)
+    phi, gx, gy, gz = C.collocate(pts, w.basis)
+    rho = np.sum((phi @ w.P) * phi, 1)
+    grad = [2 * np.sum((phi @ w.P) * d, 1) for d in (gx, gy, gz)]
+    sigma = sum(q * q for q in grad)
+    f, vr, vs = F.pbe(rho, sigma)
+    assert abs(np.sum(w.P * r.V) - np.sum(g.w * (rho * vr + 2 * sigma * vs))) < 1e-11 * abs(r.E)
+
+
+def _fd_error(w, g, pl, functional, integrate=I.integrate_method):
+    rng = np.random.default_rng(4)
+    d = rng.normal(size=w.P.shape)
+    d = 0.5 * (d + d.T)
+    h = 1e-4
+    V = integrate(g, w.basis, w.P, functional, pl).V
+    Ep = integrate(g, w.basis, w.P + h * d, functional, pl).E
+    Em = integrate(g, w.basis, w.P - h * d, functional, pl).E
+    fd = (Ep - Em) / (2 * h)
+    return abs(fd - np.sum(V * d)) / abs(fd)
+
+
+def test_V_is_dE_dP_slater(water1):
+    assert _fd_error(*water1, "slater") < 1e-7
+
+
+def test_V_is_dE_dP_pbe(water1_pbe):
+    assert _fd_error(*water1_pbe, "pbe") < 1e-7
+
+
+def test_planted_mistake_is_caught(water1_pbe, monkeypatch):
+    # drop the factor 2 of Eq. z_mat's gradient term in the oracle: the dE/dP pin must fail
+    orig = I.integrate_batch
+
+    def wrong(pts, w, phi_args, Pj, fn):
+        def fn_half(rho, sigma):
+            f, vr, vs = fn(rho, sigma)
+            return f, vr, 0.5 * vs
+        e, n, _ = orig(pts, w, phi_args, Pj, fn)
+        _, _, V = orig(pts, w, phi_args, Pj, fn_half)
+        return e, n, V
+    monkeypatch.setattr(I, "integrate_batch", wrong)
+    assert _fd_error(*water1_pbe, "pbe") > 1e-4
+
+
+def test_V_symmetric(water1_pbe):
+    w, g, pl = water1_pbe
+    V = I.integrate_method(g, w.basis, w.P, "pbe", pl).V
+    assert np.max(np.abs(V - V.T)) <= 1e-14 * np.max(np.abs(V))
+
+
+def test_definitional_equals_method_without_screening():
+    w = X.make_workload("water2_pbe_small")
+    spec = X.GridSpec(6, 4, 8, "ssf", 40, eta=1e-300)
+    g = I.make_grid(w.mol.xyz, spec)
+    pl = I.make_plan(g, w.mol.xyz, w.basis, spec)
+    # at eta = 1e-300 a dropped primitive is below exp(-690) on the batch: screening error is nil
+    assert sum(len(s) for s in pl.batch_shells) > 0
+    D = I.integrate_definitional(g, w.basis, w.P, "pbe")
+    M = I.integrate_method(g, w.basis, w.P, "pbe", pl)
+    assert abs(D.E - M.E) < 1e-13 * abs(D.E)
+    assert np.max(np.abs(D.V - M.V)) < 1e-13 * np.max(np.abs(D.V))
+
+
+def test_screening_error_is_small(water1_pbe):
+    w, g, pl = water1_pbe
+    D = I.integrate_definitional(g, w.basis, w.P, "pbe")
+    M = I.integrate_method(g, w.basis, w.P, "pbe", pl)
+    assert abs(D.E - M.E) < 1e-9 * abs(D.E)
+    assert np.max(np.abs(D.V - M.V)) < 1e-8
+
+
+def test_batch_order_invariance(water1_pbe):
+    w, g, pl = water1_pbe
+    a = I.integrate_method(g, w.basis, w.P, "pbe", pl)
+    perm = list(np.random.default_rng(0).permutation(len(pl.batch_points)))
+    b = I.integrate_method(g, w.basis, w.P, "pbe", pl, batches=perm)
+    assert abs(a.E - b.E) < 1e-13 * abs(a.E)
+    assert np.max(np.abs(a.V - b.V)) < 1e-13 * np.max(np.abs(a.V))
+    assert np.allclose(a.E_batch, b.E_batch, rtol=0, atol=0)
