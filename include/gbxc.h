@@ -1,0 +1,173 @@
+/*
+ * gbxc -- exchange-correlation integration on one GB300 (sm_103a).
+ *
+ * Computes E_xc, the potential matrix V_xc and the electron count N_el of a
+ * spin-restricted density in a contracted Cartesian Gaussian basis by atomic
+ * quadrature, following Williams-Young, de Jong, van Dam and Yang, "On the
+ * Efficient Evaluation of the Exchange Correlation Potential on Graphics
+ * Processing Unit Clusters" (Sec. 2.1-2.3, Algorithms 1-4).
+ *
+ * Conventions for every call:
+ *   - Return value: GBXC_OK (0) or a negative GBXC_E* code; no call aborts or
+ *     throws.  gbxc_last_error() gives a one-line message for the last failure
+ *     on that context.
+ *   - Units: bohr and hartree.
+ *   - The caller owns every buffer it passes in or out; the library copies
+ *     whatever it keeps.  Pointers marked "host or device" may point to host
+ *     memory (pageable or pinned) or to device memory on the context's GPU;
+ *     the library tells them apart with cudaPointerGetAttributes.
+ *   - Matrices are N_b x N_b, row-major, float64.  Basis-function order is
+ *     atom-major, then shell order as given to gbxc_load_basis, then the
+ *     Cartesian components (l, m, n) of the shell with l descending, then m
+ *     descending (xx, xy, xz, yy, yz, zz for L = 2).
+ *   - A context is not thread-safe: calls on one context must be serialised by
+ *     the caller.  Distinct contexts are independent.
+ */
+#ifndef GBXC_H
+#define GBXC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBXC_OK 0
+#define GBXC_EINVAL (-1)    /* bad argument (null pointer, size, index, enum) */
+#define GBXC_ENOMEM (-2)    /* device or host allocation failed / footprint does not fit */
+#define GBXC_ECUDA (-3)     /* a CUDA runtime call or a kernel launch failed */
+#define GBXC_ETIMEOUT (-4)  /* a bounded wait expired */
+#define GBXC_ENOTREADY (-5) /* the molecule has no grid yet, or a ticket is still running */
+#define GBXC_ENOENT (-6)    /* unknown molecule id or ticket */
+
+/* atomic partition function (Sec. 2.2) */
+#define GBXC_BECKE 0
+#define GBXC_SSF 1
+
+/* exchange-correlation functional */
+#define GBXC_SLATER 0       /* Slater (Dirac) exchange, LDA */
+#define GBXC_PBE 1          /* PBE exchange + PBE correlation (PW92 inside), GGA */
+
+/* arithmetic of the integration */
+#define GBXC_FP64 0         /* every step in float64 */
+#define GBXC_MIXED 1        /* float32 collocation, split-bf16x3 tensor-core contractions,
+                               float64 weights, low-density functional tail and accumulation */
+
+#define GBXC_MAX_PRIM 8     /* primitives per shell */
+#define GBXC_MAX_L 3        /* highest angular momentum (f) */
+
+typedef struct gbxc_ctx gbxc_ctx;
+
+/* Atomic quadrature and batching parameters (Sec. 2.2).
+ *   nrad      Mura-Knowles radial points per atom
+ *   ntheta    Gauss-Legendre nodes in cos(theta)
+ *   nphi      trapezoid nodes in phi (angular grid = ntheta * nphi points)
+ *   partition GBXC_BECKE or GBXC_SSF
+ *   max_batch batch threshold of the cuboid subdivision (the paper uses 512)
+ *   eta       screening tolerance of Eq. rcut (the paper uses 1e-10)
+ *   mk_alpha  Mura-Knowles radial scale (same for every element)        */
+typedef struct {
+    int nrad, ntheta, nphi;
+    int partition;
+    int max_batch;
+    double eta;
+    double mk_alpha;
+} gbxc_grid_spec;
+
+/* Sizes of a loaded molecule's plan. */
+typedef struct {
+    int natoms, nshell, nbf;
+    long long npts;          /* total grid points N_g */
+    int nbatch;              /* merged batches (Algorithm 3's final merge) */
+    int nleaf;               /* batches before merging */
+    long long nshell_entries;/* sum over batches of |S_j| in shells */
+    long long nfunc_entries; /* sum over batches of N_b^j */
+    long long ntiles;        /* 128-point tiles over all batches */
+    double sum_mn2;          /* sum_j N_g^j (N_b^j)^2 */
+    double work;             /* sum_j W_j of Eq. batch_work */
+} gbxc_plan_info;
+
+/* Create a context on CUDA device `device` (device = -1 creates a host-only
+ * context: basis and grid loading build the plan on the host and
+ * gbxc_export_plan returns it, except the partition weights; no CUDA call is
+ * made and integration returns GBXC_EINVAL).  `scratch_bytes` bounds the device
+ * scratch used per integration (0 = a default fraction of free memory); work
+ * that does not fit is processed in chunks of batches, like the paper's
+ * device-memory-saturating subsets (Algorithm 2). */
+int gbxc_create(gbxc_ctx **out, int device, size_t scratch_bytes);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+void gbxc_destroy(gbxc_ctx *ctx);
+
+/* Message of the last failure on `ctx` (never NULL; "" if none). */
+const char *gbxc_last_error(const gbxc_ctx *ctx);
+
+/* Register a molecule and its basis (Eq. gau_cart).
+ *   xyz        natoms x 3 nuclear positions, bohr (host)
+ *   Z          natoms nuclear charges (host; used for bookkeeping only)
+ *   nshell     number of shells; for shell s:
+ *   shell_atom[s]  atom index, shells must be grouped by atom in ascending atom order
+ *   shell_L[s]     angular momentum 0..GBXC_MAX_L
+ *   shell_nprim[s] primitives 1..GBXC_MAX_PRIM
+ *   alpha, coeff   nshell x GBXC_MAX_PRIM exponents and contraction coefficients
+ *                  (normalisation already folded into coeff; unused entries ignored)
+ * On success *mol_out is the molecule id and *nbf_out the number of functions.
+ * All inputs are host memory and are copied. */
+int gbxc_load_basis(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, int nshell,
+                    const int *shell_atom, const int *shell_L, const int *shell_nprim,
+                    const double *alpha, const double *coeff, int *mol_out, int *nbf_out);
+
+/* Build the molecular grid and the batch plan, and keep them on the device
+ * (Sec. 2.2 and Algorithm 3; the paper reuses them across SCF iterations):
+ * atomic grids, partition weights (computed on the GPU in float64), cuboid
+ * batches, Algorithm 1 screening with Eq. rcut, the merge of equal shell
+ * lists.  May be called again to replace the grid.  *npts_out and
+ * *nbatch_out may be NULL. */
+int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
+                   int *nbatch_out);
+
+/* Sizes of the plan of `mol` (after gbxc_load_grid). */
+int gbxc_plan_info_get(gbxc_ctx *ctx, int mol, gbxc_plan_info *info);
+
+/* Copy the plan to host buffers (any pointer may be NULL to skip it).
+ * Point arrays are in the library's batch order (merged batch by merged
+ * batch, points of a batch in the order the batching produced them):
+ *   x, y, z, wq, w   npts float64: coordinates, unpartitioned weights w^q and
+ *                    partitioned weights w = p_A w^q (Eq. num_int)
+ *   parent           npts int32: atom whose quadrature holds the point
+ *   point_index      npts int64: index of the point in the atom-major generation
+ *                    order (atom, radial, theta, phi)
+ *   batch_ptr        nbatch+1 int64 offsets into the point arrays
+ *   shell_ptr        nbatch+1 int64 offsets into shell_idx
+ *   shell_idx        nshell_entries int32 sorted shell lists S_j           */
+int gbxc_export_plan(gbxc_ctx *ctx, int mol, double *x, double *y, double *z, double *wq,
+                     double *w, int *parent, long long *point_index, long long *batch_ptr,
+                     long long *shell_ptr, int *shell_idx);
+
+/* Integrate E_xc, V_xc and N_el for density matrix P (Algorithm 4 over every
+ * batch of the plan; Eqs. x_mat, eval_local_den, eval_local_den_grad,
+ * eval_xc_batch, exc_batch, z_mat, vxc_batch, vxc_inc).
+ *   P          nbf x nbf symmetric density matrix, host or device; read as given
+ *   functional GBXC_SLATER or GBXC_PBE
+ *   precision  GBXC_FP64 or GBXC_MIXED
+ *   Exc, Nel   host scalars (may be NULL)
+ *   Vxc        nbf x nbf output, host or device (may be NULL); exactly symmetric
+ *   stream     cudaStream_t to run on (NULL = the context's own stream); the call
+ *              returns after the results are complete                        */
+int gbxc_integrate(gbxc_ctx *ctx, int mol, const double *P, int functional, int precision,
+                   double *Exc, double *Vxc, double *Nel, void *stream);
+
+/* As gbxc_integrate, restricted to merged batches [batch_begin, batch_end),
+ * the device subset step of Algorithm 2.  E_batch and N_batch (host, may be
+ * NULL) receive each batch's contribution, nbatch entries, zero outside the
+ * range. */
+int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int functional,
+                           int precision, int batch_begin, int batch_end, double *Exc,
+                           double *Vxc, double *Nel, double *E_batch, double *N_batch,
+                           void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBXC_H */

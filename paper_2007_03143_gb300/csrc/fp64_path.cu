@@ -1,0 +1,354 @@
+// Float64 form of the batched integration (Algorithm 4), one chunk of tiles at a time.
+//
+// Scratch layout ("slabs"): every 128-point tile t of batch j owns N_b^j rows
+// (padded to a multiple of 16) of 128 doubles each, function-major, so that the
+// 128 points of a row are contiguous.  Six slab arrays follow each other:
+// Phi, dPhi/dx, dPhi/dy, dPhi/dz, X and Z.
+//
+//   k1  collocation       Phi^j and grad Phi^j (Eq. gau_cart)            thread per point
+//   k3  X = P^j Phi^j     (Eq. x_mat) with P^j gathered from P on the fly  64 x 128 output tile
+//   k45 rho, grad rho (Eqs. eval_local_den, eval_local_den_grad), the
+//       functional (Eq. eval_xc_batch), E/N partial sums (Eq. exc_batch)
+//       and Z^j (Eq. z_mat)                                                thread per point
+//   k6  W^j = Z^jT Phi^j summed over the batch's points and scattered into
+//       V_acc[S_j, S_j] (Eqs. vxc_batch, vxc_inc); V = V_acc + V_acc^T at the end.
+//
+// On this GPU float64 runs at a small fraction of float32 and tensor rates, so
+// these kernels are bound by the float64 pipe; they are the precision anchor.
+#include <cstdint>
+
+#include "internal.h"
+#include "xc_functional.cuh"
+
+namespace gbxc {
+namespace {
+
+constexpr int NCOMP = 6;  // Phi, Phi_x, Phi_y, Phi_z, X, Z
+
+struct Slabs {
+    double *c[NCOMP];
+};
+
+__device__ __forceinline__ Slabs slabs_of(const ChunkArgs &a) {
+    Slabs s;
+    double *base = static_cast<double *>(a.scratch);
+    for (int k = 0; k < NCOMP; ++k) s.c[k] = base + (size_t)k * a.rows * TILE;
+    return s;
+}
+
+// --------------------------------------------------------------------------
+// k1: collocation.  One block per tile, one thread per point; a warp walks the
+// same shell list for 32 points (no divergence between shells).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE) colloc_f64(ChunkArgs a) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int64_t row0 = a.plan.tile_row[t] - a.row0;
+    Slabs S = slabs_of(a);
+    bool live = i < cnt;
+    int64_t p = a.plan.tile_first[t] + i;
+    double px = live ? a.plan.x[p] : 0.0, py = live ? a.plan.y[p] : 0.0,
+           pz = live ? a.plan.z[p] : 0.0;
+    int64_t s0 = a.plan.shell_ptr[j], s1 = a.plan.shell_ptr[j + 1];
+    int row = 0;
+    for (int64_t si = s0; si < s1; ++si) {
+        const DevShell &sh = a.shells[a.plan.shell_idx[si]];
+        double X = px - sh.c[0], Y = py - sh.c[1], Z = pz - sh.c[2];
+        double r2 = X * X + Y * Y + Z * Z;
+        double g = 0.0, h = 0.0;
+        for (int k = 0; k < sh.nprim; ++k) {
+            double e = exp(-sh.alpha[k] * r2);
+            g += sh.coeff[k] * e;
+            h += (-2.0 * sh.alpha[k] * sh.coeff[k]) * e;
+        }
+        double xp[GBXC_MAX_L + 2], yp[GBXC_MAX_L + 2], zp[GBXC_MAX_L + 2];
+        xp[0] = yp[0] = zp[0] = 1.0;
+        for (int k = 1; k <= sh.L; ++k) {
+            xp[k] = xp[k - 1] * X;
+            yp[k] = yp[k - 1] * Y;
+            zp[k] = zp[k - 1] * Z;
+        }
+        for (int l = sh.L; l >= 0; --l)
+            for (int m = sh.L - l; m >= 0; --m) {
+                int n = sh.L - l - m;
+                double mono = xp[l] * yp[m] * zp[n];
+                double dx = (l > 0 ? l * xp[l - 1] * yp[m] * zp[n] : 0.0) * g + mono * X * h;
+                double dy = (m > 0 ? m * xp[l] * yp[m - 1] * zp[n] : 0.0) * g + mono * Y * h;
+                double dz = (n > 0 ? n * xp[l] * yp[m] * zp[n - 1] : 0.0) * g + mono * Z * h;
+                size_t o = (size_t)(row0 + row) * TILE + i;
+                S.c[0][o] = live ? mono * g : 0.0;
+                S.c[1][o] = live ? dx : 0.0;
+                S.c[2][o] = live ? dy : 0.0;
+                S.c[3][o] = live ? dz : 0.0;
+                ++row;
+            }
+    }
+}
+
+// --------------------------------------------------------------------------
+// k3: X^j (rows = functions, cols = points) = P^j Phi^j, P^j[r][k] = P[F_r][F_k].
+// Block (tile t, row block rb) computes 64 rows x 128 points; 256 threads,
+// each 4 rows x 8 points.  K = N_b^j in steps of 16.
+// --------------------------------------------------------------------------
+constexpr int XB_R = 64, XB_K = 16;
+
+__global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a) {
+    int64_t t = a.t0 + blockIdx.x;
+    int rb = blockIdx.y;
+    int j = a.plan.tile_batch[t];
+    int64_t f0 = a.plan.func_ptr[j];
+    int n = (int)(a.plan.func_ptr[j + 1] - f0);
+    int r0 = rb * XB_R;
+    if (r0 >= n) return;
+    const int *F = a.plan.func_idx + f0;
+    Slabs S = slabs_of(a);
+    int64_t row0 = a.plan.tile_row[t] - a.row0;
+    const double *Phi = S.c[0] + (size_t)row0 * TILE;
+    double *Xo = S.c[4] + (size_t)row0 * TILE;
+
+    __shared__ double As[XB_K][XB_R + 1];
+    __shared__ double Bs[XB_K][TILE];
+    __shared__ int Frow[XB_R];
+    int tid = threadIdx.x;
+    if (tid < XB_R) Frow[tid] = (r0 + tid < n) ? F[r0 + tid] : -1;
+    int tx = tid & 15, ty = tid >> 4;
+    double acc[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.0;
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += XB_K) {
+        // A tile: P[F[r0 + rr]][F[k0 + kk]]
+        for (int e = tid; e < XB_K * XB_R; e += 256) {
+            int kk = e / XB_R, rr = e % XB_R;
+            int k = k0 + kk;
+            int fr = Frow[rr];
+            As[kk][rr] = (fr >= 0 && k < n) ? a.P[(size_t)fr * a.nbf + F[k]] : 0.0;
+        }
+        for (int e = tid; e < XB_K * TILE; e += 256) {
+            int kk = e / TILE, c = e % TILE;
+            int k = k0 + kk;
+            Bs[kk][c] = (k < n) ? Phi[(size_t)k * TILE + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < XB_K; ++kk) {
+            double av[4], bv[8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = As[kk][ty * 4 + u];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) bv[v] = Bs[kk][tx + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int r = r0 + ty * 4 + u;
+        if (r >= n) continue;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) Xo[(size_t)r * TILE + tx + 16 * v] = acc[u][v];
+    }
+}
+
+// --------------------------------------------------------------------------
+// k45: rho, grad rho, functional, E/N partials, Z.  One block per tile.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE) rho_xc_z_f64(ChunkArgs a) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int64_t row0 = a.plan.tile_row[t] - a.row0;
+    Slabs S = slabs_of(a);
+    size_t base = (size_t)row0 * TILE + i;
+    double rho = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int r = 0; r < n; ++r) {
+        size_t o = base + (size_t)r * TILE;
+        double xv = S.c[4][o];
+        rho = fma(S.c[0][o], xv, rho);
+        gx = fma(S.c[1][o], xv, gx);
+        gy = fma(S.c[2][o], xv, gy);
+        gz = fma(S.c[3][o], xv, gz);
+    }
+    gx *= 2.0;
+    gy *= 2.0;
+    gz *= 2.0;
+    double e = 0.0, nn = 0.0, ca = 0.0, bx = 0.0, by = 0.0, bz = 0.0;
+    if (i < cnt) {
+        double w = a.plan.w[a.plan.tile_first[t] + i];
+        double sigma = gx * gx + gy * gy + gz * gz;
+        double f, vr, vs;
+        xc::evaluate<double>(a.functional, rho, sigma, f, vr, vs);
+        e = w * f;
+        nn = w * rho;
+        ca = 0.5 * w * vr;
+        double b = 2.0 * w * vs;
+        bx = b * gx;
+        by = b * gy;
+        bz = b * gz;
+    }
+    for (int r = 0; r < n; ++r) {
+        size_t o = base + (size_t)r * TILE;
+        S.c[5][o] = ca * S.c[0][o] + bx * S.c[1][o] + by * S.c[2][o] + bz * S.c[3][o];
+    }
+    // deterministic block reduction of the E and N partials
+    __shared__ double re[TILE], rn[TILE];
+    re[i] = e;
+    rn[i] = nn;
+    __syncthreads();
+    for (int s = TILE / 2; s > 0; s >>= 1) {
+        if (i < s) {
+            re[i] += re[i + s];
+            rn[i] += rn[i + s];
+        }
+        __syncthreads();
+    }
+    if (i == 0) {
+        a.tileE[t] = re[0];
+        a.tileN[t] = rn[0];
+    }
+}
+
+// --------------------------------------------------------------------------
+// k6: W^j[mu][nu] = sum_i Z[mu][i] Phi[nu][i] over tiles [t0, t1) of batch j,
+// 64 x 64 output block per CTA (256 threads, 4 x 4 each), then
+// V_acc[F_mu][F_nu] += W (float64 atomics).
+// --------------------------------------------------------------------------
+constexpr int VB = 64, VK = 16;
+
+__global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a) {
+    const int *task = a.vtasks + 5 * blockIdx.x;
+    int j = task[0], mb = task[1], nb = task[2];
+    int64_t tb = task[3], te = task[4];
+    int64_t f0 = a.plan.func_ptr[j];
+    int n = (int)(a.plan.func_ptr[j + 1] - f0);
+    const int *F = a.plan.func_idx + f0;
+    int m0 = mb * VB, n0 = nb * VB;
+    Slabs S = slabs_of(a);
+    __shared__ double As[VK][VB + 1];
+    __shared__ double Bs[VK][VB + 1];
+    int tid = threadIdx.x;
+    int tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int64_t t = tb; t < te; ++t) {
+        int64_t row0 = a.plan.tile_row[t] - a.row0;
+        const double *Zs = S.c[5] + (size_t)row0 * TILE;
+        const double *Ps = S.c[0] + (size_t)row0 * TILE;
+        int cnt = a.plan.tile_count[t];
+        for (int k0 = 0; k0 < cnt; k0 += VK) {
+            for (int e = tid; e < VK * VB; e += 256) {
+                int rr = e / VK, kk = e % VK;
+                int k = k0 + kk;
+                int mr = m0 + rr, nr = n0 + rr;
+                As[kk][rr] = (mr < n && k < cnt) ? Zs[(size_t)mr * TILE + k] : 0.0;
+                Bs[kk][rr] = (nr < n && k < cnt) ? Ps[(size_t)nr * TILE + k] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < VK; ++kk) {
+                double av[4], bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) av[u] = As[kk][ty * 4 + u];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int mr = m0 + ty * 4 + u;
+        if (mr >= n) continue;
+        size_t rowg = (size_t)F[mr] * a.nbf;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int nr = n0 + tx * 4 + v;
+            if (nr < n) atomicAdd(&a.Vacc[rowg + F[nr]], acc[u][v]);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// finish: V = V_acc + V_acc^T; per-batch and total E, N in a fixed order.
+// --------------------------------------------------------------------------
+__global__ void symmetrize(const double *__restrict__ Vacc, double *__restrict__ V, int nbf) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nbf * nbf) return;
+    int r = (int)(e / nbf), c = (int)(e % nbf);
+    V[e] = Vacc[e] + Vacc[(size_t)c * nbf + r];
+}
+
+__global__ void batch_sums(FinishArgs a) {
+    int j = a.b0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.b1) return;
+    double e = 0.0, n = 0.0;
+    for (int64_t t = a.batch_tile[j]; t < a.batch_tile[j + 1]; ++t) {
+        e += a.tileE[t];
+        n += a.tileN[t];
+    }
+    a.Eb[j] = e;
+    a.Nb[j] = n;
+}
+
+__global__ void total_sums(FinishArgs a) {
+    __shared__ double se[256], sn[256];
+    double e = 0.0, n = 0.0;
+    for (int j = a.b0 + threadIdx.x; j < a.b1; j += 256) {
+        e += a.Eb[j];
+        n += a.Nb[j];
+    }
+    se[threadIdx.x] = e;
+    sn[threadIdx.x] = n;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            se[threadIdx.x] += se[threadIdx.x + s];
+            sn[threadIdx.x] += sn[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.tot[0] = se[0];
+        a.tot[1] = sn[0];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s) {
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    colloc_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
+    xgemm_f64<<<xg, 256, 0, s>>>(a);
+    rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    if (a.nvtasks > 0) vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const FinishArgs &a, cudaStream_t s) {
+    int64_t nn = (int64_t)a.nbf * a.nbf;
+    if (a.V && nn > 0) symmetrize<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(a.Vacc, a.V, a.nbf);
+    int nb = a.b1 - a.b0;
+    if (nb > 0) batch_sums<<<(nb + 127) / 128, 128, 0, s>>>(a);
+    total_sums<<<1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gbxc

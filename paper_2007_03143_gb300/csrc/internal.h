@@ -1,0 +1,125 @@
+// Internal data structures shared by the host code and the CUDA kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gbxc.h"
+
+namespace gbxc {
+
+constexpr int TILE = 128;        // grid points per tile (the M extent of the tensor-core tiles)
+constexpr int FBLK = 16;         // function padding granule (K step of a bf16 tensor-core MMA)
+
+// One contracted Cartesian shell (Eq. gau_cart), as the kernels read it.
+struct DevShell {
+    double c[3];
+    int L, nprim, fofs, pad;
+    double alpha[GBXC_MAX_PRIM];
+    double coeff[GBXC_MAX_PRIM];
+};
+
+// Host-side batch plan (Sec. 2.2, Algorithm 1, Algorithm 3).
+struct HostPlan {
+    // points in batch order
+    std::vector<double> x, y, z, wq;
+    std::vector<int> parent;
+    std::vector<int64_t> point_index;
+    // merged batches
+    std::vector<int64_t> batch_ptr;   // nbatch+1 into the point arrays
+    std::vector<int64_t> shell_ptr;   // nbatch+1
+    std::vector<int> shell_idx;
+    std::vector<int64_t> func_ptr;    // nbatch+1
+    std::vector<int> func_idx;
+    std::vector<double> work;
+    int nleaf = 0;
+    // 128-point tiles
+    std::vector<int> tile_batch;
+    std::vector<int64_t> tile_first;  // first point (batch order) of the tile
+    std::vector<int> tile_count;
+    std::vector<int64_t> tile_row;    // prefix sum of padded N_b^j over tiles (slab row offset)
+    std::vector<int64_t> batch_tile;  // nbatch+1 into the tile arrays
+    int nbatch() const { return (int)batch_ptr.size() - 1; }
+    int64_t ntiles() const { return (int64_t)tile_batch.size(); }
+};
+
+// Device views of the resident plan of one molecule.
+struct DevPlan {
+    double *x = nullptr, *y = nullptr, *z = nullptr, *wq = nullptr, *w = nullptr;
+    int *parent = nullptr;
+    int64_t *shell_ptr = nullptr;
+    int *shell_idx = nullptr;
+    int64_t *func_ptr = nullptr;
+    int *func_idx = nullptr;
+    int *tile_batch = nullptr;
+    int64_t *tile_first = nullptr;
+    int *tile_count = nullptr;
+    int64_t *tile_row = nullptr;
+    int64_t *batch_tile = nullptr;
+    int64_t *batch_ptr = nullptr;
+};
+
+// Grid generation and planning on the host (host_plan.cpp).  Bitwise contract:
+// the same coordinates and the same batches as the reference CPU planner in the
+// same process (plain IEEE double arithmetic, no contraction, platform libm).
+void build_molecular_grid(const std::vector<double> &xyz, const gbxc_grid_spec &spec,
+                          std::vector<double> &x, std::vector<double> &y, std::vector<double> &z,
+                          std::vector<double> &wq, std::vector<int> &parent);
+double shell_cutoff(const double *alpha, int nprim, double eta);
+void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &shells,
+                const std::vector<double> &rcut, int nbf, const gbxc_grid_spec &spec,
+                const std::vector<double> &x, const std::vector<double> &y,
+                const std::vector<double> &z, const std::vector<double> &wq,
+                const std::vector<int> &parent, HostPlan &plan);
+
+inline int64_t pad_funcs(int64_t n) { return (n + FBLK - 1) / FBLK * FBLK; }
+
+// ---------------------------------------------------------------------------
+// kernel launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+struct WeightsArgs {
+    const double *x, *y, *z, *wq;
+    const int *parent;
+    const double *atoms;      // natoms x 3
+    const double *rnn;        // natoms nearest-neighbour distances
+    double *w;
+    int64_t npts;
+    int natoms;
+    int scheme;
+};
+cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s);
+
+// Tiles of one chunk are [t0, t1); slab rows are tile_row[t] - row0.
+struct ChunkArgs {
+    DevPlan plan;
+    const DevShell *shells;
+    int nbf;
+    int64_t t0, t1, row0, rows;
+    int max_nfunc;            // largest N_b^j of the chunk's batches
+    int functional;
+    const double *P;          // nbf x nbf
+    double *Vacc;             // nbf x nbf accumulator (W = Z^T Phi scattered, not yet symmetrised)
+    double *tileE, *tileN;    // per-tile partial sums (indexed by global tile id)
+    void *scratch;            // chunk slabs
+    const int *vtasks;        // 5 ints per task: batch, mb, nb, t0, t1
+    int nvtasks;
+};
+cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s);
+
+struct FinishArgs {
+    const double *Vacc;
+    double *V;                // nbf x nbf symmetric result
+    int nbf;
+    const double *tileE, *tileN;
+    const int64_t *batch_tile;
+    int b0, b1;
+    double *Eb, *Nb;          // per batch (nbatch), device
+    double *tot;              // [E, N] device
+};
+cudaError_t launch_finish(const FinishArgs &a, cudaStream_t s);
+
+}  // namespace gbxc

@@ -1,0 +1,112 @@
+// Atomic partition weights w_i = p_A(r_i) w^q_i (Sec. 2.2, Eqs. atomic_partition and num_int;
+// Algorithm 4 step 1), in float64 on the GPU, one thread per grid point.
+//
+// Becke (1988) cell function: s(mu) = (1 - p(p(p(mu))))/2, p(x) = 1.5x - 0.5x^3.
+// SSF (1996): s(mu) = (1 - g(mu))/2 with g the degree-7 polynomial in mu/a on
+// |mu| < a (a = 0.64) and g = +-1 outside; plus SSF's own-atom shortcut.
+// P_B(r) = prod_{C != B} s(mu_BC), mu_BC = (|r-R_B| - |r-R_C|)/R_BC,
+// p_A = P_A / sum_B P_B.
+//
+// The natoms^2 loop is screened in the SSF case with an exact rule: if some
+// atom C has mu_BC >= a then s(mu_BC) = 0 and P_B = 0, so B is skipped once
+// that is seen for the atom C nearest to the point.
+#include <cstdint>
+
+#include "internal.h"
+
+namespace gbxc {
+namespace {
+
+constexpr double kSsfA = 0.64;
+constexpr int kMaxAtomsSmem = 1024;
+
+__device__ __forceinline__ double becke_s(double mu) {
+    double f = mu;
+    f = 1.5 * f - 0.5 * f * f * f;
+    f = 1.5 * f - 0.5 * f * f * f;
+    f = 1.5 * f - 0.5 * f * f * f;
+    return 0.5 * (1.0 - f);
+}
+
+__device__ __forceinline__ double ssf_s(double mu) {
+    if (mu <= -kSsfA) return 1.0;
+    if (mu >= kSsfA) return 0.0;
+    double z = mu / kSsfA;
+    double z2 = z * z;
+    double g = z * (35.0 + z2 * (-35.0 + z2 * (21.0 - 5.0 * z2))) / 16.0;
+    return 0.5 * (1.0 - g);
+}
+
+__global__ void partition_weights_kernel(WeightsArgs a) {
+    extern __shared__ double sm[];
+    double *ax = sm, *ay = sm + a.natoms, *az = sm + 2 * a.natoms;
+    for (int k = threadIdx.x; k < a.natoms; k += blockDim.x) {
+        ax[k] = a.atoms[3 * k];
+        ay[k] = a.atoms[3 * k + 1];
+        az[k] = a.atoms[3 * k + 2];
+    }
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.npts) return;
+    double px = a.x[i], py = a.y[i], pz = a.z[i];
+    int A = a.parent[i];
+    auto dist = [&](int k) {
+        double dx = px - ax[k], dy = py - ay[k], dz = pz - az[k];
+        return sqrt(dx * dx + dy * dy + dz * dz);
+    };
+    auto rab = [&](int k, int l) {
+        double dx = ax[k] - ax[l], dy = ay[k] - ay[l], dz = az[k] - az[l];
+        return sqrt(dx * dx + dy * dy + dz * dz);
+    };
+    double p;
+    if (a.natoms == 1) {
+        p = 1.0;
+    } else if (a.scheme == GBXC_SSF && dist(A) < 0.5 * (1.0 - kSsfA) * a.rnn[A]) {
+        p = 1.0;
+    } else {
+        int nearest = 0;
+        double dn = dist(0);
+        for (int k = 1; k < a.natoms; ++k) {
+            double d = dist(k);
+            if (d < dn) { dn = d; nearest = k; }
+        }
+        double sum = 0.0, pa = 0.0;
+        for (int B = 0; B < a.natoms; ++B) {
+            double dB = dist(B);
+            double PB = 1.0;
+            if (a.scheme == GBXC_SSF) {
+                if (B != nearest && (dB - dn) / rab(B, nearest) >= kSsfA) {
+                    PB = 0.0;
+                } else {
+                    for (int C = 0; C < a.natoms && PB != 0.0; ++C) {
+                        if (C == B) continue;
+                        PB *= ssf_s((dB - dist(C)) / rab(B, C));
+                    }
+                }
+            } else {
+                for (int C = 0; C < a.natoms; ++C) {
+                    if (C == B) continue;
+                    PB *= becke_s((dB - dist(C)) / rab(B, C));
+                }
+            }
+            sum += PB;
+            if (B == A) pa = PB;
+        }
+        p = pa / sum;
+    }
+    a.w[i] = a.wq[i] * p;
+}
+
+}  // namespace
+
+cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s) {
+    if (a.npts == 0) return cudaSuccess;
+    if (a.natoms > kMaxAtomsSmem) return cudaErrorInvalidValue;
+    int threads = 128;
+    int64_t blocks = (a.npts + threads - 1) / threads;
+    size_t smem = sizeof(double) * 3 * a.natoms;
+    partition_weights_kernel<<<(unsigned)blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gbxc
