@@ -30,7 +30,8 @@ def test_partition_weights(loaded):
     w = loaded.w
     ref = ex["wq"] * PT.partition_weights(ex["x"], ex["y"], ex["z"], ex["parent"], w.mol.xyz,
                                           w.grid.partition)
-    assert np.max(np.abs(ex["w"] - ref) / np.maximum(np.abs(ref), 1e-300)) < 1e-12
+    # partition value p = w / w^q compared absolutely (see the full-size test)
+    assert np.max(np.abs(ex["w"] - ref) / ex["wq"]) < 1e-12
 
 
 def test_fp64_matches_oracle(loaded):
