@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of XC integration (E_xc + V_xc + N_el) on one GB300, as one JSON line.
+
+Workload: the 16-water PBE cluster (48 atoms, 400 Cartesian functions, SSF partition,
+75 x 16 x 32 atomic grids = 1,843,200 points, batches <= 512, eta = 1e-10), seeded
+synthetic inputs from ``xcinputs``.  A step is one ``gbxc_integrate`` call over every
+batch of the resident plan: collocation, X = P^j Phi^j, rho/grad rho, PBE, Z, V^j and
+the scatter into V_xc, E_xc and N_el.
+
+Forms: ``fp64`` (every step in float64) and ``mixed`` (float32 collocation, split-bf16x3
+tensor-core contractions, float64 accumulation).  The headline ``value`` is the fastest
+form whose |E_xc - E_xc(fp64)| <= 1e-6 Eh.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the stream the
+library runs on; between steps a 256 MiB buffer is written to flush L2 (outside the
+events).  ``e2e`` repeats the measurement through the same public call with P and V in
+pinned host memory, so every step includes the P upload and the V download (wall clock).
+``--impl reference`` times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import xcinputs as X  # noqa: E402
+
+METRIC = "grid pts/s for E_xc+V_xc at |ΔE_xc|≤1e-6 Eh vs FP64 form; p50/p99 latency"
+UNIT = "grid pts/s"
+WORKLOAD = "water16_pbe"
+WORKLOAD_DESC = ("16-water cluster (48 atoms, 10 A box), 400 Cartesian Gaussians (O 3s2p1d, H 2s1p, "
+                 "3 primitives), PBE, SSF partition, Mura-Knowles 75 x Gauss-Legendre 16 x trapezoid 32, "
+                 "batches <= 512 points, eta = 1e-10")
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (alu bound)
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = [r.split(",") for r in open(self.tmp.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _src_hash(names):
+    h = hashlib.sha1()
+    for n in names:
+        p = os.path.join(ROOT, "paper_2007_03143_gb300", "csrc", n)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:12]
+
+
+KERNEL_SOURCES = {"xgemm": ["fp64_path.cu"], "vgemm": ["fp64_path.cu"], "colloc": ["fp64_path.cu"],
+                  "rho_z": ["fp64_path.cu"], "mixed_xgemm": ["mixed_path.cu", "umma.cuh"],
+                  "mixed_vgemm": ["mixed_path.cu", "umma.cuh"]}
+
+
+def _traffic(kernel, form):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if still current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    key = f"{form}:{kernel}"
+    e = d.get(key)
+    if not e:
+        return None
+    srcs = KERNEL_SOURCES.get(kernel if form == "fp64" else "mixed_" + kernel, [])
+    if e.get("src_hash") != _src_hash(srcs):
+        return None
+    return e.get("bytes_per_launch")
+
+
+def oracle_setup(w):
+    from oracle import integrate as I
+    g = I.make_grid(w.mol.xyz, w.grid, weights=False)
+    pl = I.make_plan(g, w.mol.xyz, w.basis, w.grid)
+    return g, pl
+
+
+def cpu_baseline(w, target_points, seed=0, setup=None):
+    """The oracle (method-equivalent mode, float64) on a seeded sample of the workload's batches."""
+    from oracle import integrate as I
+    from oracle import partition as PT
+    g, pl = setup if setup is not None else oracle_setup(w)
+    rng = np.random.default_rng(seed)
+    sel, n = [], 0
+    for j in rng.permutation(len(pl.batch_points)):
+        sel.append(int(j))
+        n += len(pl.batch_points[j])
+        if n >= target_points:
+            break
+    idx = np.concatenate([pl.batch_points[j] for j in sel])
+    g.w = np.zeros(len(g.x))
+    g.w[idx] = g.wq[idx] * PT.partition_weights(g.x[idx], g.y[idx], g.z[idx], g.parent[idx], w.mol.xyz,
+                                                w.grid.partition)
+    t0 = time.perf_counter()
+    I.integrate_method(g, w.basis, w.P, w.functional, pl, batches=sel)
+    dt = time.perf_counter() - t0
+    return n, dt, len(sel), len(pl.batch_points)
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if world > 1 and rank != 0:
+        return 0
+    w = X.make_workload(args.workload)
+    setup = oracle_setup(w)
+    times, pts = [], []
+    for s in range(args.warmup + args.steps):
+        n, dt, nsel, nb = cpu_baseline(w, args.ref_points, seed=s, setup=setup)
+        if s >= args.warmup:
+            times.append(dt)
+            pts.append(n)
+    value = sum(pts) / sum(times)
+    cores = os.cpu_count()
+    sample = (f"{args.ref_points}+ points per step from seeded random batches of the "
+              f"{nb}-batch plan; integrate step only (grid, plan, weights precomputed)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "name": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbxc", choices=["gbxc", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--forms", default="fp64,mixed")
+    ap.add_argument("--cpu-points", type=int, default=300000)
+    ap.add_argument("--ref-points", type=int, default=100000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scratch-mb", type=int, default=0, help="device scratch budget (0 = default)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2007_03143_gb300 as G
+
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = X.make_workload(args.workload)
+    nbf = w.basis.nbf
+    ctx = G.Context(local, args.scratch_mb << 20)
+    t0 = time.perf_counter()
+    mid = ctx.load_molecule(w.mol, w.basis, w.grid)
+    load_s = time.perf_counter() - t0
+    info = G.gbxc_plan_info_get(ctx.h, mid)
+    npts = info["npts"]
+
+    P_dev = torch.tensor(w.P, device=dev)
+    V_dev = torch.zeros((nbf, nbf), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def run_form(form, sampler=None):
+        for _ in range(args.warmup):
+            G.gbxc_integrate(ctx.h, mid, P_dev, w.functional, form, V_dev)
+        G.gbxc_profile_enable(ctx.h, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier()
+        if sampler:
+            sampler.start()
+        E = N = None
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            E, N = G.gbxc_integrate(ctx.h, mid, P_dev, w.functional, form, V_dev)
+            ev[k][1].record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        prof = G.gbxc_profile_read(ctx.h)
+        G.gbxc_profile_enable(ctx.h, False)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        total = sum(ms)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return dict(E=E, N=N, V=V_dev.cpu().numpy(), ms=ms, total_ms=total, prof=prof, clocks=clocks)
+
+    forms = [f for f in args.forms.split(",") if f]
+    res = {}
+    for f in forms:
+        try:
+            res[f] = run_form(f, sampler=ClockSampler(local))
+        except G.GbxcError as e:
+            res[f] = {"error": str(e)}
+    ok = {f: r for f, r in res.items() if "error" not in r}
+    if "fp64" not in ok:
+        raise SystemExit(f"fp64 form failed: {res.get('fp64')}")
+    E64 = ok["fp64"]["E"]
+    acc = {}
+    for f, r in ok.items():
+        acc[f] = {"dE_xc": abs(r["E"] - E64), "max_dV": float(np.max(np.abs(r["V"] - ok["fp64"]["V"]))),
+                  "dN_el": abs(r["N"] - ok["fp64"]["N"])}
+    valid = [f for f in ok if acc[f]["dE_xc"] <= 1e-6]
+    head = min(valid, key=lambda f: ok[f]["total_ms"])
+    R = ok[head]
+    value = world * npts * args.steps / (R["total_ms"] / 1e3)
+    ms_sorted = sorted(R["ms"])
+    p50 = statistics.median(ms_sorted)
+    p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
+
+    # roofline of the dominant kernel class of the headline form
+    peaks, peak_src = _peaks()
+    prof = R["prof"]
+    compute = {k: v for k, v in prof.items() if k in ("colloc", "xgemm", "rho_z", "vgemm", "pgather")}
+    dom = max(compute, key=lambda k: compute[k][0])
+    dom_ms, dom_launch = compute[dom]
+    per_step_flops = 2.0 * info["sum_mn2"]          # 2 m n^2 per batch for either contraction
+    if dom in ("xgemm", "vgemm"):
+        if head == "fp64":
+            achieved = per_step_flops * args.steps / (dom_ms / 1e3) / 1e9
+            roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
+                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+        else:
+            achieved = 3.0 * per_step_flops * args.steps / (dom_ms / 1e3) / 1e12
+            pk = peaks["bf16_tflops"]
+            roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "peak_source": f"{peak_src} bf16 burst (3 bf16 products per split-bf16x3 term)"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None}
+    roof["kernel"] = dom
+    roof["launches_per_step"] = dom_launch / args.steps
+    roof["ms_per_step"] = dom_ms / args.steps
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
+    roof["traffic"] = _traffic(dom, head)
+    launches = sum(v[1] for k, v in prof.items() if k != "weights")
+
+    # end to end through the public call with pinned host buffers
+    P_host = torch.from_numpy(w.P.copy()).pin_memory()
+    V_host = torch.empty((nbf, nbf), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        G.gbxc_integrate(ctx.h, mid, P_host, w.functional, head, V_host)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        G.gbxc_integrate(ctx.h, mid, P_host, w.functional, head, V_host)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * npts * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": nbf * nbf * 8, "d2h_bytes_per_step": nbf * nbf * 8 + 16}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": R["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head == "fp64" else "bf16x3+f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "name": args.workload, "npts": npts, "nbf": nbf,
+                       "nbatch": info["nbatch"], "sum_mn2": info["sum_mn2"], "form": head,
+                       "l2": "256 MiB buffer written between timed steps (outside the events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "p50_ms": p50, "p99_ms": p99, "e2e": e2e, "roofline": roof, "gpu_launches": launches,
+            "clocks": R["clocks"], "load_grid_s": load_s,
+            "forms": {f: ({"value": npts * args.steps / (r["total_ms"] / 1e3), "ms_per_step":
+                           r["total_ms"] / args.steps, **acc[f],
+                           "kernel_ms_per_step": {k: v[0] / args.steps for k, v in r["prof"].items()}}
+                          if "error" not in r else r) for f, r in res.items()}}
+    if rank == 0 and not args.no_cpu_baseline:
+        n, dt, nsel, nb = cpu_baseline(w, args.cpu_points)
+        line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{n} points in {nsel} of {nb} batches (seeded), integrate "
+                                          f"step only, numpy float64 with BLAS on all cores"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -53,6 +53,17 @@ extern "C" {
 #define GBXC_MIXED 1        /* float32 collocation, split-bf16x3 tensor-core contractions,
                                float64 weights, low-density functional tail and accumulation */
 
+/* kernel classes reported by gbxc_profile_read */
+#define GBXC_K_WEIGHTS 0    /* partition weights (grid loading) */
+#define GBXC_K_COLLOC 1     /* collocation Phi, grad Phi */
+#define GBXC_K_XGEMM 2      /* X^j = P^j Phi^j (Eq. x_mat) */
+#define GBXC_K_RHO_Z 3      /* rho, grad rho, functional, E/N, Z^j */
+#define GBXC_K_VGEMM 4      /* V^j contraction and scatter into V_xc (Eqs. vxc_batch, vxc_inc) */
+#define GBXC_K_FINISH 5     /* symmetrisation and fixed-order E/N reductions */
+#define GBXC_K_PGATHER 6    /* P^j gather/split for the mixed form */
+#define GBXC_K_OTHER 7
+#define GBXC_NKERNEL 8
+
 #define GBXC_MAX_PRIM 8     /* primitives per shell */
 #define GBXC_MAX_L 3        /* highest angular momentum (f) */
 
@@ -165,6 +176,15 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
                            int precision, int batch_begin, int batch_end, double *Exc,
                            double *Vxc, double *Nel, double *E_batch, double *N_batch,
                            void *stream);
+
+/* Per-kernel-class accounting.  Launch counts are always kept; with
+ * gbxc_profile_enable(ctx, 1) every kernel-class span is also bracketed by CUDA
+ * events on the stream it runs on.  Enabling or disabling resets both.
+ * gbxc_profile_read fills ms[GBXC_NKERNEL] (device milliseconds, NULL to skip)
+ * and launches[GBXC_NKERNEL] (kernel launches, NULL to skip) since the last
+ * reset; it synchronises with the recorded events. */
+int gbxc_profile_enable(gbxc_ctx *ctx, int on);
+int gbxc_profile_read(gbxc_ctx *ctx, double *ms, long long *launches);
 
 #ifdef __cplusplus
 }

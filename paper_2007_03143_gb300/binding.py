@@ -31,7 +31,10 @@ PARTITIONS = {"becke": GBXC_BECKE, "ssf": GBXC_SSF}
 PRECISIONS = {"fp64": GBXC_FP64, "mixed": GBXC_MIXED}
 
 EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis", "gbxc_load_grid",
-            "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches"]
+            "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
+            "gbxc_profile_enable", "gbxc_profile_read"]
+KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "other"]
+GBXC_NKERNEL = len(KERNEL_CLASSES)
 
 
 class LibraryMissing(ImportError):
@@ -81,8 +84,11 @@ def lib():
     L.gbxc_integrate.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, pd, c_void_p, pd, c_void_p]
     L.gbxc_integrate_batches.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_int, pd,
                                          c_void_p, pd, c_void_p, c_void_p, c_void_p]
+    L.gbxc_profile_enable.argtypes = [c_void_p, c_int]
+    L.gbxc_profile_read.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("gbxc_create", "gbxc_load_basis", "gbxc_load_grid", "gbxc_plan_info_get",
-                 "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches"):
+                 "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
+                 "gbxc_profile_enable", "gbxc_profile_read"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -206,6 +212,18 @@ def gbxc_integrate_batches(ctx, mol, P, functional, precision, batch_begin, batc
                                              PRECISIONS.get(precision, precision), batch_begin,
                                              batch_end, ctypes.byref(E), pV, ctypes.byref(N), pE, pN, st))
     return E.value, N.value
+
+
+def gbxc_profile_enable(ctx, on=True):
+    _check(ctx, lib().gbxc_profile_enable(ctx, int(bool(on))))
+
+
+def gbxc_profile_read(ctx) -> dict:
+    """{kernel class: (milliseconds, launches)} since the last enable/disable."""
+    ms = np.zeros(GBXC_NKERNEL)
+    n = np.zeros(GBXC_NKERNEL, np.int64)
+    _check(ctx, lib().gbxc_profile_read(ctx, ms.ctypes.data, n.ctypes.data))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 class Context:

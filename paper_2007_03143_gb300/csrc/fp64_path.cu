@@ -334,20 +334,40 @@ __global__ void total_sums(FinishArgs a) {
 cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s) {
     int64_t nt = a.t1 - a.t0;
     if (nt <= 0) return cudaSuccess;
+    Profiler &P = *a.prof;
+    P.begin(GBXC_K_COLLOC, s);
     colloc_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    P.end(GBXC_K_COLLOC, s);
     dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
+    P.begin(GBXC_K_XGEMM, s);
     xgemm_f64<<<xg, 256, 0, s>>>(a);
+    P.end(GBXC_K_XGEMM, s);
+    P.begin(GBXC_K_RHO_Z, s);
     rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
-    if (a.nvtasks > 0) vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a);
+    P.end(GBXC_K_RHO_Z, s);
+    if (a.nvtasks > 0) {
+        P.begin(GBXC_K_VGEMM, s);
+        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a);
+        P.end(GBXC_K_VGEMM, s);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish(const FinishArgs &a, cudaStream_t s) {
     int64_t nn = (int64_t)a.nbf * a.nbf;
-    if (a.V && nn > 0) symmetrize<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(a.Vacc, a.V, a.nbf);
+    int n = 0;
+    a.prof->begin(GBXC_K_FINISH, s);
+    if (a.V && nn > 0) {
+        symmetrize<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(a.Vacc, a.V, a.nbf);
+        ++n;
+    }
     int nb = a.b1 - a.b0;
-    if (nb > 0) batch_sums<<<(nb + 127) / 128, 128, 0, s>>>(a);
+    if (nb > 0) {
+        batch_sums<<<(nb + 127) / 128, 128, 0, s>>>(a);
+        ++n;
+    }
     total_sums<<<1, 256, 0, s>>>(a);
+    a.prof->end(GBXC_K_FINISH, s, n + 1);
     return cudaGetLastError();
 }
 

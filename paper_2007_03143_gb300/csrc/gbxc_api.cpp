@@ -70,6 +70,7 @@ struct gbxc_ctx {
     std::map<int, std::unique_ptr<Molecule>> mols;
     int next_id = 0;
     MixedCtx mixed;
+    Profiler prof;
 };
 
 namespace {
@@ -301,6 +302,7 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
         a.scratch = ctx->scratch;
         a.vtasks = S.d_tasks ? S.d_tasks + 5 * c.task0 : nullptr;
         a.nvtasks = (int)c.ntask;
+        a.prof = &ctx->prof;
         if (precision == GBXC_FP64)
             check(launch_fp64_chunk(a, s), "fp64 chunk");
         else
@@ -318,6 +320,7 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     f.Eb = m.d_Eb;
     f.Nb = m.d_Nb;
     f.tot = ctx->d_tot;
+    f.prof = &ctx->prof;
     if (Eb || Nb) {
         check(cudaMemsetAsync(m.d_Eb, 0, std::max(nb, 1) * 8, s), "zero Eb");
         check(cudaMemsetAsync(m.d_Nb, 0, std::max(nb, 1) * 8, s), "zero Nb");
@@ -414,6 +417,7 @@ void gbxc_destroy(gbxc_ctx *ctx) {
     }
     ctx->mols.clear();
     free_mixed_ctx(ctx->mixed);
+    ctx->prof.release();
     cudaFree(ctx->scratch);
     cudaFree(ctx->d_P);
     cudaFree(ctx->d_Vacc);
@@ -557,6 +561,7 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
         wa.npts = (int64_t)P.x.size();
         wa.natoms = m.natoms;
         wa.scheme = spec->partition;
+        wa.prof = &ctx->prof;
         check(launch_partition_weights(wa, s), "partition weights");
         check(cudaStreamSynchronize(s), "load_grid");
         m.has_grid = true;
@@ -645,6 +650,27 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
         if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
         return integrate_impl(ctx, mol, P, functional, precision, batch_begin, batch_end, Exc, Vxc,
                               Nel, E_batch, N_batch, stream);
+    });
+}
+
+int gbxc_profile_enable(gbxc_ctx *ctx, int on) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        ctx->prof.reset();
+        ctx->prof.on = on != 0;
+        return GBXC_OK;
+    });
+}
+
+int gbxc_profile_read(gbxc_ctx *ctx, double *ms, long long *launches) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        ctx->prof.collect();
+        for (int k = 0; k < GBXC_NKERNEL; ++k) {
+            if (ms) ms[k] = ctx->prof.ms[k];
+            if (launches) launches[k] = ctx->prof.launches[k];
+        }
+        return GBXC_OK;
     });
 }
 

@@ -78,6 +78,27 @@ void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &she
 
 inline int64_t pad_funcs(int64_t n) { return (n + FBLK - 1) / FBLK * FBLK; }
 
+// Per-kernel-class launch counter and optional CUDA-event timer (profiler.cpp).
+// Kernel classes are the GBXC_K_* constants of gbxc.h.
+struct Profiler {
+    bool on = false;
+    long long launches[GBXC_NKERNEL] = {};
+    double ms[GBXC_NKERNEL] = {};
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    int open_kind = -1;
+    cudaEvent_t open_ev = nullptr;
+    void begin(int kind, cudaStream_t s);
+    void end(int kind, cudaStream_t s, int nlaunch = 1);
+    void collect();
+    void reset();
+    void release();
+};
+
 // ---------------------------------------------------------------------------
 // kernel launchers (one translation unit each)
 // ---------------------------------------------------------------------------
@@ -90,6 +111,7 @@ struct WeightsArgs {
     int64_t npts;
     int natoms;
     int scheme;
+    Profiler *prof;
 };
 cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s);
 
@@ -107,6 +129,7 @@ struct ChunkArgs {
     void *scratch;            // chunk slabs
     const int *vtasks;        // 5 ints per task: batch, mb, nb, t0, t1
     int nvtasks;
+    Profiler *prof;
 };
 cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s);
 
@@ -119,6 +142,7 @@ struct FinishArgs {
     int b0, b1;
     double *Eb, *Nb;          // per batch (nbatch), device
     double *tot;              // [E, N] device
+    Profiler *prof;
 };
 cudaError_t launch_finish(const FinishArgs &a, cudaStream_t s);
 

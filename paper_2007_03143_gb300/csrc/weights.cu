@@ -105,7 +105,9 @@ cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s) {
     int threads = 128;
     int64_t blocks = (a.npts + threads - 1) / threads;
     size_t smem = sizeof(double) * 3 * a.natoms;
+    if (a.prof) a.prof->begin(GBXC_K_WEIGHTS, s);
     partition_weights_kernel<<<(unsigned)blocks, threads, smem, s>>>(a);
+    if (a.prof) a.prof->end(GBXC_K_WEIGHTS, s);
     return cudaGetLastError();
 }
 
