@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -244,12 +245,19 @@ void build_schedule(gbxc_ctx *ctx, Molecule &m, int precision, int b0, int b1) {
         S.max_rows = std::max(S.max_rows, c.rows);
     }
     S.ntasks = (int64_t)tasks.size() / 5;
+    if (precision == GBXC_MIXED) {
+        std::vector<int64_t> c0, c1;
+        for (const auto &c : S.chunks) {
+            c0.push_back(c.t0);
+            c1.push_back(c.t1);
+        }
+        build_mixed_schedule(m.plan, c0, c1, S.mixed);
+    }
     if (!tasks.empty()) {
         check(cudaMalloc(&S.d_tasks, tasks.size() * sizeof(int)), "cudaMalloc tasks");
         check(cudaMemcpy(S.d_tasks, tasks.data(), tasks.size() * sizeof(int), cudaMemcpyHostToDevice),
               "upload tasks");
     }
-    if (precision == GBXC_MIXED) build_mixed_schedule(m.plan, m.nbf, b0, b1, S.mixed);
     S.precision = precision;
     S.b0 = b0;
     S.b1 = b1;
@@ -284,7 +292,8 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     if (precision == GBXC_MIXED) {
         check(mixed_prepare(ctx->mixed, m.mixed_res, S.mixed, dP, m.nbf, s), "mixed prepare");
     }
-    for (const auto &c : S.chunks) {
+    for (size_t ci = 0; ci < S.chunks.size(); ++ci) {
+        const auto &c = S.chunks[ci];
         ChunkArgs a;
         a.plan = m.dev;
         a.shells = m.d_shells;
@@ -306,7 +315,7 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
         if (precision == GBXC_FP64)
             check(launch_fp64_chunk(a, s), "fp64 chunk");
         else
-            check(launch_mixed_chunk(a, ctx->mixed, m.mixed_res, S.mixed, s), "mixed chunk");
+            check(launch_mixed_chunk(a, ctx->mixed, m.mixed_res, S.mixed, (int)ci, s), "mixed chunk");
     }
     FinishArgs f;
     f.Vacc = ctx->d_Vacc;
@@ -332,6 +341,12 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     if (Eb) check(cudaMemcpyAsync(Eb, m.d_Eb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Eb");
     if (Nb) check(cudaMemcpyAsync(Nb, m.d_Nb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Nb");
     check(cudaStreamSynchronize(s), "integrate");
+    if (precision == GBXC_MIXED) {
+        int werr = 0;
+        check(mixed_read_error(ctx->mixed, &werr, s), "mixed status");
+        if (werr) return fail(ctx, GBXC_ETIMEOUT, "a bounded tensor-core pipeline wait expired (code " +
+                                                      std::to_string(werr) + ")");
+    }
     if (Exc) *Exc = tot[0];
     if (Nel) *Nel = tot[1];
     return GBXC_OK;

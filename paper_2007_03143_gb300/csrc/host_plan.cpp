@@ -307,7 +307,7 @@ void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &she
     int64_t row = 0;
     for (int j = 0; j < nb; ++j) {
         int64_t b0 = plan.batch_ptr[j], b1 = plan.batch_ptr[j + 1];
-        int64_t nfp = pad_funcs(plan.func_ptr[j + 1] - plan.func_ptr[j]);
+        int64_t nfp = std::max<int64_t>(pad_funcs(plan.func_ptr[j + 1] - plan.func_ptr[j]), FBLK);
         for (int64_t p = b0; p < b1; p += TILE) {
             plan.tile_batch.push_back(j);
             plan.tile_first.push_back(p);

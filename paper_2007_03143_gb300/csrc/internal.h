@@ -13,7 +13,7 @@
 namespace gbxc {
 
 constexpr int TILE = 128;        // grid points per tile (the M extent of the tensor-core tiles)
-constexpr int FBLK = 16;         // function padding granule (K step of a bf16 tensor-core MMA)
+constexpr int FBLK = 32;         // function padding granule (one 64-byte K block of bf16 operands)
 
 // One contracted Cartesian shell (Eq. gau_cart), as the kernels read it.
 struct DevShell {

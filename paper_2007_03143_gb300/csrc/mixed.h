@@ -13,32 +13,48 @@ namespace gbxc {
 size_t fp64_row_bytes();
 void append_fp64_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks);
 
-// Per-context state of the mixed form (tensor-map encoder, P split buffers).
+// Per-context state of the mixed form: tensor-map encoder, the sliced P^j blocks of the
+// current chunk and a device error word for bounded waits.
 struct MixedCtx {
     void *encode_fn = nullptr;         // cuTensorMapEncodeTiled from the driver
-    uint16_t *Phl = nullptr;           // gathered P^j blocks, bf16 hi/lo
-    size_t phl_cap = 0;
+    uint16_t *pslices = nullptr;       // 5 planes x rows x 32 bf16
+    int *pexp = nullptr;               // row exponents of the sliced P^j
+    size_t pslice_rows = 0;            // capacity of pslices in elements
+    size_t pexp_cap = 0;
+    int *d_err = nullptr;
 };
 // Per-molecule resident state of the mixed form.
 struct MixedResident {
     int dummy = 0;
 };
-// Per-schedule state of the mixed form (P^j gather layout).
+// Per-schedule state of the mixed form: for every chunk the batch range and the row
+// offsets of each batch's sliced P^j block.
 struct MixedSchedule {
-    int64_t *d_pofs = nullptr;         // per batch: element offset of its packed P^j
-    int64_t ptotal = 0;                // elements of all packed P^j
-    int b0 = 0, b1 = 0;
+    struct Chunk {
+        int j0, j1;                    // batches touched by the chunk (inclusive)
+        int64_t prow0;                 // offset of the chunk's entries in d_pofs / d_pexp_ofs
+        int64_t prows;                 // rows of the sliced P^j blocks of the chunk
+        int64_t pexp_rows;             // sum of padded N_b^j over the chunk's batches
+        int max_np;
+    };
+    std::vector<Chunk> chunks;
+    int64_t *d_pofs = nullptr;         // per (chunk, batch): first P-slice row
+    int64_t *d_pexp_ofs = nullptr;     // per (chunk, batch): first row-exponent entry
+    int64_t max_prows = 0, max_pexp = 0;
 };
 
 size_t mixed_row_bytes();
 void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks);
-void build_mixed_schedule(const HostPlan &plan, int nbf, int b0, int b1, MixedSchedule &s);
+void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chunk_t0,
+                          const std::vector<int64_t> &chunk_t1, MixedSchedule &s);
 void free_mixed_schedule(MixedSchedule &s);
 void free_mixed_resident(MixedResident &r);
 void free_mixed_ctx(MixedCtx &c);
 cudaError_t mixed_prepare(MixedCtx &c, MixedResident &r, const MixedSchedule &s, const double *P,
                           int nbf, cudaStream_t st);
 cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
-                               const MixedSchedule &s, cudaStream_t st);
+                               const MixedSchedule &s, int chunk_index, cudaStream_t st);
+// Device error word of the mixed kernels (nonzero after a bounded wait expired).
+cudaError_t mixed_read_error(MixedCtx &c, int *err, cudaStream_t st);
 
 }  // namespace gbxc

@@ -1,24 +1,742 @@
-// Mixed-precision form (placeholder until the tensor-core kernels land).
+// Tensor-core form of the batched integration (Algorithm 4) on sm_103a.
+//
+// The two contractions run on the 5th-generation tensor cores (tcgen05.mma, bf16 inputs,
+// fp32 accumulators in tensor memory, operands staged by TMA with the 64-byte swizzle):
+//
+//   X^j = P^j Phi^j (Eq. x_mat)      Ozaki-style exact slicing.  Every row of Phi (a grid
+//        point) and of P^j (a function) is scaled by a power of two to |v| <= 1 and cut
+//        into 5 integer slices v = sum_s q_s 2^-(6+7s) (34 bits).  The 15 slice products
+//        with s + t <= 4 are issued per K step into four accumulators: level d = s + t for
+//        d = 0, 1, 2, whose partial sums are integer multiples of 2^-(12+7d) below 2^24
+//        units so the fp32 sums are exact, and levels 3-4 together (rounded, 2^-21 below
+//        level 0).  X = (acc0 + acc1 + acc2 + acc3) 2^(e_i + f_mu), summed in double-float.
+//   W^j = Z^jT Phi^j (Eq. vxc_batch) float split: Z and Phi (fp32) are cut into three
+//        bf16 pieces each; the 6 products with s + t <= 2 accumulate in fp32.
+//
+// Everything that decides E_xc to 1e-9 stays above fp32 precision: collocation in
+// float64 written as double-float pairs, rho and grad rho summed in double-float, the
+// partition weights, the functional and all E/N/V accumulation in float64.
+//
+// Kernels per chunk of tiles: pslice (P^j row slices), colloc (Phi, grad Phi, Phi slices),
+// xgemm (tcgen05), rho_z (rho, grad rho, functional, E/N partials, Z and Phi pieces),
+// vgemm (tcgen05, scatter into V_acc with float64 atomics).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
 #include "mixed.h"
+#include "umma.cuh"
+#include "xc_functional.cuh"
 
 namespace gbxc {
+namespace {
 
-size_t mixed_row_bytes() { return (size_t)TILE * 16; }
-void append_mixed_vtasks(int, int, int64_t, int64_t, std::vector<int> &) {}
-void build_mixed_schedule(const HostPlan &, int, int b0, int b1, MixedSchedule &s) {
-    s.b0 = b0;
-    s.b1 = b1;
+constexpr int NSL = 5;          // Ozaki slices (X contraction)
+constexpr int NPC = 3;          // float-split pieces (V contraction)
+constexpr int BN = 128;         // N extent of one MMA (functions)
+constexpr int XSTAGES = 2, VSTAGES = 4;
+constexpr int VKS = 16;         // tiles per V task (K split)
+constexpr int SLICE_BITS = 34;  // 6 + 4 x 7
+// The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
+// at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
+constexpr double kFp32RhoMin = 1e300;
+
+// ---------------------------------------------------------------- scratch layout
+struct MixedSlabs {
+    float *phi;             // 8 planes [rows][128]: phi, dx, dy, dz as (hi, lo) pairs
+    float *x;               // 2 planes [rows][128]: X as (hi, lo)
+    __nv_bfloat16 *ax;      // 5 planes [4 rows][32]: Phi slices, K-blocked per tile
+    __nv_bfloat16 *vz;      // 3 planes [4 rows][32]: Z pieces, point-blocked per tile
+    __nv_bfloat16 *vphi;    // 3 planes [4 rows][32]: Phi pieces, point-blocked per tile
+    int *pexp;              // [tiles][128] point exponents e_i
+};
+
+__host__ __device__ inline MixedSlabs mixed_slabs(void *base, int64_t rows) {
+    char *p = static_cast<char *>(base);
+    MixedSlabs s;
+    s.phi = reinterpret_cast<float *>(p);
+    p += (size_t)8 * rows * TILE * 4;
+    s.x = reinterpret_cast<float *>(p);
+    p += (size_t)2 * rows * TILE * 4;
+    s.ax = reinterpret_cast<__nv_bfloat16 *>(p);
+    p += (size_t)NSL * rows * TILE * 2;
+    s.vz = reinterpret_cast<__nv_bfloat16 *>(p);
+    p += (size_t)NPC * rows * TILE * 2;
+    s.vphi = reinterpret_cast<__nv_bfloat16 *>(p);
+    p += (size_t)NPC * rows * TILE * 2;
+    s.pexp = reinterpret_cast<int *>(p);
+    return s;
 }
-void free_mixed_schedule(MixedSchedule &s) { s = MixedSchedule{}; }
+
+struct MixedArgs {
+    MixedSlabs s;
+    int64_t rows;
+    int j0;                      // first batch of the chunk
+    const int64_t *pofs;         // per batch of the chunk: first row of its P slices
+    const int64_t *pexp_ofs;     // per batch of the chunk: first entry of its row exponents
+    __nv_bfloat16 *pslices;      // 5 planes, plane pitch pplane rows of 32
+    int64_t pplane;
+    int *pexp;                   // row exponents of P^j
+    int *err;
+};
+
+__device__ __forceinline__ int pad32(int n) { return (n + 31) & ~31; }
+
+// ---------------------------------------------------------------- slicing
+// v = V 2^-34 with |V| <= 2^34 -> five slices q_s in [-64, 64], v = sum q_s 2^-(6+7s).
+__device__ __forceinline__ void slice5(long long V, float out[NSL]) {
+    long long q0 = (V + (1LL << 27)) >> 28;
+    long long r = V - (q0 << 28);
+    long long q1 = (r + (1LL << 20)) >> 21;
+    r -= q1 << 21;
+    long long q2 = (r + (1LL << 13)) >> 14;
+    r -= q2 << 14;
+    long long q3 = (r + (1LL << 6)) >> 7;
+    long long q4 = r - (q3 << 7);
+    out[0] = ldexpf((float)q0, -6);
+    out[1] = ldexpf((float)q1, -13);
+    out[2] = ldexpf((float)q2, -20);
+    out[3] = ldexpf((float)q3, -27);
+    out[4] = ldexpf((float)q4, -34);
+}
+
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 out[NPC]) {
+    __nv_bfloat16 a = __float2bfloat16_rn(v);
+    float r = __fsub_rn(v, __bfloat162float(a));
+    __nv_bfloat16 b = __float2bfloat16_rn(r);
+    r = __fsub_rn(r, __bfloat162float(b));
+    out[0] = a;
+    out[1] = b;
+    out[2] = __float2bfloat16_rn(r);
+}
+
+// ---------------------------------------------------------------- double-float helpers
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.h, b.h);
+    float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    return quick_two_sum(s.h, e);
+}
+
+__device__ __forceinline__ double df_to_d(df a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ df d_to_df(double d) {
+    float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+
+// ---------------------------------------------------------------- pslice
+// One warp per row mu of P^j: row exponent, then the 5 slices of P^j[mu][nu] for every
+// K block of 32 nu's.  Rows and columns past N_b^j are written as zeros.
+__global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
+    int jl = blockIdx.x;
+    int j = m.j0 + jl;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t f0 = a.plan.func_ptr[j];
+    int n = (int)(a.plan.func_ptr[j + 1] - f0);
+    int np = pad32(n);
+    int mu = blockIdx.y * 4 + warp;
+    if (mu >= np) return;
+    const int *F = a.plan.func_idx + f0;
+    const double *Prow = (mu < n) ? a.P + (size_t)F[mu] * a.nbf : nullptr;
+    double mx = 0.0;
+    if (Prow)
+        for (int nu = lane; nu < n; nu += 32) mx = fmax(mx, fabs(Prow[F[nu]]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    if (lane == 0) m.pexp[m.pexp_ofs[jl] + mu] = e;
+    int64_t pofs = m.pofs[jl];
+    for (int kb = 0; kb < np / 32; ++kb) {
+        int nu = kb * 32 + lane;
+        double v = (Prow && nu < n) ? Prow[F[nu]] : 0.0;
+        long long V = llrint(ldexp(v, SLICE_BITS - e));
+        float q[NSL];
+        slice5(V, q);
+        size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + lane;
+#pragma unroll
+        for (int s = 0; s < NSL; ++s) m.pslices[(size_t)s * m.pplane * 32 + o] = __float2bfloat16_rn(q[s]);
+    }
+}
+
+// ---------------------------------------------------------------- collocation
+// Thread per point; float64 evaluation of Eq. gau_cart and its gradient, stored as
+// double-float planes; then the point's Ozaki slices of Phi, K-blocked by 32 functions.
+__global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int64_t r0 = a.plan.tile_row[t] - a.row0;
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int np = pad32(n);
+    bool live = i < cnt;
+    int64_t p = a.plan.tile_first[t] + i;
+    double px = live ? a.plan.x[p] : 0.0, py = live ? a.plan.y[p] : 0.0, pz = live ? a.plan.z[p] : 0.0;
+    const size_t plane = (size_t)m.rows * TILE;
+    float *phi = m.s.phi;
+    int64_t s0 = a.plan.shell_ptr[j], s1 = a.plan.shell_ptr[j + 1];
+    int row = 0;
+    double mx = 0.0;
+    for (int64_t si = s0; si < s1; ++si) {
+        const DevShell &sh = a.shells[a.plan.shell_idx[si]];
+        double X = px - sh.c[0], Y = py - sh.c[1], Z = pz - sh.c[2];
+        double r2 = X * X + Y * Y + Z * Z;
+        double g = 0.0, h = 0.0;
+        for (int k = 0; k < sh.nprim; ++k) {
+            double ex = exp(-sh.alpha[k] * r2);
+            g += sh.coeff[k] * ex;
+            h += (-2.0 * sh.alpha[k] * sh.coeff[k]) * ex;
+        }
+        double xp[GBXC_MAX_L + 2], yp[GBXC_MAX_L + 2], zp[GBXC_MAX_L + 2];
+        xp[0] = yp[0] = zp[0] = 1.0;
+        for (int k = 1; k <= sh.L; ++k) {
+            xp[k] = xp[k - 1] * X;
+            yp[k] = yp[k - 1] * Y;
+            zp[k] = zp[k - 1] * Z;
+        }
+        for (int l = sh.L; l >= 0; --l)
+            for (int mm = sh.L - l; mm >= 0; --mm) {
+                int nn = sh.L - l - mm;
+                double mono = xp[l] * yp[mm] * zp[nn];
+                double v[4];
+                v[0] = mono * g;
+                v[1] = (l > 0 ? l * xp[l - 1] * yp[mm] * zp[nn] : 0.0) * g + mono * X * h;
+                v[2] = (mm > 0 ? mm * xp[l] * yp[mm - 1] * zp[nn] : 0.0) * g + mono * Y * h;
+                v[3] = (nn > 0 ? nn * xp[l] * yp[mm] * zp[nn - 1] : 0.0) * g + mono * Z * h;
+                size_t o = (size_t)(r0 + row) * TILE + i;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    double vv = live ? v[c] : 0.0;
+                    df d = d_to_df(vv);
+                    phi[(2 * c) * plane + o] = d.h;
+                    phi[(2 * c + 1) * plane + o] = d.l;
+                }
+                if (live) mx = fmax(mx, fabs(v[0]));
+                ++row;
+            }
+    }
+    for (; row < np; ++row) {
+        size_t o = (size_t)(r0 + row) * TILE + i;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) phi[c * plane + o] = 0.0f;
+    }
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    m.s.pexp[(t - a.t0) * TILE + i] = e;
+    // Ozaki slices of this point's row of Phi: K block kb -> row 4 r0 + 128 kb + i, 32 values
+    for (int kb = 0; kb < np / 32; ++kb) {
+        __align__(16) __nv_bfloat16 buf[NSL][32];
+        for (int c = 0; c < 32; ++c) {
+            size_t o = (size_t)(r0 + kb * 32 + c) * TILE + i;
+            float hi = phi[o], lo = phi[plane + o];
+            long long V = __float2ll_rn(ldexpf(hi, SLICE_BITS - e)) + __float2ll_rn(ldexpf(lo, SLICE_BITS - e));
+            float q[NSL];
+            slice5(V, q);
+#pragma unroll
+            for (int s = 0; s < NSL; ++s) buf[s][c] = __float2bfloat16_rn(q[s]);
+        }
+        size_t orow = (size_t)(4 * r0 + (int64_t)kb * TILE + i) * 32;
+#pragma unroll
+        for (int s = 0; s < NSL; ++s) {
+            uint4 *dst = reinterpret_cast<uint4 *>(m.s.ax + (size_t)s * plane + orow);
+            const uint4 *src = reinterpret_cast<const uint4 *>(buf[s]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = src[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- tcgen05 GEMM core
+struct MmaOp {
+    unsigned char a, b, acc;
+};
+
+// X contraction: accumulator d holds slice level d = s + t for d = 0, 1, 2 (each an exact
+// integer multiple of 2^-(12+7d) below 2^24 units for K <= 1184), accumulator 3 the rounded
+// remainder of levels 3 and 4.
+constexpr int XACC = 4;
+__constant__ MmaOp kXOps[15] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {0, 2, 2}, {1, 1, 2},
+                                {2, 0, 2}, {0, 3, 3}, {1, 2, 3}, {2, 1, 3}, {3, 0, 3},
+                                {0, 4, 3}, {1, 3, 3}, {2, 2, 3}, {3, 1, 3}, {4, 0, 3}};
+__constant__ MmaOp kVOps[6] = {{0, 0, 0}, {0, 1, 0}, {1, 0, 0}, {0, 2, 0}, {1, 1, 0}, {2, 0, 0}};
+
+template <int SA, int SB, int STAGES>
+struct GemmSmem {
+    static constexpr int A_BYTES = SA * 128 * 64;
+    static constexpr int B_BYTES = SB * BN * 64;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int TOTAL = 1024 + STAGES * STAGE + 256;
+};
+
+// Producer (thread 0) and MMA issuer (thread 32) of one output tile; returns after the
+// final commit has been observed by every thread (or a bounded wait expired).
+template <int SA, int SB, int STAGES, int NOPS, typename Coords>
+__device__ __forceinline__ void gemm_tile(uint8_t *smem, uint64_t *full, uint64_t *empty, uint64_t *done,
+                                          uint32_t tmem, const CUtensorMap *ta, const CUtensorMap *tb,
+                                          int nkb, const MmaOp *ops, Coords coords, int *err,
+                                          volatile int *abort_flag) {
+    using L = GemmSmem<SA, SB, STAGES>;
+    const int tid = threadIdx.x;
+    const uint32_t idesc = umma::idesc_bf16(128, BN);
+    if (tid == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            int s = kb % STAGES;
+            if (kb >= STAGES && !umma::mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+                atomicOr(err, 1);
+                *abort_flag = 1;
+                break;
+            }
+            if (*abort_flag) break;
+            int ay, by;
+            coords(kb, ay, by);
+            umma::mbar_arrive_expect_tx(&full[s], L::STAGE);
+            uint8_t *sa = smem + s * L::STAGE;
+            umma::tma_load_3d(sa, ta, &full[s], 0, ay, 0);
+            umma::tma_load_3d(sa + L::A_BYTES, tb, &full[s], 0, by, 0);
+        }
+    } else if (tid == 32) {
+        uint32_t init = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            int s = kb % STAGES;
+            if (!umma::mbar_wait(&full[s], (kb / STAGES) & 1)) {
+                atomicOr(err, 2);
+                *abort_flag = 1;
+                break;
+            }
+            umma::fence_after_sync();
+            uint32_t sa = umma::smem_u32(smem + s * L::STAGE), sb = sa + L::A_BYTES;
+#pragma unroll
+            for (int k16 = 0; k16 < 2; ++k16) {
+#pragma unroll
+                for (int q = 0; q < NOPS; ++q) {
+                    MmaOp op = ops[q];
+                    uint64_t ad = umma::desc_sw64(sa + op.a * 128 * 64 + k16 * 32);
+                    uint64_t bd = umma::desc_sw64(sb + op.b * BN * 64 + k16 * 32);
+                    umma::mma_bf16(tmem + op.acc * BN, ad, bd, idesc, (init >> op.acc) & 1);
+                    init |= 1u << op.acc;
+                }
+            }
+            umma::mma_commit(&empty[s]);
+        }
+        umma::mma_commit(done);
+    }
+    __syncwarp();
+    if (!umma::mbar_wait(done, 0)) atomicOr(err, 4);
+    umma::fence_after_sync();
+    __syncwarp();
+}
+
+template <int SA, int SB, int STAGES>
+__device__ __forceinline__ void gemm_setup(uint8_t *&smem, uint64_t *&full, uint64_t *&empty, uint64_t *&done,
+                                           uint32_t *&tmem_slot, const CUtensorMap *ta,
+                                           const CUtensorMap *tb, uint32_t ncols) {
+    using L = GemmSmem<SA, SB, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint32_t base = umma::smem_u32(smem_raw);
+    smem = smem_raw + (((base + 1023) & ~1023u) - base);
+    full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE);
+    empty = full + STAGES;
+    done = empty + STAGES;
+    tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            umma::mbar_init(&full[s], 1);
+            umma::mbar_init(&empty[s], 1);
+        }
+        umma::mbar_init(done, 1);
+        umma::fence_mbar_init();
+        umma::prefetch_tmap(ta);
+        umma::prefetch_tmap(tb);
+    }
+    if ((threadIdx.x >> 5) == 2) umma::tmem_alloc(tmem_slot, ncols);
+    __syncthreads();
+    umma::fence_after_sync();
+}
+
+// ---------------------------------------------------------------- X contraction
+// CTA (tile t, N chunk nc): X[points 128][functions nc*128 .. +128] over K = N_b^j.
+__global__ void __launch_bounds__(128) xgemm_tc(const __grid_constant__ CUtensorMap tax,
+                                                const __grid_constant__ CUtensorMap tp, ChunkArgs a,
+                                                MixedArgs m) {
+    int64_t t = a.t0 + blockIdx.x;
+    int nc = blockIdx.y;
+    int j = a.plan.tile_batch[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    if (nc * BN >= n) return;
+    int np = pad32(n);
+    int64_t r0 = a.plan.tile_row[t] - a.row0;
+    int jl = j - m.j0;
+    int64_t pofs = m.pofs[jl];
+    uint8_t *smem;
+    uint64_t *full, *empty, *done;
+    uint32_t *tmem_slot;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) abort_flag = 0;
+    gemm_setup<NSL, NSL, XSTAGES>(smem, full, empty, done, tmem_slot, &tax, &tp, XACC * BN);
+    uint32_t tmem = *tmem_slot;
+    auto coords = [&](int kb, int &ay, int &by) {
+        ay = (int)(4 * r0 + (int64_t)kb * TILE);
+        by = (int)(pofs + (int64_t)kb * np + nc * BN);
+    };
+    gemm_tile<NSL, NSL, XSTAGES, 15>(smem, full, empty, done, tmem, &tax, &tp, np / 32, kXOps, coords, m.err,
+                                     &abort_flag);
+    // epilogue: thread = point (TMEM lane), 128 function columns
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int i = warp * 32 + lane;
+    int ei = m.s.pexp[(t - a.t0) * TILE + i];
+    const int *fexp = m.pexp + m.pexp_ofs[jl];
+    const size_t plane = (size_t)m.rows * TILE;
+    uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c = 0; c < BN; c += 16) {
+        float v0[16], v1[16], v2[16], v3[16];
+        umma::tmem_ld16(lane_base + c, v0);
+        umma::tmem_ld16(lane_base + BN + c, v1);
+        umma::tmem_ld16(lane_base + 2 * BN + c, v2);
+        umma::tmem_ld16(lane_base + 3 * BN + c, v3);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            int mu = nc * BN + c + k;
+            if (mu < n) {
+                df x = df_add(df_add(two_sum(v0[k], v1[k]), {v2[k], 0.f}), {v3[k], 0.f});
+                int sc = ei + fexp[mu];
+                size_t o = (size_t)(r0 + mu) * TILE + i;
+                m.s.x[o] = ldexpf(x.h, sc);
+                m.s.x[plane + o] = ldexpf(x.l, sc);
+            }
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 2) umma::tmem_dealloc(tmem, XACC * BN);
+    (void)np;
+}
+
+// ---------------------------------------------------------------- rho, functional, Z
+__global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int np = pad32(n);
+    int64_t r0 = a.plan.tile_row[t] - a.row0;
+    const size_t plane = (size_t)m.rows * TILE;
+    const float *phi = m.s.phi;
+    df rho{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
+    for (int mu = 0; mu < n; ++mu) {
+        size_t o = (size_t)(r0 + mu) * TILE + i;
+        df x{m.s.x[o], m.s.x[plane + o]};
+        rho = df_add(rho, df_mul({phi[o], phi[plane + o]}, x));
+        gx = df_add(gx, df_mul({phi[2 * plane + o], phi[3 * plane + o]}, x));
+        gy = df_add(gy, df_mul({phi[4 * plane + o], phi[5 * plane + o]}, x));
+        gz = df_add(gz, df_mul({phi[6 * plane + o], phi[7 * plane + o]}, x));
+    }
+    double r = df_to_d(rho);
+    double dx = 2.0 * df_to_d(gx), dy = 2.0 * df_to_d(gy), dz = 2.0 * df_to_d(gz);
+    double e = 0.0, nn = 0.0;
+    float ca = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    if (i < cnt) {
+        double w = a.plan.w[a.plan.tile_first[t] + i];
+        double sigma = dx * dx + dy * dy + dz * dz;
+        double f, vr, vs;
+        if (r >= kFp32RhoMin) {
+            float ff, fr, fs;
+            xc::evaluate<float>(a.functional, (float)r, (float)sigma, ff, fr, fs);
+            f = ff;
+            vr = fr;
+            vs = fs;
+        } else {
+            xc::evaluate<double>(a.functional, r, sigma, f, vr, vs);
+        }
+        e = w * f;
+        nn = w * r;
+        ca = (float)(0.5 * w * vr);
+        double b = 2.0 * w * vs;
+        bx = (float)(b * dx);
+        by = (float)(b * dy);
+        bz = (float)(b * dz);
+    }
+    // Z and Phi pieces, point-blocked: row 4 r0 + pk * np + mu, column i % 32
+    int pk = i >> 5, col = i & 31;
+    for (int mu = 0; mu < np; ++mu) {
+        size_t o = (size_t)(r0 + mu) * TILE + i;
+        float p = phi[o];
+        float z = ca * p + bx * phi[2 * plane + o] + by * phi[4 * plane + o] + bz * phi[6 * plane + o];
+        __nv_bfloat16 zp[NPC], pp[NPC];
+        split3(z, zp);
+        split3(p, pp);
+        size_t orow = (size_t)(4 * r0 + (int64_t)pk * np + mu) * 32 + col;
+#pragma unroll
+        for (int s = 0; s < NPC; ++s) {
+            m.s.vz[(size_t)s * plane + orow] = zp[s];
+            m.s.vphi[(size_t)s * plane + orow] = pp[s];
+        }
+    }
+    __shared__ double re[TILE], rn[TILE];
+    re[i] = e;
+    rn[i] = nn;
+    __syncthreads();
+    for (int s = TILE / 2; s > 0; s >>= 1) {
+        if (i < s) {
+            re[i] += re[i + s];
+            rn[i] += rn[i + s];
+        }
+        __syncthreads();
+    }
+    if (i == 0) {
+        a.tileE[t] = re[0];
+        a.tileN[t] = rn[0];
+    }
+}
+
+// ---------------------------------------------------------------- V contraction
+// Task (batch j, row block mc, column block nc, tiles [tb, te)): W[mu][nu] =
+// sum over the tiles' points of Z[i][mu] Phi[i][nu], then V_acc[F_mu][F_nu] += W.
+__global__ void __launch_bounds__(128) vgemm_tc(const __grid_constant__ CUtensorMap tz,
+                                                const __grid_constant__ CUtensorMap tphi, ChunkArgs a,
+                                                MixedArgs m) {
+    const int *task = a.vtasks + 5 * blockIdx.x;
+    int j = task[0], mc = task[1], nc = task[2];
+    int64_t tb = task[3], te = task[4];
+    int64_t f0 = a.plan.func_ptr[j];
+    int n = (int)(a.plan.func_ptr[j + 1] - f0);
+    int np = pad32(n);
+    const int *F = a.plan.func_idx + f0;
+    uint8_t *smem;
+    uint64_t *full, *empty, *done;
+    uint32_t *tmem_slot;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) abort_flag = 0;
+    gemm_setup<NPC, NPC, VSTAGES>(smem, full, empty, done, tmem_slot, &tz, &tphi, BN);
+    uint32_t tmem = *tmem_slot;
+    auto coords = [&](int kb, int &ay, int &by) {
+        int64_t t = tb + kb / 4;
+        int pk = kb % 4;
+        int64_t base = 4 * (a.plan.tile_row[t] - a.row0) + (int64_t)pk * np;
+        ay = (int)(base + mc * BN);
+        by = (int)(base + nc * BN);
+    };
+    gemm_tile<NPC, NPC, VSTAGES, 6>(smem, full, empty, done, tmem, &tz, &tphi, (int)(te - tb) * 4, kVOps,
+                                    coords, m.err, &abort_flag);
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int mu = mc * BN + warp * 32 + lane;
+    uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    size_t rowg = (mu < n) ? (size_t)F[mu] * a.nbf : 0;
+    for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        umma::tmem_ld16(lane_base + c, v);
+        if (mu < n) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                int nu = nc * BN + c + k;
+                if (nu < n) atomicAdd(&a.Vacc[rowg + F[nu]], (double)v[k]);
+            }
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 2) umma::tmem_dealloc(tmem, BN);
+}
+
+// ---------------------------------------------------------------- host helpers
+CUtensorMap make_map(MixedCtx &c, void *ptr, int64_t rows, int64_t plane_rows, int planes, cudaError_t &err) {
+    CUtensorMap mp;
+    std::memset(&mp, 0, sizeof(mp));
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(c.encode_fn);
+    cuuint64_t dims[3] = {32, (cuuint64_t)std::max<int64_t>(rows, 1), (cuuint64_t)planes};
+    cuuint64_t strides[2] = {64, (cuuint64_t)plane_rows * 64};
+    cuuint32_t box[3] = {32, 128, (cuuint32_t)planes};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = encode(&mp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) err = cudaErrorInvalidValue;
+    return mp;
+}
+
+template <typename T>
+cudaError_t grow(T *&p, size_t &cap, size_t need) {
+    if (need <= cap && p) return cudaSuccess;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(need, 1) * sizeof(T));
+    if (e == cudaSuccess) cap = need;
+    return e;
+}
+
+}  // namespace
+
+size_t mixed_row_bytes() { return (size_t)TILE * (8 * 4 + 2 * 4 + NSL * 2 + 2 * NPC * 2) + 16; }
+
+void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks) {
+    int nblk = (n + BN - 1) / BN;
+    for (int64_t k = s0; k < s1; k += VKS) {
+        int64_t k1 = std::min<int64_t>(k + VKS, s1);
+        for (int mb = 0; mb < nblk; ++mb)
+            for (int nb = 0; nb < nblk; ++nb) {
+                tasks.push_back(j);
+                tasks.push_back(mb);
+                tasks.push_back(nb);
+                tasks.push_back((int)k);
+                tasks.push_back((int)k1);
+            }
+    }
+}
+
+void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chunk_t0,
+                          const std::vector<int64_t> &chunk_t1, MixedSchedule &s) {
+    free_mixed_schedule(s);
+    std::vector<int64_t> pofs, pexp;
+    for (size_t c = 0; c < chunk_t0.size(); ++c) {
+        MixedSchedule::Chunk ch;
+        ch.j0 = plan.tile_batch[chunk_t0[c]];
+        ch.j1 = plan.tile_batch[chunk_t1[c] - 1];
+        ch.prow0 = (int64_t)pofs.size();
+        int64_t rows = 0, erows = 0;
+        ch.max_np = 0;
+        for (int j = ch.j0; j <= ch.j1; ++j) {
+            int64_t n = plan.func_ptr[j + 1] - plan.func_ptr[j];
+            int64_t np = pad_funcs(n);
+            pofs.push_back(rows);
+            pexp.push_back(erows);
+            rows += (np / 32) * np;
+            erows += np;
+            ch.max_np = std::max<int>(ch.max_np, (int)np);
+        }
+        ch.prows = rows;
+        ch.pexp_rows = erows;
+        s.max_prows = std::max(s.max_prows, rows);
+        s.max_pexp = std::max(s.max_pexp, erows);
+        s.chunks.push_back(ch);
+    }
+    if (!pofs.empty()) {
+        cudaMalloc(&s.d_pofs, pofs.size() * sizeof(int64_t));
+        cudaMemcpy(s.d_pofs, pofs.data(), pofs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        cudaMalloc(&s.d_pexp_ofs, pexp.size() * sizeof(int64_t));
+        cudaMemcpy(s.d_pexp_ofs, pexp.data(), pexp.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    }
+}
+
+void free_mixed_schedule(MixedSchedule &s) {
+    cudaFree(s.d_pofs);
+    cudaFree(s.d_pexp_ofs);
+    s = MixedSchedule{};
+}
+
 void free_mixed_resident(MixedResident &r) { r = MixedResident{}; }
-void free_mixed_ctx(MixedCtx &c) { c = MixedCtx{}; }
-cudaError_t mixed_prepare(MixedCtx &, MixedResident &, const MixedSchedule &, const double *, int,
-                          cudaStream_t) {
-    return cudaErrorNotSupported;
+
+void free_mixed_ctx(MixedCtx &c) {
+    cudaFree(c.pslices);
+    cudaFree(c.pexp);
+    cudaFree(c.d_err);
+    c = MixedCtx{};
 }
-cudaError_t launch_mixed_chunk(const ChunkArgs &, MixedCtx &, MixedResident &,
-                               const MixedSchedule &, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+cudaError_t mixed_prepare(MixedCtx &c, MixedResident &, const MixedSchedule &s, const double *, int,
+                          cudaStream_t st) {
+    if (!c.encode_fn) {
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &c.encode_fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || !c.encode_fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    }
+    if (!c.d_err) {
+        cudaError_t e = cudaMalloc(&c.d_err, sizeof(int));
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = grow(c.pslices, c.pslice_rows, (size_t)std::max<int64_t>(s.max_prows, 1) * 32 * NSL);
+    if (e != cudaSuccess) return e;
+    e = grow(c.pexp, c.pexp_cap, (size_t)std::max<int64_t>(s.max_pexp, 1));
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
+}
+
+cudaError_t mixed_read_error(MixedCtx &c, int *err, cudaStream_t st) {
+    *err = 0;
+    if (!c.d_err) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &, const MixedSchedule &s,
+                               int chunk_index, cudaStream_t st) {
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    const MixedSchedule::Chunk &ch = s.chunks[chunk_index];
+    MixedArgs m;
+    m.s = mixed_slabs(a.scratch, a.rows);
+    m.rows = a.rows;
+    m.j0 = ch.j0;
+    m.pofs = s.d_pofs + ch.prow0;
+    m.pexp_ofs = s.d_pexp_ofs + ch.prow0;
+    m.pslices = reinterpret_cast<__nv_bfloat16 *>(c.pslices);
+    m.pplane = std::max<int64_t>(s.max_prows, 1);
+    m.pexp = c.pexp;
+    m.err = c.d_err;
+    cudaError_t err = cudaSuccess;
+    CUtensorMap tax = make_map(c, m.s.ax, 4 * a.rows, 4 * a.rows, NSL, err);
+    CUtensorMap tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, err);
+    CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NPC, err);
+    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NPC, err);
+    if (err != cudaSuccess) return err;
+    using LX = GemmSmem<NSL, NSL, XSTAGES>;
+    using LV = GemmSmem<NPC, NPC, VSTAGES>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(xgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LX::TOTAL);
+        cudaFuncSetAttribute(vgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LV::TOTAL);
+        attr_set = true;
+    }
+    Profiler &P = *a.prof;
+    P.begin(GBXC_K_PGATHER, st);
+    pslice_kernel<<<dim3(ch.j1 - ch.j0 + 1, (ch.max_np + 3) / 4), 128, 0, st>>>(a, m);
+    P.end(GBXC_K_PGATHER, st);
+    P.begin(GBXC_K_COLLOC, st);
+    colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    P.end(GBXC_K_COLLOC, st);
+    P.begin(GBXC_K_XGEMM, st);
+    xgemm_tc<<<dim3((unsigned)nt, (unsigned)((a.max_nfunc + BN - 1) / BN)), 128, LX::TOTAL, st>>>(tax, tp, a, m);
+    P.end(GBXC_K_XGEMM, st);
+    P.begin(GBXC_K_RHO_Z, st);
+    rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    P.end(GBXC_K_RHO_Z, st);
+    if (a.nvtasks > 0) {
+        P.begin(GBXC_K_VGEMM, st);
+        vgemm_tc<<<(unsigned)a.nvtasks, 128, LV::TOTAL, st>>>(tz, tph, a, m);
+        P.end(GBXC_K_VGEMM, st);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace gbxc

@@ -37,6 +37,8 @@ __device__ __forceinline__ double m_sqrt(double v) { return sqrt(v); }
 __device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double m_exp(double v) { return exp(v); }
 __device__ __forceinline__ float m_exp(float v) { return expf(v); }
+__device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
+__device__ __forceinline__ float m_expm1(float v) { return expm1f(v); }
 __device__ __forceinline__ double m_log1p(double v) { return log1p(v); }
 __device__ __forceinline__ float m_log1p(float v) { return log1pf(v); }
 
@@ -74,8 +76,9 @@ __device__ __forceinline__ void pbe_c(T rho, T sigma, T &f, T &vrho, T &vsigma) 
     T deps_drs = T(-2.0 * kPwA * kPwA1) * lg +
                  T(2.0 * kPwA) * (T(1) + T(kPwA1) * rs) * dQ / (Q * (T(2.0 * kPwA) * Q + T(1)));
     T deps_drho = deps_drs * (-rs / (T(3) * rho));
-    T E = m_exp(-eps / T(kGamma));
-    T A = T(kBeta / kGamma) / (E - T(1));
+    T Em1 = m_expm1(-eps / T(kGamma));      // exp(-eps/gamma) - 1 without cancellation
+    T E = Em1 + T(1);
+    T A = T(kBeta / kGamma) / Em1;
     T dA_deps = A * A * E / T(kBeta);
     T du_dsigma = T(kT2Scale) / (rho * rho * r13);
     T u = sigma * du_dsigma;                 // t^2
