@@ -10,16 +10,18 @@
 //        d = 0, 1, 2, whose partial sums are integer multiples of 2^-(12+7d) below 2^24
 //        units so the fp32 sums are exact, and levels 3-4 together (rounded, 2^-21 below
 //        level 0).  X = (acc0 + acc1 + acc2 + acc3) 2^(e_i + f_mu), summed in double-float.
-//   W^j = Z^jT Phi^j (Eq. vxc_batch) float split: Z and Phi (fp32) are cut into three
-//        bf16 pieces each; the 6 products with s + t <= 2 accumulate in fp32.
+//   W^j = Z^jT Phi^j (Eq. vxc_batch) the same slicing over K = grid points: each function
+//        row of Z and of Phi is scaled by the maximum over the points of its V task (at
+//        most 8 tiles = 1024 points, so levels 0-2 stay exact) and sliced the same way.
 //
 // Everything that decides E_xc to 1e-9 stays above fp32 precision: collocation in
 // float64 written as double-float pairs, rho and grad rho summed in double-float, the
 // partition weights, the functional and all E/N/V accumulation in float64.
 //
 // Kernels per chunk of tiles: pslice (P^j row slices), colloc (Phi, grad Phi, Phi slices),
-// xgemm (tcgen05), rho_z (rho, grad rho, functional, E/N partials, Z and Phi pieces),
-// vgemm (tcgen05, scatter into V_acc with float64 atomics).
+// xgemm (tcgen05), rho_z (rho, grad rho, functional, E/N partials, Z in double-float and
+// per-tile exponent maxima), slice_v (Z and Phi slices per V task), vgemm (tcgen05,
+// scatter into V_acc with float64 atomics).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -36,10 +38,9 @@ namespace gbxc {
 namespace {
 
 constexpr int NSL = 5;          // Ozaki slices (X contraction)
-constexpr int NPC = 3;          // float-split pieces (V contraction)
 constexpr int BN = 128;         // N extent of one MMA (functions)
-constexpr int XSTAGES = 2, VSTAGES = 4;
-constexpr int VKS = 16;         // tiles per V task (K split)
+constexpr int XSTAGES = 2, VSTAGES = 2;
+constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
 constexpr int SLICE_BITS = 34;  // 6 + 4 x 7
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
 // at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
@@ -50,8 +51,10 @@ struct MixedSlabs {
     float *phi;             // 8 planes [rows][128]: phi, dx, dy, dz as (hi, lo) pairs
     float *x;               // 2 planes [rows][128]: X as (hi, lo)
     __nv_bfloat16 *ax;      // 5 planes [4 rows][32]: Phi slices, K-blocked per tile
-    __nv_bfloat16 *vz;      // 3 planes [4 rows][32]: Z pieces, point-blocked per tile
-    __nv_bfloat16 *vphi;    // 3 planes [4 rows][32]: Phi pieces, point-blocked per tile
+    __nv_bfloat16 *vz;      // 5 planes [4 rows][32]: Z slices, point-blocked per tile
+    __nv_bfloat16 *vphi;    // 5 planes [4 rows][32]: Phi slices, point-blocked per tile
+    int *zexp, *fexp;       // [rows]: per tile and function, exponent of max |Z|, |Phi| over
+                            // the tile's points (group maxima on the group's first tile)
     int *pexp;              // [tiles][128] point exponents e_i
 };
 
@@ -65,9 +68,13 @@ __host__ __device__ inline MixedSlabs mixed_slabs(void *base, int64_t rows) {
     s.ax = reinterpret_cast<__nv_bfloat16 *>(p);
     p += (size_t)NSL * rows * TILE * 2;
     s.vz = reinterpret_cast<__nv_bfloat16 *>(p);
-    p += (size_t)NPC * rows * TILE * 2;
+    p += (size_t)NSL * rows * TILE * 2;
     s.vphi = reinterpret_cast<__nv_bfloat16 *>(p);
-    p += (size_t)NPC * rows * TILE * 2;
+    p += (size_t)NSL * rows * TILE * 2;
+    s.zexp = reinterpret_cast<int *>(p);
+    p += (size_t)rows * 4;
+    s.fexp = reinterpret_cast<int *>(p);
+    p += (size_t)rows * 4;
     s.pexp = reinterpret_cast<int *>(p);
     return s;
 }
@@ -102,16 +109,6 @@ __device__ __forceinline__ void slice5(long long V, float out[NSL]) {
     out[2] = ldexpf((float)q2, -20);
     out[3] = ldexpf((float)q3, -27);
     out[4] = ldexpf((float)q4, -34);
-}
-
-__device__ __forceinline__ void split3(float v, __nv_bfloat16 out[NPC]) {
-    __nv_bfloat16 a = __float2bfloat16_rn(v);
-    float r = __fsub_rn(v, __bfloat162float(a));
-    __nv_bfloat16 b = __float2bfloat16_rn(r);
-    r = __fsub_rn(r, __bfloat162float(b));
-    out[0] = a;
-    out[1] = b;
-    out[2] = __float2bfloat16_rn(r);
 }
 
 // ---------------------------------------------------------------- double-float helpers
@@ -287,7 +284,7 @@ constexpr int XACC = 4;
 __constant__ MmaOp kXOps[15] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {0, 2, 2}, {1, 1, 2},
                                 {2, 0, 2}, {0, 3, 3}, {1, 2, 3}, {2, 1, 3}, {3, 0, 3},
                                 {0, 4, 3}, {1, 3, 3}, {2, 2, 3}, {3, 1, 3}, {4, 0, 3}};
-__constant__ MmaOp kVOps[6] = {{0, 0, 0}, {0, 1, 0}, {1, 0, 0}, {0, 2, 0}, {1, 1, 0}, {2, 0, 0}};
+// W contraction: the same level scheme with K <= 1024 points per task.
 
 template <int SA, int SB, int STAGES>
 struct GemmSmem {
@@ -451,6 +448,10 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     const float *phi = m.s.phi;
+    if (np > 1184) {   // the exponent scratch below holds 1184 rows; larger batches are rejected
+        if (i == 0) atomicOr(m.err, 8);
+        return;
+    }
     df rho{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
     for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     double r = df_to_d(rho);
     double dx = 2.0 * df_to_d(gx), dy = 2.0 * df_to_d(gy), dz = 2.0 * df_to_d(gz);
     double e = 0.0, nn = 0.0;
-    float ca = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    double ca_d = 0.0, bx_d = 0.0, by_d = 0.0, bz_d = 0.0;
     if (i < cnt) {
         double w = a.plan.w[a.plan.tile_first[t] + i];
         double sigma = dx * dx + dy * dy + dz * dz;
@@ -479,27 +480,45 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
         }
         e = w * f;
         nn = w * r;
-        ca = (float)(0.5 * w * vr);
+        ca_d = 0.5 * w * vr;
         double b = 2.0 * w * vs;
-        bx = (float)(b * dx);
-        by = (float)(b * dy);
-        bz = (float)(b * dz);
+        bx_d = b * dx;
+        by_d = b * dy;
+        bz_d = b * dz;
     }
-    // Z and Phi pieces, point-blocked: row 4 r0 + pk * np + mu, column i % 32
-    int pk = i >> 5, col = i & 31;
+    // Z (Eq. z_mat) in double-float, written over X (each thread touches its own point);
+    // warp maxima of |Z| and |Phi| per function row for the V-side slicing exponents
+    __shared__ float wmax[2][4][1184];
+    df cz = d_to_df(ca_d), cbx = d_to_df(bx_d), cby = d_to_df(by_d), cbz = d_to_df(bz_d);
+    int warp = i >> 5, lane = i & 31;
     for (int mu = 0; mu < np; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        float p = phi[o];
-        float z = ca * p + bx * phi[2 * plane + o] + by * phi[4 * plane + o] + bz * phi[6 * plane + o];
-        __nv_bfloat16 zp[NPC], pp[NPC];
-        split3(z, zp);
-        split3(p, pp);
-        size_t orow = (size_t)(4 * r0 + (int64_t)pk * np + mu) * 32 + col;
+        df z = df_mul(cz, {phi[o], phi[plane + o]});
+        z = df_add(z, df_mul(cbx, {phi[2 * plane + o], phi[3 * plane + o]}));
+        z = df_add(z, df_mul(cby, {phi[4 * plane + o], phi[5 * plane + o]}));
+        z = df_add(z, df_mul(cbz, {phi[6 * plane + o], phi[7 * plane + o]}));
+        m.s.x[o] = z.h;
+        m.s.x[plane + o] = z.l;
+        float az = fabsf(z.h), ap = fabsf(phi[o]);
 #pragma unroll
-        for (int s = 0; s < NPC; ++s) {
-            m.s.vz[(size_t)s * plane + orow] = zp[s];
-            m.s.vphi[(size_t)s * plane + orow] = pp[s];
+        for (int q = 16; q > 0; q >>= 1) {
+            az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
+            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
         }
+        if (lane == 0) {
+            wmax[0][warp][mu] = az;
+            wmax[1][warp][mu] = ap;
+        }
+    }
+    __syncthreads();
+    for (int mu = i; mu < np; mu += TILE) {
+        float az = fmaxf(fmaxf(wmax[0][0][mu], wmax[0][1][mu]), fmaxf(wmax[0][2][mu], wmax[0][3][mu]));
+        float ap = fmaxf(fmaxf(wmax[1][0][mu], wmax[1][1][mu]), fmaxf(wmax[1][2][mu], wmax[1][3][mu]));
+        int ez = 0, ep = 0;
+        if (az > 0.f) frexpf(az, &ez);
+        if (ap > 0.f) frexpf(ap, &ep);
+        m.s.zexp[r0 + mu] = ez;
+        m.s.fexp[r0 + mu] = ep;
     }
     __shared__ double re[TILE], rn[TILE];
     re[i] = e;
@@ -515,6 +534,53 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     if (i == 0) {
         a.tileE[t] = re[0];
         a.tileN[t] = rn[0];
+    }
+}
+
+// ---------------------------------------------------------------- V-side slicing
+// Thread per point.  The K group of the tile (the V task it belongs to) shares one
+// exponent per function for Z and one for Phi: the maximum of the per-tile exponents.
+// The group's first tile stores those maxima for the V epilogue.
+__global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int np = pad32(n);
+    int64_t s0 = a.plan.batch_tile[j] > a.t0 ? a.plan.batch_tile[j] : a.t0;
+    int64_t s1 = a.plan.batch_tile[j + 1] < a.t1 ? a.plan.batch_tile[j + 1] : a.t1;
+    int64_t g0 = s0 + (t - s0) / VKS * VKS;
+    int64_t g1 = g0 + VKS < s1 ? g0 + VKS : s1;
+    int64_t r0 = a.plan.tile_row[t] - a.row0;
+    int64_t rg = a.plan.tile_row[g0] - a.row0;
+    const size_t plane = (size_t)m.rows * TILE;
+    int pk = i >> 5, col = i & 31;
+    for (int mu = 0; mu < np; ++mu) {
+        int ez = -1000, ep = -1000;
+        for (int64_t u = g0; u < g1; ++u) {
+            int64_t ru = a.plan.tile_row[u] - a.row0;
+            ez = max(ez, m.s.zexp[ru + mu]);
+            ep = max(ep, m.s.fexp[ru + mu]);
+        }
+        size_t o = (size_t)(r0 + mu) * TILE + i;
+        long long VZ = __float2ll_rn(ldexpf(m.s.x[o], SLICE_BITS - ez)) +
+                       __float2ll_rn(ldexpf(m.s.x[plane + o], SLICE_BITS - ez));
+        long long VP = __float2ll_rn(ldexpf(m.s.phi[o], SLICE_BITS - ep)) +
+                       __float2ll_rn(ldexpf(m.s.phi[plane + o], SLICE_BITS - ep));
+        float qz[NSL], qp[NSL];
+        slice5(VZ, qz);
+        slice5(VP, qp);
+        size_t orow = (size_t)(4 * r0 + (int64_t)pk * np + mu) * 32 + col;
+#pragma unroll
+        for (int s = 0; s < NSL; ++s) {
+            m.s.vz[(size_t)s * plane + orow] = __float2bfloat16_rn(qz[s]);
+            m.s.vphi[(size_t)s * plane + orow] = __float2bfloat16_rn(qp[s]);
+        }
+        __syncthreads();   // every thread has read the per-tile exponents of row mu ...
+        if (t == g0 && i == 0) {   // ... before the group's first tile overwrites them
+            m.s.zexp[rg + mu] = ez;
+            m.s.fexp[rg + mu] = ep;
+        }
     }
 }
 
@@ -536,7 +602,7 @@ __global__ void __launch_bounds__(128) vgemm_tc(const __grid_constant__ CUtensor
     uint32_t *tmem_slot;
     __shared__ int abort_flag;
     if (threadIdx.x == 0) abort_flag = 0;
-    gemm_setup<NPC, NPC, VSTAGES>(smem, full, empty, done, tmem_slot, &tz, &tphi, BN);
+    gemm_setup<NSL, NSL, VSTAGES>(smem, full, empty, done, tmem_slot, &tz, &tphi, XACC * BN);
     uint32_t tmem = *tmem_slot;
     auto coords = [&](int kb, int &ay, int &by) {
         int64_t t = tb + kb / 4;
@@ -545,26 +611,35 @@ __global__ void __launch_bounds__(128) vgemm_tc(const __grid_constant__ CUtensor
         ay = (int)(base + mc * BN);
         by = (int)(base + nc * BN);
     };
-    gemm_tile<NPC, NPC, VSTAGES, 6>(smem, full, empty, done, tmem, &tz, &tphi, (int)(te - tb) * 4, kVOps,
-                                    coords, m.err, &abort_flag);
+    gemm_tile<NSL, NSL, VSTAGES, 15>(smem, full, empty, done, tmem, &tz, &tphi, (int)(te - tb) * 4, kXOps,
+                                     coords, m.err, &abort_flag);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int mu = mc * BN + warp * 32 + lane;
     uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     size_t rowg = (mu < n) ? (size_t)F[mu] * a.nbf : 0;
+    int64_t rg = a.plan.tile_row[tb] - a.row0;     // group exponents live on the first tile
+    int ez = (mu < n) ? m.s.zexp[rg + mu] : 0;
     for (int c = 0; c < BN; c += 16) {
-        float v[16];
-        umma::tmem_ld16(lane_base + c, v);
+        float v0[16], v1[16], v2[16], v3[16];
+        umma::tmem_ld16(lane_base + c, v0);
+        umma::tmem_ld16(lane_base + BN + c, v1);
+        umma::tmem_ld16(lane_base + 2 * BN + c, v2);
+        umma::tmem_ld16(lane_base + 3 * BN + c, v3);
         if (mu < n) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 int nu = nc * BN + c + k;
-                if (nu < n) atomicAdd(&a.Vacc[rowg + F[nu]], (double)v[k]);
+                if (nu < n) {
+                    df w = df_add(df_add(two_sum(v0[k], v1[k]), {v2[k], 0.f}), {v3[k], 0.f});
+                    int sc = ez + m.s.fexp[rg + nu];
+                    atomicAdd(&a.Vacc[rowg + F[nu]], ldexp(df_to_d(w), sc));
+                }
             }
         }
     }
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 2) umma::tmem_dealloc(tmem, BN);
+    if (warp == 2) umma::tmem_dealloc(tmem, XACC * BN);
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -596,7 +671,7 @@ cudaError_t grow(T *&p, size_t &cap, size_t need) {
 
 }  // namespace
 
-size_t mixed_row_bytes() { return (size_t)TILE * (8 * 4 + 2 * 4 + NSL * 2 + 2 * NPC * 2) + 16; }
+size_t mixed_row_bytes() { return (size_t)TILE * (8 * 4 + 2 * 4 + 3 * NSL * 2) + 8 + 16; }
 
 void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks) {
     int nblk = (n + BN - 1) / BN;
@@ -707,11 +782,11 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &,
     cudaError_t err = cudaSuccess;
     CUtensorMap tax = make_map(c, m.s.ax, 4 * a.rows, 4 * a.rows, NSL, err);
     CUtensorMap tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, err);
-    CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NPC, err);
-    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NPC, err);
+    CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NSL, err);
+    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NSL, err);
     if (err != cudaSuccess) return err;
     using LX = GemmSmem<NSL, NSL, XSTAGES>;
-    using LV = GemmSmem<NPC, NPC, VSTAGES>;
+    using LV = GemmSmem<NSL, NSL, VSTAGES>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(xgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LX::TOTAL);
@@ -730,7 +805,8 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &,
     P.end(GBXC_K_XGEMM, st);
     P.begin(GBXC_K_RHO_Z, st);
     rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
-    P.end(GBXC_K_RHO_Z, st);
+    slice_v<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    P.end(GBXC_K_RHO_Z, st, 2);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, st);
         vgemm_tc<<<(unsigned)a.nvtasks, 128, LV::TOTAL, st>>>(tz, tph, a, m);

@@ -72,3 +72,22 @@ def test_full_trace_identity_fp64(big):
     E, N, V = big.integrate("fp64", functional="slater")
     assert abs(np.sum(big.w.P * V) - 4.0 / 3.0 * E) < 1e-10 * abs(E)
     assert np.array_equal(V, V.T)
+
+
+def test_mixed_full_size_against_fp64_and_oracle(big):
+    # the mixed form's bound on the full workload: |E_mixed - E_fp64| <= 1e-6 Eh
+    G = big.G
+    E64, N64, V64 = big.integrate("fp64")
+    Em, Nm, Vm = big.integrate("mixed")
+    assert abs(Em - E64) <= 1e-6
+    assert abs(Nm - N64) <= 1e-6
+    assert np.max(np.abs(Vm - V64)) <= 1e-5
+    assert np.array_equal(Vm, Vm.T)
+    # sampled batches against the oracle
+    g, pl = big.oracle()
+    nb = big.info["nbatch"]
+    sel = _sample(nb, seed=3)
+    ref = I.integrate_method(g, big.w.basis, big.w.P, "pbe", pl, batches=sel)
+    Eb = np.zeros(nb)
+    G.gbxc_integrate_batches(big.ctx.h, big.mid, big.w.P, "pbe", "mixed", 0, nb, None, Eb)
+    assert np.max(np.abs(Eb[sel] - ref.E_batch[sel])) <= 1e-8
