@@ -149,7 +149,6 @@ void free_grid(Molecule &m) {
     for (void *p : m.dev_allocs) cudaFree(p);
     m.dev_allocs.clear();
     free_schedule(m.sched);
-    free_mixed_resident(m.mixed_res);
     m.dev = DevPlan{};
     m.has_grid = false;
 }
@@ -427,6 +426,7 @@ void gbxc_destroy(gbxc_ctx *ctx) {
     for (auto &kv : ctx->mols) {
         free_grid(*kv.second);
         cudaFree(kv.second->d_shells);
+        free_mixed_resident(kv.second->mixed_res);
         cudaFree(kv.second->d_atoms);
         cudaFree(kv.second->d_rnn);
     }
@@ -487,6 +487,7 @@ int gbxc_load_basis(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, 
             ctx->mols[id] = std::move(m);
             return GBXC_OK;
         }
+        check(build_mixed_resident(m->shells, m->mixed_res), "double-float shells");
         check(cudaMalloc(&m->d_shells, sizeof(DevShell) * nshell), "cudaMalloc shells");
         check(cudaMemcpy(m->d_shells, m->shells.data(), sizeof(DevShell) * nshell,
                          cudaMemcpyHostToDevice), "upload shells");

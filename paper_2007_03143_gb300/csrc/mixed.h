@@ -23,10 +23,19 @@ struct MixedCtx {
     size_t pexp_cap = 0;
     int *d_err = nullptr;
 };
+// A shell with every constant split into a double-float pair (hi + lo).
+struct DfShell {
+    float ch[3], cl[3];                               // centre
+    float ah[GBXC_MAX_PRIM], al[GBXC_MAX_PRIM];       // exponents alpha
+    float dh[GBXC_MAX_PRIM], dl[GBXC_MAX_PRIM];       // coefficients d
+    float gh[GBXC_MAX_PRIM], gl[GBXC_MAX_PRIM];       // -2 alpha d (gradient coefficients)
+    int L, nprim, fofs, pad;
+};
 // Per-molecule resident state of the mixed form.
 struct MixedResident {
-    int dummy = 0;
+    DfShell *d_shells = nullptr;
 };
+cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResident &r);
 // Per-schedule state of the mixed form: for every chunk the batch range and the row
 // offsets of each batch's sliced P^j block.
 struct MixedSchedule {

@@ -31,6 +31,7 @@
 #include <cstring>
 
 #include "mixed.h"
+#include "dfloat.cuh"
 #include "umma.cuh"
 #include "xc_functional.cuh"
 
@@ -112,42 +113,12 @@ __device__ __forceinline__ void slice5(long long V, float out[NSL]) {
 }
 
 // ---------------------------------------------------------------- double-float helpers
-struct df {
-    float h, l;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-
-__device__ __forceinline__ df quick_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-    float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    return quick_two_sum(p, e);
-}
-
-__device__ __forceinline__ df df_add(df a, df b) {
-    df s = two_sum(a.h, b.h);
-    float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
-    return quick_two_sum(s.h, e);
-}
-
-__device__ __forceinline__ double df_to_d(df a) { return (double)a.h + (double)a.l; }
-
-__device__ __forceinline__ df d_to_df(double d) {
-    float h = (float)d;
-    return {h, (float)(d - (double)h)};
-}
+using dfl::df;
+using dfl::two_sum;
+__device__ __forceinline__ df df_mul(df a, df b) { return dfl::mul(a, b); }
+__device__ __forceinline__ df df_add(df a, df b) { return dfl::add(a, b); }
+__device__ __forceinline__ double df_to_d(df a) { return dfl::to_double(a); }
+__device__ __forceinline__ df d_to_df(double d) { return dfl::from_double(d); }
 
 // ---------------------------------------------------------------- pslice
 // One warp per row mu of P^j: row exponent, then the 5 slices of P^j[mu][nu] for every
@@ -185,9 +156,10 @@ __global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
 }
 
 // ---------------------------------------------------------------- collocation
-// Thread per point; float64 evaluation of Eq. gau_cart and its gradient, stored as
-// double-float planes; then the point's Ozaki slices of Phi, K-blocked by 32 functions.
-__global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m) {
+// Thread per point; Eq. gau_cart and its gradient in double-float arithmetic on the
+// float32 pipe (exp(-alpha r^2) by dfl::exp_neg), stored as (hi, lo) planes; then the
+// point's Ozaki slices of Phi, K-blocked by 32 functions.
+__global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells) {
     int64_t t = a.t0 + blockIdx.x;
     int i = threadIdx.x;
     int j = a.plan.tile_batch[t];
@@ -197,47 +169,53 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m) {
     int np = pad32(n);
     bool live = i < cnt;
     int64_t p = a.plan.tile_first[t] + i;
-    double px = live ? a.plan.x[p] : 0.0, py = live ? a.plan.y[p] : 0.0, pz = live ? a.plan.z[p] : 0.0;
+    df px = d_to_df(live ? a.plan.x[p] : 0.0), py = d_to_df(live ? a.plan.y[p] : 0.0),
+       pz = d_to_df(live ? a.plan.z[p] : 0.0);
     const size_t plane = (size_t)m.rows * TILE;
     float *phi = m.s.phi;
     int64_t s0 = a.plan.shell_ptr[j], s1 = a.plan.shell_ptr[j + 1];
     int row = 0;
-    double mx = 0.0;
+    float mx = 0.f;
     for (int64_t si = s0; si < s1; ++si) {
-        const DevShell &sh = a.shells[a.plan.shell_idx[si]];
-        double X = px - sh.c[0], Y = py - sh.c[1], Z = pz - sh.c[2];
-        double r2 = X * X + Y * Y + Z * Z;
-        double g = 0.0, h = 0.0;
+        const DfShell &sh = shells[a.plan.shell_idx[si]];
+        df X = dfl::sub(px, {sh.ch[0], sh.cl[0]});
+        df Y = dfl::sub(py, {sh.ch[1], sh.cl[1]});
+        df Z = dfl::sub(pz, {sh.ch[2], sh.cl[2]});
+        df r2 = df_add(df_add(df_mul(X, X), df_mul(Y, Y)), df_mul(Z, Z));
+        df g = {0.f, 0.f}, h = {0.f, 0.f};
         for (int k = 0; k < sh.nprim; ++k) {
-            double ex = exp(-sh.alpha[k] * r2);
-            g += sh.coeff[k] * ex;
-            h += (-2.0 * sh.alpha[k] * sh.coeff[k]) * ex;
+            df ex = dfl::exp_neg(df_mul({sh.ah[k], sh.al[k]}, r2));
+            g = df_add(g, df_mul({sh.dh[k], sh.dl[k]}, ex));
+            h = df_add(h, df_mul({sh.gh[k], sh.gl[k]}, ex));
         }
-        double xp[GBXC_MAX_L + 2], yp[GBXC_MAX_L + 2], zp[GBXC_MAX_L + 2];
-        xp[0] = yp[0] = zp[0] = 1.0;
+        df xp[GBXC_MAX_L + 1], yp[GBXC_MAX_L + 1], zp[GBXC_MAX_L + 1];
+        xp[0] = yp[0] = zp[0] = {1.f, 0.f};
         for (int k = 1; k <= sh.L; ++k) {
-            xp[k] = xp[k - 1] * X;
-            yp[k] = yp[k - 1] * Y;
-            zp[k] = zp[k - 1] * Z;
+            xp[k] = df_mul(xp[k - 1], X);
+            yp[k] = df_mul(yp[k - 1], Y);
+            zp[k] = df_mul(zp[k - 1], Z);
         }
+        df Xh = df_mul(X, h), Yh = df_mul(Y, h), Zh = df_mul(Z, h);
         for (int l = sh.L; l >= 0; --l)
             for (int mm = sh.L - l; mm >= 0; --mm) {
                 int nn = sh.L - l - mm;
-                double mono = xp[l] * yp[mm] * zp[nn];
-                double v[4];
-                v[0] = mono * g;
-                v[1] = (l > 0 ? l * xp[l - 1] * yp[mm] * zp[nn] : 0.0) * g + mono * X * h;
-                v[2] = (mm > 0 ? mm * xp[l] * yp[mm - 1] * zp[nn] : 0.0) * g + mono * Y * h;
-                v[3] = (nn > 0 ? nn * xp[l] * yp[mm] * zp[nn - 1] : 0.0) * g + mono * Z * h;
+                df ym_zn = df_mul(yp[mm], zp[nn]);
+                df mono = df_mul(xp[l], ym_zn);
+                df v[4];
+                v[0] = df_mul(mono, g);
+                v[1] = df_mul(mono, Xh);
+                v[2] = df_mul(mono, Yh);
+                v[3] = df_mul(mono, Zh);
+                if (l > 0) v[1] = df_add(v[1], df_mul(dfl::mul_f(df_mul(xp[l - 1], ym_zn), (float)l), g));
+                if (mm > 0) v[2] = df_add(v[2], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm - 1]), zp[nn]), (float)mm), g));
+                if (nn > 0) v[3] = df_add(v[3], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm]), zp[nn - 1]), (float)nn), g));
                 size_t o = (size_t)(r0 + row) * TILE + i;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    double vv = live ? v[c] : 0.0;
-                    df d = d_to_df(vv);
-                    phi[(2 * c) * plane + o] = d.h;
-                    phi[(2 * c + 1) * plane + o] = d.l;
+                    phi[(2 * c) * plane + o] = live ? v[c].h : 0.f;
+                    phi[(2 * c + 1) * plane + o] = live ? v[c].l : 0.f;
                 }
-                if (live) mx = fmax(mx, fabs(v[0]));
+                if (live) mx = fmaxf(mx, fabsf(v[0].h));
                 ++row;
             }
     }
@@ -246,8 +224,9 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) phi[c * plane + o] = 0.0f;
     }
+    // exponent of the row maximum, with headroom for the lo part (|hi + lo| <= 2^e)
     int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
+    if (mx > 0.f) frexpf(mx * 1.0000002f, &e);
     m.s.pexp[(t - a.t0) * TILE + i] = e;
     // Ozaki slices of this point's row of Phi: K block kb -> row 4 r0 + 128 kb + i, 32 values
     for (int kb = 0; kb < np / 32; ++kb) {
@@ -728,7 +707,37 @@ void free_mixed_schedule(MixedSchedule &s) {
     s = MixedSchedule{};
 }
 
-void free_mixed_resident(MixedResident &r) { r = MixedResident{}; }
+void free_mixed_resident(MixedResident &r) {
+    cudaFree(r.d_shells);
+    r = MixedResident{};
+}
+
+cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResident &r) {
+    std::vector<DfShell> h(shells.size());
+    auto split = [](double v, float &hi, float &lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    for (size_t s = 0; s < shells.size(); ++s) {
+        const DevShell &d = shells[s];
+        DfShell &o = h[s];
+        std::memset(&o, 0, sizeof(o));
+        for (int c = 0; c < 3; ++c) split(d.c[c], o.ch[c], o.cl[c]);
+        for (int k = 0; k < d.nprim; ++k) {
+            split(d.alpha[k], o.ah[k], o.al[k]);
+            split(d.coeff[k], o.dh[k], o.dl[k]);
+            split(-2.0 * d.alpha[k] * d.coeff[k], o.gh[k], o.gl[k]);
+        }
+        o.L = d.L;
+        o.nprim = d.nprim;
+        o.fofs = d.fofs;
+    }
+    cudaFree(r.d_shells);
+    r.d_shells = nullptr;
+    cudaError_t e = cudaMalloc(&r.d_shells, std::max<size_t>(h.size(), 1) * sizeof(DfShell));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(r.d_shells, h.data(), h.size() * sizeof(DfShell), cudaMemcpyHostToDevice);
+}
 
 void free_mixed_ctx(MixedCtx &c) {
     cudaFree(c.pslices);
@@ -764,8 +773,9 @@ cudaError_t mixed_read_error(MixedCtx &c, int *err, cudaStream_t st) {
     return cudaStreamSynchronize(st);
 }
 
-cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &, const MixedSchedule &s,
+cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r, const MixedSchedule &s,
                                int chunk_index, cudaStream_t st) {
+    if (!r.d_shells) return cudaErrorInvalidValue;
     int64_t nt = a.t1 - a.t0;
     if (nt <= 0) return cudaSuccess;
     const MixedSchedule::Chunk &ch = s.chunks[chunk_index];
@@ -798,7 +808,7 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &,
     pslice_kernel<<<dim3(ch.j1 - ch.j0 + 1, (ch.max_np + 3) / 4), 128, 0, st>>>(a, m);
     P.end(GBXC_K_PGATHER, st);
     P.begin(GBXC_K_COLLOC, st);
-    colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells);
     P.end(GBXC_K_COLLOC, st);
     P.begin(GBXC_K_XGEMM, st);
     xgemm_tc<<<dim3((unsigned)nt, (unsigned)((a.max_nfunc + BN - 1) / BN)), 128, LX::TOTAL, st>>>(tax, tp, a, m);
