@@ -21,6 +21,8 @@ struct MixedCtx {
     int *pexp = nullptr;               // row exponents of the sliced P^j
     size_t pslice_rows = 0;            // capacity of pslices in elements
     size_t pexp_cap = 0;
+    float *pdf = nullptr;              // P as double-float planes (hi, lo)
+    size_t pdf_cap = 0;
     int *d_err = nullptr;
 };
 // A shell with every constant split into a double-float pair (hi + lo).

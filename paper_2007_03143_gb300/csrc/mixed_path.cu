@@ -42,7 +42,6 @@ constexpr int NSL = 5;          // Ozaki slices (X contraction)
 constexpr int BN = 128;         // N extent of one MMA (functions)
 constexpr int XSTAGES = 2, VSTAGES = 2;
 constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
-constexpr int SLICE_BITS = 34;  // 6 + 4 x 7
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
 // at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
 constexpr double kFp32RhoMin = 1e300;
@@ -89,27 +88,37 @@ struct MixedArgs {
     __nv_bfloat16 *pslices;      // 5 planes, plane pitch pplane rows of 32
     int64_t pplane;
     int *pexp;                   // row exponents of P^j
+    const float *ph, *pl;        // P as double-float planes (nbf x nbf each)
     int *err;
 };
 
 __device__ __forceinline__ int pad32(int n) { return (n + 31) & ~31; }
 
 // ---------------------------------------------------------------- slicing
-// v = V 2^-34 with |V| <= 2^34 -> five slices q_s in [-64, 64], v = sum q_s 2^-(6+7s).
-__device__ __forceinline__ void slice5(long long V, float out[NSL]) {
-    long long q0 = (V + (1LL << 27)) >> 28;
-    long long r = V - (q0 << 28);
-    long long q1 = (r + (1LL << 20)) >> 21;
-    r -= q1 << 21;
-    long long q2 = (r + (1LL << 13)) >> 14;
-    r -= q2 << 14;
-    long long q3 = (r + (1LL << 6)) >> 7;
-    long long q4 = r - (q3 << 7);
-    out[0] = ldexpf((float)q0, -6);
-    out[1] = ldexpf((float)q1, -13);
-    out[2] = ldexpf((float)q2, -20);
-    out[3] = ldexpf((float)q3, -27);
-    out[4] = ldexpf((float)q4, -34);
+// v = (h + l) 2^-e with |v| <= 1 -> five slices q_s 2^-(6+7s), q_s integers in [-64, 64],
+// float32 only: each q_s is the rounding of the running remainder to the slice grid; the
+// subtraction is exact (Sterbenz) and two-sum folds the low word back in.
+__device__ __forceinline__ void slice5(float h, float l, int e, float out[NSL]) {
+    float rh = ldexpf(h, -e), rl = ldexpf(l, -e);
+#pragma unroll
+    for (int s = 0; s < NSL; ++s) {
+        const int sh = 6 + 7 * s;
+        float qs = ldexpf(rintf(ldexpf(rh, sh)), -sh);
+        out[s] = qs;
+        rh = __fsub_rn(rh, qs);
+        float ss = __fadd_rn(rh, rl);
+        float bb = __fsub_rn(ss, rh);
+        rl = __fadd_rn(__fsub_rn(rh, __fsub_rn(ss, bb)), __fsub_rn(rl, bb));
+        rh = ss;
+    }
+}
+
+// exponent e with |x| < 2^e for x > 0 (0 for x == 0), from the float's exponent bits
+__device__ __forceinline__ int exp_of(float x) {
+    if (!(x > 0.f)) return 0;
+    int e;
+    frexpf(x * 1.0000002f, &e);
+    return e;
 }
 
 // ---------------------------------------------------------------- double-float helpers
@@ -121,6 +130,16 @@ __device__ __forceinline__ double df_to_d(df a) { return dfl::to_double(a); }
 __device__ __forceinline__ df d_to_df(double d) { return dfl::from_double(d); }
 
 // ---------------------------------------------------------------- pslice
+// P as double-float planes, once per integration (the only float64 pass over P).
+__global__ void p_to_df(const double *__restrict__ P, float *__restrict__ ph, float *__restrict__ pl,
+                        int64_t nn) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nn) return;
+    df d = d_to_df(P[k]);
+    ph[k] = d.h;
+    pl[k] = d.l;
+}
+
 // One warp per row mu of P^j: row exponent, then the 5 slices of P^j[mu][nu] for every
 // K block of 32 nu's.  Rows and columns past N_b^j are written as zeros.
 __global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
@@ -133,22 +152,21 @@ __global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
     int mu = blockIdx.y * 4 + warp;
     if (mu >= np) return;
     const int *F = a.plan.func_idx + f0;
-    const double *Prow = (mu < n) ? a.P + (size_t)F[mu] * a.nbf : nullptr;
-    double mx = 0.0;
-    if (Prow)
-        for (int nu = lane; nu < n; nu += 32) mx = fmax(mx, fabs(Prow[F[nu]]));
+    const size_t rowoff = (mu < n) ? (size_t)F[mu] * a.nbf : 0;
+    float mx = 0.f;
+    if (mu < n)
+        for (int nu = lane; nu < n; nu += 32) mx = fmaxf(mx, fabsf(m.ph[rowoff + F[nu]]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = exp_of(mx);
     if (lane == 0) m.pexp[m.pexp_ofs[jl] + mu] = e;
     int64_t pofs = m.pofs[jl];
     for (int kb = 0; kb < np / 32; ++kb) {
         int nu = kb * 32 + lane;
-        double v = (Prow && nu < n) ? Prow[F[nu]] : 0.0;
-        long long V = llrint(ldexp(v, SLICE_BITS - e));
+        bool in = mu < n && nu < n;
+        float h = in ? m.ph[rowoff + F[nu]] : 0.f, l = in ? m.pl[rowoff + F[nu]] : 0.f;
         float q[NSL];
-        slice5(V, q);
+        slice5(h, l, e, q);
         size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + lane;
 #pragma unroll
         for (int s = 0; s < NSL; ++s) m.pslices[(size_t)s * m.pplane * 32 + o] = __float2bfloat16_rn(q[s]);
@@ -224,19 +242,15 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
 #pragma unroll
         for (int c = 0; c < 8; ++c) phi[c * plane + o] = 0.0f;
     }
-    // exponent of the row maximum, with headroom for the lo part (|hi + lo| <= 2^e)
-    int e = 0;
-    if (mx > 0.f) frexpf(mx * 1.0000002f, &e);
+    int e = exp_of(mx);
     m.s.pexp[(t - a.t0) * TILE + i] = e;
     // Ozaki slices of this point's row of Phi: K block kb -> row 4 r0 + 128 kb + i, 32 values
     for (int kb = 0; kb < np / 32; ++kb) {
         __align__(16) __nv_bfloat16 buf[NSL][32];
         for (int c = 0; c < 32; ++c) {
             size_t o = (size_t)(r0 + kb * 32 + c) * TILE + i;
-            float hi = phi[o], lo = phi[plane + o];
-            long long V = __float2ll_rn(ldexpf(hi, SLICE_BITS - e)) + __float2ll_rn(ldexpf(lo, SLICE_BITS - e));
             float q[NSL];
-            slice5(V, q);
+            slice5(phi[o], phi[plane + o], e, q);
 #pragma unroll
             for (int s = 0; s < NSL; ++s) buf[s][c] = __float2bfloat16_rn(q[s]);
         }
@@ -360,7 +374,9 @@ __device__ __forceinline__ void gemm_setup(uint8_t *&smem, uint64_t *&full, uint
 
 // ---------------------------------------------------------------- X contraction
 // CTA (tile t, N chunk nc): X[points 128][functions nc*128 .. +128] over K = N_b^j.
-__global__ void __launch_bounds__(128) xgemm_tc(const __grid_constant__ CUtensorMap tax,
+constexpr int GEMM_THREADS = 256;   // warps 0-3 and 4-7 split the epilogue columns
+
+__global__ void __launch_bounds__(GEMM_THREADS) xgemm_tc(const __grid_constant__ CUtensorMap tax,
                                                 const __grid_constant__ CUtensorMap tp, ChunkArgs a,
                                                 MixedArgs m) {
     int64_t t = a.t0 + blockIdx.x;
@@ -385,14 +401,15 @@ __global__ void __launch_bounds__(128) xgemm_tc(const __grid_constant__ CUtensor
     };
     gemm_tile<NSL, NSL, XSTAGES, 15>(smem, full, empty, done, tmem, &tax, &tp, np / 32, kXOps, coords, m.err,
                                      &abort_flag);
-    // epilogue: thread = point (TMEM lane), 128 function columns
+    // epilogue: thread = point (TMEM lane of its warp's quarter), half of the 128 columns
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int i = warp * 32 + lane;
+    int quarter = warp & 3, half = warp >> 2;
+    int i = quarter * 32 + lane;
     int ei = m.s.pexp[(t - a.t0) * TILE + i];
     const int *fexp = m.pexp + m.pexp_ofs[jl];
     const size_t plane = (size_t)m.rows * TILE;
-    uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c = 0; c < BN; c += 16) {
+    uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
         float v0[16], v1[16], v2[16], v3[16];
         umma::tmem_ld16(lane_base + c, v0);
         umma::tmem_ld16(lane_base + BN + c, v1);
@@ -432,13 +449,17 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
         return;
     }
     df rho{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
+#pragma unroll 2
     for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        df x{m.s.x[o], m.s.x[plane + o]};
-        rho = df_add(rho, df_mul({phi[o], phi[plane + o]}, x));
-        gx = df_add(gx, df_mul({phi[2 * plane + o], phi[3 * plane + o]}, x));
-        gy = df_add(gy, df_mul({phi[4 * plane + o], phi[5 * plane + o]}, x));
-        gz = df_add(gz, df_mul({phi[6 * plane + o], phi[7 * plane + o]}, x));
+        float x0 = m.s.x[o], x1 = m.s.x[plane + o];
+        float p0 = phi[o], p1 = phi[plane + o], p2 = phi[2 * plane + o], p3 = phi[3 * plane + o];
+        float p4 = phi[4 * plane + o], p5 = phi[5 * plane + o], p6 = phi[6 * plane + o], p7 = phi[7 * plane + o];
+        df x{x0, x1};
+        rho = df_add(rho, df_mul({p0, p1}, x));
+        gx = df_add(gx, df_mul({p2, p3}, x));
+        gy = df_add(gy, df_mul({p4, p5}, x));
+        gz = df_add(gz, df_mul({p6, p7}, x));
     }
     double r = df_to_d(rho);
     double dx = 2.0 * df_to_d(gx), dy = 2.0 * df_to_d(gy), dz = 2.0 * df_to_d(gz);
@@ -466,38 +487,42 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
         bz_d = b * dz;
     }
     // Z (Eq. z_mat) in double-float, written over X (each thread touches its own point);
-    // warp maxima of |Z| and |Phi| per function row for the V-side slicing exponents
-    __shared__ float wmax[2][4][1184];
+    // maxima of |Z| and |Phi| per function row over the tile's points, kept as float bits
+    // (non-negative floats order like their bit patterns) for the V-side slicing exponents
+    __shared__ int zmax[1184], fmx[1184];
+    for (int mu = i; mu < np; mu += TILE) {
+        zmax[mu] = 0;
+        fmx[mu] = 0;
+    }
+    __syncthreads();
     df cz = d_to_df(ca_d), cbx = d_to_df(bx_d), cby = d_to_df(by_d), cbz = d_to_df(bz_d);
-    int warp = i >> 5, lane = i & 31;
+    int lane = i & 31;
+#pragma unroll 2
     for (int mu = 0; mu < np; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        df z = df_mul(cz, {phi[o], phi[plane + o]});
-        z = df_add(z, df_mul(cbx, {phi[2 * plane + o], phi[3 * plane + o]}));
-        z = df_add(z, df_mul(cby, {phi[4 * plane + o], phi[5 * plane + o]}));
-        z = df_add(z, df_mul(cbz, {phi[6 * plane + o], phi[7 * plane + o]}));
+        float p0 = phi[o], p1 = phi[plane + o], p2 = phi[2 * plane + o], p3 = phi[3 * plane + o];
+        float p4 = phi[4 * plane + o], p5 = phi[5 * plane + o], p6 = phi[6 * plane + o], p7 = phi[7 * plane + o];
+        df z = df_mul(cz, {p0, p1});
+        z = df_add(z, df_mul(cbx, {p2, p3}));
+        z = df_add(z, df_mul(cby, {p4, p5}));
+        z = df_add(z, df_mul(cbz, {p6, p7}));
         m.s.x[o] = z.h;
         m.s.x[plane + o] = z.l;
-        float az = fabsf(z.h), ap = fabsf(phi[o]);
+        float az = fabsf(z.h), ap = fabsf(p0);
 #pragma unroll
         for (int q = 16; q > 0; q >>= 1) {
             az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
             ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
         }
         if (lane == 0) {
-            wmax[0][warp][mu] = az;
-            wmax[1][warp][mu] = ap;
+            atomicMax(&zmax[mu], __float_as_int(az));
+            atomicMax(&fmx[mu], __float_as_int(ap));
         }
     }
     __syncthreads();
     for (int mu = i; mu < np; mu += TILE) {
-        float az = fmaxf(fmaxf(wmax[0][0][mu], wmax[0][1][mu]), fmaxf(wmax[0][2][mu], wmax[0][3][mu]));
-        float ap = fmaxf(fmaxf(wmax[1][0][mu], wmax[1][1][mu]), fmaxf(wmax[1][2][mu], wmax[1][3][mu]));
-        int ez = 0, ep = 0;
-        if (az > 0.f) frexpf(az, &ez);
-        if (ap > 0.f) frexpf(ap, &ep);
-        m.s.zexp[r0 + mu] = ez;
-        m.s.fexp[r0 + mu] = ep;
+        m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[mu]));
+        m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu]));
     }
     __shared__ double re[TILE], rn[TILE];
     re[i] = e;
@@ -542,13 +567,9 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
             ep = max(ep, m.s.fexp[ru + mu]);
         }
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        long long VZ = __float2ll_rn(ldexpf(m.s.x[o], SLICE_BITS - ez)) +
-                       __float2ll_rn(ldexpf(m.s.x[plane + o], SLICE_BITS - ez));
-        long long VP = __float2ll_rn(ldexpf(m.s.phi[o], SLICE_BITS - ep)) +
-                       __float2ll_rn(ldexpf(m.s.phi[plane + o], SLICE_BITS - ep));
         float qz[NSL], qp[NSL];
-        slice5(VZ, qz);
-        slice5(VP, qp);
+        slice5(m.s.x[o], m.s.x[plane + o], ez, qz);
+        slice5(m.s.phi[o], m.s.phi[plane + o], ep, qp);
         size_t orow = (size_t)(4 * r0 + (int64_t)pk * np + mu) * 32 + col;
 #pragma unroll
         for (int s = 0; s < NSL; ++s) {
@@ -566,7 +587,7 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
 // ---------------------------------------------------------------- V contraction
 // Task (batch j, row block mc, column block nc, tiles [tb, te)): W[mu][nu] =
 // sum over the tiles' points of Z[i][mu] Phi[i][nu], then V_acc[F_mu][F_nu] += W.
-__global__ void __launch_bounds__(128) vgemm_tc(const __grid_constant__ CUtensorMap tz,
+__global__ void __launch_bounds__(GEMM_THREADS) vgemm_tc(const __grid_constant__ CUtensorMap tz,
                                                 const __grid_constant__ CUtensorMap tphi, ChunkArgs a,
                                                 MixedArgs m) {
     const int *task = a.vtasks + 5 * blockIdx.x;
@@ -593,12 +614,13 @@ __global__ void __launch_bounds__(128) vgemm_tc(const __grid_constant__ CUtensor
     gemm_tile<NSL, NSL, VSTAGES, 15>(smem, full, empty, done, tmem, &tz, &tphi, (int)(te - tb) * 4, kXOps,
                                      coords, m.err, &abort_flag);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int mu = mc * BN + warp * 32 + lane;
-    uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    int quarter = warp & 3, half = warp >> 2;
+    int mu = mc * BN + quarter * 32 + lane;
+    uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     size_t rowg = (mu < n) ? (size_t)F[mu] * a.nbf : 0;
     int64_t rg = a.plan.tile_row[tb] - a.row0;     // group exponents live on the first tile
     int ez = (mu < n) ? m.s.zexp[rg + mu] : 0;
-    for (int c = 0; c < BN; c += 16) {
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
         float v0[16], v1[16], v2[16], v3[16];
         umma::tmem_ld16(lane_base + c, v0);
         umma::tmem_ld16(lane_base + BN + c, v1);
@@ -611,7 +633,7 @@ __global__ void __launch_bounds__(128) vgemm_tc(const __grid_constant__ CUtensor
                 if (nu < n) {
                     df w = df_add(df_add(two_sum(v0[k], v1[k]), {v2[k], 0.f}), {v3[k], 0.f});
                     int sc = ez + m.s.fexp[rg + nu];
-                    atomicAdd(&a.Vacc[rowg + F[nu]], ldexp(df_to_d(w), sc));
+                    atomicAdd(&a.Vacc[rowg + F[nu]], (double)ldexpf(w.h, sc) + (double)ldexpf(w.l, sc));
                 }
             }
         }
@@ -740,13 +762,14 @@ cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResid
 }
 
 void free_mixed_ctx(MixedCtx &c) {
+    cudaFree(c.pdf);
     cudaFree(c.pslices);
     cudaFree(c.pexp);
     cudaFree(c.d_err);
     c = MixedCtx{};
 }
 
-cudaError_t mixed_prepare(MixedCtx &c, MixedResident &, const MixedSchedule &s, const double *, int,
+cudaError_t mixed_prepare(MixedCtx &c, MixedResident &, const MixedSchedule &s, const double *P, int nbf,
                           cudaStream_t st) {
     if (!c.encode_fn) {
         cudaDriverEntryPointQueryResult q;
@@ -761,6 +784,12 @@ cudaError_t mixed_prepare(MixedCtx &c, MixedResident &, const MixedSchedule &s, 
     cudaError_t e = grow(c.pslices, c.pslice_rows, (size_t)std::max<int64_t>(s.max_prows, 1) * 32 * NSL);
     if (e != cudaSuccess) return e;
     e = grow(c.pexp, c.pexp_cap, (size_t)std::max<int64_t>(s.max_pexp, 1));
+    if (e != cudaSuccess) return e;
+    int64_t nn = (int64_t)nbf * nbf;
+    e = grow(c.pdf, c.pdf_cap, (size_t)std::max<int64_t>(2 * nn, 1));
+    if (e != cudaSuccess) return e;
+    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, c.pdf, c.pdf + nn, nn);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
 }
@@ -788,6 +817,8 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     m.pslices = reinterpret_cast<__nv_bfloat16 *>(c.pslices);
     m.pplane = std::max<int64_t>(s.max_prows, 1);
     m.pexp = c.pexp;
+    m.ph = c.pdf;
+    m.pl = c.pdf + (size_t)a.nbf * a.nbf;
     m.err = c.d_err;
     cudaError_t err = cudaSuccess;
     CUtensorMap tax = make_map(c, m.s.ax, 4 * a.rows, 4 * a.rows, NSL, err);
@@ -811,7 +842,7 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells);
     P.end(GBXC_K_COLLOC, st);
     P.begin(GBXC_K_XGEMM, st);
-    xgemm_tc<<<dim3((unsigned)nt, (unsigned)((a.max_nfunc + BN - 1) / BN)), 128, LX::TOTAL, st>>>(tax, tp, a, m);
+    xgemm_tc<<<dim3((unsigned)nt, (unsigned)((a.max_nfunc + BN - 1) / BN)), GEMM_THREADS, LX::TOTAL, st>>>(tax, tp, a, m);
     P.end(GBXC_K_XGEMM, st);
     P.begin(GBXC_K_RHO_Z, st);
     rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
@@ -819,7 +850,7 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     P.end(GBXC_K_RHO_Z, st, 2);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, st);
-        vgemm_tc<<<(unsigned)a.nvtasks, 128, LV::TOTAL, st>>>(tz, tph, a, m);
+        vgemm_tc<<<(unsigned)a.nvtasks, GEMM_THREADS, LV::TOTAL, st>>>(tz, tph, a, m);
         P.end(GBXC_K_VGEMM, st);
     }
     return cudaGetLastError();
