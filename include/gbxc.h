@@ -177,6 +177,28 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
                            double *Vxc, double *Nel, double *E_batch, double *N_batch,
                            void *stream);
 
+/* Float64 integration over every batch of `mol` for callers that cannot allocate
+ * device memory (for example code running where cudaMalloc is unavailable or forbidden,
+ * such as inside another library's memory pool or a pre-allocated real-time region).
+ * This call itself allocates no device memory: its slab scratch is a static 64 MiB
+ * device array inside the library (held by every GPU that loads the library until the
+ * process exits), and everything else is caller-owned or was allocated when the
+ * molecule was loaded.  The paper has no counterpart; it is a deployment variant of
+ * gbxc_integrate with precision GBXC_FP64.
+ *   P    nbf x nbf density matrix, DEVICE memory, read only
+ *   Vxc  nbf x nbf DEVICE output; used as the accumulator, then symmetrised in place
+ *   EN   2 doubles of DEVICE memory: {E_xc, N_el}
+ *   stream  cudaStream_t (NULL = the context's stream)
+ * The work is queued on `stream` and the call returns without waiting: results are
+ * ready when the stream reaches this point.  The first call on a device resolves the
+ * static array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Calls share the one static array, so calls whose work overlaps
+ * on the GPU (different streams, or different contexts on one device) race and must
+ * not be issued concurrently.  A batch whose tile needs more than 64 MiB of float64
+ * slabs (more than about 10,900 padded functions) is rejected with GBXC_ENOMEM. */
+int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int functional, double *Vxc,
+                                double *EN, void *stream);
+
 /* Per-kernel-class accounting.  Launch counts are always kept; with
  * gbxc_profile_enable(ctx, 1) every kernel-class span is also bracketed by CUDA
  * events on the stream it runs on.  Enabling or disabling resets both.

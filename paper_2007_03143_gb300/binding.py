@@ -32,7 +32,7 @@ PRECISIONS = {"fp64": GBXC_FP64, "mixed": GBXC_MIXED}
 
 EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis", "gbxc_load_grid",
             "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
-            "gbxc_profile_enable", "gbxc_profile_read"]
+            "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "other"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -84,6 +84,9 @@ def lib():
     L.gbxc_integrate.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, pd, c_void_p, pd, c_void_p]
     L.gbxc_integrate_batches.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_int, pd,
                                          c_void_p, pd, c_void_p, c_void_p, c_void_p]
+    L.gbxc_integrate_fp64_noalloc.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
+                                               c_void_p]
+    L.gbxc_integrate_fp64_noalloc.restype = c_int
     L.gbxc_profile_enable.argtypes = [c_void_p, c_int]
     L.gbxc_profile_read.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("gbxc_create", "gbxc_load_basis", "gbxc_load_grid", "gbxc_plan_info_get",
@@ -212,6 +215,19 @@ def gbxc_integrate_batches(ctx, mol, P, functional, precision, batch_begin, batc
                                              PRECISIONS.get(precision, precision), batch_begin,
                                              batch_end, ctypes.byref(E), pV, ctypes.byref(N), pE, pN, st))
     return E.value, N.value
+
+
+def gbxc_integrate_fp64_noalloc(ctx, mol, P, V, EN, functional="pbe", stream=None):
+    """Float64 integration without device allocation; P, V (nbf x nbf) and EN (2) are CUDA
+    tensors.  Queued on the stream (torch's current stream by default); does not wait."""
+    pP, kP, cP = _ptr(P)
+    pV, kV, cV = _ptr(V)
+    pE, kE, cE = _ptr(EN)
+    if not (cP and cV and cE):
+        raise ValueError("P, V and EN must be CUDA tensors")
+    st = _stream_for(stream, P)
+    _check(ctx, lib().gbxc_integrate_fp64_noalloc(ctx, mol, pP, FUNCTIONALS.get(functional, functional),
+                                                  pV, pE, st))
 
 
 def gbxc_profile_enable(ctx, on=True):

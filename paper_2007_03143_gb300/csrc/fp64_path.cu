@@ -329,6 +329,71 @@ __global__ void total_sums(FinishArgs a) {
     }
 }
 
+// --------------------------------------------------------------------------
+// Allocation-free variant (gbxc_integrate_fp64_noalloc).  Its slab scratch is this
+// file-scope device array, which every GPU that loads the library holds until exit.
+// Host code may not use the array's name as a device address: the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+// --------------------------------------------------------------------------
+constexpr size_t kNoallocScratchBytes = (size_t)64 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// W^j over one tile (K = its 128 points) for the 64 x 64 block (blockIdx.y, blockIdx.z),
+// scattered into V_acc with float64 atomics.
+__global__ void __launch_bounds__(256) vgemm_f64_tile(ChunkArgs a) {
+    int64_t t = a.t0 + blockIdx.x;
+    int mb = blockIdx.y, nb = blockIdx.z;
+    int j = a.plan.tile_batch[t];
+    int64_t f0 = a.plan.func_ptr[j];
+    int n = (int)(a.plan.func_ptr[j + 1] - f0);
+    int m0 = mb * VB, n0 = nb * VB;
+    if (m0 >= n || n0 >= n) return;
+    const int *F = a.plan.func_idx + f0;
+    Slabs S = slabs_of(a);
+    int64_t row0 = a.plan.tile_row[t] - a.row0;
+    const double *Zs = S.c[5] + (size_t)row0 * TILE;
+    const double *Ps = S.c[0] + (size_t)row0 * TILE;
+    int cnt = a.plan.tile_count[t];
+    __shared__ double As[VK][VB + 1];
+    __shared__ double Bs[VK][VB + 1];
+    int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < cnt; k0 += VK) {
+        for (int e = tid; e < VK * VB; e += 256) {
+            int rr = e / VK, kk = e % VK, k = k0 + kk;
+            As[kk][rr] = (m0 + rr < n && k < cnt) ? Zs[(size_t)(m0 + rr) * TILE + k] : 0.0;
+            Bs[kk][rr] = (n0 + rr < n && k < cnt) ? Ps[(size_t)(n0 + rr) * TILE + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < VK; ++kk)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(As[kk][ty * 4 + u], Bs[kk][tx * 4 + v], acc[u][v]);
+        __syncthreads();
+    }
+    for (int u = 0; u < 4; ++u) {
+        int mr = m0 + ty * 4 + u;
+        if (mr >= n) continue;
+        for (int v = 0; v < 4; ++v) {
+            int nr = n0 + tx * 4 + v;
+            if (nr < n) atomicAdd(&a.Vacc[(size_t)F[mr] * a.nbf + F[nr]], acc[u][v]);
+        }
+    }
+}
+
+// V <- V + V^T in place: the thread of pair (r, c), r < c, owns both entries.
+__global__ void symmetrize_inplace(double *V, int nbf) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nbf * nbf) return;
+    int r = (int)(e / nbf), c = (int)(e % nbf);
+    if (r > c) return;
+    double s = V[e] + V[(size_t)c * nbf + r];
+    V[e] = s;
+    V[(size_t)c * nbf + r] = s;
+}
+
 }  // namespace
 
 cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s) {
@@ -350,6 +415,42 @@ cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s) {
         vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a);
         P.end(GBXC_K_VGEMM, s);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes) {
+    // one cached address per device; the first call on a device resolves it
+    static void *cache[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!cache[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        cache[dev] = p;
+    }
+    *ptr = cache[dev];
+    *bytes = kNoallocScratchBytes;
+    return cudaSuccess;
+}
+
+cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s) {
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    colloc_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
+    xgemm_f64<<<xg, 256, 0, s>>>(a);
+    rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    unsigned nblk = (unsigned)((a.max_nfunc + VB - 1) / VB);
+    vgemm_f64_tile<<<dim3((unsigned)nt, nblk, nblk), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize_inplace(double *V, int nbf, cudaStream_t s) {
+    int64_t nn = (int64_t)nbf * nbf;
+    if (nn > 0) symmetrize_inplace<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(V, nbf);
     return cudaGetLastError();
 }
 

@@ -669,6 +669,75 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
     });
 }
 
+int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int functional, double *Vxc,
+                                double *EN, void *stream) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(ctx->device >= 0, "integration needs a device context");
+        REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "unknown functional");
+        REQUIRE(P && Vxc && EN, "P, Vxc and EN must be device pointers");
+        REQUIRE(is_device_ptr(P) && is_device_ptr(Vxc) && is_device_ptr(EN),
+                "P, Vxc and EN must be device pointers");
+        Molecule &m = get_mol(ctx, mol);
+        if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
+        void *scratch = nullptr;
+        size_t cap = 0;
+        check(noalloc_scratch(&scratch, &cap), "static scratch address");
+        const HostPlan &H = m.plan;
+        int64_t max_rows = (int64_t)(cap / fp64_row_bytes());
+        for (int64_t t = 0; t < H.ntiles(); ++t)
+            if (H.tile_row[t + 1] - H.tile_row[t] > max_rows)
+                return fail(ctx, GBXC_ENOMEM, "a batch needs more slab rows than the static scratch holds");
+        cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+        size_t nn = (size_t)m.nbf * m.nbf;
+        check(cudaMemsetAsync(Vxc, 0, nn * 8, s), "zero V");
+        int64_t t = 0, nt = H.ntiles();
+        while (t < nt) {
+            ChunkArgs a;
+            a.plan = m.dev;
+            a.shells = m.d_shells;
+            a.nbf = m.nbf;
+            a.t0 = t;
+            a.row0 = H.tile_row[t];
+            a.max_nfunc = 0;
+            while (t < nt && H.tile_row[t + 1] - a.row0 <= max_rows) {
+                int j = H.tile_batch[t];
+                a.max_nfunc = std::max(a.max_nfunc, (int)(H.func_ptr[j + 1] - H.func_ptr[j]));
+                ++t;
+            }
+            a.t1 = t;
+            a.rows = H.tile_row[t] - a.row0;
+            a.functional = functional;
+            a.P = P;
+            a.Vacc = Vxc;
+            a.tileE = m.d_tileE;
+            a.tileN = m.d_tileN;
+            a.scratch = scratch;
+            a.vtasks = nullptr;
+            a.nvtasks = 0;
+            a.prof = nullptr;
+            check(launch_fp64_chunk_noalloc(a, s), "fp64 chunk (static scratch)");
+        }
+        check(launch_symmetrize_inplace(Vxc, m.nbf, s), "symmetrise");
+        Profiler quiet;   // counts only; never records events
+        FinishArgs f;
+        f.Vacc = nullptr;
+        f.V = nullptr;
+        f.nbf = m.nbf;
+        f.tileE = m.d_tileE;
+        f.tileN = m.d_tileN;
+        f.batch_tile = m.dev.batch_tile;
+        f.b0 = 0;
+        f.b1 = H.nbatch();
+        f.Eb = m.d_Eb;
+        f.Nb = m.d_Nb;
+        f.tot = EN;
+        f.prof = &quiet;
+        check(launch_finish(f, s), "finish");
+        return GBXC_OK;
+    });
+}
+
 int gbxc_profile_enable(gbxc_ctx *ctx, int on) {
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {

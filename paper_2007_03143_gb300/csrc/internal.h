@@ -146,4 +146,10 @@ struct FinishArgs {
 };
 cudaError_t launch_finish(const FinishArgs &a, cudaStream_t s);
 
+// Allocation-free float64 variant: the static device scratch (address and size), one chunk
+// of the float64 pipeline with per-tile V tasks, and the in-place V + V^T.
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
+cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s);
+cudaError_t launch_symmetrize_inplace(double *V, int nbf, cudaStream_t s);
+
 }  // namespace gbxc
