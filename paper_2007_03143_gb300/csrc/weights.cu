@@ -1,5 +1,5 @@
 // Atomic partition weights w_i = p_A(r_i) w^q_i (Sec. 2.2, Eqs. atomic_partition and num_int;
-// Algorithm 4 step 1), in float64 on the GPU, one thread per grid point.
+// Algorithm 4's partition-weight update), in float64 on the GPU, one thread per grid point.
 //
 // Becke (1988) cell function: s(mu) = (1 - p(p(p(mu))))/2, p(x) = 1.5x - 0.5x^3.
 // SSF (1996): s(mu) = (1 - g(mu))/2 with g the degree-7 polynomial in mu/a on
