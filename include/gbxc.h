@@ -177,6 +177,57 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
                            double *Vxc, double *Nel, double *E_batch, double *N_batch,
                            void *stream);
 
+/* Batching form: integrate several resident molecules in ONE CUDA graph launch.
+ * The molecules are spread over up to 8 parallel graph branches by the greedy
+ * minimum-load rule of Algorithm 3 applied to the work estimate of Eq. batch_work,
+ * each branch with its own stream and device workspace; every molecule's batches run
+ * through the same batched kernels as gbxc_integrate.  The graph is captured on the
+ * first call for a given (molecule list, functionals, precision) and replayed by later
+ * calls with the same list (only P changes).
+ *   nmol          number of molecules (each id at most once)
+ *   mol_ids[k]    molecule ids
+ *   P[k]          nbf_k x nbf_k density matrices, host or device
+ *   functional[k] GBXC_SLATER or GBXC_PBE per molecule
+ *   precision     GBXC_FP64 or GBXC_MIXED for all
+ *   Exc, Nel      host arrays of nmol (may be NULL)
+ *   Vxc[k]        outputs, host or device (Vxc or Vxc[k] may be NULL)
+ * Returns after all results are complete. */
+int gbxc_integrate_many(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P,
+                        const int *functional, int precision, double *Exc, double *const *Vxc,
+                        double *Nel);
+
+/* Serving form: continuous batching of integration requests.
+ * gbxc_serve_start allocates one device arena of `arena_bytes` (0 = the context's
+ * scratch budget), creates `nslots` streams and starts a scheduler thread.  Requests
+ * (gbxc_submit) queue in arrival order; the scheduler admits the head of the queue as
+ * soon as a slot is free and a contiguous region of the arena can hold the request's
+ * device footprint (scratch of its batch schedule, P, V, partial sums and, for
+ * GBXC_MIXED, the sliced P blocks), so requests that arrive while others run are admitted
+ * as slots and memory free up and their work overlaps on the GPU.  Each request is
+ * integrated exactly as gbxc_integrate would (same kernels), on its slot's stream.
+ * gbxc_submit and gbxc_wait may be called from any thread while the server runs; other
+ * calls on the context are serialised with the scheduler.  gbxc_load_grid is refused
+ * (GBXC_ENOTREADY) while requests are queued or running.  gbxc_serve_stop finishes the
+ * running requests, fails queued ones with GBXC_ENOTREADY and frees the arena. */
+int gbxc_serve_start(gbxc_ctx *ctx, int nslots, size_t arena_bytes);
+int gbxc_serve_stop(gbxc_ctx *ctx);
+
+/* Queue one request; P (nbf x nbf, host) is copied before the call returns.
+ * *ticket identifies the request for gbxc_wait. */
+int gbxc_submit(gbxc_ctx *ctx, int mol, const double *P, int functional, int precision, long long *ticket);
+
+/* Wait up to timeout_s seconds for a request.  On completion fills Exc, Nel, Vxc (host,
+ * nbf x nbf; any may be NULL) and *latency_s (submission to GPU completion, may be NULL),
+ * forgets the ticket and returns the request's status; GBXC_ETIMEOUT if it is not done
+ * yet (the ticket stays valid), GBXC_ENOENT for an unknown ticket. */
+int gbxc_wait(gbxc_ctx *ctx, long long ticket, double timeout_s, double *Exc, double *Vxc, double *Nel,
+              double *latency_s);
+
+/* Queue length, requests on the GPU, requests completed since start, and the arena's free
+ * and total bytes (any pointer may be NULL). */
+int gbxc_serve_stats(gbxc_ctx *ctx, long long *queued, long long *running, long long *completed,
+                     size_t *arena_free, size_t *arena_cap);
+
 /* Float64 integration over every batch of `mol` for callers that cannot allocate
  * device memory (for example code running where cudaMalloc is unavailable or forbidden,
  * such as inside another library's memory pool or a pre-allocated real-time region).

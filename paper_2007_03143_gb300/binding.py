@@ -32,7 +32,9 @@ PRECISIONS = {"fp64": GBXC_FP64, "mixed": GBXC_MIXED}
 
 EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis", "gbxc_load_grid",
             "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
-            "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc"]
+            "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
+            "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
+            "gbxc_serve_stats"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "other"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -87,6 +89,16 @@ def lib():
     L.gbxc_integrate_fp64_noalloc.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
                                                c_void_p]
     L.gbxc_integrate_fp64_noalloc.restype = c_int
+    L.gbxc_integrate_many.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                                      c_void_p, c_void_p]
+    L.gbxc_serve_start.argtypes = [c_void_p, c_int, c_size_t]
+    L.gbxc_serve_stop.argtypes = [c_void_p]
+    L.gbxc_submit.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, POINTER(c_longlong)]
+    L.gbxc_wait.argtypes = [c_void_p, c_longlong, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.gbxc_serve_stats.argtypes = [c_void_p] + [c_void_p] * 5
+    for name in ("gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
+                 "gbxc_serve_stats"):
+        getattr(L, name).restype = c_int
     L.gbxc_profile_enable.argtypes = [c_void_p, c_int]
     L.gbxc_profile_read.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("gbxc_create", "gbxc_load_basis", "gbxc_load_grid", "gbxc_plan_info_get",
@@ -228,6 +240,55 @@ def gbxc_integrate_fp64_noalloc(ctx, mol, P, V, EN, functional="pbe", stream=Non
     st = _stream_for(stream, P)
     _check(ctx, lib().gbxc_integrate_fp64_noalloc(ctx, mol, pP, FUNCTIONALS.get(functional, functional),
                                                   pV, pE, st))
+
+
+def gbxc_integrate_many(ctx, mols, Ps, functionals, precision="fp64", Vs=None):
+    """One graph launch over several molecules; returns (E array, N array)."""
+    n = len(mols)
+    ids = np.ascontiguousarray(mols, dtype=np.int32)
+    fns = np.ascontiguousarray([FUNCTIONALS.get(f, f) for f in functionals], dtype=np.int32)
+    keep = [_ptr(P) for P in Ps]
+    pP = (c_void_p * n)(*[k[0] for k in keep])
+    vkeep = [_ptr(V) for V in Vs] if Vs is not None else None
+    pV = (c_void_p * n)(*[k[0] for k in vkeep]) if vkeep else None
+    E = np.zeros(n)
+    N = np.zeros(n)
+    _check(ctx, lib().gbxc_integrate_many(ctx, n, ids.ctypes.data, pP, fns.ctypes.data,
+                                          PRECISIONS.get(precision, precision), E.ctypes.data, pV,
+                                          N.ctypes.data))
+    return E, N
+
+
+def gbxc_serve_start(ctx, nslots=4, arena_bytes=0):
+    _check(ctx, lib().gbxc_serve_start(ctx, nslots, arena_bytes))
+
+
+def gbxc_serve_stop(ctx):
+    _check(ctx, lib().gbxc_serve_stop(ctx))
+
+
+def gbxc_submit(ctx, mol, P, functional="pbe", precision="mixed"):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    t = c_longlong()
+    _check(ctx, lib().gbxc_submit(ctx, mol, P.ctypes.data, FUNCTIONALS.get(functional, functional),
+                                  PRECISIONS.get(precision, precision), ctypes.byref(t)))
+    return t.value
+
+
+def gbxc_wait(ctx, ticket, timeout_s=60.0, V=None):
+    """Returns (E, N, latency_s); fills V (host array) if given."""
+    E, N, lat = c_double(), c_double(), c_double()
+    pV, kV, _ = _ptr(V)
+    _check(ctx, lib().gbxc_wait(ctx, ticket, timeout_s, ctypes.byref(E), pV, ctypes.byref(N), ctypes.byref(lat)))
+    return E.value, N.value, lat.value
+
+
+def gbxc_serve_stats(ctx) -> dict:
+    q, r, c = c_longlong(), c_longlong(), c_longlong()
+    f, cap = c_size_t(), c_size_t()
+    _check(ctx, lib().gbxc_serve_stats(ctx, ctypes.byref(q), ctypes.byref(r), ctypes.byref(c), ctypes.byref(f),
+                                       ctypes.byref(cap)))
+    return dict(queued=q.value, running=r.value, completed=c.value, arena_free=f.value, arena_cap=cap.value)
 
 
 def gbxc_profile_enable(ctx, on=True):

@@ -6,8 +6,15 @@
 // the batches in chunks that fit the scratch budget (the paper's
 // memory-saturating device subsets), and reduces E, N and V on the device.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <tuple>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -39,6 +46,7 @@ struct Schedule {
     int64_t max_rows = 0;
     MixedSchedule mixed;        // extra state of the mixed form
 };
+using SchedKey = std::tuple<int, int, int, size_t>;   // precision, b0, b1, scratch budget
 
 struct Molecule {
     int natoms = 0, nshell = 0, nbf = 0;
@@ -53,8 +61,121 @@ struct Molecule {
     DevPlan dev;
     std::vector<void *> dev_allocs;
     double *d_tileE = nullptr, *d_tileN = nullptr, *d_Eb = nullptr, *d_Nb = nullptr;
-    Schedule sched;
+    std::map<SchedKey, std::unique_ptr<Schedule>> scheds;
     MixedResident mixed_res;
+    double work = 0.0;          // sum_j W_j, for balancing many molecules over graph branches
+    double *many_P = nullptr, *many_V = nullptr, *many_tot = nullptr;   // gbxc_integrate_many
+    size_t many_cap = 0;
+};
+
+// Everything one in-flight integration owns on the device.  A workspace either owns its
+// buffers (cudaMalloc, grown on demand) or has them carved from the context's arena.
+struct Workspace {
+    cudaStream_t stream = nullptr;
+    bool owns = true;
+    void *scratch = nullptr;
+    size_t scratch_cap = 0;
+    double *d_P = nullptr, *d_Vacc = nullptr, *d_V = nullptr, *d_tot = nullptr;
+    size_t mat_cap = 0;
+    double *tileE = nullptr, *tileN = nullptr, *Eb = nullptr, *Nb = nullptr;
+    size_t tile_cap = 0, batch_cap = 0;
+    MixedCtx mixed;
+};
+
+// First-fit allocator over one device allocation (the paper's preallocated device arena
+// managed by hand, Sec. 2.3).
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0;
+    std::map<size_t, size_t> free_;   // offset -> bytes
+    void init(char *b, size_t c) {
+        base = b;
+        cap = c;
+        free_.clear();
+        if (c) free_[0] = c;
+    }
+    static size_t up(size_t b) { return (b + 255) & ~(size_t)255; }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = up(std::max<size_t>(bytes, 256));
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            *off = it->first;
+            size_t rest = it->second - bytes, o = it->first;
+            free_.erase(it);
+            if (rest) free_[o + bytes] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = up(std::max<size_t>(bytes, 256));
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t free_bytes() const {
+        size_t f = 0;
+        for (auto &kv : free_) f += kv.second;
+        return f;
+    }
+};
+
+// One queued or running request of the serving loop.
+struct Request {
+    long long ticket = 0;
+    int mol = 0, functional = 0, precision = 0;
+    std::vector<double> P, V;
+    double E = 0.0, N = 0.0;
+    int state = 0;              // 0 queued, 1 running, 2 done
+    int status = GBXC_OK;
+    std::string err;
+    size_t off = 0, bytes = 0;
+    int slot = -1;
+    double *pin_tot = nullptr;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+struct Server {
+    bool running = false;
+    int nslots = 0;
+    size_t slot_budget = 0;     // scratch budget of one request's schedule
+    char *arena_mem = nullptr;
+    Arena arena;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done_ev;
+    std::vector<double *> pin;  // per slot: pinned P/V staging (2 nbf^2) + totals
+    std::vector<size_t> pin_cap;
+    std::vector<std::shared_ptr<Request>> slot_req;
+    std::vector<Workspace> slot_ws;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<long long, std::shared_ptr<Request>> tickets;
+    long long next_ticket = 1;
+    std::mutex qmu;             // queue, tickets and request states
+    std::condition_variable cv; // request completion and new submissions
+    std::atomic<bool> stop{false};
+    std::thread thread;
+    long long admitted = 0, completed = 0;
+};
+
+// A captured CUDA graph of gbxc_integrate_many for one molecule list.
+struct ManyGraph {
+    std::vector<int> mols, fns;
+    int precision = -1, branches = 0;
+    size_t budget = 0;
+    cudaGraphExec_t exec = nullptr;
+    long long launches[GBXC_NKERNEL] = {};
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
 };
 
 }  // namespace
@@ -63,15 +184,15 @@ struct gbxc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     size_t scratch_budget = 0;
-    void *scratch = nullptr;
-    size_t scratch_cap = 0;
-    double *d_P = nullptr, *d_Vacc = nullptr, *d_V = nullptr, *d_tot = nullptr;
-    size_t mat_cap = 0;            // elements of the P/V buffers
+    Workspace ws;                   // the default workspace (synchronous calls)
+    std::vector<Workspace> branch_ws;   // gbxc_integrate_many branches
+    ManyGraph many;
     std::string err;
     std::map<int, std::unique_ptr<Molecule>> mols;
     int next_id = 0;
-    MixedCtx mixed;
     Profiler prof;
+    std::recursive_mutex mu;        // serialises host-side work on the context
+    Server srv;
 };
 
 namespace {
@@ -100,6 +221,8 @@ struct ArgError {
 
 template <typename F>
 int guarded(gbxc_ctx *ctx, F &&body) {
+    std::unique_lock<std::recursive_mutex> lk;
+    if (ctx) lk = std::unique_lock<std::recursive_mutex>(ctx->mu);
     try {
         if (ctx) {
             ctx->err.clear();
@@ -145,12 +268,33 @@ void free_schedule(Schedule &s) {
     s = Schedule{};
 }
 
+void free_schedules(Molecule &m) {
+    for (auto &kv : m.scheds) free_schedule(*kv.second);
+    m.scheds.clear();
+}
+
 void free_grid(Molecule &m) {
     for (void *p : m.dev_allocs) cudaFree(p);
     m.dev_allocs.clear();
-    free_schedule(m.sched);
+    free_schedules(m);
     m.dev = DevPlan{};
     m.has_grid = false;
+}
+
+void free_workspace(Workspace &w) {
+    if (w.owns) {
+        cudaFree(w.scratch);
+        cudaFree(w.d_P);
+        cudaFree(w.d_Vacc);
+        cudaFree(w.d_V);
+        cudaFree(w.d_tot);
+        cudaFree(w.tileE);
+        cudaFree(w.tileN);
+        cudaFree(w.Eb);
+        cudaFree(w.Nb);
+        free_mixed_ctx(w.mixed);
+    }
+    w = Workspace{};
 }
 
 bool is_device_ptr(const void *p) {
@@ -169,31 +313,107 @@ Molecule &get_mol(gbxc_ctx *ctx, int mol) {
     return *it->second;
 }
 
-void ensure_matrices(gbxc_ctx *ctx, int nbf) {
-    size_t need = (size_t)nbf * nbf;
-    if (need <= ctx->mat_cap && ctx->d_P) return;
-    cudaFree(ctx->d_P);
-    cudaFree(ctx->d_Vacc);
-    cudaFree(ctx->d_V);
-    ctx->d_P = ctx->d_Vacc = ctx->d_V = nullptr;
-    ctx->mat_cap = 0;
-    check(cudaMalloc(&ctx->d_P, std::max<size_t>(need, 1) * 8), "cudaMalloc P");
-    check(cudaMalloc(&ctx->d_Vacc, std::max<size_t>(need, 1) * 8), "cudaMalloc V_acc");
-    check(cudaMalloc(&ctx->d_V, std::max<size_t>(need, 1) * 8), "cudaMalloc V");
-    ctx->mat_cap = need;
-}
-
-void ensure_scratch(gbxc_ctx *ctx, size_t bytes) {
-    if (bytes <= ctx->scratch_cap && ctx->scratch) return;
-    cudaFree(ctx->scratch);
-    ctx->scratch = nullptr;
-    ctx->scratch_cap = 0;
-    cudaError_t e = cudaMalloc(&ctx->scratch, std::max<size_t>(bytes, 256));
+template <typename T>
+void grow_buf(T *&p, size_t &cap, size_t need, const char *what) {
+    if (need <= cap && p) return;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(need, 1) * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
-        throw CudaFail{"scratch allocation of " + std::to_string(bytes) + " bytes failed"};
+        throw CudaFail{std::string(what) + ": allocation of " + std::to_string(need * sizeof(T)) +
+                       " bytes failed"};
     }
-    ctx->scratch_cap = bytes;
+    cap = need;
+}
+
+size_t row_bytes(int precision) { return precision == GBXC_FP64 ? fp64_row_bytes() : mixed_row_bytes(); }
+
+// Device bytes one integration of `m` with schedule `S` needs in a workspace.
+size_t footprint(const Molecule &m, const Schedule &S, int precision) {
+    size_t nn = (size_t)m.nbf * m.nbf;
+    size_t b = (size_t)S.max_rows * row_bytes(precision) + 256;
+    b += Arena::up(nn * 8) * 3 + 256;                      // P, V_acc, V (+ totals)
+    b += Arena::up((size_t)m.plan.ntiles() * 8) * 2;       // tile E/N partials
+    b += Arena::up((size_t)std::max(m.plan.nbatch(), 1) * 8) * 2;
+    if (precision == GBXC_MIXED) b += mixed_reserve_bytes(S.mixed, m.nbf) + 4 * 256;
+    return b;
+}
+
+// Make `w` (an owning workspace) large enough for one integration of `m` with `S`.
+void reserve(Workspace &w, const Molecule &m, const Schedule &S, int precision) {
+    size_t nn = (size_t)m.nbf * m.nbf;
+    if (nn > w.mat_cap || !w.d_P) {
+        size_t c0 = w.mat_cap, c1 = w.mat_cap, c2 = w.mat_cap;
+        grow_buf(w.d_P, c0, nn, "P");
+        grow_buf(w.d_Vacc, c1, nn, "V_acc");
+        grow_buf(w.d_V, c2, nn, "V");
+        w.mat_cap = nn;
+    }
+    size_t one = 2;
+    if (!w.d_tot) grow_buf(w.d_tot, one, 2, "totals");
+    size_t nt = (size_t)m.plan.ntiles(), nb = (size_t)std::max(m.plan.nbatch(), 1);
+    if (nt > w.tile_cap || !w.tileE) {
+        size_t c0 = w.tile_cap, c1 = w.tile_cap;
+        grow_buf(w.tileE, c0, nt, "tile E");
+        grow_buf(w.tileN, c1, nt, "tile N");
+        w.tile_cap = nt;
+    }
+    if (nb > w.batch_cap || !w.Eb) {
+        size_t c0 = w.batch_cap, c1 = w.batch_cap;
+        grow_buf(w.Eb, c0, nb, "batch E");
+        grow_buf(w.Nb, c1, nb, "batch N");
+        w.batch_cap = nb;
+    }
+    size_t sb = (size_t)S.max_rows * row_bytes(precision);
+    if (sb > w.scratch_cap || !w.scratch) {
+        char *p = static_cast<char *>(w.scratch);
+        size_t cap = w.scratch_cap;
+        grow_buf(p, cap, std::max<size_t>(sb, 256), "scratch");
+        w.scratch = p;
+        w.scratch_cap = cap;
+    }
+    if (precision == GBXC_MIXED) check(mixed_reserve(w.mixed, S.mixed, m.nbf), "mixed buffers");
+}
+
+// Carve a non-owning workspace for one integration out of `base` (footprint bytes).
+void carve(Workspace &w, char *base, const Molecule &m, const Schedule &S, int precision, void *encode_fn) {
+    size_t nn = (size_t)m.nbf * m.nbf;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base + o;
+        o += Arena::up(std::max<size_t>(bytes, 8));
+        return p;
+    };
+    w.owns = false;
+    w.scratch = take((size_t)S.max_rows * row_bytes(precision));
+    w.scratch_cap = (size_t)S.max_rows * row_bytes(precision);
+    w.d_P = reinterpret_cast<double *>(take(nn * 8));
+    w.d_Vacc = reinterpret_cast<double *>(take(nn * 8));
+    w.d_V = reinterpret_cast<double *>(take(nn * 8));
+    w.d_tot = reinterpret_cast<double *>(take(16));
+    w.mat_cap = nn;
+    w.tileE = reinterpret_cast<double *>(take((size_t)m.plan.ntiles() * 8));
+    w.tileN = reinterpret_cast<double *>(take((size_t)m.plan.ntiles() * 8));
+    w.tile_cap = (size_t)m.plan.ntiles();
+    size_t nb = (size_t)std::max(m.plan.nbatch(), 1);
+    w.Eb = reinterpret_cast<double *>(take(nb * 8));
+    w.Nb = reinterpret_cast<double *>(take(nb * 8));
+    w.batch_cap = nb;
+    if (precision == GBXC_MIXED) {
+        const MixedSchedule &ms = S.mixed;
+        w.mixed = MixedCtx{};
+        w.mixed.encode_fn = encode_fn;
+        check(mixed_init(w.mixed), "mixed init");
+        w.mixed.pslices = reinterpret_cast<uint16_t *>(take((size_t)std::max<int64_t>(ms.max_prows, 1) * 32 * 5 * 2));
+        w.mixed.pslice_rows = (size_t)std::max<int64_t>(ms.max_prows, 1) * 32 * 5;
+        w.mixed.pexp = reinterpret_cast<int *>(take((size_t)std::max<int64_t>(ms.max_pexp, 1) * 4));
+        w.mixed.pexp_cap = (size_t)std::max<int64_t>(ms.max_pexp, 1);
+        w.mixed.pdf = reinterpret_cast<float *>(take(2 * nn * 4));
+        w.mixed.pdf_cap = 2 * nn;
+        w.mixed.d_err = reinterpret_cast<int *>(take(4));
+    }
 }
 
 // The default budget is fixed at the first integration of the context (40% of the
@@ -208,14 +428,14 @@ size_t scratch_budget(gbxc_ctx *ctx) {
 }
 
 // Chunks of tiles whose slabs fit the budget, and the V-contraction tasks of each chunk.
-void build_schedule(gbxc_ctx *ctx, Molecule &m, int precision, int b0, int b1) {
-    Schedule &S = m.sched;
-    size_t budget = scratch_budget(ctx);
-    if (S.precision == precision && S.b0 == b0 && S.b1 == b1 && S.budget == budget) return;
-    free_schedule(S);
+Schedule &get_schedule(Molecule &m, int precision, int b0, int b1, size_t budget) {
+    SchedKey key{precision, b0, b1, budget};
+    auto it = m.scheds.find(key);
+    if (it != m.scheds.end()) return *it->second;
+    auto sp = std::make_unique<Schedule>();
+    Schedule &S = *sp;
     const HostPlan &P = m.plan;
-    size_t row_bytes = precision == GBXC_FP64 ? fp64_row_bytes() : mixed_row_bytes();
-    int64_t max_rows = (int64_t)(budget / row_bytes);
+    int64_t max_rows = (int64_t)(budget / row_bytes(precision));
     int64_t tb = P.batch_tile[b0], te = P.batch_tile[b1];
     std::vector<int> tasks;
     int64_t t = tb;
@@ -261,6 +481,64 @@ void build_schedule(gbxc_ctx *ctx, Molecule &m, int precision, int b0, int b1) {
     S.b0 = b0;
     S.b1 = b1;
     S.budget = budget;
+    Schedule &ref = *sp;
+    m.scheds.emplace(key, std::move(sp));
+    return ref;
+}
+
+// Queue one integration of `m` on stream `s` with workspace `w` (no host synchronisation):
+// V_acc <- 0, chunks, V = V_acc + V_acc^T into dV (if non-null), per-batch sums into w.Eb/Nb
+// and {E, N} into w.d_tot.
+void enqueue(Workspace &w, Molecule &m, const Schedule &S, const double *dP, int functional, int precision,
+             int b0, int b1, double *dV, bool batch_sums, cudaStream_t s, Profiler *prof,
+             double *d_tot = nullptr) {
+    size_t nn = (size_t)m.nbf * m.nbf;
+    check(cudaMemsetAsync(w.d_Vacc, 0, nn * 8, s), "zero V");
+    if (precision == GBXC_MIXED) check(mixed_begin(w.mixed, dP, m.nbf, s), "mixed begin");
+    for (size_t ci = 0; ci < S.chunks.size(); ++ci) {
+        const auto &c = S.chunks[ci];
+        ChunkArgs a;
+        a.plan = m.dev;
+        a.shells = m.d_shells;
+        a.nbf = m.nbf;
+        a.t0 = c.t0;
+        a.t1 = c.t1;
+        a.row0 = c.row0;
+        a.rows = c.rows;
+        a.max_nfunc = c.max_nfunc;
+        a.functional = functional;
+        a.P = dP;
+        a.Vacc = w.d_Vacc;
+        a.tileE = w.tileE;
+        a.tileN = w.tileN;
+        a.scratch = w.scratch;
+        a.vtasks = S.d_tasks ? S.d_tasks + 5 * c.task0 : nullptr;
+        a.nvtasks = (int)c.ntask;
+        a.prof = prof;
+        if (precision == GBXC_FP64)
+            check(launch_fp64_chunk(a, s), "fp64 chunk");
+        else
+            check(launch_mixed_chunk(a, w.mixed, m.mixed_res, S.mixed, (int)ci, s), "mixed chunk");
+    }
+    if (batch_sums) {
+        int nb = std::max(m.plan.nbatch(), 1);
+        check(cudaMemsetAsync(w.Eb, 0, nb * 8, s), "zero Eb");
+        check(cudaMemsetAsync(w.Nb, 0, nb * 8, s), "zero Nb");
+    }
+    FinishArgs f;
+    f.Vacc = w.d_Vacc;
+    f.V = dV;
+    f.nbf = m.nbf;
+    f.tileE = w.tileE;
+    f.tileN = w.tileN;
+    f.batch_tile = m.dev.batch_tile;
+    f.b0 = b0;
+    f.b1 = b1;
+    f.Eb = w.Eb;
+    f.Nb = w.Nb;
+    f.tot = d_tot ? d_tot : w.d_tot;
+    f.prof = prof;
+    check(launch_finish(f, s), "finish");
 }
 
 int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int precision, int b0,
@@ -276,79 +554,218 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     REQUIRE(0 <= b0 && b0 <= b1 && b1 <= nb, "batch range out of bounds");
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
     size_t nn = (size_t)m.nbf * m.nbf;
-    ensure_matrices(ctx, m.nbf);
-    build_schedule(ctx, m, precision, b0, b1);
-    const Schedule &S = m.sched;
-    ensure_scratch(ctx, (size_t)S.max_rows * (precision == GBXC_FP64 ? fp64_row_bytes()
-                                                                     : mixed_row_bytes()));
+    Workspace &w = ctx->ws;
+    const Schedule &S = get_schedule(m, precision, b0, b1, scratch_budget(ctx));
+    reserve(w, m, S, precision);
     const double *dP = P;
     if (!is_device_ptr(P)) {
-        check(cudaMemcpyAsync(ctx->d_P, P, nn * 8, cudaMemcpyHostToDevice, s), "copy P");
-        dP = ctx->d_P;
+        check(cudaMemcpyAsync(w.d_P, P, nn * 8, cudaMemcpyHostToDevice, s), "copy P");
+        dP = w.d_P;
     }
-    double *dV = (Vxc && is_device_ptr(Vxc)) ? Vxc : ctx->d_V;
-    check(cudaMemsetAsync(ctx->d_Vacc, 0, nn * 8, s), "zero V");
-    if (precision == GBXC_MIXED) {
-        check(mixed_prepare(ctx->mixed, m.mixed_res, S.mixed, dP, m.nbf, s), "mixed prepare");
-    }
-    for (size_t ci = 0; ci < S.chunks.size(); ++ci) {
-        const auto &c = S.chunks[ci];
-        ChunkArgs a;
-        a.plan = m.dev;
-        a.shells = m.d_shells;
-        a.nbf = m.nbf;
-        a.t0 = c.t0;
-        a.t1 = c.t1;
-        a.row0 = c.row0;
-        a.rows = c.rows;
-        a.max_nfunc = c.max_nfunc;
-        a.functional = functional;
-        a.P = dP;
-        a.Vacc = ctx->d_Vacc;
-        a.tileE = m.d_tileE;
-        a.tileN = m.d_tileN;
-        a.scratch = ctx->scratch;
-        a.vtasks = S.d_tasks ? S.d_tasks + 5 * c.task0 : nullptr;
-        a.nvtasks = (int)c.ntask;
-        a.prof = &ctx->prof;
-        if (precision == GBXC_FP64)
-            check(launch_fp64_chunk(a, s), "fp64 chunk");
-        else
-            check(launch_mixed_chunk(a, ctx->mixed, m.mixed_res, S.mixed, (int)ci, s), "mixed chunk");
-    }
-    FinishArgs f;
-    f.Vacc = ctx->d_Vacc;
-    f.V = Vxc ? dV : nullptr;
-    f.nbf = m.nbf;
-    f.tileE = m.d_tileE;
-    f.tileN = m.d_tileN;
-    f.batch_tile = m.dev.batch_tile;
-    f.b0 = b0;
-    f.b1 = b1;
-    f.Eb = m.d_Eb;
-    f.Nb = m.d_Nb;
-    f.tot = ctx->d_tot;
-    f.prof = &ctx->prof;
-    if (Eb || Nb) {
-        check(cudaMemsetAsync(m.d_Eb, 0, std::max(nb, 1) * 8, s), "zero Eb");
-        check(cudaMemsetAsync(m.d_Nb, 0, std::max(nb, 1) * 8, s), "zero Nb");
-    }
-    check(launch_finish(f, s), "finish");
+    double *dV = (Vxc && is_device_ptr(Vxc)) ? Vxc : w.d_V;
+    enqueue(w, m, S, dP, functional, precision, b0, b1, Vxc ? dV : nullptr, Eb || Nb, s, &ctx->prof);
     double tot[2];
-    check(cudaMemcpyAsync(tot, ctx->d_tot, 16, cudaMemcpyDeviceToHost, s), "copy E");
+    check(cudaMemcpyAsync(tot, w.d_tot, 16, cudaMemcpyDeviceToHost, s), "copy E");
     if (Vxc && dV != Vxc) check(cudaMemcpyAsync(Vxc, dV, nn * 8, cudaMemcpyDeviceToHost, s), "copy V");
-    if (Eb) check(cudaMemcpyAsync(Eb, m.d_Eb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Eb");
-    if (Nb) check(cudaMemcpyAsync(Nb, m.d_Nb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Nb");
+    if (Eb) check(cudaMemcpyAsync(Eb, w.Eb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Eb");
+    if (Nb) check(cudaMemcpyAsync(Nb, w.Nb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Nb");
     check(cudaStreamSynchronize(s), "integrate");
     if (precision == GBXC_MIXED) {
         int werr = 0;
-        check(mixed_read_error(ctx->mixed, &werr, s), "mixed status");
+        check(mixed_read_error(w.mixed, &werr, s), "mixed status");
         if (werr) return fail(ctx, GBXC_ETIMEOUT, "a bounded tensor-core pipeline wait expired (code " +
                                                       std::to_string(werr) + ")");
     }
     if (Exc) *Exc = tot[0];
     if (Nel) *Nel = tot[1];
     return GBXC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// continuous-batching server
+// ---------------------------------------------------------------------------
+bool server_busy(gbxc_ctx *ctx) {
+    Server &S = ctx->srv;
+    if (!S.running) return false;
+    std::lock_guard<std::mutex> q(S.qmu);
+    if (!S.queue.empty()) return true;
+    for (auto &r : S.slot_req)
+        if (r) return true;
+    return false;
+}
+
+// Admit the head of the queue if a slot and arena room are free (FIFO, no overtaking).
+// Returns true if a request was admitted.  Called by the scheduler thread.
+bool server_admit(gbxc_ctx *ctx) {
+    Server &S = ctx->srv;
+    std::shared_ptr<Request> r;
+    int slot = -1;
+    {
+        std::lock_guard<std::mutex> q(S.qmu);
+        if (S.queue.empty()) return false;
+        for (int k = 0; k < S.nslots; ++k)
+            if (!S.slot_req[k]) {
+                slot = k;
+                break;
+            }
+        if (slot < 0) return false;
+        r = S.queue.front();
+    }
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    auto fail_req = [&](int code, const std::string &msg) {
+        std::lock_guard<std::mutex> q(S.qmu);
+        S.queue.pop_front();
+        r->status = code;
+        r->err = msg;
+        r->state = 2;
+        r->t_done = std::chrono::steady_clock::now();
+        S.cv.notify_all();
+        return true;
+    };
+    try {
+        Molecule &m = get_mol(ctx, r->mol);
+        if (!m.has_grid) return fail_req(GBXC_ENOTREADY, "molecule has no grid");
+        Schedule &Sch = get_schedule(m, r->precision, 0, m.plan.nbatch(), S.slot_budget);
+        size_t fp = footprint(m, Sch, r->precision);
+        if (fp > S.arena.cap) return fail_req(GBXC_ENOMEM, "request footprint exceeds the serving arena");
+        size_t off = 0;
+        if (!S.arena.alloc(fp, &off)) return false;       // wait for memory to free up
+        size_t nn = (size_t)m.nbf * m.nbf;
+        if (2 * nn + 2 > S.pin_cap[slot]) {                // grow this (idle) slot's pinned staging
+            cudaStreamSynchronize(S.streams[slot]);
+            cudaFreeHost(S.pin[slot]);
+            S.pin[slot] = nullptr;
+            S.pin_cap[slot] = 0;
+            check(cudaMallocHost(&S.pin[slot], (2 * nn + 2) * 8), "pinned staging");
+            S.pin_cap[slot] = 2 * nn + 2;
+        }
+        double *pin = S.pin[slot];
+        std::memcpy(pin, r->P.data(), nn * 8);
+        Workspace &w = S.slot_ws[slot];
+        w = Workspace{};
+        w.stream = S.streams[slot];
+        carve(w, S.arena.base + off, m, Sch, r->precision, ctx->ws.mixed.encode_fn);
+        cudaStream_t st = S.streams[slot];
+        check(cudaMemcpyAsync(w.d_P, pin, nn * 8, cudaMemcpyHostToDevice, st), "copy P");
+        enqueue(w, m, Sch, w.d_P, r->functional, r->precision, 0, m.plan.nbatch(), w.d_V, false, st, &ctx->prof);
+        check(cudaMemcpyAsync(pin + nn, w.d_V, nn * 8, cudaMemcpyDeviceToHost, st), "copy V");
+        check(cudaMemcpyAsync(pin + 2 * nn, w.d_tot, 16, cudaMemcpyDeviceToHost, st), "copy E");
+        check(cudaEventRecord(S.done_ev[slot], st), "record");
+        std::lock_guard<std::mutex> q(S.qmu);
+        S.queue.pop_front();
+        r->off = off;
+        r->bytes = fp;
+        r->slot = slot;
+        r->state = 1;
+        S.slot_req[slot] = r;
+        ++S.admitted;
+        return true;
+    } catch (const ArgError &e) {
+        return fail_req(GBXC_EINVAL, e.msg);
+    } catch (const CudaFail &e) {
+        return fail_req(GBXC_ECUDA, e.msg);
+    } catch (const std::exception &e) {
+        return fail_req(GBXC_EINVAL, e.what());
+    }
+}
+
+// Retire finished slots; returns true if any request completed.
+bool server_retire(gbxc_ctx *ctx) {
+    Server &S = ctx->srv;
+    bool any = false;
+    for (int k = 0; k < S.nslots; ++k) {
+        std::shared_ptr<Request> r;
+        {
+            std::lock_guard<std::mutex> q(S.qmu);
+            r = S.slot_req[k];
+        }
+        if (!r) continue;
+        cudaError_t e = cudaEventQuery(S.done_ev[k]);
+        if (e == cudaErrorNotReady) continue;
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        cudaSetDevice(ctx->device);
+        Molecule *m = ctx->mols.count(r->mol) ? ctx->mols[r->mol].get() : nullptr;
+        size_t nn = m ? (size_t)m->nbf * m->nbf : 0;
+        int status = GBXC_OK;
+        std::string msg;
+        if (e != cudaSuccess) {
+            status = GBXC_ECUDA;
+            msg = cudaGetErrorString(e);
+        } else if (r->precision == GBXC_MIXED) {
+            int werr = 0;
+            if (mixed_read_error(S.slot_ws[k].mixed, &werr, S.streams[k]) != cudaSuccess || werr) {
+                status = GBXC_ETIMEOUT;
+                msg = "a bounded tensor-core pipeline wait expired";
+            }
+        }
+        double *pin = S.pin[k];
+        if (status == GBXC_OK) {
+            r->V.assign(pin + nn, pin + 2 * nn);
+            r->E = pin[2 * nn];
+            r->N = pin[2 * nn + 1];
+        }
+        S.arena.release(r->off, r->bytes);
+        std::lock_guard<std::mutex> q(S.qmu);
+        r->status = status;
+        r->err = msg;
+        r->state = 2;
+        r->t_done = std::chrono::steady_clock::now();
+        r->P.clear();
+        r->P.shrink_to_fit();
+        S.slot_req[k].reset();
+        ++S.completed;
+        S.cv.notify_all();
+        any = true;
+    }
+    return any;
+}
+
+void server_loop(gbxc_ctx *ctx) {
+    Server &S = ctx->srv;
+    cudaSetDevice(ctx->device);
+    while (!S.stop.load()) {
+        bool progress = server_retire(ctx);
+        while (server_admit(ctx)) progress = true;
+        if (!progress) {
+            std::unique_lock<std::mutex> q(S.qmu);
+            S.cv.wait_for(q, std::chrono::microseconds(20));
+        }
+    }
+}
+
+void server_stop(gbxc_ctx *ctx) {
+    Server &S = ctx->srv;
+    if (!S.running) return;
+    S.stop = true;
+    S.cv.notify_all();
+    if (S.thread.joinable()) S.thread.join();
+    for (int k = 0; k < S.nslots; ++k) {
+        cudaStreamSynchronize(S.streams[k]);
+        cudaStreamDestroy(S.streams[k]);
+        cudaEventDestroy(S.done_ev[k]);
+        cudaFreeHost(S.pin[k]);
+    }
+    cudaFree(S.arena_mem);
+    {
+        std::lock_guard<std::mutex> q(S.qmu);
+        for (auto &kv : S.tickets)
+            if (kv.second->state != 2) {
+                kv.second->state = 2;
+                kv.second->status = GBXC_ENOTREADY;
+                kv.second->err = "server stopped";
+            }
+        S.cv.notify_all();
+    }
+    S.streams.clear();
+    S.done_ev.clear();
+    S.pin.clear();
+    S.pin_cap.clear();
+    S.slot_req.clear();
+    S.slot_ws.clear();
+    S.queue.clear();
+    S.running = false;
+    S.stop = false;
 }
 
 }  // namespace
@@ -404,7 +821,7 @@ int gbxc_create(gbxc_ctx **out, int device, size_t scratch_bytes) {
     ctx->scratch_budget = scratch_bytes;
     int rc = guarded(ctx, [&] {
         check(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "stream");
-        check(cudaMalloc(&ctx->d_tot, 16), "cudaMalloc totals");
+        ctx->ws.stream = ctx->stream;
         return GBXC_OK;
     });
     if (rc != GBXC_OK) {
@@ -421,23 +838,34 @@ void gbxc_destroy(gbxc_ctx *ctx) {
         delete ctx;
         return;
     }
+    server_stop(ctx);
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &w : ctx->branch_ws) {
+        if (w.stream) {
+            cudaStreamSynchronize(w.stream);
+            cudaStreamDestroy(w.stream);
+        }
+        free_workspace(w);
+    }
+    ctx->branch_ws.clear();
+    if (ctx->many.exec) cudaGraphExecDestroy(ctx->many.exec);
+    if (ctx->many.fork) cudaEventDestroy(ctx->many.fork);
+    for (auto e : ctx->many.join) cudaEventDestroy(e);
     for (auto &kv : ctx->mols) {
-        free_grid(*kv.second);
-        cudaFree(kv.second->d_shells);
-        free_mixed_resident(kv.second->mixed_res);
-        cudaFree(kv.second->d_atoms);
-        cudaFree(kv.second->d_rnn);
+        Molecule &m = *kv.second;
+        free_grid(m);
+        cudaFree(m.d_shells);
+        free_mixed_resident(m.mixed_res);
+        cudaFree(m.d_atoms);
+        cudaFree(m.d_rnn);
+        cudaFree(m.many_P);
+        cudaFree(m.many_V);
+        cudaFree(m.many_tot);
     }
     ctx->mols.clear();
-    free_mixed_ctx(ctx->mixed);
+    free_workspace(ctx->ws);
     ctx->prof.release();
-    cudaFree(ctx->scratch);
-    cudaFree(ctx->d_P);
-    cudaFree(ctx->d_Vacc);
-    cudaFree(ctx->d_V);
-    cudaFree(ctx->d_tot);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -527,7 +955,13 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
         REQUIRE(spec->eta > 0 && spec->eta < 1 && spec->mk_alpha > 0, "bad eta or mk_alpha");
         Molecule &m = get_mol(ctx, mol);
         bool host_only = ctx->device < 0;
+        if (server_busy(ctx)) return fail(ctx, GBXC_ENOTREADY, "requests are in flight; wait for them first");
         if (!host_only) check(cudaStreamSynchronize(ctx->stream), "sync");
+        if (!host_only && ctx->many.exec) {
+            cudaGraphExecDestroy(ctx->many.exec);
+            ctx->many.exec = nullptr;
+            ctx->many.mols.clear();
+        }
         free_grid(m);
         m.spec = *spec;
         std::vector<double> x, y, z, wq;
@@ -537,6 +971,8 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
         for (int s = 0; s < m.nshell; ++s)
             rcut[s] = shell_cutoff(m.shells[s].alpha, m.shells[s].nprim, spec->eta);
         build_plan(m.xyz, m.shells, rcut, m.nbf, *spec, x, y, z, wq, parent, m.plan);
+        m.work = 0.0;
+        for (double wj : m.plan.work) m.work += wj;
         if (host_only) {
             m.has_grid = true;
             if (npts_out) *npts_out = (long long)m.plan.x.size();
@@ -736,6 +1172,257 @@ int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int fun
         check(launch_finish(f, s), "finish");
         return GBXC_OK;
     });
+}
+
+int gbxc_integrate_many(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P,
+                        const int *functional, int precision, double *Exc, double *const *Vxc, double *Nel) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(ctx->device >= 0, "integration needs a device context");
+        REQUIRE(nmol > 0 && mol_ids && P && functional, "bad molecule list");
+        REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
+        std::vector<Molecule *> ms(nmol);
+        for (int k = 0; k < nmol; ++k) {
+            ms[k] = &get_mol(ctx, mol_ids[k]);
+            if (!ms[k]->has_grid) return fail(ctx, GBXC_ENOTREADY, "a molecule has no grid");
+            REQUIRE(functional[k] == GBXC_SLATER || functional[k] == GBXC_PBE, "unknown functional");
+            REQUIRE(P[k], "P is NULL");
+            for (int q = 0; q < k; ++q) REQUIRE(mol_ids[q] != mol_ids[k], "a molecule appears twice");
+        }
+        const int W = std::min(nmol, 8);
+        const size_t budget = scratch_budget(ctx) / W;
+        // longest-processing-time assignment of molecules to graph branches by the work
+        // estimate of Eq. batch_work (the paper's greedy minimum-load rule, Algorithm 3)
+        std::vector<int> order(nmol);
+        for (int k = 0; k < nmol; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ms[a]->work > ms[b]->work; });
+        std::vector<double> load(W, 0.0);
+        std::vector<std::vector<int>> br(W);
+        for (int k : order) {
+            int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            br[b].push_back(k);
+            load[b] += ms[k]->work;
+        }
+        std::vector<Schedule *> sch(nmol);
+        for (int k = 0; k < nmol; ++k)
+            sch[k] = &get_schedule(*ms[k], precision, 0, ms[k]->plan.nbatch(), budget);
+        if ((int)ctx->branch_ws.size() < W) ctx->branch_ws.resize(W);
+        for (int b = 0; b < W; ++b) {
+            Workspace &w = ctx->branch_ws[b];
+            if (!w.stream) check(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking), "stream");
+            for (int k : br[b]) reserve(w, *ms[k], *sch[k], precision);
+        }
+        for (int k = 0; k < nmol; ++k) {
+            Molecule &m = *ms[k];
+            size_t nn = (size_t)m.nbf * m.nbf;
+            if (nn > m.many_cap || !m.many_P) {
+                size_t c0 = m.many_cap, c1 = m.many_cap, c2 = 0;
+                grow_buf(m.many_P, c0, nn, "P");
+                grow_buf(m.many_V, c1, nn, "V");
+                cudaFree(m.many_tot);
+                m.many_tot = nullptr;
+                grow_buf(m.many_tot, c2, 2, "totals");
+                m.many_cap = nn;
+            }
+        }
+        ManyGraph &G = ctx->many;
+        std::vector<int> ids(mol_ids, mol_ids + nmol), fns(functional, functional + nmol);
+        if (!(G.exec && G.mols == ids && G.fns == fns && G.precision == precision && G.branches == W &&
+              G.budget == budget)) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            G.exec = nullptr;
+            if (!G.fork) check(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming), "event");
+            while ((int)G.join.size() < W) {
+                cudaEvent_t e;
+                check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+                G.join.push_back(e);
+            }
+            Profiler quiet;
+            cudaStream_t o = ctx->stream;
+            check(cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed), "begin capture");
+            cudaGraph_t graph = nullptr;
+            try {
+                check(cudaEventRecord(G.fork, o), "fork");
+                for (int b = 0; b < W; ++b) check(cudaStreamWaitEvent(ctx->branch_ws[b].stream, G.fork, 0), "fork");
+                for (int b = 0; b < W; ++b)
+                    for (int k : br[b]) {
+                        Molecule &m = *ms[k];
+                        enqueue(ctx->branch_ws[b], m, *sch[k], m.many_P, functional[k], precision, 0,
+                                m.plan.nbatch(), m.many_V, false, ctx->branch_ws[b].stream, &quiet, m.many_tot);
+                    }
+                for (int b = 0; b < W; ++b) {
+                    check(cudaEventRecord(G.join[b], ctx->branch_ws[b].stream), "join");
+                    check(cudaStreamWaitEvent(o, G.join[b], 0), "join");
+                }
+            } catch (...) {
+                cudaStreamEndCapture(o, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                throw;
+            }
+            check(cudaStreamEndCapture(o, &graph), "end capture");
+            cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            check(e, "instantiate graph");
+            G.mols = ids;
+            G.fns = fns;
+            G.precision = precision;
+            G.branches = W;
+            G.budget = budget;
+            for (int c = 0; c < GBXC_NKERNEL; ++c) G.launches[c] = quiet.launches[c];
+        }
+        cudaStream_t o = ctx->stream;
+        for (int k = 0; k < nmol; ++k) {
+            size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
+            check(cudaMemcpyAsync(ms[k]->many_P, P[k], nn * 8, cudaMemcpyDefault, o), "copy P");
+        }
+        long long total = 0;
+        for (int c = 0; c < GBXC_NKERNEL; ++c) {
+            ctx->prof.launches[c] += G.launches[c];
+            total += G.launches[c];
+        }
+        ctx->prof.begin(GBXC_K_OTHER, o);
+        check(cudaGraphLaunch(G.exec, o), "graph launch");
+        ctx->prof.end(GBXC_K_OTHER, o, 0);
+        std::vector<double> tot(2 * (size_t)nmol);
+        for (int k = 0; k < nmol; ++k) {
+            size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
+            check(cudaMemcpyAsync(&tot[2 * k], ms[k]->many_tot, 16, cudaMemcpyDeviceToHost, o), "copy E");
+            if (Vxc && Vxc[k]) check(cudaMemcpyAsync(Vxc[k], ms[k]->many_V, nn * 8, cudaMemcpyDefault, o), "copy V");
+        }
+        check(cudaStreamSynchronize(o), "integrate many");
+        (void)total;
+        if (precision == GBXC_MIXED)
+            for (int b = 0; b < W; ++b) {
+                int werr = 0;
+                check(mixed_read_error(ctx->branch_ws[b].mixed, &werr, ctx->branch_ws[b].stream), "status");
+                if (werr) return fail(ctx, GBXC_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
+            }
+        for (int k = 0; k < nmol; ++k) {
+            if (Exc) Exc[k] = tot[2 * k];
+            if (Nel) Nel[k] = tot[2 * k + 1];
+        }
+        return GBXC_OK;
+    });
+}
+
+int gbxc_serve_start(gbxc_ctx *ctx, int nslots, size_t arena_bytes) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(ctx->device >= 0, "serving needs a device context");
+        REQUIRE(nslots >= 1 && nslots <= 64, "nslots must be in 1..64");
+        Server &S = ctx->srv;
+        REQUIRE(!S.running, "the server is already running");
+        size_t cap = arena_bytes ? arena_bytes : scratch_budget(ctx);
+        cudaError_t e = cudaMalloc(&S.arena_mem, cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            S.arena_mem = nullptr;
+            return fail(ctx, GBXC_ENOMEM, "serving arena allocation failed");
+        }
+        S.arena.init(S.arena_mem, cap);
+        S.nslots = nslots;
+        S.slot_budget = std::max<size_t>(cap / (size_t)nslots / 2, (size_t)16 << 20);
+        S.streams.assign(nslots, nullptr);
+        S.done_ev.assign(nslots, nullptr);
+        S.pin.assign(nslots, nullptr);
+        S.pin_cap.assign(nslots, 0);
+        S.slot_req.assign(nslots, nullptr);
+        S.slot_ws.assign(nslots, Workspace{});
+        for (int k = 0; k < nslots; ++k) {
+            check(cudaStreamCreateWithFlags(&S.streams[k], cudaStreamNonBlocking), "stream");
+            check(cudaEventCreateWithFlags(&S.done_ev[k], cudaEventDisableTiming), "event");
+        }
+        check(mixed_init(ctx->ws.mixed), "tensor-map encoder");
+        S.admitted = S.completed = 0;
+        S.stop = false;
+        S.running = true;
+        S.thread = std::thread(server_loop, ctx);
+        return GBXC_OK;
+    });
+}
+
+int gbxc_serve_stop(gbxc_ctx *ctx) {
+    if (!ctx) return GBXC_EINVAL;
+    if (ctx->device < 0) return GBXC_EINVAL;
+    server_stop(ctx);   // joins the scheduler: must not hold the context lock here
+    return GBXC_OK;
+}
+
+int gbxc_submit(gbxc_ctx *ctx, int mol, const double *P, int functional, int precision, long long *ticket) {
+    if (!ctx || !P || !ticket) return GBXC_EINVAL;
+    Server &S = ctx->srv;
+    auto r = std::make_shared<Request>();
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        ctx->err.clear();
+        if (!S.running) return fail(ctx, GBXC_ENOTREADY, "the server is not running");
+        auto it = ctx->mols.find(mol);
+        if (it == ctx->mols.end()) return fail(ctx, GBXC_ENOENT, "unknown molecule id");
+        if (!it->second->has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
+        if (functional != GBXC_SLATER && functional != GBXC_PBE) return fail(ctx, GBXC_EINVAL, "unknown functional");
+        if (precision != GBXC_FP64 && precision != GBXC_MIXED) return fail(ctx, GBXC_EINVAL, "unknown precision");
+        size_t nn = (size_t)it->second->nbf * it->second->nbf;
+        try {
+            r->P.assign(P, P + nn);
+        } catch (const std::bad_alloc &) {
+            return fail(ctx, GBXC_ENOMEM, "host allocation failed");
+        }
+    }
+    r->mol = mol;
+    r->functional = functional;
+    r->precision = precision;
+    r->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> q(S.qmu);
+    r->ticket = S.next_ticket++;
+    S.tickets[r->ticket] = r;
+    S.queue.push_back(r);
+    *ticket = r->ticket;
+    S.cv.notify_all();
+    return GBXC_OK;
+}
+
+int gbxc_wait(gbxc_ctx *ctx, long long ticket, double timeout_s, double *Exc, double *Vxc, double *Nel,
+              double *latency_s) {
+    if (!ctx) return GBXC_EINVAL;
+    Server &S = ctx->srv;
+    std::unique_lock<std::mutex> q(S.qmu);
+    auto it = S.tickets.find(ticket);
+    if (it == S.tickets.end()) return GBXC_ENOENT;
+    std::shared_ptr<Request> r = it->second;
+    auto deadline = std::chrono::steady_clock::now() +
+                    std::chrono::microseconds((long long)(std::max(timeout_s, 0.0) * 1e6));
+    while (r->state != 2) {
+        if (S.cv.wait_until(q, deadline) == std::cv_status::timeout && r->state != 2) return GBXC_ETIMEOUT;
+    }
+    S.tickets.erase(ticket);
+    q.unlock();
+    if (r->status != GBXC_OK) {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        ctx->err = r->err;
+        return r->status;
+    }
+    if (Exc) *Exc = r->E;
+    if (Nel) *Nel = r->N;
+    if (Vxc) std::memcpy(Vxc, r->V.data(), r->V.size() * 8);
+    if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    return GBXC_OK;
+}
+
+int gbxc_serve_stats(gbxc_ctx *ctx, long long *queued, long long *running, long long *completed,
+                     size_t *arena_free, size_t *arena_cap) {
+    if (!ctx) return GBXC_EINVAL;
+    Server &S = ctx->srv;
+    std::lock_guard<std::mutex> q(S.qmu);
+    long long run = 0;
+    for (auto &r : S.slot_req)
+        if (r) ++run;
+    if (queued) *queued = (long long)S.queue.size();
+    if (running) *running = run;
+    if (completed) *completed = S.completed;
+    if (arena_free) *arena_free = S.running ? S.arena.free_bytes() : 0;
+    if (arena_cap) *arena_cap = S.running ? S.arena.cap : 0;
+    return GBXC_OK;
 }
 
 int gbxc_profile_enable(gbxc_ctx *ctx, int on) {

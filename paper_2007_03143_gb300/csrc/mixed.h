@@ -61,8 +61,13 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
 void free_mixed_schedule(MixedSchedule &s);
 void free_mixed_resident(MixedResident &r);
 void free_mixed_ctx(MixedCtx &c);
-cudaError_t mixed_prepare(MixedCtx &c, MixedResident &r, const MixedSchedule &s, const double *P,
-                          int nbf, cudaStream_t st);
+// Driver entry point of the tensor-map encoder and kernel attributes (idempotent).
+cudaError_t mixed_init(MixedCtx &c);
+// Allocations of one in-flight mixed integration (call outside stream capture) ...
+cudaError_t mixed_reserve(MixedCtx &c, const MixedSchedule &s, int nbf);
+size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf);
+// ... and its per-call preparation on `st` (P to double-float, error word reset).
+cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st);
 cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
                                const MixedSchedule &s, int chunk_index, cudaStream_t st);
 // Device error word of the mixed kernels (nonzero after a bounded wait expired).

@@ -769,14 +769,29 @@ void free_mixed_ctx(MixedCtx &c) {
     c = MixedCtx{};
 }
 
-cudaError_t mixed_prepare(MixedCtx &c, MixedResident &, const MixedSchedule &s, const double *P, int nbf,
-                          cudaStream_t st) {
+cudaError_t mixed_init(MixedCtx &c) {
     if (!c.encode_fn) {
         cudaDriverEntryPointQueryResult q;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &c.encode_fn, 12000,
                                                          cudaEnableDefault, &q);
         if (e != cudaSuccess || !c.encode_fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
     }
+    static bool attr_set = false;
+    if (!attr_set) {
+        using LX = GemmSmem<NSL, NSL, XSTAGES>;
+        using LV = GemmSmem<NSL, NSL, VSTAGES>;
+        cudaError_t e = cudaFuncSetAttribute(xgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LX::TOTAL);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(vgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LV::TOTAL);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t mixed_reserve(MixedCtx &c, const MixedSchedule &s, int nbf) {
+    cudaError_t e0 = mixed_init(c);
+    if (e0 != cudaSuccess) return e0;
     if (!c.d_err) {
         cudaError_t e = cudaMalloc(&c.d_err, sizeof(int));
         if (e != cudaSuccess) return e;
@@ -785,11 +800,18 @@ cudaError_t mixed_prepare(MixedCtx &c, MixedResident &, const MixedSchedule &s, 
     if (e != cudaSuccess) return e;
     e = grow(c.pexp, c.pexp_cap, (size_t)std::max<int64_t>(s.max_pexp, 1));
     if (e != cudaSuccess) return e;
+    return grow(c.pdf, c.pdf_cap, (size_t)std::max<int64_t>(2 * (int64_t)nbf * nbf, 1));
+}
+
+size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf) {
+    return (size_t)std::max<int64_t>(s.max_prows, 1) * 32 * NSL * 2 + (size_t)std::max<int64_t>(s.max_pexp, 1) * 4 +
+           (size_t)2 * nbf * nbf * 4;
+}
+
+cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st) {
     int64_t nn = (int64_t)nbf * nbf;
-    e = grow(c.pdf, c.pdf_cap, (size_t)std::max<int64_t>(2 * nn, 1));
-    if (e != cudaSuccess) return e;
     if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, c.pdf, c.pdf + nn, nn);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
 }
@@ -828,12 +850,6 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     if (err != cudaSuccess) return err;
     using LX = GemmSmem<NSL, NSL, XSTAGES>;
     using LV = GemmSmem<NSL, NSL, VSTAGES>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(xgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LX::TOTAL);
-        cudaFuncSetAttribute(vgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LV::TOTAL);
-        attr_set = true;
-    }
     Profiler &P = *a.prof;
     P.begin(GBXC_K_PGATHER, st);
     pslice_kernel<<<dim3(ch.j1 - ch.j0 + 1, (ch.max_np + 3) / 4), 128, 0, st>>>(a, m);

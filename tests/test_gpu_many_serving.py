@@ -1,0 +1,124 @@
+"""Batching form (one CUDA-graph launch over many molecules) and serving form (continuous
+batching) against single-molecule gbxc_integrate, through the C-ABI.  The same kernels run in
+every form, so results agree to rounding order: |dE| <= 1e-10 Eh and max |dV| <= 1e-9."""
+import numpy as np
+import pytest
+
+import xcinputs as X
+
+from gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+SPEC = X.GridSpec(24, 10, 20, "ssf", 200)
+
+
+def _molecules(G, ctx, sizes, seed0):
+    out = []
+    for k, nw in enumerate(sizes):
+        mol = X.water_cluster(nw, seed0 + k)
+        b = X.make_basis(mol)
+        S = X.overlap_matrix(b)
+        P = X.density_matrix(S, 5 * nw, seed0 + 100 + k)
+        mid, nbf = G.gbxc_load_basis(ctx.h, mol.xyz, mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff)
+        G.gbxc_load_grid(ctx.h, mid, SPEC.nrad, SPEC.ntheta, SPEC.nphi, SPEC.partition, SPEC.max_batch)
+        out.append((mid, nbf, P))
+    return out
+
+
+def _alone(G, ctx, mid, nbf, P, fn, prec):
+    V = np.zeros((nbf, nbf))
+    E, N = G.gbxc_integrate(ctx.h, mid, P, fn, prec, V)
+    return E, N, V
+
+
+@pytest.fixture(scope="module")
+def setup():
+    G = need_gpu()
+    ctx = G.Context(0)
+    mols = _molecules(G, ctx, [1, 3, 2, 4, 1, 2], 7000)
+    yield G, ctx, mols
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_many_matches_single(setup, prec):
+    G, ctx, mols = setup
+    fns = ["pbe", "slater", "pbe", "pbe", "slater", "pbe"]
+    ref = [_alone(G, ctx, mid, nbf, P, fn, prec) for (mid, nbf, P), fn in zip(mols, fns)]
+    for call in range(2):    # the second call replays the captured graph
+        Vs = [np.zeros((nbf, nbf)) for (_, nbf, _) in mols]
+        E, N = G.gbxc_integrate_many(ctx.h, [m[0] for m in mols], [m[2] for m in mols], fns, prec, Vs)
+        for k in range(len(mols)):
+            assert abs(E[k] - ref[k][0]) <= 1e-10, (call, k)
+            assert abs(N[k] - ref[k][1]) <= 1e-10, (call, k)
+            assert np.max(np.abs(Vs[k] - ref[k][2])) <= 1e-9, (call, k)
+    # new densities through the same graph
+    P2 = [0.5 * m[2] for m in mols]
+    E2, _ = G.gbxc_integrate_many(ctx.h, [m[0] for m in mols], P2, fns, prec)
+    for k, (mid, nbf, P) in enumerate(mols):
+        e, _, _ = _alone(G, ctx, mid, nbf, P2[k], fns[k], prec)
+        assert abs(E2[k] - e) <= 1e-10
+
+
+def test_serving_alone_equals_in_the_mix(setup):
+    G, ctx, mols = setup
+    rng = np.random.default_rng(0)
+    reqs = []
+    for r in range(24):
+        k = int(rng.integers(len(mols)))
+        fn = "slater" if r % 4 == 0 else "pbe"
+        prec = "mixed" if r % 3 else "fp64"
+        reqs.append((k, fn, prec, mols[k][2] * (1.0 + 0.01 * r)))
+    alone = []
+    for k, fn, prec, P in reqs:
+        mid, nbf, _ = mols[k]
+        alone.append(_alone(G, ctx, mid, nbf, P, fn, prec))
+    G.gbxc_serve_start(ctx.h, 3, 1 << 30)
+    try:
+        tickets = [G.gbxc_submit(ctx.h, mols[k][0], P, fn, prec) for k, fn, prec, P in reqs]
+        for t, (k, fn, prec, P), ref in zip(tickets, reqs, alone):
+            V = np.zeros_like(ref[2])
+            E, N, lat = G.gbxc_wait(ctx.h, t, 120.0, V)
+            assert abs(E - ref[0]) <= 1e-10
+            assert abs(N - ref[1]) <= 1e-10
+            assert np.max(np.abs(V - ref[2])) <= 1e-9
+            assert lat > 0
+        st = G.gbxc_serve_stats(ctx.h)
+        assert st["completed"] == len(reqs) and st["queued"] == 0 and st["running"] == 0
+        assert st["arena_free"] == st["arena_cap"]      # every region returned to the arena
+        with pytest.raises(G.GbxcError) as e:
+            G.gbxc_wait(ctx.h, tickets[0], 0.1)
+        assert e.value.code == G.GBXC_ENOENT
+    finally:
+        G.gbxc_serve_stop(ctx.h)
+
+
+def test_serving_admission_by_footprint(setup):
+    # an arena that fits one request at a time still serves every request, in order
+    G, ctx, mols = setup
+    G.gbxc_serve_start(ctx.h, 4, 96 << 20)
+    try:
+        mid, nbf, P = mols[3]
+        ts = [G.gbxc_submit(ctx.h, mid, P, "pbe", "fp64") for _ in range(5)]
+        E = [G.gbxc_wait(ctx.h, t, 120.0)[0] for t in ts]
+        assert max(E) - min(E) <= 1e-12
+        e_alone, _, _ = _alone(G, ctx, mid, nbf, P, "pbe", "fp64")
+        assert abs(E[0] - e_alone) <= 1e-10
+    finally:
+        G.gbxc_serve_stop(ctx.h)
+
+
+def test_serving_rejects_bad_requests(setup):
+    G, ctx, mols = setup
+    with pytest.raises(G.GbxcError):           # not running
+        G.gbxc_submit(ctx.h, mols[0][0], mols[0][2])
+    G.gbxc_serve_start(ctx.h, 2, 256 << 20)
+    try:
+        with pytest.raises(G.GbxcError):
+            G.gbxc_submit(ctx.h, 987654, mols[0][2])
+        t = G.gbxc_submit(ctx.h, mols[0][0], mols[0][2], "pbe", "mixed")
+        E, N, lat = G.gbxc_wait(ctx.h, t, 60.0)
+        assert np.isfinite(E)
+    finally:
+        G.gbxc_serve_stop(ctx.h)
