@@ -120,7 +120,8 @@ def _src_hash(names):
 
 KERNEL_SOURCES = {"xgemm": ["fp64_path.cu"], "vgemm": ["fp64_path.cu"], "colloc": ["fp64_path.cu"],
                   "rho_z": ["fp64_path.cu"], "mixed_xgemm": ["mixed_path.cu", "umma.cuh"],
-                  "mixed_vgemm": ["mixed_path.cu", "umma.cuh"]}
+                  "mixed_vgemm": ["mixed_path.cu", "umma.cuh"], "mixed_rho_z": ["mixed_path.cu", "dfloat.cuh"],
+                  "mixed_colloc": ["mixed_path.cu", "dfloat.cuh"], "mixed_vslice": ["mixed_path.cu"]}
 
 
 def _traffic(kernel, form):
@@ -137,6 +138,45 @@ def _traffic(kernel, form):
     if e.get("src_hash") != _src_hash(srcs):
         return None
     return e.get("bytes_per_launch")
+
+
+# Per-unit work of each kernel class (the unit is one batch's (point, function) element, or
+# 2 m n^2 flops for a contraction).  Contractions: algorithmic flops 2 m n^2 each; the mixed
+# form issues 15 bf16 slice products per term, so its tensor work is 15 x 2 m n^2.
+# Streaming steps: the bytes of the step's inputs and outputs at the precision the form
+# carries (double-float = 8 B per value in the mixed form, float64 = 8 B):
+#   colloc  writes Phi and grad Phi (4 values) [+ 5 bf16 Phi slices in the mixed form]
+#   rho_z   reads Phi, grad Phi, X (5 values), writes Z (1 value)
+#   vslice  reads Z and Phi (2 values), writes 10 bf16 slices
+STREAM_BYTES = {"fp64": {"colloc": 32, "rho_z": 48},
+                "mixed": {"colloc": 32 + 10, "rho_z": 48, "vslice": 16 + 20}}
+
+
+def roofline(kind, ms, form, info, peaks, peak_src):
+    if ms <= 0:
+        return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}
+    if kind in ("xgemm", "vgemm"):
+        flops = 2.0 * info["sum_mn2"]
+        if form == "fp64":
+            ach = flops / (ms / 1e3) / 1e12
+            r = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz",
+                 "algorithmic_per_unit": "2 m n^2 flops per batch"}
+        else:
+            ach = 15.0 * flops / (ms / 1e3) / 1e12
+            r = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                 "peak_source": f"{peak_src} bf16 burst",
+                 "algorithmic_per_unit": "15 bf16 slice products x 2 m n^2 flops per batch"}
+    elif kind in STREAM_BYTES.get(form, {}):
+        nbytes = STREAM_BYTES[form][kind] * info["sum_mn"]
+        ach = nbytes / (ms / 1e3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "peak_source": f"{peak_src} copy bandwidth",
+             "algorithmic_per_unit": f"{STREAM_BYTES[form][kind]} B per (point, function) element"}
+    else:
+        return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
 
 
 def oracle_setup(w):
@@ -195,6 +235,136 @@ def run_reference(args):
     return 0
 
 
+def _water_pool(G, ctx, sizes, seed0, spec):
+    """Register seeded water clusters of the given sizes; returns [(mol id, nbf, npts, P)]."""
+    out = []
+    for k, nw in enumerate(sizes):
+        mol = X.water_cluster(nw, seed0 + k)
+        b = X.make_basis(mol)
+        S = X.overlap_matrix(b)
+        P = X.density_matrix(S, 5 * nw, seed0 + 5000 + k)
+        mid, nbf = G.gbxc_load_basis(ctx.h, mol.xyz, mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff)
+        npts, _ = G.gbxc_load_grid(ctx.h, mid, spec.nrad, spec.ntheta, spec.nphi, spec.partition,
+                                   spec.max_batch, spec.eta, spec.mk_alpha)
+        out.append((mid, nbf, npts, P))
+    return out
+
+
+def run_many(args):
+    """Batching form: one CUDA-graph launch over many molecules of uneven size."""
+    import torch
+    import paper_2007_03143_gb300 as G
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4000)
+    sizes = [int(v) for v in rng.integers(1, args.max_waters + 1, size=args.nmol)]
+    spec = X.GridSpec(75, 16, 32, "ssf", 512)
+    ctx = G.Context(0)
+    pool = _water_pool(G, ctx, sizes, 40000, spec)
+    ids = [p[0] for p in pool]
+    Ps = [torch.tensor(p[3], device="cuda") for p in pool]
+    fns = ["pbe"] * len(pool)
+    npts = sum(p[2] for p in pool)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        for _ in range(args.warmup):
+            G.gbxc_integrate_many(ctx.h, ids, Ps, fns, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            E, N = G.gbxc_integrate_many(ctx.h, ids, Ps, fns, prec)
+        dt = (time.perf_counter() - t0) / args.steps
+        res[prec] = {"value": npts / dt, "ms_per_step": dt * 1e3, "E": E}
+    dE = float(np.max(np.abs(res["mixed"]["E"] - res["fp64"]["E"])))
+    line = {"mode": "many", "metric": "grid pts/s, one CUDA-graph launch over many molecules", "unit": UNIT,
+            "value": res["mixed"]["value"], "ms_per_step": res["mixed"]["ms_per_step"],
+            "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"]},
+            "max_dE_xc_mixed_vs_fp64": dE, "n_molecules": len(pool), "waters": sizes, "npts": npts,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "timing": "wall clock around the call (inputs resident on the device)"}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def run_serve(args):
+    """Serving form: Poisson stream of requests from a pool of resident molecules."""
+    import threading
+    import torch
+    import paper_2007_03143_gb300 as G
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5000)
+    sizes = [int(v) for v in rng.integers(1, args.max_waters + 1, size=args.pool)]
+    spec = X.GridSpec(75, 16, 32, "ssf", 512)
+    ctx = G.Context(0)
+    pool = _water_pool(G, ctx, sizes, 50000, spec)
+    # float64 per-request path for comparison (one request per molecule, sequential)
+    t0 = time.perf_counter()
+    pts64 = 0
+    for mid, nbf, npts, P in pool[:4]:
+        G.gbxc_integrate(ctx.h, mid, P, "pbe", "fp64")
+        pts64 += npts
+    fp64_rate = pts64 / (time.perf_counter() - t0)
+    G.gbxc_serve_start(ctx.h, args.slots, 0)
+    reqs = []
+    for r in range(args.requests + args.warmup_requests):
+        k = int(rng.integers(len(pool)))
+        fn = "slater" if rng.uniform() < 0.25 else "pbe"
+        P = pool[k][3] * (1.0 + 1e-3 * rng.standard_normal())
+        reqs.append((k, fn, P, float(rng.exponential(1.0 / args.rate))))
+    tickets = []
+    lock = threading.Lock()
+
+    def submitter():
+        t_next = time.perf_counter()
+        for k, fn, P, gap in reqs:
+            t_next += gap
+            while True:
+                d = t_next - time.perf_counter()
+                if d <= 0:
+                    break
+                time.sleep(min(d, 0.002))
+            t = G.gbxc_submit(ctx.h, pool[k][0], P, fn, "mixed")
+            with lock:
+                tickets.append((t, k, time.perf_counter()))
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    lat, done_pts, t_first, t_last = [], 0, None, None
+    i = 0
+    while i < len(reqs):
+        with lock:
+            ready = i < len(tickets)
+            item = tickets[i] if ready else None
+        if not ready:
+            time.sleep(0.0005)
+            continue
+        t, k, ts = item
+        E, N, l = G.gbxc_wait(ctx.h, t, 600.0)
+        if i >= args.warmup_requests:
+            lat.append(l)
+            done_pts += pool[k][2]
+            t_first = ts if t_first is None else t_first
+            t_last = time.perf_counter()
+        i += 1
+    th.join()
+    G.gbxc_serve_stop(ctx.h)
+    lat = sorted(lat)
+    span = t_last - t_first
+    offered = args.rate
+    served = len(lat) / span
+    line = {"mode": "serve", "metric": "p50/p99 latency and grid pts/s of a Poisson request stream",
+            "unit": UNIT, "value": done_pts / span, "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "offered_req_per_s": offered, "served_req_per_s": served, "requests": len(lat),
+            "slots": args.slots, "pool_waters": sizes, "precision": "mixed", "lda_to_pbe": "1:3",
+            "fp64_per_request_path": {"value": fp64_rate, "unit": UNIT}, "data": "synthetic",
+            "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,11 +377,23 @@ def main():
     ap.add_argument("--ref-points", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scratch-mb", type=int, default=0, help="device scratch budget (0 = default)")
+    ap.add_argument("--mode", default="single", choices=["single", "many", "serve"])
+    ap.add_argument("--nmol", type=int, default=64)
+    ap.add_argument("--max-waters", type=int, default=8)
+    ap.add_argument("--pool", type=int, default=16)
+    ap.add_argument("--rate", type=float, default=40.0, help="serving: mean requests per second")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--warmup-requests", type=int, default=20)
+    ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "many":
+        return run_many(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     import torch
     import paper_2007_03143_gb300 as G
@@ -301,27 +483,16 @@ def main():
     # roofline of the dominant kernel class of the headline form
     peaks, peak_src = _peaks()
     prof = R["prof"]
-    compute = {k: v for k, v in prof.items() if k in ("colloc", "xgemm", "rho_z", "vgemm", "pgather")}
+    compute = {k: v for k, v in prof.items() if k in ("colloc", "xgemm", "rho_z", "vgemm", "pgather", "vslice")}
     dom = max(compute, key=lambda k: compute[k][0])
     dom_ms, dom_launch = compute[dom]
-    per_step_flops = 2.0 * info["sum_mn2"]          # 2 m n^2 per batch for either contraction
-    if dom in ("xgemm", "vgemm"):
-        if head == "fp64":
-            achieved = per_step_flops * args.steps / (dom_ms / 1e3) / 1e9
-            roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
-                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
-        else:
-            achieved = 3.0 * per_step_flops * args.steps / (dom_ms / 1e3) / 1e12
-            pk = peaks["bf16_tflops"]
-            roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                    "peak_source": f"{peak_src} bf16 burst (3 bf16 products per split-bf16x3 term)"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None}
+    roof = roofline(dom, dom_ms / args.steps, head, info, peaks, peak_src)
     roof["kernel"] = dom
     roof["launches_per_step"] = dom_launch / args.steps
     roof["ms_per_step"] = dom_ms / args.steps
-    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
     roof["traffic"] = _traffic(dom, head)
+    roof["all_classes"] = {k: roofline(k, v[0] / args.steps, head, info, peaks, peak_src)
+                           for k, v in compute.items() if v[0] > 0}
     launches = sum(v[1] for k, v in prof.items() if k != "weights")
 
     # end to end through the public call with pinned host buffers

@@ -61,8 +61,9 @@ extern "C" {
 #define GBXC_K_VGEMM 4      /* V^j contraction and scatter into V_xc (Eqs. vxc_batch, vxc_inc) */
 #define GBXC_K_FINISH 5     /* symmetrisation and fixed-order E/N reductions */
 #define GBXC_K_PGATHER 6    /* P^j gather/split for the mixed form */
-#define GBXC_K_OTHER 7
-#define GBXC_NKERNEL 8
+#define GBXC_K_OTHER 7       /* whole CUDA-graph launches of gbxc_integrate_many */
+#define GBXC_K_SLICE 8       /* Ozaki slicing of the V-contraction operands (mixed form) */
+#define GBXC_NKERNEL 9
 
 #define GBXC_MAX_PRIM 8     /* primitives per shell */
 #define GBXC_MAX_L 3        /* highest angular momentum (f) */
@@ -96,6 +97,7 @@ typedef struct {
     long long ntiles;        /* 128-point tiles over all batches */
     double sum_mn2;          /* sum_j N_g^j (N_b^j)^2 */
     double work;             /* sum_j W_j of Eq. batch_work */
+    double sum_mn;           /* sum_j N_g^j N_b^j (grid-point x function elements) */
 } gbxc_plan_info;
 
 /* Create a context on CUDA device `device` (device = -1 creates a host-only

@@ -35,7 +35,7 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
             "gbxc_serve_stats"]
-KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "other"]
+KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
 
@@ -58,7 +58,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("natoms", c_int), ("nshell", c_int), ("nbf", c_int), ("npts", c_longlong),
                 ("nbatch", c_int), ("nleaf", c_int), ("nshell_entries", c_longlong),
                 ("nfunc_entries", c_longlong), ("ntiles", c_longlong), ("sum_mn2", c_double),
-                ("work", c_double)]
+                ("work", c_double), ("sum_mn", c_double)]
 
 
 _lib = None

@@ -1040,14 +1040,16 @@ int gbxc_plan_info_get(gbxc_ctx *ctx, int mol, gbxc_plan_info *info) {
         info->nshell_entries = (long long)P.shell_idx.size();
         info->nfunc_entries = (long long)P.func_idx.size();
         info->ntiles = (long long)P.ntiles();
-        double smn = 0, work = 0;
+        double smn = 0, smn1 = 0, work = 0;
         for (int j = 0; j < P.nbatch(); ++j) {
             double mj = (double)(P.batch_ptr[j + 1] - P.batch_ptr[j]);
             double nj = (double)(P.func_ptr[j + 1] - P.func_ptr[j]);
             smn += mj * nj * nj;
+            smn1 += mj * nj;
             work += P.work[j];
         }
         info->sum_mn2 = smn;
+        info->sum_mn = smn1;
         info->work = work;
         return GBXC_OK;
     });

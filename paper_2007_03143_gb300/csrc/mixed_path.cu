@@ -293,10 +293,11 @@ template <int SA, int SB, int STAGES, int NOPS, typename Coords>
 __device__ __forceinline__ void gemm_tile(uint8_t *smem, uint64_t *full, uint64_t *empty, uint64_t *done,
                                           uint32_t tmem, const CUtensorMap *ta, const CUtensorMap *tb,
                                           int nkb, const MmaOp *ops, Coords coords, int *err,
-                                          volatile int *abort_flag) {
+                                          volatile int *abort_flag, int n_cols) {
     using L = GemmSmem<SA, SB, STAGES>;
     const int tid = threadIdx.x;
-    const uint32_t idesc = umma::idesc_bf16(128, BN);
+    // N of the MMAs: the columns this tile still needs, rounded up to 16 (<= BN)
+    const uint32_t idesc = umma::idesc_bf16(128, n_cols);
     if (tid == 0) {
         for (int kb = 0; kb < nkb; ++kb) {
             int s = kb % STAGES;
@@ -399,8 +400,9 @@ __global__ void __launch_bounds__(GEMM_THREADS) xgemm_tc(const __grid_constant__
         ay = (int)(4 * r0 + (int64_t)kb * TILE);
         by = (int)(pofs + (int64_t)kb * np + nc * BN);
     };
+    int ncols = min(BN, ((n - nc * BN) + 15) & ~15);
     gemm_tile<NSL, NSL, XSTAGES, 15>(smem, full, empty, done, tmem, &tax, &tp, np / 32, kXOps, coords, m.err,
-                                     &abort_flag);
+                                     &abort_flag, ncols);
     // epilogue: thread = point (TMEM lane of its warp's quarter), half of the 128 columns
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int quarter = warp & 3, half = warp >> 2;
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) xgemm_tc(const __grid_constant__
     const size_t plane = (size_t)m.rows * TILE;
     uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+        if (nc * BN + c >= n) break;          // warp-uniform: columns past N_b^j were not computed
         float v0[16], v1[16], v2[16], v3[16];
         umma::tmem_ld16(lane_base + c, v0);
         umma::tmem_ld16(lane_base + BN + c, v1);
@@ -497,8 +500,9 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     __syncthreads();
     df cz = d_to_df(ca_d), cbx = d_to_df(bx_d), cby = d_to_df(by_d), cbz = d_to_df(bz_d);
     int lane = i & 31;
+    // rows >= N_b^j of the V operands are never used (they only feed discarded outputs)
 #pragma unroll 2
-    for (int mu = 0; mu < np; ++mu) {
+    for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
         float p0 = phi[o], p1 = phi[plane + o], p2 = phi[2 * plane + o], p3 = phi[3 * plane + o];
         float p4 = phi[4 * plane + o], p5 = phi[5 * plane + o], p6 = phi[6 * plane + o], p7 = phi[7 * plane + o];
@@ -520,7 +524,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
         }
     }
     __syncthreads();
-    for (int mu = i; mu < np; mu += TILE) {
+    for (int mu = i; mu < n; mu += TILE) {
         m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[mu]));
         m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu]));
     }
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
     int64_t rg = a.plan.tile_row[g0] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     int pk = i >> 5, col = i & 31;
-    for (int mu = 0; mu < np; ++mu) {
+    for (int mu = 0; mu < n; ++mu) {
         int ez = -1000, ep = -1000;
         for (int64_t u = g0; u < g1; ++u) {
             int64_t ru = a.plan.tile_row[u] - a.row0;
@@ -611,8 +615,9 @@ __global__ void __launch_bounds__(GEMM_THREADS) vgemm_tc(const __grid_constant__
         ay = (int)(base + mc * BN);
         by = (int)(base + nc * BN);
     };
+    int ncols = min(BN, ((n - nc * BN) + 15) & ~15);
     gemm_tile<NSL, NSL, VSTAGES, 15>(smem, full, empty, done, tmem, &tz, &tphi, (int)(te - tb) * 4, kXOps,
-                                     coords, m.err, &abort_flag);
+                                     coords, m.err, &abort_flag, ncols);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int quarter = warp & 3, half = warp >> 2;
     int mu = mc * BN + quarter * 32 + lane;
@@ -621,6 +626,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) vgemm_tc(const __grid_constant__
     int64_t rg = a.plan.tile_row[tb] - a.row0;     // group exponents live on the first tile
     int ez = (mu < n) ? m.s.zexp[rg + mu] : 0;
     for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+        if (nc * BN + c >= n) break;          // warp-uniform: columns past N_b^j were not computed
         float v0[16], v1[16], v2[16], v3[16];
         umma::tmem_ld16(lane_base + c, v0);
         umma::tmem_ld16(lane_base + BN + c, v1);
@@ -862,8 +868,10 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     P.end(GBXC_K_XGEMM, st);
     P.begin(GBXC_K_RHO_Z, st);
     rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    P.end(GBXC_K_RHO_Z, st);
+    P.begin(GBXC_K_SLICE, st);
     slice_v<<<(unsigned)nt, TILE, 0, st>>>(a, m);
-    P.end(GBXC_K_RHO_Z, st, 2);
+    P.end(GBXC_K_SLICE, st);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, st);
         vgemm_tc<<<(unsigned)a.nvtasks, GEMM_THREADS, LV::TOTAL, st>>>(tz, tph, a, m);
