@@ -23,6 +23,7 @@ struct MixedCtx {
     size_t pexp_cap = 0;
     float *pdf = nullptr;              // P as double-float planes (hi, lo)
     size_t pdf_cap = 0;
+    int num_sms = 0;                   // persistent-GEMM grid size
     int *d_err = nullptr;
 };
 // A shell with every constant split into a double-float pair (hi + lo).
@@ -47,8 +48,10 @@ struct MixedSchedule {
         int64_t prows;                 // rows of the sliced P^j blocks of the chunk
         int64_t pexp_rows;             // sum of padded N_b^j over the chunk's batches
         int max_np;
+        int64_t xtask0, nxtask;        // X-contraction tasks (tile, N chunk) of the chunk
     };
     std::vector<Chunk> chunks;
+    int *d_xtasks = nullptr;           // (tile, N chunk) pairs of every chunk
     int64_t *d_pofs = nullptr;         // per (chunk, batch): first P-slice row
     int64_t *d_pexp_ofs = nullptr;     // per (chunk, batch): first row-exponent entry
     int64_t max_prows = 0, max_pexp = 0;

@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <utility>
 
 #include "mixed.h"
 #include "dfloat.cuh"
@@ -40,7 +41,6 @@ namespace {
 
 constexpr int NSL = 5;          // Ozaki slices (X contraction)
 constexpr int BN = 128;         // N extent of one MMA (functions)
-constexpr int XSTAGES = 2, VSTAGES = 2;
 constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
 // at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
@@ -266,18 +266,11 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
 }
 
 // ---------------------------------------------------------------- tcgen05 GEMM core
-struct MmaOp {
-    unsigned char a, b, acc;
-};
-
-// X contraction: accumulator d holds slice level d = s + t for d = 0, 1, 2 (each an exact
-// integer multiple of 2^-(12+7d) below 2^24 units for K <= 1184), accumulator 3 the rounded
-// remainder of levels 3 and 4.
+// Slice products of one K step, by accumulator: level d = s + t for d = 0, 1, 2 in
+// accumulators 0, 1, 2 (exact: integer multiples of 2^-(12+7d) below 2^24 units for
+// K <= 1184 functions or 1024 points) and levels 3-4 in accumulator 3 (rounded, 2^-21 below
+// level 0).  The issue order is listed in issue_op().
 constexpr int XACC = 4;
-__constant__ MmaOp kXOps[15] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {0, 2, 2}, {1, 1, 2},
-                                {2, 0, 2}, {0, 3, 3}, {1, 2, 3}, {2, 1, 3}, {3, 0, 3},
-                                {0, 4, 3}, {1, 3, 3}, {2, 2, 3}, {3, 1, 3}, {4, 0, 3}};
-// W contraction: the same level scheme with K <= 1024 points per task.
 
 template <int SA, int SB, int STAGES>
 struct GemmSmem {
@@ -287,153 +280,275 @@ struct GemmSmem {
     static constexpr int TOTAL = 1024 + STAGES * STAGE + 256;
 };
 
-// Producer (thread 0) and MMA issuer (thread 32) of one output tile; returns after the
-// final commit has been observed by every thread (or a bounded wait expired).
-template <int SA, int SB, int STAGES, int NOPS, typename Coords>
-__device__ __forceinline__ void gemm_tile(uint8_t *smem, uint64_t *full, uint64_t *empty, uint64_t *done,
-                                          uint32_t tmem, const CUtensorMap *ta, const CUtensorMap *tb,
-                                          int nkb, const MmaOp *ops, Coords coords, int *err,
-                                          volatile int *abort_flag, int n_cols) {
-    using L = GemmSmem<SA, SB, STAGES>;
-    const int tid = threadIdx.x;
-    // N of the MMAs: the columns this tile still needs, rounded up to 16 (<= BN)
-    const uint32_t idesc = umma::idesc_bf16(128, n_cols);
-    if (tid == 0) {
-        for (int kb = 0; kb < nkb; ++kb) {
-            int s = kb % STAGES;
-            if (kb >= STAGES && !umma::mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
-                atomicOr(err, 1);
-                *abort_flag = 1;
-                break;
-            }
-            if (*abort_flag) break;
-            int ay, by;
-            coords(kb, ay, by);
-            umma::mbar_arrive_expect_tx(&full[s], L::STAGE);
-            uint8_t *sa = smem + s * L::STAGE;
-            umma::tma_load_3d(sa, ta, &full[s], 0, ay, 0);
-            umma::tma_load_3d(sa + L::A_BYTES, tb, &full[s], 0, by, 0);
-        }
-    } else if (tid == 32) {
-        uint32_t init = 0;
-        for (int kb = 0; kb < nkb; ++kb) {
-            int s = kb % STAGES;
-            if (!umma::mbar_wait(&full[s], (kb / STAGES) & 1)) {
-                atomicOr(err, 2);
-                *abort_flag = 1;
-                break;
-            }
-            umma::fence_after_sync();
-            uint32_t sa = umma::smem_u32(smem + s * L::STAGE), sb = sa + L::A_BYTES;
-#pragma unroll
-            for (int k16 = 0; k16 < 2; ++k16) {
-#pragma unroll
-                for (int q = 0; q < NOPS; ++q) {
-                    MmaOp op = ops[q];
-                    uint64_t ad = umma::desc_sw64(sa + op.a * 128 * 64 + k16 * 32);
-                    uint64_t bd = umma::desc_sw64(sb + op.b * BN * 64 + k16 * 32);
-                    umma::mma_bf16(tmem + op.acc * BN, ad, bd, idesc, (init >> op.acc) & 1);
-                    init |= 1u << op.acc;
-                }
-            }
-            umma::mma_commit(&empty[s]);
-        }
-        umma::mma_commit(done);
-    }
-    __syncwarp();
-    if (!umma::mbar_wait(done, 0)) atomicOr(err, 4);
-    umma::fence_after_sync();
-    __syncwarp();
+// The 2 x 15 MMAs of one 32-wide K block with compile-time operand offsets.  `first` is 0
+// only for the first K block of a task: then the first product into each accumulator
+// overwrites it (levels 0, 1, 2, 3 start at ops 0, 1, 3, 6).
+template <int Q>
+__device__ __forceinline__ void issue_op(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first,
+                                         int k16) {
+    constexpr int A[15] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+    constexpr int B[15] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+    constexpr int C[15] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+    constexpr bool LEAD[15] = {true, true, false, true, false, false, true, false, false, false,
+                               false, false, false, false, false};
+    const uint64_t ad = a0 + (uint64_t)(A[Q] * (128 * 64 / 16) + k16 * 2);
+    const uint64_t bd = b0 + (uint64_t)(B[Q] * (BN * 64 / 16) + k16 * 2);
+    const uint32_t acc = (LEAD[Q] && k16 == 0) ? first : 1u;
+    umma::mma_bf16(tmem + C[Q] * BN, ad, bd, idesc, acc);
 }
 
-template <int SA, int SB, int STAGES>
-__device__ __forceinline__ void gemm_setup(uint8_t *&smem, uint64_t *&full, uint64_t *&empty, uint64_t *&done,
-                                           uint32_t *&tmem_slot, const CUtensorMap *ta,
-                                           const CUtensorMap *tb, uint32_t ncols) {
-    using L = GemmSmem<SA, SB, STAGES>;
+template <int... Q>
+__device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first,
+                                          int k16, std::integer_sequence<int, Q...>) {
+    (issue_op<Q>(tmem, a0, b0, idesc, first, k16), ...);
+}
+
+__device__ __forceinline__ void issue_slice_mmas(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc,
+                                                 uint32_t first) {
+    issue_ops(tmem, a0, b0, idesc, first, 0, std::make_integer_sequence<int, 15>{});
+    issue_ops(tmem, a0, b0, idesc, first, 1, std::make_integer_sequence<int, 15>{});
+}
+
+// ---------------------------------------------------------------- persistent GEMM
+// One CTA per SM walks tasks blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
+//   warp 0 lane 0  TMA producer; its stage ring runs across task boundaries, so the next
+//                  task's operands stream in while the current task's epilogue runs
+//   warp 1 lane 0  MMA issuer (15 slice products per 16-wide K step into 4 accumulators)
+//   warp 2         owns the tensor-memory allocation (all 512 columns)
+//   warps 4-11     epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31, columns half (w - 4) / 4
+// tmem_full (MMA -> epilogue) and tmem_empty (epilogue -> MMA) hand the accumulators over.
+constexpr int GEMM_THREADS = 384;   // 4 control warps + 8 epilogue warps
+constexpr int GEMM_STAGES = 2;
+using GL = GemmSmem<NSL, NSL, GEMM_STAGES>;
+
+struct XGeom {
+    int64_t t, r0, pofs;
+    int j, jl, n, np, nc;
+};
+__device__ __forceinline__ XGeom x_geom(const ChunkArgs &a, const MixedArgs &m, const int *tasks, int k) {
+    XGeom g;
+    g.t = tasks[2 * k];
+    g.nc = tasks[2 * k + 1];
+    g.j = a.plan.tile_batch[g.t];
+    g.n = (int)(a.plan.func_ptr[g.j + 1] - a.plan.func_ptr[g.j]);
+    g.np = pad32(g.n);
+    g.r0 = a.plan.tile_row[g.t] - a.row0;
+    g.jl = g.j - m.j0;
+    g.pofs = m.pofs[g.jl];
+    return g;
+}
+
+struct VGeom {
+    int64_t tb, te;
+    int j, mc, nc, n, np;
+};
+__device__ __forceinline__ VGeom v_geom(const ChunkArgs &a, const int *tasks, int k) {
+    VGeom g;
+    const int *q = tasks + 5 * k;
+    g.j = q[0];
+    g.mc = q[1];
+    g.nc = q[2];
+    g.tb = q[3];
+    g.te = q[4];
+    g.n = (int)(a.plan.func_ptr[g.j + 1] - a.plan.func_ptr[g.j]);
+    g.np = pad32(g.n);
+    return g;
+}
+
+// KIND 0: X^j = P^j Phi^j tiles (tasks: tile, N chunk).  KIND 1: W^j = Z^T Phi tiles
+// (tasks: batch, row block, column block, tile range).
+template <int KIND>
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_constant__ CUtensorMap ta,
+                                                                   const __grid_constant__ CUtensorMap tb,
+                                                                   ChunkArgs a, MixedArgs m, const int *tasks,
+                                                                   int ntasks) {
     extern __shared__ uint8_t smem_raw[];
     uint32_t base = umma::smem_u32(smem_raw);
-    smem = smem_raw + (((base + 1023) & ~1023u) - base);
-    full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE);
-    empty = full + STAGES;
-    done = empty + STAGES;
-    tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint8_t *smem = smem_raw + (((base + 1023) & ~1023u) - base);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + GEMM_STAGES * GL::STAGE);
+    uint64_t *empty = full + GEMM_STAGES;
+    uint64_t *tfull = empty + GEMM_STAGES;
+    uint64_t *tempty = tfull + 1;
+    uint64_t *drain = tempty + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    __shared__ volatile int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        abort_flag = 0;
+        for (int s = 0; s < GEMM_STAGES; ++s) {
             umma::mbar_init(&full[s], 1);
             umma::mbar_init(&empty[s], 1);
         }
-        umma::mbar_init(done, 1);
+        umma::mbar_init(tfull, 1);
+        umma::mbar_init(tempty, 8);
+        umma::mbar_init(drain, 1);
         umma::fence_mbar_init();
-        umma::prefetch_tmap(ta);
-        umma::prefetch_tmap(tb);
+        umma::prefetch_tmap(&ta);
+        umma::prefetch_tmap(&tb);
     }
-    if ((threadIdx.x >> 5) == 2) umma::tmem_alloc(tmem_slot, ncols);
+    if (warp == 2) umma::tmem_alloc(tmem_slot, XACC * BN);
     __syncthreads();
     umma::fence_after_sync();
-}
+    const uint32_t tmem = *tmem_slot;
 
-// ---------------------------------------------------------------- X contraction
-// CTA (tile t, N chunk nc): X[points 128][functions nc*128 .. +128] over K = N_b^j.
-constexpr int GEMM_THREADS = 256;   // warps 0-3 and 4-7 split the epilogue columns
-
-__global__ void __launch_bounds__(GEMM_THREADS) xgemm_tc(const __grid_constant__ CUtensorMap tax,
-                                                const __grid_constant__ CUtensorMap tp, ChunkArgs a,
-                                                MixedArgs m) {
-    int64_t t = a.t0 + blockIdx.x;
-    int nc = blockIdx.y;
-    int j = a.plan.tile_batch[t];
-    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
-    if (nc * BN >= n) return;
-    int np = pad32(n);
-    int64_t r0 = a.plan.tile_row[t] - a.row0;
-    int jl = j - m.j0;
-    int64_t pofs = m.pofs[jl];
-    uint8_t *smem;
-    uint64_t *full, *empty, *done;
-    uint32_t *tmem_slot;
-    __shared__ int abort_flag;
-    if (threadIdx.x == 0) abort_flag = 0;
-    gemm_setup<NSL, NSL, XSTAGES>(smem, full, empty, done, tmem_slot, &tax, &tp, XACC * BN);
-    uint32_t tmem = *tmem_slot;
-    auto coords = [&](int kb, int &ay, int &by) {
-        ay = (int)(4 * r0 + (int64_t)kb * TILE);
-        by = (int)(pofs + (int64_t)kb * np + nc * BN);
+    auto task_geom = [&](int k, int &nkb, int &ncols) {
+        if (KIND == 0) {
+            XGeom g = x_geom(a, m, tasks, k);
+            nkb = g.np / 32;
+            ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
+        } else {
+            VGeom g = v_geom(a, tasks, k);
+            nkb = (int)(g.te - g.tb) * 4;
+            ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
+        }
     };
-    int ncols = min(BN, ((n - nc * BN) + 15) & ~15);
-    gemm_tile<NSL, NSL, XSTAGES, 15>(smem, full, empty, done, tmem, &tax, &tp, np / 32, kXOps, coords, m.err,
-                                     &abort_flag, ncols);
-    // epilogue: thread = point (TMEM lane of its warp's quarter), half of the 128 columns
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int quarter = warp & 3, half = warp >> 2;
-    int i = quarter * 32 + lane;
-    int ei = m.s.pexp[(t - a.t0) * TILE + i];
-    const int *fexp = m.pexp + m.pexp_ofs[jl];
-    const size_t plane = (size_t)m.rows * TILE;
-    uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
-        if (nc * BN + c >= n) break;          // warp-uniform: columns past N_b^j were not computed
-        float v0[16], v1[16], v2[16], v3[16];
-        umma::tmem_ld16(lane_base + c, v0);
-        umma::tmem_ld16(lane_base + BN + c, v1);
-        umma::tmem_ld16(lane_base + 2 * BN + c, v2);
-        umma::tmem_ld16(lane_base + 3 * BN + c, v3);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            int mu = nc * BN + c + k;
-            if (mu < n) {
-                df x = df_add(df_add(two_sum(v0[k], v1[k]), {v2[k], 0.f}), {v3[k], 0.f});
-                int sc = ei + fexp[mu];
-                size_t o = (size_t)(r0 + mu) * TILE + i;
-                m.s.x[o] = ldexpf(x.h, sc);
-                m.s.x[plane + o] = ldexpf(x.l, sc);
+
+    if (warp == 0) {
+        if (lane == 0) {   // ------------------------------------------------ producer
+            uint32_t gk = 0;
+            for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x) {
+                XGeom xg;
+                VGeom vg;
+                int nkb;
+                if (KIND == 0) {
+                    xg = x_geom(a, m, tasks, k);
+                    nkb = xg.np / 32;
+                } else {
+                    vg = v_geom(a, tasks, k);
+                    nkb = (int)(vg.te - vg.tb) * 4;
+                }
+                for (int kb = 0; kb < nkb; ++kb, ++gk) {
+                    int s = gk % GEMM_STAGES;
+                    if (gk >= GEMM_STAGES && !umma::mbar_wait(&empty[s], ((gk / GEMM_STAGES) - 1) & 1)) {
+                        atomicOr(m.err, 1);
+                        abort_flag = 1;
+                        break;
+                    }
+                    int ay, by;
+                    if (KIND == 0) {
+                        ay = (int)(4 * xg.r0 + (int64_t)kb * TILE);
+                        by = (int)(xg.pofs + (int64_t)kb * xg.np + xg.nc * BN);
+                    } else {
+                        int64_t t = vg.tb + kb / 4;
+                        int64_t b0 = 4 * (a.plan.tile_row[t] - a.row0) + (int64_t)(kb % 4) * vg.np;
+                        ay = (int)(b0 + vg.mc * BN);
+                        by = (int)(b0 + vg.nc * BN);
+                    }
+                    umma::mbar_arrive_expect_tx(&full[s], GL::STAGE);
+                    uint8_t *sa = smem + s * GL::STAGE;
+                    umma::tma_load_3d(sa, &ta, &full[s], 0, ay, 0);
+                    umma::tma_load_3d(sa + GL::A_BYTES, &tb, &full[s], 0, by, 0);
+                }
             }
         }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ------------------------------------------------ MMA issuer
+            uint32_t gk = 0, tau = 0;
+            for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x, ++tau) {
+                int nkb, ncols;
+                task_geom(k, nkb, ncols);
+                const uint32_t idesc = umma::idesc_bf16(128, ncols);
+                if (tau > 0 && !umma::mbar_wait(tempty, (tau - 1) & 1)) {
+                    atomicOr(m.err, 2);
+                    abort_flag = 1;
+                    break;
+                }
+                umma::fence_after_sync();
+                for (int kb = 0; kb < nkb; ++kb, ++gk) {
+                    int s = gk % GEMM_STAGES;
+                    if (!umma::mbar_wait(&full[s], (gk / GEMM_STAGES) & 1)) {
+                        atomicOr(m.err, 2);
+                        abort_flag = 1;
+                        break;
+                    }
+                    umma::fence_after_sync();
+                    uint32_t sa = umma::smem_u32(smem + s * GL::STAGE), sb = sa + GL::A_BYTES;
+                    // descriptors of slice 0 at K step 0; every other operand is a fixed
+                    // offset in 16-byte units (slice tiles 8 KB apart, K steps 32 B apart)
+                    const uint64_t a0 = umma::desc_sw64(sa), b0 = umma::desc_sw64(sb);
+                    const uint32_t first = kb == 0 ? 0u : 1u;
+                    issue_slice_mmas(tmem, a0, b0, idesc, first);
+                    umma::mma_commit(&empty[s]);
+                }
+                if (abort_flag) break;
+                umma::mma_commit(tfull);
+            }
+            // every MMA this thread issued has completed before the allocation is released
+            umma::mma_commit(drain);
+            if (!umma::mbar_wait(drain, 0)) atomicOr(m.err, 4);
+        }
+    } else if (warp >= 4) {   // ---------------------------------------------- epilogue
+        const int q = warp & 3, half = (warp - 4) >> 2;
+        const int i = q * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        const size_t plane = (size_t)m.rows * TILE;
+        uint32_t tau = 0;
+        for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x, ++tau) {
+            if (!umma::mbar_wait(tfull, tau & 1)) {
+                atomicOr(m.err, 4);
+                abort_flag = 1;
+                break;
+            }
+            umma::fence_after_sync();
+            __syncwarp();
+            if (KIND == 0) {
+                XGeom g = x_geom(a, m, tasks, k);
+                int ei = m.s.pexp[(g.t - a.t0) * TILE + i];
+                const int *fexp = m.pexp + m.pexp_ofs[g.jl];
+                for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+                    if (g.nc * BN + c >= g.n) break;   // warp-uniform
+                    float v0[16], v1[16], v2[16], v3[16];
+                    umma::tmem_ld16(lane_base + c, v0);
+                    umma::tmem_ld16(lane_base + BN + c, v1);
+                    umma::tmem_ld16(lane_base + 2 * BN + c, v2);
+                    umma::tmem_ld16(lane_base + 3 * BN + c, v3);
+#pragma unroll
+                    for (int kk = 0; kk < 16; ++kk) {
+                        int mu = g.nc * BN + c + kk;
+                        if (mu < g.n) {
+                            df x = df_add(df_add(two_sum(v0[kk], v1[kk]), {v2[kk], 0.f}), {v3[kk], 0.f});
+                            int sc = ei + fexp[mu];
+                            size_t o = (size_t)(g.r0 + mu) * TILE + i;
+                            m.s.x[o] = ldexpf(x.h, sc);
+                            m.s.x[plane + o] = ldexpf(x.l, sc);
+                        }
+                    }
+                }
+            } else {
+                VGeom g = v_geom(a, tasks, k);
+                const int *F = a.plan.func_idx + a.plan.func_ptr[g.j];
+                int mu = g.mc * BN + i;
+                size_t rowg = (mu < g.n) ? (size_t)F[mu] * a.nbf : 0;
+                int64_t rg = a.plan.tile_row[g.tb] - a.row0;   // group exponents on the first tile
+                int ez = (mu < g.n) ? m.s.zexp[rg + mu] : 0;
+                for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+                    if (g.nc * BN + c >= g.n) break;   // warp-uniform
+                    float v0[16], v1[16], v2[16], v3[16];
+                    umma::tmem_ld16(lane_base + c, v0);
+                    umma::tmem_ld16(lane_base + BN + c, v1);
+                    umma::tmem_ld16(lane_base + 2 * BN + c, v2);
+                    umma::tmem_ld16(lane_base + 3 * BN + c, v3);
+                    if (mu < g.n) {
+#pragma unroll
+                        for (int kk = 0; kk < 16; ++kk) {
+                            int nu = g.nc * BN + c + kk;
+                            if (nu < g.n) {
+                                df w = df_add(df_add(two_sum(v0[kk], v1[kk]), {v2[kk], 0.f}), {v3[kk], 0.f});
+                                int sc = ez + m.s.fexp[rg + nu];
+                                atomicAdd(&a.Vacc[rowg + F[nu]], (double)ldexpf(w.h, sc) + (double)ldexpf(w.l, sc));
+                            }
+                        }
+                    }
+                }
+            }
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(tempty);
+        }
     }
-    umma::fence_before_sync();
     __syncthreads();
+    umma::fence_after_sync();
     if (warp == 2) umma::tmem_dealloc(tmem, XACC * BN);
-    (void)np;
 }
 
 // ---------------------------------------------------------------- rho, functional, Z
@@ -588,67 +703,6 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
     }
 }
 
-// ---------------------------------------------------------------- V contraction
-// Task (batch j, row block mc, column block nc, tiles [tb, te)): W[mu][nu] =
-// sum over the tiles' points of Z[i][mu] Phi[i][nu], then V_acc[F_mu][F_nu] += W.
-__global__ void __launch_bounds__(GEMM_THREADS) vgemm_tc(const __grid_constant__ CUtensorMap tz,
-                                                const __grid_constant__ CUtensorMap tphi, ChunkArgs a,
-                                                MixedArgs m) {
-    const int *task = a.vtasks + 5 * blockIdx.x;
-    int j = task[0], mc = task[1], nc = task[2];
-    int64_t tb = task[3], te = task[4];
-    int64_t f0 = a.plan.func_ptr[j];
-    int n = (int)(a.plan.func_ptr[j + 1] - f0);
-    int np = pad32(n);
-    const int *F = a.plan.func_idx + f0;
-    uint8_t *smem;
-    uint64_t *full, *empty, *done;
-    uint32_t *tmem_slot;
-    __shared__ int abort_flag;
-    if (threadIdx.x == 0) abort_flag = 0;
-    gemm_setup<NSL, NSL, VSTAGES>(smem, full, empty, done, tmem_slot, &tz, &tphi, XACC * BN);
-    uint32_t tmem = *tmem_slot;
-    auto coords = [&](int kb, int &ay, int &by) {
-        int64_t t = tb + kb / 4;
-        int pk = kb % 4;
-        int64_t base = 4 * (a.plan.tile_row[t] - a.row0) + (int64_t)pk * np;
-        ay = (int)(base + mc * BN);
-        by = (int)(base + nc * BN);
-    };
-    int ncols = min(BN, ((n - nc * BN) + 15) & ~15);
-    gemm_tile<NSL, NSL, VSTAGES, 15>(smem, full, empty, done, tmem, &tz, &tphi, (int)(te - tb) * 4, kXOps,
-                                     coords, m.err, &abort_flag, ncols);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int quarter = warp & 3, half = warp >> 2;
-    int mu = mc * BN + quarter * 32 + lane;
-    uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    size_t rowg = (mu < n) ? (size_t)F[mu] * a.nbf : 0;
-    int64_t rg = a.plan.tile_row[tb] - a.row0;     // group exponents live on the first tile
-    int ez = (mu < n) ? m.s.zexp[rg + mu] : 0;
-    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
-        if (nc * BN + c >= n) break;          // warp-uniform: columns past N_b^j were not computed
-        float v0[16], v1[16], v2[16], v3[16];
-        umma::tmem_ld16(lane_base + c, v0);
-        umma::tmem_ld16(lane_base + BN + c, v1);
-        umma::tmem_ld16(lane_base + 2 * BN + c, v2);
-        umma::tmem_ld16(lane_base + 3 * BN + c, v3);
-        if (mu < n) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                int nu = nc * BN + c + k;
-                if (nu < n) {
-                    df w = df_add(df_add(two_sum(v0[k], v1[k]), {v2[k], 0.f}), {v3[k], 0.f});
-                    int sc = ez + m.s.fexp[rg + nu];
-                    atomicAdd(&a.Vacc[rowg + F[nu]], (double)ldexpf(w.h, sc) + (double)ldexpf(w.l, sc));
-                }
-            }
-        }
-    }
-    umma::fence_before_sync();
-    __syncthreads();
-    if (warp == 2) umma::tmem_dealloc(tmem, XACC * BN);
-}
-
 // ---------------------------------------------------------------- host helpers
 CUtensorMap make_map(MixedCtx &c, void *ptr, int64_t rows, int64_t plane_rows, int planes, cudaError_t &err) {
     CUtensorMap mp;
@@ -699,6 +753,7 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
                           const std::vector<int64_t> &chunk_t1, MixedSchedule &s) {
     free_mixed_schedule(s);
     std::vector<int64_t> pofs, pexp;
+    std::vector<int> xt;
     for (size_t c = 0; c < chunk_t0.size(); ++c) {
         MixedSchedule::Chunk ch;
         ch.j0 = plan.tile_batch[chunk_t0[c]];
@@ -706,6 +761,16 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
         ch.prow0 = (int64_t)pofs.size();
         int64_t rows = 0, erows = 0;
         ch.max_np = 0;
+        ch.xtask0 = (int64_t)xt.size() / 2;
+        for (int64_t t = chunk_t0[c]; t < chunk_t1[c]; ++t) {
+            int j = plan.tile_batch[t];
+            int64_t n = plan.func_ptr[j + 1] - plan.func_ptr[j];
+            for (int nc = 0; (int64_t)nc * BN < n; ++nc) {
+                xt.push_back((int)t);
+                xt.push_back(nc);
+            }
+        }
+        ch.nxtask = (int64_t)xt.size() / 2 - ch.xtask0;
         for (int j = ch.j0; j <= ch.j1; ++j) {
             int64_t n = plan.func_ptr[j + 1] - plan.func_ptr[j];
             int64_t np = pad_funcs(n);
@@ -721,6 +786,10 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
         s.max_pexp = std::max(s.max_pexp, erows);
         s.chunks.push_back(ch);
     }
+    if (!xt.empty()) {
+        cudaMalloc(&s.d_xtasks, xt.size() * sizeof(int));
+        cudaMemcpy(s.d_xtasks, xt.data(), xt.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
     if (!pofs.empty()) {
         cudaMalloc(&s.d_pofs, pofs.size() * sizeof(int64_t));
         cudaMemcpy(s.d_pofs, pofs.data(), pofs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -730,6 +799,7 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
 }
 
 void free_mixed_schedule(MixedSchedule &s) {
+    cudaFree(s.d_xtasks);
     cudaFree(s.d_pofs);
     cudaFree(s.d_pexp_ofs);
     s = MixedSchedule{};
@@ -784,13 +854,18 @@ cudaError_t mixed_init(MixedCtx &c) {
     }
     static bool attr_set = false;
     if (!attr_set) {
-        using LX = GemmSmem<NSL, NSL, XSTAGES>;
-        using LV = GemmSmem<NSL, NSL, VSTAGES>;
-        cudaError_t e = cudaFuncSetAttribute(xgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LX::TOTAL);
+        cudaError_t e = cudaFuncSetAttribute(gemm_persistent<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GL::TOTAL);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(vgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LV::TOTAL);
+        e = cudaFuncSetAttribute(gemm_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, GL::TOTAL);
         if (e != cudaSuccess) return e;
         attr_set = true;
+    }
+    if (!c.num_sms) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        c.num_sms = sms > 0 ? sms : 1;
     }
     return cudaSuccess;
 }
@@ -854,8 +929,6 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NSL, err);
     CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NSL, err);
     if (err != cudaSuccess) return err;
-    using LX = GemmSmem<NSL, NSL, XSTAGES>;
-    using LV = GemmSmem<NSL, NSL, VSTAGES>;
     Profiler &P = *a.prof;
     P.begin(GBXC_K_PGATHER, st);
     pslice_kernel<<<dim3(ch.j1 - ch.j0 + 1, (ch.max_np + 3) / 4), 128, 0, st>>>(a, m);
@@ -863,9 +936,14 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     P.begin(GBXC_K_COLLOC, st);
     colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells);
     P.end(GBXC_K_COLLOC, st);
-    P.begin(GBXC_K_XGEMM, st);
-    xgemm_tc<<<dim3((unsigned)nt, (unsigned)((a.max_nfunc + BN - 1) / BN)), GEMM_THREADS, LX::TOTAL, st>>>(tax, tp, a, m);
-    P.end(GBXC_K_XGEMM, st);
+    const int *xtasks = s.d_xtasks + 2 * ch.xtask0;
+    int nx = (int)ch.nxtask;
+    if (nx > 0) {
+        P.begin(GBXC_K_XGEMM, st);
+        gemm_persistent<0><<<(unsigned)std::min(nx, c.num_sms), GEMM_THREADS, GL::TOTAL, st>>>(tax, tp, a, m,
+                                                                                                xtasks, nx);
+        P.end(GBXC_K_XGEMM, st);
+    }
     P.begin(GBXC_K_RHO_Z, st);
     rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
     P.end(GBXC_K_RHO_Z, st);
@@ -874,7 +952,8 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     P.end(GBXC_K_SLICE, st);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, st);
-        vgemm_tc<<<(unsigned)a.nvtasks, GEMM_THREADS, LV::TOTAL, st>>>(tz, tph, a, m);
+        gemm_persistent<1><<<(unsigned)std::min(a.nvtasks, c.num_sms), GEMM_THREADS, GL::TOTAL, st>>>(
+            tz, tph, a, m, a.vtasks, a.nvtasks);
         P.end(GBXC_K_VGEMM, st);
     }
     return cudaGetLastError();
