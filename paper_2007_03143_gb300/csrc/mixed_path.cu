@@ -1,7 +1,7 @@
 // Tensor-core form of the batched integration (Algorithm 4) on sm_103a.
 //
 // The two contractions run on the 5th-generation tensor cores (tcgen05.mma, bf16 inputs,
-// fp32 accumulators in tensor memory, operands staged by TMA with the 64-byte swizzle):
+// fp32 accumulators in tensor memory, operands staged by TMA with the 32-byte swizzle):
 //
 //   X^j = P^j Phi^j (Eq. x_mat)      Ozaki-style exact slicing.  Every row of Phi (a grid
 //        point) and of P^j (a function) is scaled by a power of two to |v| <= 1 and cut
@@ -48,8 +48,8 @@ constexpr double kFp32RhoMin = 1e300;
 
 // ---------------------------------------------------------------- scratch layout
 struct MixedSlabs {
-    float *phi;             // 8 planes [rows][128]: phi, dx, dy, dz as (hi, lo) pairs
-    float *x;               // 2 planes [rows][128]: X as (hi, lo)
+    float2 *phi;            // 4 planes [rows][128]: phi, dx, dy, dz as (hi, lo) pairs
+    float2 *x;              // 1 plane [rows][128]: X (later Z) as (hi, lo)
     __nv_bfloat16 *ax;      // 5 planes [4 rows][32]: Phi slices, K-blocked per tile
     __nv_bfloat16 *vz;      // 5 planes [4 rows][32]: Z slices, point-blocked per tile
     __nv_bfloat16 *vphi;    // 5 planes [4 rows][32]: Phi slices, point-blocked per tile
@@ -61,9 +61,9 @@ struct MixedSlabs {
 __host__ __device__ inline MixedSlabs mixed_slabs(void *base, int64_t rows) {
     char *p = static_cast<char *>(base);
     MixedSlabs s;
-    s.phi = reinterpret_cast<float *>(p);
+    s.phi = reinterpret_cast<float2 *>(p);
     p += (size_t)8 * rows * TILE * 4;
-    s.x = reinterpret_cast<float *>(p);
+    s.x = reinterpret_cast<float2 *>(p);
     p += (size_t)2 * rows * TILE * 4;
     s.ax = reinterpret_cast<__nv_bfloat16 *>(p);
     p += (size_t)NSL * rows * TILE * 2;
@@ -95,15 +95,26 @@ struct MixedArgs {
 __device__ __forceinline__ int pad32(int n) { return (n + 31) & ~31; }
 
 // ---------------------------------------------------------------- slicing
+// 2^k as a float for k in [-126, 127] (built from the exponent field)
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+// x 2^k for |k| <= 252 as two exact power-of-two products; the intermediate lies between x
+// and the result in magnitude, so nothing is lost that the result could hold
+__device__ __forceinline__ float scale2(float x, int k) {
+    const int k1 = k >> 1;
+    return __fmul_rn(__fmul_rn(x, pow2f(k1)), pow2f(k - k1));
+}
+
 // v = (h + l) 2^-e with |v| <= 1 -> five slices q_s 2^-(6+7s), q_s integers in [-64, 64],
-// float32 only: each q_s is the rounding of the running remainder to the slice grid; the
-// subtraction is exact (Sterbenz) and two-sum folds the low word back in.
+// float32 only: each q_s is the rounding of the running remainder to the slice grid (the
+// power-of-two products are exact), the subtraction is exact (Sterbenz) and two-sum folds
+// the low word back in.
 __device__ __forceinline__ void slice5(float h, float l, int e, float out[NSL]) {
-    float rh = ldexpf(h, -e), rl = ldexpf(l, -e);
+    float rh = scale2(h, -e), rl = scale2(l, -e);
 #pragma unroll
     for (int s = 0; s < NSL; ++s) {
-        const int sh = 6 + 7 * s;
-        float qs = ldexpf(rintf(ldexpf(rh, sh)), -sh);
+        const float up = (float)(1ull << (6 + 7 * s));
+        float qs = __fmul_rn(rintf(__fmul_rn(rh, up)), 1.0f / up);
         out[s] = qs;
         rh = __fsub_rn(rh, qs);
         float ss = __fadd_rn(rh, rl);
@@ -190,7 +201,7 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
     df px = d_to_df(live ? a.plan.x[p] : 0.0), py = d_to_df(live ? a.plan.y[p] : 0.0),
        pz = d_to_df(live ? a.plan.z[p] : 0.0);
     const size_t plane = (size_t)m.rows * TILE;
-    float *phi = m.s.phi;
+    float2 *phi = m.s.phi;
     int64_t s0 = a.plan.shell_ptr[j], s1 = a.plan.shell_ptr[j + 1];
     int row = 0;
     float mx = 0.f;
@@ -229,10 +240,7 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
                 if (nn > 0) v[3] = df_add(v[3], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm]), zp[nn - 1]), (float)nn), g));
                 size_t o = (size_t)(r0 + row) * TILE + i;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    phi[(2 * c) * plane + o] = live ? v[c].h : 0.f;
-                    phi[(2 * c + 1) * plane + o] = live ? v[c].l : 0.f;
-                }
+                for (int c = 0; c < 4; ++c) phi[c * plane + o] = live ? make_float2(v[c].h, v[c].l) : make_float2(0.f, 0.f);
                 if (live) mx = fmaxf(mx, fabsf(v[0].h));
                 ++row;
             }
@@ -240,27 +248,33 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
     for (; row < np; ++row) {
         size_t o = (size_t)(r0 + row) * TILE + i;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) phi[c * plane + o] = 0.0f;
+        for (int c = 0; c < 4; ++c) phi[c * plane + o] = make_float2(0.f, 0.f);
     }
     int e = exp_of(mx);
     m.s.pexp[(t - a.t0) * TILE + i] = e;
     // Ozaki slices of this point's row of Phi: K block kb -> row 4 r0 + 128 kb + i, 32 values
     for (int kb = 0; kb < np / 32; ++kb) {
-        __align__(16) __nv_bfloat16 buf[NSL][32];
-        for (int c = 0; c < 32; ++c) {
-            size_t o = (size_t)(r0 + kb * 32 + c) * TILE + i;
-            float q[NSL];
-            slice5(phi[o], phi[plane + o], e, q);
+        const size_t orow = (size_t)(4 * r0 + (int64_t)kb * TILE + i) * 32;
+#pragma unroll 1
+        for (int c8 = 0; c8 < 32; c8 += 8) {   // 8 functions -> one 16-byte store per slice
+            uint32_t w[NSL][4];
 #pragma unroll
-            for (int s = 0; s < NSL; ++s) buf[s][c] = __float2bfloat16_rn(q[s]);
-        }
-        size_t orow = (size_t)(4 * r0 + (int64_t)kb * TILE + i) * 32;
+            for (int pr = 0; pr < 4; ++pr) {
+                size_t o = (size_t)(r0 + kb * 32 + c8 + 2 * pr) * TILE + i;
+                float2 f0 = phi[o], f1 = phi[o + TILE];
+                float q0[NSL], q1[NSL];
+                slice5(f0.x, f0.y, e, q0);
+                slice5(f1.x, f1.y, e, q1);
 #pragma unroll
-        for (int s = 0; s < NSL; ++s) {
-            uint4 *dst = reinterpret_cast<uint4 *>(m.s.ax + (size_t)s * plane + orow);
-            const uint4 *src = reinterpret_cast<const uint4 *>(buf[s]);
+                for (int s = 0; s < NSL; ++s) {
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(q0[s], q1[s]);
+                    w[s][pr] = *reinterpret_cast<uint32_t *>(&b2);
+                }
+            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = src[q];
+            for (int s = 0; s < NSL; ++s)
+                *reinterpret_cast<uint4 *>(m.s.ax + (size_t)s * plane + orow + c8) =
+                    make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
         }
     }
 }
@@ -271,54 +285,61 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
 // K <= 1184 functions or 1024 points) and levels 3-4 in accumulator 3 (rounded, 2^-21 below
 // level 0).  The issue order is listed in issue_op().
 constexpr int XACC = 4;
+constexpr int BM = 128;                        // M extent of one MMA (points or functions)
+constexpr int NBUF = 512 / (XACC * BN);        // accumulator sets that fit in tensor memory
+constexpr int TMEM_COLS = NBUF * XACC * BN;    // 512 columns
+static_assert(NBUF >= 1 && NBUF <= 2, "one or two accumulator sets");
 
+// One pipeline stage holds one 16-wide K step of every slice of both operands: the global
+// rows of 32 values are fetched as two 32-byte halves with the 32-byte swizzle.
 template <int SA, int SB, int STAGES>
 struct GemmSmem {
-    static constexpr int A_BYTES = SA * 128 * 64;
-    static constexpr int B_BYTES = SB * BN * 64;
+    static constexpr int A_BYTES = SA * BM * 32;
+    static constexpr int B_BYTES = SB * BN * 32;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int TOTAL = 1024 + STAGES * STAGE + 256;
 };
 
-// The 2 x 15 MMAs of one 32-wide K block with compile-time operand offsets.  `first` is 0
-// only for the first K block of a task: then the first product into each accumulator
-// overwrites it (levels 0, 1, 2, 3 start at ops 0, 1, 3, 6).
+// The 15 MMAs of one 16-wide K step with compile-time operand offsets.  `first` is 0 only
+// for the first K step of a task: then the first product into each accumulator overwrites
+// it (levels 0, 1, 2, 3 start at ops 0, 1, 3, 6).
 template <int Q>
-__device__ __forceinline__ void issue_op(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first,
-                                         int k16) {
+__device__ __forceinline__ void issue_op(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first) {
     constexpr int A[15] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
     constexpr int B[15] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
     constexpr int C[15] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3};
     constexpr bool LEAD[15] = {true, true, false, true, false, false, true, false, false, false,
                                false, false, false, false, false};
-    const uint64_t ad = a0 + (uint64_t)(A[Q] * (128 * 64 / 16) + k16 * 2);
-    const uint64_t bd = b0 + (uint64_t)(B[Q] * (BN * 64 / 16) + k16 * 2);
-    const uint32_t acc = (LEAD[Q] && k16 == 0) ? first : 1u;
+    const uint64_t ad = a0 + (uint64_t)(A[Q] * (BM * 32 / 16));
+    const uint64_t bd = b0 + (uint64_t)(B[Q] * (BN * 32 / 16));
+    const uint32_t acc = LEAD[Q] ? first : 1u;
     umma::mma_bf16(tmem + C[Q] * BN, ad, bd, idesc, acc);
 }
 
 template <int... Q>
 __device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first,
-                                          int k16, std::integer_sequence<int, Q...>) {
-    (issue_op<Q>(tmem, a0, b0, idesc, first, k16), ...);
+                                          std::integer_sequence<int, Q...>) {
+    (issue_op<Q>(tmem, a0, b0, idesc, first), ...);
 }
 
 __device__ __forceinline__ void issue_slice_mmas(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc,
                                                  uint32_t first) {
-    issue_ops(tmem, a0, b0, idesc, first, 0, std::make_integer_sequence<int, 15>{});
-    issue_ops(tmem, a0, b0, idesc, first, 1, std::make_integer_sequence<int, 15>{});
+    issue_ops(tmem, a0, b0, idesc, first, std::make_integer_sequence<int, 15>{});
 }
 
 // ---------------------------------------------------------------- persistent GEMM
 // One CTA per SM walks tasks blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
-//   warp 0 lane 0  TMA producer; its stage ring runs across task boundaries, so the next
-//                  task's operands stream in while the current task's epilogue runs
+//   warp 0 lane 0  TMA producer; its stage ring runs across task boundaries
 //   warp 1 lane 0  MMA issuer (15 slice products per 16-wide K step into 4 accumulators)
 //   warp 2         owns the tensor-memory allocation (all 512 columns)
-//   warps 4-11     epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31, columns half (w - 4) / 4
-// tmem_full (MMA -> epilogue) and tmem_empty (epilogue -> MMA) hand the accumulators over.
+//   warps 4-11     epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one half of the
+//                  columns of each accumulator
+// Task tau uses accumulator set tau % NBUF (with two sets the epilogue of one task overlaps
+// the MMAs of the next); tmem_full[b] (MMA -> epilogue) and tmem_empty[b] (epilogue -> MMA)
+// hand set b over.  The epilogue is kept short: a 4-term combine, power-of-two scaling
+// from exponent bits, one store or one float64 atomic per element.
 constexpr int GEMM_THREADS = 384;   // 4 control warps + 8 epilogue warps
-constexpr int GEMM_STAGES = 2;
+constexpr int GEMM_STAGES = BN == 128 ? 5 : 7;
 using GL = GemmSmem<NSL, NSL, GEMM_STAGES>;
 
 struct XGeom {
@@ -355,8 +376,27 @@ __device__ __forceinline__ VGeom v_geom(const ChunkArgs &a, const int *tasks, in
     return g;
 }
 
-// KIND 0: X^j = P^j Phi^j tiles (tasks: tile, N chunk).  KIND 1: W^j = Z^T Phi tiles
-// (tasks: batch, row block, column block, tile range).
+// The four level accumulators as an unnormalised pair: levels 0 + 1 by two-sum (exact), levels
+// 2-4 added to the low word (|v2| + |v3| < 2^-13 of level 0, so the rounding stays below 2^-37)
+__device__ __forceinline__ df combine4(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+    df s = two_sum(__uint_as_float(v0), __uint_as_float(v1));
+    return {s.h, __fadd_rn(s.l, __fadd_rn(__uint_as_float(v2), __uint_as_float(v3)))};
+}
+
+// (double)f * 2^k from the bit fields, for a zero or normal float and a result exponent that
+// stays normal (k in [-296, 258] here); partial sums of the slice products are multiples of
+// 2^-40 or zero, so subnormal inputs do not occur
+__device__ __forceinline__ double f2d_scaled(float f, int k) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t ex = (b >> 23) & 0xFFu;
+    if (ex == 0) return 0.0;
+    const uint64_t d = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(ex + 896 + k) << 52) |
+                       ((uint64_t)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// KIND 0: X^j = P^j Phi^j tiles (tasks: point tile, 64-function column chunk).
+// KIND 1: W^j = Z^T Phi tiles (tasks: batch, 128-row block, 64-column block, tile range).
 template <int KIND>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_constant__ CUtensorMap ta,
                                                                    const __grid_constant__ CUtensorMap tb,
@@ -367,9 +407,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
     uint8_t *smem = smem_raw + (((base + 1023) & ~1023u) - base);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + GEMM_STAGES * GL::STAGE);
     uint64_t *empty = full + GEMM_STAGES;
-    uint64_t *tfull = empty + GEMM_STAGES;
-    uint64_t *tempty = tfull + 1;
-    uint64_t *drain = tempty + 1;
+    uint64_t *tfull = empty + GEMM_STAGES;   // [NBUF]
+    uint64_t *tempty = tfull + NBUF;         // [NBUF]
+    uint64_t *drain = tempty + NBUF;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     __shared__ volatile int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -379,29 +419,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             umma::mbar_init(&full[s], 1);
             umma::mbar_init(&empty[s], 1);
         }
-        umma::mbar_init(tfull, 1);
-        umma::mbar_init(tempty, 8);
+        for (int b = 0; b < NBUF; ++b) {
+            umma::mbar_init(&tfull[b], 1);
+            umma::mbar_init(&tempty[b], 8);
+        }
         umma::mbar_init(drain, 1);
         umma::fence_mbar_init();
         umma::prefetch_tmap(&ta);
         umma::prefetch_tmap(&tb);
     }
-    if (warp == 2) umma::tmem_alloc(tmem_slot, XACC * BN);
+    if (warp == 2) umma::tmem_alloc(tmem_slot, TMEM_COLS);
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-
-    auto task_geom = [&](int k, int &nkb, int &ncols) {
-        if (KIND == 0) {
-            XGeom g = x_geom(a, m, tasks, k);
-            nkb = g.np / 32;
-            ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
-        } else {
-            VGeom g = v_geom(a, tasks, k);
-            nkb = (int)(g.te - g.tb) * 4;
-            ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
-        }
-    };
 
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
@@ -409,15 +439,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x) {
                 XGeom xg;
                 VGeom vg;
-                int nkb;
+                int nks;   // 16-wide K steps: two per stored block of 32
                 if (KIND == 0) {
                     xg = x_geom(a, m, tasks, k);
-                    nkb = xg.np / 32;
+                    nks = xg.np / 16;
                 } else {
                     vg = v_geom(a, tasks, k);
-                    nkb = (int)(vg.te - vg.tb) * 4;
+                    nks = (int)(vg.te - vg.tb) * 8;
                 }
-                for (int kb = 0; kb < nkb; ++kb, ++gk) {
+                for (int ks = 0; ks < nks; ++ks, ++gk) {
+                    const int kb = ks >> 1, kx = (ks & 1) * 16;
                     int s = gk % GEMM_STAGES;
                     if (gk >= GEMM_STAGES && !umma::mbar_wait(&empty[s], ((gk / GEMM_STAGES) - 1) & 1)) {
                         atomicOr(m.err, 1);
@@ -431,13 +462,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     } else {
                         int64_t t = vg.tb + kb / 4;
                         int64_t b0 = 4 * (a.plan.tile_row[t] - a.row0) + (int64_t)(kb % 4) * vg.np;
-                        ay = (int)(b0 + vg.mc * BN);
+                        ay = (int)(b0 + vg.mc * BM);
                         by = (int)(b0 + vg.nc * BN);
                     }
                     umma::mbar_arrive_expect_tx(&full[s], GL::STAGE);
                     uint8_t *sa = smem + s * GL::STAGE;
-                    umma::tma_load_3d(sa, &ta, &full[s], 0, ay, 0);
-                    umma::tma_load_3d(sa + GL::A_BYTES, &tb, &full[s], 0, by, 0);
+                    umma::tma_load_3d(sa, &ta, &full[s], kx, ay, 0);
+                    umma::tma_load_3d(sa + GL::A_BYTES, &tb, &full[s], kx, by, 0);
                 }
             }
         }
@@ -445,16 +476,26 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
         if (lane == 0) {   // ------------------------------------------------ MMA issuer
             uint32_t gk = 0, tau = 0;
             for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x, ++tau) {
-                int nkb, ncols;
-                task_geom(k, nkb, ncols);
-                const uint32_t idesc = umma::idesc_bf16(128, ncols);
-                if (tau > 0 && !umma::mbar_wait(tempty, (tau - 1) & 1)) {
+                int nks, ncols;
+                if (KIND == 0) {
+                    XGeom g = x_geom(a, m, tasks, k);
+                    nks = g.np / 16;
+                    ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
+                } else {
+                    VGeom g = v_geom(a, tasks, k);
+                    nks = (int)(g.te - g.tb) * 8;
+                    ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
+                }
+                const uint32_t idesc = umma::idesc_bf16(BM, ncols);
+                const uint32_t b = tau % NBUF, use = tau / NBUF;
+                if (tau >= NBUF && !umma::mbar_wait(&tempty[b], (use - 1) & 1)) {
                     atomicOr(m.err, 2);
                     abort_flag = 1;
                     break;
                 }
                 umma::fence_after_sync();
-                for (int kb = 0; kb < nkb; ++kb, ++gk) {
+                const uint32_t tacc = tmem + b * (XACC * BN);
+                for (int ks = 0; ks < nks; ++ks, ++gk) {
                     int s = gk % GEMM_STAGES;
                     if (!umma::mbar_wait(&full[s], (gk / GEMM_STAGES) & 1)) {
                         atomicOr(m.err, 2);
@@ -463,15 +504,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     }
                     umma::fence_after_sync();
                     uint32_t sa = umma::smem_u32(smem + s * GL::STAGE), sb = sa + GL::A_BYTES;
-                    // descriptors of slice 0 at K step 0; every other operand is a fixed
-                    // offset in 16-byte units (slice tiles 8 KB apart, K steps 32 B apart)
-                    const uint64_t a0 = umma::desc_sw64(sa), b0 = umma::desc_sw64(sb);
-                    const uint32_t first = kb == 0 ? 0u : 1u;
-                    issue_slice_mmas(tmem, a0, b0, idesc, first);
+                    // descriptors of slice 0; every other slice is a fixed offset in 16-byte
+                    // units (slice tiles BM x 32 B and BN x 32 B apart)
+                    const uint64_t a0 = umma::desc_sw32(sa), b0 = umma::desc_sw32(sb);
+                    issue_slice_mmas(tacc, a0, b0, idesc, ks == 0 ? 0u : 1u);
                     umma::mma_commit(&empty[s]);
                 }
                 if (abort_flag) break;
-                umma::mma_commit(tfull);
+                umma::mma_commit(&tfull[b]);
             }
             // every MMA this thread issued has completed before the allocation is released
             umma::mma_commit(drain);
@@ -480,62 +520,70 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
     } else if (warp >= 4) {   // ---------------------------------------------- epilogue
         const int q = warp & 3, half = (warp - 4) >> 2;
         const int i = q * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        const size_t plane = (size_t)m.rows * TILE;
         uint32_t tau = 0;
         for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x, ++tau) {
-            if (!umma::mbar_wait(tfull, tau & 1)) {
+            const uint32_t b = tau % NBUF, use = tau / NBUF;
+            if (!umma::mbar_wait(&tfull[b], use & 1)) {
                 atomicOr(m.err, 4);
                 abort_flag = 1;
                 break;
             }
             umma::fence_after_sync();
             __syncwarp();
+            const uint32_t lane_base = tmem + b * (XACC * BN) + ((uint32_t)(q * 32) << 16);
             if (KIND == 0) {
                 XGeom g = x_geom(a, m, tasks, k);
                 int ei = m.s.pexp[(g.t - a.t0) * TILE + i];
                 const int *fexp = m.pexp + m.pexp_ofs[g.jl];
+#pragma unroll 1
                 for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
                     if (g.nc * BN + c >= g.n) break;   // warp-uniform
-                    float v0[16], v1[16], v2[16], v3[16];
-                    umma::tmem_ld16(lane_base + c, v0);
-                    umma::tmem_ld16(lane_base + BN + c, v1);
-                    umma::tmem_ld16(lane_base + 2 * BN + c, v2);
-                    umma::tmem_ld16(lane_base + 3 * BN + c, v3);
+                    uint32_t v0[16], v1[16], v2[16], v3[16];
+                    umma::tmem_ld16_nw(lane_base + c, v0);
+                    umma::tmem_ld16_nw(lane_base + BN + c, v1);
+                    umma::tmem_ld16_nw(lane_base + 2 * BN + c, v2);
+                    umma::tmem_ld16_nw(lane_base + 3 * BN + c, v3);
+                    umma::tmem_wait_ld();
 #pragma unroll
                     for (int kk = 0; kk < 16; ++kk) {
                         int mu = g.nc * BN + c + kk;
                         if (mu < g.n) {
-                            df x = df_add(df_add(two_sum(v0[kk], v1[kk]), {v2[kk], 0.f}), {v3[kk], 0.f});
-                            int sc = ei + fexp[mu];
-                            size_t o = (size_t)(g.r0 + mu) * TILE + i;
-                            m.s.x[o] = ldexpf(x.h, sc);
-                            m.s.x[plane + o] = ldexpf(x.l, sc);
+                            df x = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
+                            const int sc = min(max(ei + fexp[mu], -252), 252);
+                            const float s1 = pow2f(sc >> 1), s2 = pow2f(sc - (sc >> 1));
+                            m.s.x[(size_t)(g.r0 + mu) * TILE + i] =
+                                make_float2(__fmul_rn(__fmul_rn(x.h, s1), s2), __fmul_rn(__fmul_rn(x.l, s1), s2));
                         }
                     }
                 }
             } else {
+                // W^j is added transposed (V_acc[nu][mu] += W[mu][nu]); the final
+                // V = V_acc + V_acc^T is unchanged, and the 32 lanes of a warp (consecutive
+                // mu) then update neighbouring words of one row of V_acc
                 VGeom g = v_geom(a, tasks, k);
                 const int *F = a.plan.func_idx + a.plan.func_ptr[g.j];
-                int mu = g.mc * BN + i;
-                size_t rowg = (mu < g.n) ? (size_t)F[mu] * a.nbf : 0;
+                int mu = g.mc * BM + i;
+                size_t colg = (mu < g.n) ? (size_t)F[mu] : 0;
                 int64_t rg = a.plan.tile_row[g.tb] - a.row0;   // group exponents on the first tile
                 int ez = (mu < g.n) ? m.s.zexp[rg + mu] : 0;
+#pragma unroll 1
                 for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
                     if (g.nc * BN + c >= g.n) break;   // warp-uniform
-                    float v0[16], v1[16], v2[16], v3[16];
-                    umma::tmem_ld16(lane_base + c, v0);
-                    umma::tmem_ld16(lane_base + BN + c, v1);
-                    umma::tmem_ld16(lane_base + 2 * BN + c, v2);
-                    umma::tmem_ld16(lane_base + 3 * BN + c, v3);
+                    uint32_t v0[16], v1[16], v2[16], v3[16];
+                    umma::tmem_ld16_nw(lane_base + c, v0);
+                    umma::tmem_ld16_nw(lane_base + BN + c, v1);
+                    umma::tmem_ld16_nw(lane_base + 2 * BN + c, v2);
+                    umma::tmem_ld16_nw(lane_base + 3 * BN + c, v3);
+                    umma::tmem_wait_ld();
                     if (mu < g.n) {
 #pragma unroll
                         for (int kk = 0; kk < 16; ++kk) {
                             int nu = g.nc * BN + c + kk;
                             if (nu < g.n) {
-                                df w = df_add(df_add(two_sum(v0[kk], v1[kk]), {v2[kk], 0.f}), {v3[kk], 0.f});
+                                df w = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
                                 int sc = ez + m.s.fexp[rg + nu];
-                                atomicAdd(&a.Vacc[rowg + F[nu]], (double)ldexpf(w.h, sc) + (double)ldexpf(w.l, sc));
+                                atomicAdd(&a.Vacc[(size_t)F[nu] * a.nbf + colg],
+                                          f2d_scaled(w.h, sc) + f2d_scaled(w.l, sc));
                             }
                         }
                     }
@@ -543,12 +591,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             }
             umma::fence_before_sync();
             __syncwarp();
-            if (lane == 0) umma::mbar_arrive(tempty);
+            if (lane == 0) umma::mbar_arrive(&tempty[b]);
         }
     }
     __syncthreads();
     umma::fence_after_sync();
-    if (warp == 2) umma::tmem_dealloc(tmem, XACC * BN);
+    if (warp == 2) umma::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // ---------------------------------------------------------------- rho, functional, Z
@@ -561,7 +609,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     int np = pad32(n);
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
-    const float *phi = m.s.phi;
+    const float2 *phi = m.s.phi;
     if (np > 1184) {   // the exponent scratch below holds 1184 rows; larger batches are rejected
         if (i == 0) atomicOr(m.err, 8);
         return;
@@ -570,14 +618,13 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
 #pragma unroll 2
     for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        float x0 = m.s.x[o], x1 = m.s.x[plane + o];
-        float p0 = phi[o], p1 = phi[plane + o], p2 = phi[2 * plane + o], p3 = phi[3 * plane + o];
-        float p4 = phi[4 * plane + o], p5 = phi[5 * plane + o], p6 = phi[6 * plane + o], p7 = phi[7 * plane + o];
-        df x{x0, x1};
-        rho = df_add(rho, df_mul({p0, p1}, x));
-        gx = df_add(gx, df_mul({p2, p3}, x));
-        gy = df_add(gy, df_mul({p4, p5}, x));
-        gz = df_add(gz, df_mul({p6, p7}, x));
+        const float2 xv = m.s.x[o], f0 = phi[o], f1 = phi[plane + o], f2 = phi[2 * plane + o],
+                     f3 = phi[3 * plane + o];
+        df x{xv.x, xv.y};
+        rho = df_add(rho, df_mul({f0.x, f0.y}, x));
+        gx = df_add(gx, df_mul({f1.x, f1.y}, x));
+        gy = df_add(gy, df_mul({f2.x, f2.y}, x));
+        gz = df_add(gz, df_mul({f3.x, f3.y}, x));
     }
     double r = df_to_d(rho);
     double dx = 2.0 * df_to_d(gx), dy = 2.0 * df_to_d(gy), dz = 2.0 * df_to_d(gz);
@@ -619,15 +666,13 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
 #pragma unroll 2
     for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        float p0 = phi[o], p1 = phi[plane + o], p2 = phi[2 * plane + o], p3 = phi[3 * plane + o];
-        float p4 = phi[4 * plane + o], p5 = phi[5 * plane + o], p6 = phi[6 * plane + o], p7 = phi[7 * plane + o];
-        df z = df_mul(cz, {p0, p1});
-        z = df_add(z, df_mul(cbx, {p2, p3}));
-        z = df_add(z, df_mul(cby, {p4, p5}));
-        z = df_add(z, df_mul(cbz, {p6, p7}));
-        m.s.x[o] = z.h;
-        m.s.x[plane + o] = z.l;
-        float az = fabsf(z.h), ap = fabsf(p0);
+        const float2 f0 = phi[o], f1 = phi[plane + o], f2 = phi[2 * plane + o], f3 = phi[3 * plane + o];
+        df z = df_mul(cz, {f0.x, f0.y});
+        z = df_add(z, df_mul(cbx, {f1.x, f1.y}));
+        z = df_add(z, df_mul(cby, {f2.x, f2.y}));
+        z = df_add(z, df_mul(cbz, {f3.x, f3.y}));
+        m.s.x[o] = make_float2(z.h, z.l);
+        float az = fabsf(z.h), ap = fabsf(f0.x);
 #pragma unroll
         for (int q = 16; q > 0; q >>= 1) {
             az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
@@ -687,8 +732,9 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
         }
         size_t o = (size_t)(r0 + mu) * TILE + i;
         float qz[NSL], qp[NSL];
-        slice5(m.s.x[o], m.s.x[plane + o], ez, qz);
-        slice5(m.s.phi[o], m.s.phi[plane + o], ep, qp);
+        const float2 zv = m.s.x[o], fv = m.s.phi[o];
+        slice5(zv.x, zv.y, ez, qz);
+        slice5(fv.x, fv.y, ep, qp);
         size_t orow = (size_t)(4 * r0 + (int64_t)pk * np + mu) * 32 + col;
 #pragma unroll
         for (int s = 0; s < NSL; ++s) {
@@ -704,16 +750,17 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
 }
 
 // ---------------------------------------------------------------- host helpers
-CUtensorMap make_map(MixedCtx &c, void *ptr, int64_t rows, int64_t plane_rows, int planes, cudaError_t &err) {
+CUtensorMap make_map(MixedCtx &c, void *ptr, int64_t rows, int64_t plane_rows, int planes, int box_rows,
+                     cudaError_t &err) {
     CUtensorMap mp;
     std::memset(&mp, 0, sizeof(mp));
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(c.encode_fn);
     cuuint64_t dims[3] = {32, (cuuint64_t)std::max<int64_t>(rows, 1), (cuuint64_t)planes};
     cuuint64_t strides[2] = {64, (cuuint64_t)plane_rows * 64};
-    cuuint32_t box[3] = {32, 128, (cuuint32_t)planes};
+    cuuint32_t box[3] = {16, (cuuint32_t)box_rows, (cuuint32_t)planes};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = encode(&mp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) err = cudaErrorInvalidValue;
     return mp;
@@ -735,10 +782,10 @@ cudaError_t grow(T *&p, size_t &cap, size_t need) {
 size_t mixed_row_bytes() { return (size_t)TILE * (8 * 4 + 2 * 4 + 3 * NSL * 2) + 8 + 16; }
 
 void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks) {
-    int nblk = (n + BN - 1) / BN;
+    int mblk = (n + BM - 1) / BM, nblk = (n + BN - 1) / BN;
     for (int64_t k = s0; k < s1; k += VKS) {
         int64_t k1 = std::min<int64_t>(k + VKS, s1);
-        for (int mb = 0; mb < nblk; ++mb)
+        for (int mb = 0; mb < mblk; ++mb)
             for (int nb = 0; nb < nblk; ++nb) {
                 tasks.push_back(j);
                 tasks.push_back(mb);
@@ -924,10 +971,10 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     m.pl = c.pdf + (size_t)a.nbf * a.nbf;
     m.err = c.d_err;
     cudaError_t err = cudaSuccess;
-    CUtensorMap tax = make_map(c, m.s.ax, 4 * a.rows, 4 * a.rows, NSL, err);
-    CUtensorMap tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, err);
-    CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NSL, err);
-    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NSL, err);
+    CUtensorMap tax = make_map(c, m.s.ax, 4 * a.rows, 4 * a.rows, NSL, BM, err);
+    CUtensorMap tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, BN, err);
+    CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NSL, BM, err);
+    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NSL, BN, err);
     if (err != cudaSuccess) return err;
     Profiler &P = *a.prof;
     P.begin(GBXC_K_PGATHER, st);

@@ -2,10 +2,10 @@
 // loads, tensor-memory allocation, tcgen05.mma (kind::f16, bf16 inputs, fp32 accumulate,
 // cta_group::1), commits and tensor-memory loads.
 //
-// Operand layout used throughout: K-major tiles with the 64-byte swizzle, i.e. rows of
-// 32 bf16 (64 B) in 8-row groups of 512 B.  A TMA box {32, rows, planes} lands as
-// `planes` consecutive [rows x 64 B] tiles, each swizzled in place; shared-memory
-// descriptors address a 128-row (or N-row) tile and advance 32 B per 16-element K step.
+// Operand layouts: K-major tiles with the 64-byte swizzle (rows of 32 bf16, 8-row groups
+// of 512 B) or the 32-byte swizzle (rows of 16 bf16, 8-row groups of 256 B).  A TMA box
+// {k, rows, planes} lands as `planes` consecutive [rows x 2k B] tiles, each swizzled in
+// place; shared-memory descriptors address a 128-row (or N-row) tile.
 //
 // Every wait is bounded: on timeout the caller records an error and stops issuing work.
 #pragma once
@@ -113,6 +113,18 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
     return d;
 }
 
+// The same for K-major operands with the 32-byte swizzle: rows of 16 bf16 (32 B), 8-row
+// groups 256 B apart, layout type 6.
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+    d |= static_cast<uint64_t>(1) << 16;
+    d |= static_cast<uint64_t>(256 >> 4) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(6) << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: fp32 accumulator (bits 4-5 = 1), bf16 A and B
 // (bits 7-9 and 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -154,6 +166,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// The same without the wait: several loads may be in flight; tmem_wait_ld() completes them
+// before any of their registers is read.
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 }  // namespace umma
 }  // namespace gbxc
