@@ -332,13 +332,15 @@ __device__ __forceinline__ void issue_slice_mmas(uint32_t tmem, uint64_t a0, uin
 //   warp 0 lane 0  TMA producer; its stage ring runs across task boundaries
 //   warp 1 lane 0  MMA issuer (15 slice products per 16-wide K step into 4 accumulators)
 //   warp 2         owns the tensor-memory allocation (all 512 columns)
-//   warps 4-11     epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one half of the
-//                  columns of each accumulator
+//   warps 4-19     epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one quarter of
+//                  the columns of each accumulator
 // Task tau uses accumulator set tau % NBUF (with two sets the epilogue of one task overlaps
 // the MMAs of the next); tmem_full[b] (MMA -> epilogue) and tmem_empty[b] (epilogue -> MMA)
 // hand set b over.  The epilogue is kept short: a 4-term combine, power-of-two scaling
 // from exponent bits, one store or one float64 atomic per element.
-constexpr int GEMM_THREADS = 384;   // 4 control warps + 8 epilogue warps
+constexpr int EPI_WARPS = 16;
+constexpr int GEMM_THREADS = 32 * (4 + EPI_WARPS);   // 4 control warps + the epilogue warps
+constexpr int EPI_COLS = BN / (EPI_WARPS / 4);       // columns per epilogue warp
 constexpr int GEMM_STAGES = BN == 128 ? 5 : 7;
 using GL = GemmSmem<NSL, NSL, GEMM_STAGES>;
 
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
         }
         for (int b = 0; b < NBUF; ++b) {
             umma::mbar_init(&tfull[b], 1);
-            umma::mbar_init(&tempty[b], 8);
+            umma::mbar_init(&tempty[b], EPI_WARPS);
         }
         umma::mbar_init(drain, 1);
         umma::fence_mbar_init();
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             if (!umma::mbar_wait(drain, 0)) atomicOr(m.err, 4);
         }
     } else if (warp >= 4) {   // ---------------------------------------------- epilogue
-        const int q = warp & 3, half = (warp - 4) >> 2;
+        const int q = warp & 3, cpart = (warp - 4) >> 2;
         const int i = q * 32 + lane;
         uint32_t tau = 0;
         for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x, ++tau) {
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                 int ei = m.s.pexp[(g.t - a.t0) * TILE + i];
                 const int *fexp = m.pexp + m.pexp_ofs[g.jl];
 #pragma unroll 1
-                for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+                for (int c = cpart * EPI_COLS; c < (cpart + 1) * EPI_COLS; c += 16) {
                     if (g.nc * BN + c >= g.n) break;   // warp-uniform
                     uint32_t v0[16], v1[16], v2[16], v3[16];
                     umma::tmem_ld16_nw(lane_base + c, v0);
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                 int64_t rg = a.plan.tile_row[g.tb] - a.row0;   // group exponents on the first tile
                 int ez = (mu < g.n) ? m.s.zexp[rg + mu] : 0;
 #pragma unroll 1
-                for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
+                for (int c = cpart * EPI_COLS; c < (cpart + 1) * EPI_COLS; c += 16) {
                     if (g.nc * BN + c >= g.n) break;   // warp-uniform
                     uint32_t v0[16], v1[16], v2[16], v3[16];
                     umma::tmem_ld16_nw(lane_base + c, v0);
