@@ -5,9 +5,10 @@
 // contraction can change it.
 //
 // df_exp_neg(t) = exp(-t) for t >= 0: Cody-Waite reduction t = k ln2 + r (|r| <= ln2/2,
-// ln2 in three float parts), Taylor series of exp(-r/8) to degree 8 (coefficients 1/n!
-// as df below degree 5), three squarings, scaling by 2^-k.  Relative error ~1e-13;
-// results below 2^-126 are returned as zero.
+// ln2 in three float parts), Taylor series of exp(-r/8) to degree 7 (terms from y^4 on
+// summed in float32: |y| <= 0.0434 puts their rounding below 2^-47; coefficients 1/n! as df
+// below that), three squarings, scaling by 2^-k.  Relative error ~1e-13; results below
+// 2^-126 lose precision gradually and are zero from t = 87 on.
 #pragma once
 
 #include <cstdint>
@@ -85,24 +86,23 @@ __device__ __forceinline__ df exp_neg(df t) {
     r = add_f(r, -__fmul_rn(k, C3));
     // y = -r / 8, |y| <= 0.0434
     df y = {ldexpf(-r.h, -3), ldexpf(-r.l, -3)};
-    // Taylor: 1 + y + y^2/2 + y^3/6 + y^4/24 + y^5/120 + ... + y^8/40320 (Horner)
+    // Taylor: 1 + y + y^2/2 + y^3/6 + y^4 (1/24 + y/120 + y^2/720 + y^3/5040) (Horner)
     const df I2 = {0.5f, 0.f};
     const df I3 = {1.666666716e-01f, -4.967053879e-09f};
-    const df I4 = {4.166666791e-02f, -1.241763470e-09f};
-    float q = 2.480158764e-05f;                    // 1/8!
-    q = __fmaf_rn(q, y.h, 1.984127011e-04f);       // 1/7!
+    float q = 1.984127011e-04f;                    // 1/7!
     q = __fmaf_rn(q, y.h, 1.388888923e-03f);       // 1/6!
     q = __fmaf_rn(q, y.h, 8.333333768e-03f);       // 1/5!
-    df s = add(mul_f(y, q), I4);
-    s = add(mul(s, y), I3);
+    q = __fmaf_rn(q, y.h, 4.166666791e-02f);       // 1/4!
+    df s = add(mul_f(y, q), I3);
     s = add(mul(s, y), I2);
     s = add_f(mul(s, y), 1.0f);
     s = add_f(mul(s, y), 1.0f);
     s = mul(s, s);
     s = mul(s, s);
     s = mul(s, s);
-    int ki = (int)k;
-    return ldexp_df(s, -ki);
+    // 2^-k with 0 <= k <= 126 (t < 87), from the exponent field
+    const float sc = __int_as_float((127 - (int)k) << 23);
+    return {__fmul_rn(s.h, sc), __fmul_rn(s.l, sc)};
 }
 
 }  // namespace dfl

@@ -185,9 +185,51 @@ __global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
 }
 
 // ---------------------------------------------------------------- collocation
+// The (L+1)(L+2)/2 Cartesian functions of one shell at one point (Eq. gau_cart) and their
+// gradients, from X, Y, Z = r - A and the radial sums g = sum_k d_k e_k and
+// h = sum_k (-2 alpha_k d_k) e_k (e_k = exp(-alpha_k r^2)):
+//   phi = x^l y^m z^n g,  d/dx phi = l x^(l-1) y^m z^n g + x^(l+1) y^m z^n h  (y, z alike).
+// L is a template parameter so every monomial index is a compile-time constant.
+template <int L>
+__device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, float2 *__restrict__ phi, size_t plane,
+                                             size_t o, bool live, float &mx) {
+    df xp[L + 1], yp[L + 1], zp[L + 1];
+    xp[0] = yp[0] = zp[0] = {1.f, 0.f};
+#pragma unroll
+    for (int k = 1; k <= L; ++k) {
+        xp[k] = df_mul(xp[k - 1], X);
+        yp[k] = df_mul(yp[k - 1], Y);
+        zp[k] = df_mul(zp[k - 1], Z);
+    }
+    const df Xh = df_mul(X, h), Yh = df_mul(Y, h), Zh = df_mul(Z, h);
+    int f = 0;
+#pragma unroll
+    for (int l = L; l >= 0; --l)
+#pragma unroll
+        for (int mm = L - l; mm >= 0; --mm) {
+            const int nn = L - l - mm;
+            const df ym_zn = df_mul(yp[mm], zp[nn]);
+            const df mono = df_mul(xp[l], ym_zn);
+            df v[4];
+            v[0] = df_mul(mono, g);
+            v[1] = df_mul(mono, Xh);
+            v[2] = df_mul(mono, Yh);
+            v[3] = df_mul(mono, Zh);
+            if (l > 0) v[1] = df_add(v[1], df_mul(dfl::mul_f(df_mul(xp[l - 1], ym_zn), (float)l), g));
+            if (mm > 0) v[2] = df_add(v[2], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm - 1]), zp[nn]), (float)mm), g));
+            if (nn > 0) v[3] = df_add(v[3], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm]), zp[nn - 1]), (float)nn), g));
+            const size_t of = o + (size_t)f * TILE;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) phi[c * plane + of] = live ? make_float2(v[c].h, v[c].l) : make_float2(0.f, 0.f);
+            if (live) mx = fmaxf(mx, fabsf(v[0].h));
+            ++f;
+        }
+}
+
 // Thread per point; Eq. gau_cart and its gradient in double-float arithmetic on the
-// float32 pipe (exp(-alpha r^2) by dfl::exp_neg), stored as (hi, lo) planes; then the
-// point's Ozaki slices of Phi, K-blocked by 32 functions.
+// float32 pipe (exp(-alpha r^2) by dfl::exp_neg), stored as (hi, lo) pairs; then the
+// point's Ozaki slices of Phi, K-blocked by 32 functions.  Consecutive shells on one centre
+// share X, Y, Z and r^2.
 __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells) {
     int64_t t = a.t0 + blockIdx.x;
     int i = threadIdx.x;
@@ -205,45 +247,32 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
     int64_t s0 = a.plan.shell_ptr[j], s1 = a.plan.shell_ptr[j + 1];
     int row = 0;
     float mx = 0.f;
+    float cx = __int_as_float(0x7fc00000), cy = 0.f, cz = 0.f;   // centre of X, Y, Z (NaN: none yet)
+    df X{0.f, 0.f}, Y{0.f, 0.f}, Z{0.f, 0.f}, r2{0.f, 0.f};
     for (int64_t si = s0; si < s1; ++si) {
         const DfShell &sh = shells[a.plan.shell_idx[si]];
-        df X = dfl::sub(px, {sh.ch[0], sh.cl[0]});
-        df Y = dfl::sub(py, {sh.ch[1], sh.cl[1]});
-        df Z = dfl::sub(pz, {sh.ch[2], sh.cl[2]});
-        df r2 = df_add(df_add(df_mul(X, X), df_mul(Y, Y)), df_mul(Z, Z));
+        if (!(sh.ch[0] == cx && sh.ch[1] == cy && sh.ch[2] == cz)) {   // uniform over the block
+            cx = sh.ch[0];
+            cy = sh.ch[1];
+            cz = sh.ch[2];
+            X = dfl::sub(px, {sh.ch[0], sh.cl[0]});
+            Y = dfl::sub(py, {sh.ch[1], sh.cl[1]});
+            Z = dfl::sub(pz, {sh.ch[2], sh.cl[2]});
+            r2 = df_add(df_add(df_mul(X, X), df_mul(Y, Y)), df_mul(Z, Z));
+        }
         df g = {0.f, 0.f}, h = {0.f, 0.f};
         for (int k = 0; k < sh.nprim; ++k) {
             df ex = dfl::exp_neg(df_mul({sh.ah[k], sh.al[k]}, r2));
             g = df_add(g, df_mul({sh.dh[k], sh.dl[k]}, ex));
             h = df_add(h, df_mul({sh.gh[k], sh.gl[k]}, ex));
         }
-        df xp[GBXC_MAX_L + 1], yp[GBXC_MAX_L + 1], zp[GBXC_MAX_L + 1];
-        xp[0] = yp[0] = zp[0] = {1.f, 0.f};
-        for (int k = 1; k <= sh.L; ++k) {
-            xp[k] = df_mul(xp[k - 1], X);
-            yp[k] = df_mul(yp[k - 1], Y);
-            zp[k] = df_mul(zp[k - 1], Z);
+        const size_t o = (size_t)(r0 + row) * TILE + i;
+        switch (sh.L) {
+            case 0: colloc_shell<0>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 1; break;
+            case 1: colloc_shell<1>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 3; break;
+            case 2: colloc_shell<2>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 6; break;
+            default: colloc_shell<3>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 10; break;
         }
-        df Xh = df_mul(X, h), Yh = df_mul(Y, h), Zh = df_mul(Z, h);
-        for (int l = sh.L; l >= 0; --l)
-            for (int mm = sh.L - l; mm >= 0; --mm) {
-                int nn = sh.L - l - mm;
-                df ym_zn = df_mul(yp[mm], zp[nn]);
-                df mono = df_mul(xp[l], ym_zn);
-                df v[4];
-                v[0] = df_mul(mono, g);
-                v[1] = df_mul(mono, Xh);
-                v[2] = df_mul(mono, Yh);
-                v[3] = df_mul(mono, Zh);
-                if (l > 0) v[1] = df_add(v[1], df_mul(dfl::mul_f(df_mul(xp[l - 1], ym_zn), (float)l), g));
-                if (mm > 0) v[2] = df_add(v[2], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm - 1]), zp[nn]), (float)mm), g));
-                if (nn > 0) v[3] = df_add(v[3], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm]), zp[nn - 1]), (float)nn), g));
-                size_t o = (size_t)(r0 + row) * TILE + i;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) phi[c * plane + o] = live ? make_float2(v[c].h, v[c].l) : make_float2(0.f, 0.f);
-                if (live) mx = fmaxf(mx, fabsf(v[0].h));
-                ++row;
-            }
     }
     for (; row < np; ++row) {
         size_t o = (size_t)(r0 + row) * TILE + i;
@@ -710,7 +739,9 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
 // ---------------------------------------------------------------- V-side slicing
 // Thread per point.  The K group of the tile (the V task it belongs to) shares one
 // exponent per function for Z and one for Phi: the maximum of the per-tile exponents.
-// The group's first tile stores those maxima for the V epilogue.
+// The group's first tile stores those maxima for the V epilogue over its own per-tile
+// entries; a reader in another block that sees the new value takes the same maximum, so
+// no ordering between the blocks of a group is needed.
 __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
     int64_t t = a.t0 + blockIdx.x;
     int i = threadIdx.x;
@@ -743,8 +774,7 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
             m.s.vz[(size_t)s * plane + orow] = __float2bfloat16_rn(qz[s]);
             m.s.vphi[(size_t)s * plane + orow] = __float2bfloat16_rn(qp[s]);
         }
-        __syncthreads();   // every thread has read the per-tile exponents of row mu ...
-        if (t == g0 && i == 0) {   // ... before the group's first tile overwrites them
+        if (t == g0 && i == 0) {
             m.s.zexp[rg + mu] = ez;
             m.s.fexp[rg + mu] = ep;
         }
