@@ -5,7 +5,7 @@
 //
 //   X^j = P^j Phi^j (Eq. x_mat)      Ozaki-style exact slicing.  Every row of Phi (a grid
 //        point) and of P^j (a function) is scaled by a power of two to |v| <= 1 and cut
-//        into 5 integer slices v = sum_s q_s 2^-(6+7s) (34 bits).  The 15 slice products
+//        into 5 integer slices v = sum_s q_s 2^-(6+7s) (34 bits, |q_s| <= 64 for s <= 2).  The 15 slice products
 //        with s + t <= 4 are issued per K step into four accumulators: level d = s + t for
 //        d = 0, 1, 2, whose partial sums are integer multiples of 2^-(12+7d) below 2^24
 //        units so the fp32 sums are exact, and levels 3-4 together (rounded, 2^-21 below
@@ -105,22 +105,22 @@ __device__ __forceinline__ float scale2(float x, int k) {
     return __fmul_rn(__fmul_rn(x, pow2f(k1)), pow2f(k - k1));
 }
 
-// v = (h + l) 2^-e with |v| <= 1 -> five slices q_s 2^-(6+7s), q_s integers in [-64, 64],
-// float32 only: each q_s is the rounding of the running remainder to the slice grid (the
-// power-of-two products are exact), the subtraction is exact (Sterbenz) and two-sum folds
-// the low word back in.
+// v = (h + l) 2^-e with |v| <= 1 -> five slices q_s 2^-(6+7s), q_s integers, float32 only:
+// each q_s is the rounding of the running remainder to the slice grid (the power-of-two
+// products are exact) and the subtraction is exact (Sterbenz).  Slices 0-2 come from h
+// alone and lie in [-64, 64] (the bound the exact accumulator levels 0-2 rely on).  The
+// low word joins the remainder after them, when |remainder| <= 2^-21, so that rounding is
+// below 2^-45; slice 3 may then reach +-72, which only feeds the rounded levels 3-4.
 __device__ __forceinline__ void slice5(float h, float l, int e, float out[NSL]) {
-    float rh = scale2(h, -e), rl = scale2(l, -e);
+    float rh = scale2(h, -e);
+    const float rl = scale2(l, -e);
 #pragma unroll
     for (int s = 0; s < NSL; ++s) {
+        if (s == 3) rh = __fadd_rn(rh, rl);
         const float up = (float)(1ull << (6 + 7 * s));
-        float qs = __fmul_rn(rintf(__fmul_rn(rh, up)), 1.0f / up);
+        const float qs = __fmul_rn(rintf(__fmul_rn(rh, up)), 1.0f / up);
         out[s] = qs;
         rh = __fsub_rn(rh, qs);
-        float ss = __fadd_rn(rh, rl);
-        float bb = __fsub_rn(ss, rh);
-        rl = __fadd_rn(__fsub_rn(rh, __fsub_rn(ss, bb)), __fsub_rn(rl, bb));
-        rh = ss;
     }
 }
 
@@ -744,7 +744,6 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
 // no ordering between the blocks of a group is needed.
 __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
     int64_t t = a.t0 + blockIdx.x;
-    int i = threadIdx.x;
     int j = a.plan.tile_batch[t];
     int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
     int np = pad32(n);
@@ -755,26 +754,44 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     int64_t rg = a.plan.tile_row[g0] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
-    int pk = i >> 5, col = i & 31;
-    for (int mu = 0; mu < n; ++mu) {
+    // thread = (function row within 8, group of 8 points): 64-byte loads, 16-byte stores
+    const int lr = threadIdx.x >> 4, pg = threadIdx.x & 15;
+    const int pk = pg >> 2, col = (pg & 3) * 8;
+    for (int mu = lr; mu < n; mu += 8) {
         int ez = -1000, ep = -1000;
         for (int64_t u = g0; u < g1; ++u) {
             int64_t ru = a.plan.tile_row[u] - a.row0;
             ez = max(ez, m.s.zexp[ru + mu]);
             ep = max(ep, m.s.fexp[ru + mu]);
         }
-        size_t o = (size_t)(r0 + mu) * TILE + i;
-        float qz[NSL], qp[NSL];
-        const float2 zv = m.s.x[o], fv = m.s.phi[o];
-        slice5(zv.x, zv.y, ez, qz);
-        slice5(fv.x, fv.y, ep, qp);
-        size_t orow = (size_t)(4 * r0 + (int64_t)pk * np + mu) * 32 + col;
+        const size_t o = (size_t)(r0 + mu) * TILE + 8 * pg;
+        const float4 *zs = reinterpret_cast<const float4 *>(m.s.x + o);
+        const float4 *fs = reinterpret_cast<const float4 *>(m.s.phi + o);
+        uint32_t wz[NSL][4], wp[NSL][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {   // points 2q, 2q + 1 as (hi, lo, hi, lo)
+            const float4 z4 = zs[q], f4 = fs[q];
+            float a0[NSL], a1[NSL], b0[NSL], b1[NSL];
+            slice5(z4.x, z4.y, ez, a0);
+            slice5(z4.z, z4.w, ez, a1);
+            slice5(f4.x, f4.y, ep, b0);
+            slice5(f4.z, f4.w, ep, b1);
+#pragma unroll
+            for (int s = 0; s < NSL; ++s) {
+                __nv_bfloat162 bz = __floats2bfloat162_rn(a0[s], a1[s]);
+                __nv_bfloat162 bp = __floats2bfloat162_rn(b0[s], b1[s]);
+                wz[s][q] = *reinterpret_cast<uint32_t *>(&bz);
+                wp[s][q] = *reinterpret_cast<uint32_t *>(&bp);
+            }
+        }
+        const size_t orow = (size_t)(4 * r0 + (int64_t)pk * np + mu) * 32 + col;
 #pragma unroll
         for (int s = 0; s < NSL; ++s) {
-            m.s.vz[(size_t)s * plane + orow] = __float2bfloat16_rn(qz[s]);
-            m.s.vphi[(size_t)s * plane + orow] = __float2bfloat16_rn(qp[s]);
+            *reinterpret_cast<uint4 *>(m.s.vz + (size_t)s * plane + orow) = make_uint4(wz[s][0], wz[s][1], wz[s][2], wz[s][3]);
+            *reinterpret_cast<uint4 *>(m.s.vphi + (size_t)s * plane + orow) =
+                make_uint4(wp[s][0], wp[s][1], wp[s][2], wp[s][3]);
         }
-        if (t == g0 && i == 0) {
+        if (t == g0 && pg == 0) {
             m.s.zexp[rg + mu] = ez;
             m.s.fexp[rg + mu] = ep;
         }
