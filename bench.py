@@ -256,7 +256,7 @@ def run_many(args):
     import paper_2007_03143_gb300 as G
     torch.cuda.set_device(0)
     rng = np.random.default_rng(4000)
-    sizes = [int(v) for v in rng.integers(1, args.max_waters + 1, size=args.nmol)]
+    sizes = [int(v) for v in rng.integers(args.min_waters, args.max_waters + 1, size=args.nmol)]
     spec = X.GridSpec(75, 16, 32, "ssf", 512)
     ctx = G.Context(0)
     pool = _water_pool(G, ctx, sizes, 40000, spec)
@@ -286,31 +286,16 @@ def run_many(args):
     return 0
 
 
-def run_serve(args):
-    """Serving form: Poisson stream of requests from a pool of resident molecules."""
+def _stream(G, ctx, pool, rate, nreq, nwarm, seed):
+    """One Poisson stream of mixed-precision requests (LDA:PBE = 1:3) at `rate` per second."""
     import threading
-    import torch
-    import paper_2007_03143_gb300 as G
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(5000)
-    sizes = [int(v) for v in rng.integers(1, args.max_waters + 1, size=args.pool)]
-    spec = X.GridSpec(75, 16, 32, "ssf", 512)
-    ctx = G.Context(0)
-    pool = _water_pool(G, ctx, sizes, 50000, spec)
-    # float64 per-request path for comparison (one request per molecule, sequential)
-    t0 = time.perf_counter()
-    pts64 = 0
-    for mid, nbf, npts, P in pool[:4]:
-        G.gbxc_integrate(ctx.h, mid, P, "pbe", "fp64")
-        pts64 += npts
-    fp64_rate = pts64 / (time.perf_counter() - t0)
-    G.gbxc_serve_start(ctx.h, args.slots, 0)
+    rng = np.random.default_rng(seed)
     reqs = []
-    for r in range(args.requests + args.warmup_requests):
+    for r in range(nreq + nwarm):
         k = int(rng.integers(len(pool)))
         fn = "slater" if rng.uniform() < 0.25 else "pbe"
         P = pool[k][3] * (1.0 + 1e-3 * rng.standard_normal())
-        reqs.append((k, fn, P, float(rng.exponential(1.0 / args.rate))))
+        reqs.append((k, fn, P, float(rng.exponential(1.0 / rate))))
     tickets = []
     lock = threading.Lock()
 
@@ -341,25 +326,59 @@ def run_serve(args):
             continue
         t, k, ts = item
         E, N, l = G.gbxc_wait(ctx.h, t, 600.0)
-        if i >= args.warmup_requests:
+        if i >= nwarm:
             lat.append(l)
             done_pts += pool[k][2]
             t_first = ts if t_first is None else t_first
             t_last = time.perf_counter()
         i += 1
     th.join()
-    G.gbxc_serve_stop(ctx.h)
     lat = sorted(lat)
     span = t_last - t_first
-    offered = args.rate
-    served = len(lat) / span
+    return {"offered_req_per_s": rate, "served_req_per_s": len(lat) / span, "value": done_pts / span,
+            "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "requests": len(lat), "wall_s": time.perf_counter() - t_start}
+
+
+def run_serve(args):
+    """Serving form: Poisson streams of requests from a pool of resident molecules, one per
+    offered rate of the sweep; the first rate is the headline line."""
+    import torch
+    import paper_2007_03143_gb300 as G
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5000)
+    sizes = [int(v) for v in rng.integers(args.min_waters, args.max_waters + 1, size=args.pool)]
+    spec = X.GridSpec(75, 16, 32, "ssf", 512)
+    ctx = G.Context(0)
+    t0 = time.perf_counter()
+    pool = _water_pool(G, ctx, sizes, 50000, spec)
+    load_s = time.perf_counter() - t0
+    # float64 per-request path for comparison (one request per molecule, sequential)
+    t0 = time.perf_counter()
+    pts64 = 0
+    for mid, nbf, npts, P in pool[:4]:
+        G.gbxc_integrate(ctx.h, mid, P, "pbe", "fp64")
+        pts64 += npts
+    fp64_rate = pts64 / (time.perf_counter() - t0)
+    # mixed per-request path, sequential: the capacity without overlap
+    t0 = time.perf_counter()
+    ptsm = 0
+    for mid, nbf, npts, P in pool[:8]:
+        G.gbxc_integrate(ctx.h, mid, P, "pbe", "mixed")
+        ptsm += npts
+    mixed_rate = ptsm / (time.perf_counter() - t0)
+    rates = [float(r) for r in args.rates.split(",")] if args.rates else [args.rate]
+    G.gbxc_serve_start(ctx.h, args.slots, 0)
+    sweep = [_stream(G, ctx, pool, r, args.requests, args.warmup_requests, 5100 + k) for k, r in enumerate(rates)]
+    G.gbxc_serve_stop(ctx.h)
+    head = sweep[0]
     line = {"mode": "serve", "metric": "p50/p99 latency and grid pts/s of a Poisson request stream",
-            "unit": UNIT, "value": done_pts / span, "p50_ms": 1e3 * lat[len(lat) // 2],
-            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "offered_req_per_s": offered, "served_req_per_s": served, "requests": len(lat),
-            "slots": args.slots, "pool_waters": sizes, "precision": "mixed", "lda_to_pbe": "1:3",
-            "fp64_per_request_path": {"value": fp64_rate, "unit": UNIT}, "data": "synthetic",
-            "wall_s": time.perf_counter() - t_start}
+            "unit": UNIT, **head, "sweep": sweep, "slots": args.slots, "pool_waters": sizes,
+            "mean_points_per_request": float(np.mean([p[2] for p in pool])),
+            "precision": "mixed", "lda_to_pbe": "1:3",
+            "fp64_per_request_path": {"value": fp64_rate, "unit": UNIT},
+            "mixed_per_request_path": {"value": mixed_rate, "unit": UNIT},
+            "load_grid_s": load_s, "data": "synthetic"}
     print(json.dumps(line))
     ctx.close()
     return 0
@@ -379,9 +398,11 @@ def main():
     ap.add_argument("--scratch-mb", type=int, default=0, help="device scratch budget (0 = default)")
     ap.add_argument("--mode", default="single", choices=["single", "many", "serve"])
     ap.add_argument("--nmol", type=int, default=64)
+    ap.add_argument("--min-waters", type=int, default=1)
     ap.add_argument("--max-waters", type=int, default=8)
     ap.add_argument("--pool", type=int, default=16)
     ap.add_argument("--rate", type=float, default=40.0, help="serving: mean requests per second")
+    ap.add_argument("--rates", default="", help="serving: comma-separated sweep of offered rates")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--warmup-requests", type=int, default=20)
     ap.add_argument("--slots", type=int, default=4)
