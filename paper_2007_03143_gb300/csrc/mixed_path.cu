@@ -33,13 +33,18 @@
 
 #include "mixed.h"
 #include "dfloat.cuh"
+#include "slicing.cuh"
 #include "umma.cuh"
 #include "xc_functional.cuh"
 
 namespace gbxc {
 namespace {
 
-constexpr int NSL = 5;          // Ozaki slices (X contraction)
+using slc::NSL;
+using slc::pow2f;
+using slc::scale2;
+using slc::slice5;
+using slc::exp_of;
 constexpr int BN = 128;         // N extent of one MMA (functions)
 constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
@@ -48,7 +53,9 @@ constexpr double kFp32RhoMin = 1e300;
 
 // ---------------------------------------------------------------- scratch layout
 struct MixedSlabs {
-    float2 *phi;            // 4 planes [rows][128]: phi, dx, dy, dz as (hi, lo) pairs
+    float2 *phi;            // [rows][128]: Phi as (hi, lo) pairs
+    float *ghi, *glo;       // 3 planes each [rows][128]: hi and lo words of dPhi/dx, /dy, /dz
+                            // (the Z pass reads the hi words alone)
     float2 *x;              // 1 plane [rows][128]: X (later Z) as (hi, lo)
     __nv_bfloat16 *ax;      // 5 planes [4 rows][32]: Phi slices, K-blocked per tile
     __nv_bfloat16 *vz;      // 5 planes [4 rows][32]: Z slices, point-blocked per tile
@@ -62,7 +69,11 @@ __host__ __device__ inline MixedSlabs mixed_slabs(void *base, int64_t rows) {
     char *p = static_cast<char *>(base);
     MixedSlabs s;
     s.phi = reinterpret_cast<float2 *>(p);
-    p += (size_t)8 * rows * TILE * 4;
+    p += (size_t)2 * rows * TILE * 4;
+    s.ghi = reinterpret_cast<float *>(p);
+    p += (size_t)3 * rows * TILE * 4;
+    s.glo = reinterpret_cast<float *>(p);
+    p += (size_t)3 * rows * TILE * 4;
     s.x = reinterpret_cast<float2 *>(p);
     p += (size_t)2 * rows * TILE * 4;
     s.ax = reinterpret_cast<__nv_bfloat16 *>(p);
@@ -93,44 +104,6 @@ struct MixedArgs {
 };
 
 __device__ __forceinline__ int pad32(int n) { return (n + 31) & ~31; }
-
-// ---------------------------------------------------------------- slicing
-// 2^k as a float for k in [-126, 127] (built from the exponent field)
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
-
-// x 2^k for |k| <= 252 as two exact power-of-two products; the intermediate lies between x
-// and the result in magnitude, so nothing is lost that the result could hold
-__device__ __forceinline__ float scale2(float x, int k) {
-    const int k1 = k >> 1;
-    return __fmul_rn(__fmul_rn(x, pow2f(k1)), pow2f(k - k1));
-}
-
-// v = (h + l) 2^-e with |v| <= 1 -> five slices q_s 2^-(6+7s), q_s integers, float32 only:
-// each q_s is the rounding of the running remainder to the slice grid (the power-of-two
-// products are exact) and the subtraction is exact (Sterbenz).  Slices 0-2 come from h
-// alone and lie in [-64, 64] (the bound the exact accumulator levels 0-2 rely on).  The
-// low word joins the remainder after them, when |remainder| <= 2^-21, so that rounding is
-// below 2^-45; slice 3 may then reach +-72, which only feeds the rounded levels 3-4.
-__device__ __forceinline__ void slice5(float h, float l, int e, float out[NSL]) {
-    float rh = scale2(h, -e);
-    const float rl = scale2(l, -e);
-#pragma unroll
-    for (int s = 0; s < NSL; ++s) {
-        if (s == 3) rh = __fadd_rn(rh, rl);
-        const float up = (float)(1ull << (6 + 7 * s));
-        const float qs = __fmul_rn(rintf(__fmul_rn(rh, up)), 1.0f / up);
-        out[s] = qs;
-        rh = __fsub_rn(rh, qs);
-    }
-}
-
-// exponent e with |x| < 2^e for x > 0 (0 for x == 0), from the float's exponent bits
-__device__ __forceinline__ int exp_of(float x) {
-    if (!(x > 0.f)) return 0;
-    int e;
-    frexpf(x * 1.0000002f, &e);
-    return e;
-}
 
 // ---------------------------------------------------------------- double-float helpers
 using dfl::df;
@@ -191,7 +164,7 @@ __global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
 //   phi = x^l y^m z^n g,  d/dx phi = l x^(l-1) y^m z^n g + x^(l+1) y^m z^n h  (y, z alike).
 // L is a template parameter so every monomial index is a compile-time constant.
 template <int L>
-__device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, float2 *__restrict__ phi, size_t plane,
+__device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const MixedSlabs &sl, size_t plane,
                                              size_t o, bool live, float &mx) {
     df xp[L + 1], yp[L + 1], zp[L + 1];
     xp[0] = yp[0] = zp[0] = {1.f, 0.f};
@@ -219,8 +192,12 @@ __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, float
             if (mm > 0) v[2] = df_add(v[2], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm - 1]), zp[nn]), (float)mm), g));
             if (nn > 0) v[3] = df_add(v[3], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm]), zp[nn - 1]), (float)nn), g));
             const size_t of = o + (size_t)f * TILE;
+            sl.phi[of] = live ? make_float2(v[0].h, v[0].l) : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) phi[c * plane + of] = live ? make_float2(v[c].h, v[c].l) : make_float2(0.f, 0.f);
+            for (int c = 0; c < 3; ++c) {
+                sl.ghi[c * plane + of] = live ? v[c + 1].h : 0.f;
+                sl.glo[c * plane + of] = live ? v[c + 1].l : 0.f;
+            }
             if (live) mx = fmaxf(mx, fabsf(v[0].h));
             ++f;
         }
@@ -243,7 +220,7 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
     df px = d_to_df(live ? a.plan.x[p] : 0.0), py = d_to_df(live ? a.plan.y[p] : 0.0),
        pz = d_to_df(live ? a.plan.z[p] : 0.0);
     const size_t plane = (size_t)m.rows * TILE;
-    float2 *phi = m.s.phi;
+    const float2 *phi = m.s.phi;
     int64_t s0 = a.plan.shell_ptr[j], s1 = a.plan.shell_ptr[j + 1];
     int row = 0;
     float mx = 0.f;
@@ -268,16 +245,21 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
         }
         const size_t o = (size_t)(r0 + row) * TILE + i;
         switch (sh.L) {
-            case 0: colloc_shell<0>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 1; break;
-            case 1: colloc_shell<1>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 3; break;
-            case 2: colloc_shell<2>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 6; break;
-            default: colloc_shell<3>(X, Y, Z, g, h, phi, plane, o, live, mx); row += 10; break;
+            case 0: colloc_shell<0>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 1; break;
+            case 1: colloc_shell<1>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 3; break;
+            case 2: colloc_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 6; break;
+            default: colloc_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 10; break;
         }
     }
     for (; row < np; ++row) {
         size_t o = (size_t)(r0 + row) * TILE + i;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) phi[c * plane + o] = make_float2(0.f, 0.f);
+        m.s.phi[o] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            m.s.ghi[c * plane + o] = 0.f;
+            m.s.glo[c * plane + o] = 0.f;
+        }
     }
     int e = exp_of(mx);
     m.s.pexp[(t - a.t0) * TILE + i] = e;
@@ -649,13 +631,14 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
 #pragma unroll 2
     for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        const float2 xv = m.s.x[o], f0 = phi[o], f1 = phi[plane + o], f2 = phi[2 * plane + o],
-                     f3 = phi[3 * plane + o];
+        const float2 xv = m.s.x[o], f0 = phi[o];
+        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
+        const float l1 = m.s.glo[o], l2 = m.s.glo[plane + o], l3 = m.s.glo[2 * plane + o];
         df x{xv.x, xv.y};
         rho = df_add(rho, df_mul({f0.x, f0.y}, x));
-        gx = df_add(gx, df_mul({f1.x, f1.y}, x));
-        gy = df_add(gy, df_mul({f2.x, f2.y}, x));
-        gz = df_add(gz, df_mul({f3.x, f3.y}, x));
+        gx = df_add(gx, df_mul({h1, l1}, x));
+        gy = df_add(gy, df_mul({h2, l2}, x));
+        gz = df_add(gz, df_mul({h3, l3}, x));
     }
     double r = df_to_d(rho);
     double dx = 2.0 * df_to_d(gx), dy = 2.0 * df_to_d(gy), dz = 2.0 * df_to_d(gz);
@@ -697,11 +680,15 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
 #pragma unroll 2
     for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
-        const float2 f0 = phi[o], f1 = phi[plane + o], f2 = phi[2 * plane + o], f3 = phi[3 * plane + o];
+        // the gradient terms take the hi words only (dropping the low words moved max|dV|
+        // against float64 from 9.2e-8 to 9.4e-8 on the 16-water workload), while rho and
+        // grad rho above use both words: without them |dE_xc| grew from 7e-10 to 6e-8 Eh
+        const float2 f0 = phi[o];
+        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
         df z = df_mul(cz, {f0.x, f0.y});
-        z = df_add(z, df_mul(cbx, {f1.x, f1.y}));
-        z = df_add(z, df_mul(cby, {f2.x, f2.y}));
-        z = df_add(z, df_mul(cbz, {f3.x, f3.y}));
+        z = df_add(z, dfl::mul_f(cbx, h1));
+        z = df_add(z, dfl::mul_f(cby, h2));
+        z = df_add(z, dfl::mul_f(cbz, h3));
         m.s.x[o] = make_float2(z.h, z.l);
         float az = fabsf(z.h), ap = fabsf(f0.x);
 #pragma unroll
