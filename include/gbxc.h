@@ -198,6 +198,27 @@ int gbxc_integrate_many(gbxc_ctx *ctx, int nmol, const int *mol_ids, const doubl
                         const int *functional, int precision, double *Exc, double *const *Vxc,
                         double *Nel);
 
+/* Autotuner of the batching form (no counterpart in the paper, which uses MAGMA's fixed
+ * kernels): times gbxc_integrate_many on this molecule list for every candidate schedule --
+ * graph branch counts {1, 2, 4, 8, 16} (at most nmol) and, for GBXC_MIXED, the tcgen05 GEMM
+ * N tile (128 functions with one TMEM accumulator set, or 64 with two, which lets a tile's
+ * epilogue overlap the next tile's MMAs) -- by CUDA events around the graph launch (best of
+ * two replays after a capturing run), keeps the fastest for later gbxc_integrate_many calls
+ * with the same (molecule list, precision) on this context, and returns it.
+ *   arguments as gbxc_integrate_many (P is read; no results are returned)
+ *   branches_out, tile_n_out  the chosen schedule (may be NULL)
+ *   ms_out                    its device time per call in milliseconds (may be NULL)
+ * Each candidate integrates the list three times, so a call costs about 3 x (number of
+ * candidates) integrations. */
+int gbxc_autotune(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P,
+                  const int *functional, int precision, int *branches_out, int *tile_n_out,
+                  double *ms_out);
+
+/* Sets the schedule gbxc_integrate_many uses for (molecule list, precision) on this context,
+ * as gbxc_autotune would: `branches` graph branches (1..64, at most nmol are used) and GEMM
+ * N tile `tile_n` (64 or 128; the float64 form ignores it).  GBXC_EINVAL otherwise. */
+int gbxc_set_schedule(gbxc_ctx *ctx, int nmol, const int *mol_ids, int precision, int branches, int tile_n);
+
 /* Serving form: continuous batching of integration requests.
  * gbxc_serve_start allocates one device arena of `arena_bytes` (0 = the context's
  * scratch budget), creates `nslots` streams and starts a scheduler thread.  Requests

@@ -34,7 +34,7 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
-            "gbxc_serve_stats"]
+            "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -91,13 +91,16 @@ def lib():
     L.gbxc_integrate_fp64_noalloc.restype = c_int
     L.gbxc_integrate_many.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p,
                                       c_void_p, c_void_p]
+    L.gbxc_autotune.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_int),
+                                POINTER(c_int), POINTER(c_double)]
+    L.gbxc_set_schedule.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, c_int]
     L.gbxc_serve_start.argtypes = [c_void_p, c_int, c_size_t]
     L.gbxc_serve_stop.argtypes = [c_void_p]
     L.gbxc_submit.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, POINTER(c_longlong)]
     L.gbxc_wait.argtypes = [c_void_p, c_longlong, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
     L.gbxc_serve_stats.argtypes = [c_void_p] + [c_void_p] * 5
     for name in ("gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
-                 "gbxc_serve_stats"):
+                 "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule"):
         getattr(L, name).restype = c_int
     L.gbxc_profile_enable.argtypes = [c_void_p, c_int]
     L.gbxc_profile_read.argtypes = [c_void_p, c_void_p, c_void_p]
@@ -257,6 +260,26 @@ def gbxc_integrate_many(ctx, mols, Ps, functionals, precision="fp64", Vs=None):
                                           PRECISIONS.get(precision, precision), E.ctypes.data, pV,
                                           N.ctypes.data))
     return E, N
+
+
+def gbxc_autotune(ctx, mols, Ps, functionals, precision="mixed"):
+    """Pick the fastest batching schedule for this molecule list; returns (branches, tile_n, ms)."""
+    n = len(mols)
+    ids = np.ascontiguousarray(mols, dtype=np.int32)
+    fns = np.ascontiguousarray([FUNCTIONALS.get(f, f) for f in functionals], dtype=np.int32)
+    keep = [_ptr(P) for P in Ps]
+    pP = (c_void_p * n)(*[k[0] for k in keep])
+    w, t, ms = c_int(), c_int(), c_double()
+    _check(ctx, lib().gbxc_autotune(ctx, n, ids.ctypes.data, pP, fns.ctypes.data,
+                                    PRECISIONS.get(precision, precision), ctypes.byref(w), ctypes.byref(t),
+                                    ctypes.byref(ms)))
+    return w.value, t.value, ms.value
+
+
+def gbxc_set_schedule(ctx, mols, precision, branches, tile_n):
+    ids = np.ascontiguousarray(mols, dtype=np.int32)
+    _check(ctx, lib().gbxc_set_schedule(ctx, len(mols), ids.ctypes.data, PRECISIONS.get(precision, precision),
+                                        branches, tile_n))
 
 
 def gbxc_serve_start(ctx, nslots=4, arena_bytes=0):

@@ -46,7 +46,7 @@ struct Schedule {
     int64_t max_rows = 0;
     MixedSchedule mixed;        // extra state of the mixed form
 };
-using SchedKey = std::tuple<int, int, int, size_t>;   // precision, b0, b1, scratch budget
+using SchedKey = std::tuple<int, int, int, size_t, int>;   // precision, b0, b1, scratch budget, N tile
 
 struct Molecule {
     int natoms = 0, nshell = 0, nbf = 0;
@@ -170,7 +170,7 @@ struct Server {
 // A captured CUDA graph of gbxc_integrate_many for one molecule list.
 struct ManyGraph {
     std::vector<int> mols, fns;
-    int precision = -1, branches = 0;
+    int precision = -1, branches = 0, tile_n = 0;
     size_t budget = 0;
     cudaGraphExec_t exec = nullptr;
     long long launches[GBXC_NKERNEL] = {};
@@ -187,12 +187,15 @@ struct gbxc_ctx {
     Workspace ws;                   // the default workspace (synchronous calls)
     std::vector<Workspace> branch_ws;   // gbxc_integrate_many branches
     ManyGraph many;
+    // gbxc_autotune results: (molecule list, precision) -> {graph branches, GEMM N tile}
+    std::map<std::pair<std::vector<int>, int>, std::pair<int, int>> tuned;
     std::string err;
     std::map<int, std::unique_ptr<Molecule>> mols;
     int next_id = 0;
     Profiler prof;
     std::recursive_mutex mu;        // serialises host-side work on the context
     Server srv;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // timing of graph launches (gbxc_autotune)
 };
 
 namespace {
@@ -428,8 +431,9 @@ size_t scratch_budget(gbxc_ctx *ctx) {
 }
 
 // Chunks of tiles whose slabs fit the budget, and the V-contraction tasks of each chunk.
-Schedule &get_schedule(Molecule &m, int precision, int b0, int b1, size_t budget) {
-    SchedKey key{precision, b0, b1, budget};
+Schedule &get_schedule(Molecule &m, int precision, int b0, int b1, size_t budget, int tile_n = 128) {
+    if (precision == GBXC_FP64) tile_n = 128;   // the float64 kernels have one tile shape
+    SchedKey key{precision, b0, b1, budget, tile_n};
     auto it = m.scheds.find(key);
     if (it != m.scheds.end()) return *it->second;
     auto sp = std::make_unique<Schedule>();
@@ -457,7 +461,7 @@ Schedule &get_schedule(Molecule &m, int precision, int b0, int b1, size_t budget
             if (precision == GBXC_FP64)
                 append_fp64_vtasks(j, n, s0, s1, tasks);
             else
-                append_mixed_vtasks(j, n, s0, s1, tasks);
+                append_mixed_vtasks(j, n, s0, s1, tile_n, tasks);
         }
         c.ntask = (int64_t)tasks.size() / 5 - c.task0;
         S.chunks.push_back(c);
@@ -470,7 +474,7 @@ Schedule &get_schedule(Molecule &m, int precision, int b0, int b1, size_t budget
             c0.push_back(c.t0);
             c1.push_back(c.t1);
         }
-        build_mixed_schedule(m.plan, c0, c1, S.mixed);
+        build_mixed_schedule(m.plan, c0, c1, tile_n, S.mixed);
     }
     if (!tasks.empty()) {
         check(cudaMalloc(&S.d_tasks, tasks.size() * sizeof(int)), "cudaMalloc tasks");
@@ -852,6 +856,8 @@ void gbxc_destroy(gbxc_ctx *ctx) {
     if (ctx->many.exec) cudaGraphExecDestroy(ctx->many.exec);
     if (ctx->many.fork) cudaEventDestroy(ctx->many.fork);
     for (auto e : ctx->many.join) cudaEventDestroy(e);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (auto &kv : ctx->mols) {
         Molecule &m = *kv.second;
         free_grid(m);
@@ -1176,134 +1182,213 @@ int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int fun
     });
 }
 
+namespace {
+
+// gbxc_integrate_many with an explicit schedule: W graph branches, GEMM N tile `tile_n`.
+// Returns the device time of the graph launch in *ms_out (CUDA events on the context stream).
+int many_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P, const int *functional,
+              int precision, int W, int tile_n, double *Exc, double *const *Vxc, double *Nel, float *ms_out) {
+    REQUIRE(ctx->device >= 0, "integration needs a device context");
+    REQUIRE(nmol > 0 && mol_ids && P && functional, "bad molecule list");
+    REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
+    std::vector<Molecule *> ms(nmol);
+    for (int k = 0; k < nmol; ++k) {
+        ms[k] = &get_mol(ctx, mol_ids[k]);
+        if (!ms[k]->has_grid) return fail(ctx, GBXC_ENOTREADY, "a molecule has no grid");
+        REQUIRE(functional[k] == GBXC_SLATER || functional[k] == GBXC_PBE, "unknown functional");
+        REQUIRE(P[k], "P is NULL");
+        for (int q = 0; q < k; ++q) REQUIRE(mol_ids[q] != mol_ids[k], "a molecule appears twice");
+    }
+    W = std::max(1, std::min(W, nmol));
+    if (precision == GBXC_FP64) tile_n = 128;
+    REQUIRE(mixed_tile_supported(tile_n), "unsupported GEMM tile");
+    const size_t budget = scratch_budget(ctx) / W;
+    // longest-processing-time assignment of molecules to graph branches by the work
+    // estimate of Eq. batch_work (the paper's greedy minimum-load rule, Algorithm 3)
+    std::vector<int> order(nmol);
+    for (int k = 0; k < nmol; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ms[a]->work > ms[b]->work; });
+    std::vector<double> load(W, 0.0);
+    std::vector<std::vector<int>> br(W);
+    for (int k : order) {
+        int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        br[b].push_back(k);
+        load[b] += ms[k]->work;
+    }
+    std::vector<Schedule *> sch(nmol);
+    for (int k = 0; k < nmol; ++k)
+        sch[k] = &get_schedule(*ms[k], precision, 0, ms[k]->plan.nbatch(), budget, tile_n);
+    if ((int)ctx->branch_ws.size() < W) ctx->branch_ws.resize(W);
+    for (int b = 0; b < W; ++b) {
+        Workspace &w = ctx->branch_ws[b];
+        if (!w.stream) check(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking), "stream");
+        for (int k : br[b]) reserve(w, *ms[k], *sch[k], precision);
+    }
+    for (int k = 0; k < nmol; ++k) {
+        Molecule &m = *ms[k];
+        size_t nn = (size_t)m.nbf * m.nbf;
+        if (nn > m.many_cap || !m.many_P) {
+            size_t c0 = m.many_cap, c1 = m.many_cap, c2 = 0;
+            grow_buf(m.many_P, c0, nn, "P");
+            grow_buf(m.many_V, c1, nn, "V");
+            cudaFree(m.many_tot);
+            m.many_tot = nullptr;
+            grow_buf(m.many_tot, c2, 2, "totals");
+            m.many_cap = nn;
+        }
+    }
+    ManyGraph &G = ctx->many;
+    std::vector<int> ids(mol_ids, mol_ids + nmol), fns(functional, functional + nmol);
+    if (!(G.exec && G.mols == ids && G.fns == fns && G.precision == precision && G.branches == W &&
+          G.tile_n == tile_n && G.budget == budget)) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+        if (!G.fork) check(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming), "event");
+        while ((int)G.join.size() < W) {
+            cudaEvent_t e;
+            check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+            G.join.push_back(e);
+        }
+        Profiler quiet;
+        cudaStream_t o = ctx->stream;
+        check(cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed), "begin capture");
+        cudaGraph_t graph = nullptr;
+        try {
+            check(cudaEventRecord(G.fork, o), "fork");
+            for (int b = 0; b < W; ++b) check(cudaStreamWaitEvent(ctx->branch_ws[b].stream, G.fork, 0), "fork");
+            for (int b = 0; b < W; ++b)
+                for (int k : br[b]) {
+                    Molecule &m = *ms[k];
+                    enqueue(ctx->branch_ws[b], m, *sch[k], m.many_P, functional[k], precision, 0,
+                            m.plan.nbatch(), m.many_V, false, ctx->branch_ws[b].stream, &quiet, m.many_tot);
+                }
+            for (int b = 0; b < W; ++b) {
+                check(cudaEventRecord(G.join[b], ctx->branch_ws[b].stream), "join");
+                check(cudaStreamWaitEvent(o, G.join[b], 0), "join");
+            }
+        } catch (...) {
+            cudaStreamEndCapture(o, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            throw;
+        }
+        check(cudaStreamEndCapture(o, &graph), "end capture");
+        cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        check(e, "instantiate graph");
+        G.mols = ids;
+        G.fns = fns;
+        G.precision = precision;
+        G.branches = W;
+        G.tile_n = tile_n;
+        G.budget = budget;
+        for (int c = 0; c < GBXC_NKERNEL; ++c) G.launches[c] = quiet.launches[c];
+    }
+    cudaStream_t o = ctx->stream;
+    for (int k = 0; k < nmol; ++k) {
+        size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
+        check(cudaMemcpyAsync(ms[k]->many_P, P[k], nn * 8, cudaMemcpyDefault, o), "copy P");
+    }
+    long long total = 0;
+    for (int c = 0; c < GBXC_NKERNEL; ++c) {
+        ctx->prof.launches[c] += G.launches[c];
+        total += G.launches[c];
+    }
+    if (!ctx->ev0) {
+        check(cudaEventCreate(&ctx->ev0), "event");
+        check(cudaEventCreate(&ctx->ev1), "event");
+    }
+    ctx->prof.begin(GBXC_K_OTHER, o);
+    check(cudaEventRecord(ctx->ev0, o), "event");
+    check(cudaGraphLaunch(G.exec, o), "graph launch");
+    check(cudaEventRecord(ctx->ev1, o), "event");
+    ctx->prof.end(GBXC_K_OTHER, o, 0);
+    std::vector<double> tot(2 * (size_t)nmol);
+    for (int k = 0; k < nmol; ++k) {
+        size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
+        check(cudaMemcpyAsync(&tot[2 * k], ms[k]->many_tot, 16, cudaMemcpyDeviceToHost, o), "copy E");
+        if (Vxc && Vxc[k]) check(cudaMemcpyAsync(Vxc[k], ms[k]->many_V, nn * 8, cudaMemcpyDefault, o), "copy V");
+    }
+    check(cudaStreamSynchronize(o), "integrate many");
+    (void)total;
+    if (precision == GBXC_MIXED)
+        for (int b = 0; b < W; ++b) {
+            int werr = 0;
+            check(mixed_read_error(ctx->branch_ws[b].mixed, &werr, ctx->branch_ws[b].stream), "status");
+            if (werr) return fail(ctx, GBXC_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
+        }
+    for (int k = 0; k < nmol; ++k) {
+        if (Exc) Exc[k] = tot[2 * k];
+        if (Nel) Nel[k] = tot[2 * k + 1];
+    }
+    if (ms_out) check(cudaEventElapsedTime(ms_out, ctx->ev0, ctx->ev1), "event time");
+    return GBXC_OK;
+}
+
+}  // namespace
+
 int gbxc_integrate_many(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P,
                         const int *functional, int precision, double *Exc, double *const *Vxc, double *Nel) {
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {
-        REQUIRE(ctx->device >= 0, "integration needs a device context");
-        REQUIRE(nmol > 0 && mol_ids && P && functional, "bad molecule list");
+        REQUIRE(nmol > 0 && mol_ids, "bad molecule list");
+        int W = std::min(nmol, 8), tile_n = 128;
+        auto it = ctx->tuned.find({std::vector<int>(mol_ids, mol_ids + nmol), precision});
+        if (it != ctx->tuned.end()) {
+            W = it->second.first;
+            tile_n = it->second.second;
+        }
+        return many_impl(ctx, nmol, mol_ids, P, functional, precision, W, tile_n, Exc, Vxc,
+                         Nel, nullptr);
+    });
+}
+
+int gbxc_set_schedule(gbxc_ctx *ctx, int nmol, const int *mol_ids, int precision, int branches, int tile_n) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(nmol > 0 && mol_ids, "bad molecule list");
         REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
-        std::vector<Molecule *> ms(nmol);
-        for (int k = 0; k < nmol; ++k) {
-            ms[k] = &get_mol(ctx, mol_ids[k]);
-            if (!ms[k]->has_grid) return fail(ctx, GBXC_ENOTREADY, "a molecule has no grid");
-            REQUIRE(functional[k] == GBXC_SLATER || functional[k] == GBXC_PBE, "unknown functional");
-            REQUIRE(P[k], "P is NULL");
-            for (int q = 0; q < k; ++q) REQUIRE(mol_ids[q] != mol_ids[k], "a molecule appears twice");
-        }
-        const int W = std::min(nmol, 8);
-        const size_t budget = scratch_budget(ctx) / W;
-        // longest-processing-time assignment of molecules to graph branches by the work
-        // estimate of Eq. batch_work (the paper's greedy minimum-load rule, Algorithm 3)
-        std::vector<int> order(nmol);
-        for (int k = 0; k < nmol; ++k) order[k] = k;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ms[a]->work > ms[b]->work; });
-        std::vector<double> load(W, 0.0);
-        std::vector<std::vector<int>> br(W);
-        for (int k : order) {
-            int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            br[b].push_back(k);
-            load[b] += ms[k]->work;
-        }
-        std::vector<Schedule *> sch(nmol);
-        for (int k = 0; k < nmol; ++k)
-            sch[k] = &get_schedule(*ms[k], precision, 0, ms[k]->plan.nbatch(), budget);
-        if ((int)ctx->branch_ws.size() < W) ctx->branch_ws.resize(W);
-        for (int b = 0; b < W; ++b) {
-            Workspace &w = ctx->branch_ws[b];
-            if (!w.stream) check(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking), "stream");
-            for (int k : br[b]) reserve(w, *ms[k], *sch[k], precision);
-        }
-        for (int k = 0; k < nmol; ++k) {
-            Molecule &m = *ms[k];
-            size_t nn = (size_t)m.nbf * m.nbf;
-            if (nn > m.many_cap || !m.many_P) {
-                size_t c0 = m.many_cap, c1 = m.many_cap, c2 = 0;
-                grow_buf(m.many_P, c0, nn, "P");
-                grow_buf(m.many_V, c1, nn, "V");
-                cudaFree(m.many_tot);
-                m.many_tot = nullptr;
-                grow_buf(m.many_tot, c2, 2, "totals");
-                m.many_cap = nn;
-            }
-        }
-        ManyGraph &G = ctx->many;
-        std::vector<int> ids(mol_ids, mol_ids + nmol), fns(functional, functional + nmol);
-        if (!(G.exec && G.mols == ids && G.fns == fns && G.precision == precision && G.branches == W &&
-              G.budget == budget)) {
-            if (G.exec) cudaGraphExecDestroy(G.exec);
-            G.exec = nullptr;
-            if (!G.fork) check(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming), "event");
-            while ((int)G.join.size() < W) {
-                cudaEvent_t e;
-                check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
-                G.join.push_back(e);
-            }
-            Profiler quiet;
-            cudaStream_t o = ctx->stream;
-            check(cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed), "begin capture");
-            cudaGraph_t graph = nullptr;
-            try {
-                check(cudaEventRecord(G.fork, o), "fork");
-                for (int b = 0; b < W; ++b) check(cudaStreamWaitEvent(ctx->branch_ws[b].stream, G.fork, 0), "fork");
-                for (int b = 0; b < W; ++b)
-                    for (int k : br[b]) {
-                        Molecule &m = *ms[k];
-                        enqueue(ctx->branch_ws[b], m, *sch[k], m.many_P, functional[k], precision, 0,
-                                m.plan.nbatch(), m.many_V, false, ctx->branch_ws[b].stream, &quiet, m.many_tot);
-                    }
-                for (int b = 0; b < W; ++b) {
-                    check(cudaEventRecord(G.join[b], ctx->branch_ws[b].stream), "join");
-                    check(cudaStreamWaitEvent(o, G.join[b], 0), "join");
+        REQUIRE(branches >= 1 && branches <= 64, "branches must be in 1..64");
+        REQUIRE(mixed_tile_supported(tile_n), "tile_n must be 64 or 128");
+        ctx->tuned[{std::vector<int>(mol_ids, mol_ids + nmol), precision}] = {branches, tile_n};
+        return GBXC_OK;
+    });
+}
+
+int gbxc_autotune(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P, const int *functional,
+                  int precision, int *branches_out, int *tile_n_out, double *ms_out) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(nmol > 0 && mol_ids, "bad molecule list");
+        REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
+        std::vector<int> Ws;
+        for (int w : {1, 2, 4, 8, 16})
+            if (w <= nmol) Ws.push_back(w);
+        if (Ws.back() < std::min(nmol, 16)) Ws.push_back(std::min(nmol, 16));
+        std::vector<int> tiles = precision == GBXC_MIXED ? std::vector<int>{128, 64} : std::vector<int>{128};
+        double best = 1e300;
+        int bw = Ws.front(), bt = tiles.front();
+        for (int t : tiles)
+            for (int w : Ws) {
+                float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+                int rc = many_impl(ctx, nmol, mol_ids, P, functional, precision, w, t, nullptr, nullptr, nullptr,
+                                   &m0);   // capture + first replay
+                if (rc != GBXC_OK) return rc;
+                rc = many_impl(ctx, nmol, mol_ids, P, functional, precision, w, t, nullptr, nullptr, nullptr, &m1);
+                if (rc != GBXC_OK) return rc;
+                rc = many_impl(ctx, nmol, mol_ids, P, functional, precision, w, t, nullptr, nullptr, nullptr, &m2);
+                if (rc != GBXC_OK) return rc;
+                const double v = std::min(m1, m2);
+                if (v < best) {
+                    best = v;
+                    bw = w;
+                    bt = t;
                 }
-            } catch (...) {
-                cudaStreamEndCapture(o, &graph);
-                if (graph) cudaGraphDestroy(graph);
-                cudaGetLastError();
-                throw;
             }
-            check(cudaStreamEndCapture(o, &graph), "end capture");
-            cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            check(e, "instantiate graph");
-            G.mols = ids;
-            G.fns = fns;
-            G.precision = precision;
-            G.branches = W;
-            G.budget = budget;
-            for (int c = 0; c < GBXC_NKERNEL; ++c) G.launches[c] = quiet.launches[c];
-        }
-        cudaStream_t o = ctx->stream;
-        for (int k = 0; k < nmol; ++k) {
-            size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
-            check(cudaMemcpyAsync(ms[k]->many_P, P[k], nn * 8, cudaMemcpyDefault, o), "copy P");
-        }
-        long long total = 0;
-        for (int c = 0; c < GBXC_NKERNEL; ++c) {
-            ctx->prof.launches[c] += G.launches[c];
-            total += G.launches[c];
-        }
-        ctx->prof.begin(GBXC_K_OTHER, o);
-        check(cudaGraphLaunch(G.exec, o), "graph launch");
-        ctx->prof.end(GBXC_K_OTHER, o, 0);
-        std::vector<double> tot(2 * (size_t)nmol);
-        for (int k = 0; k < nmol; ++k) {
-            size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
-            check(cudaMemcpyAsync(&tot[2 * k], ms[k]->many_tot, 16, cudaMemcpyDeviceToHost, o), "copy E");
-            if (Vxc && Vxc[k]) check(cudaMemcpyAsync(Vxc[k], ms[k]->many_V, nn * 8, cudaMemcpyDefault, o), "copy V");
-        }
-        check(cudaStreamSynchronize(o), "integrate many");
-        (void)total;
-        if (precision == GBXC_MIXED)
-            for (int b = 0; b < W; ++b) {
-                int werr = 0;
-                check(mixed_read_error(ctx->branch_ws[b].mixed, &werr, ctx->branch_ws[b].stream), "status");
-                if (werr) return fail(ctx, GBXC_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
-            }
-        for (int k = 0; k < nmol; ++k) {
-            if (Exc) Exc[k] = tot[2 * k];
-            if (Nel) Nel[k] = tot[2 * k + 1];
-        }
+        ctx->tuned[{std::vector<int>(mol_ids, mol_ids + nmol), precision}] = {bw, bt};
+        if (branches_out) *branches_out = bw;
+        if (tile_n_out) *tile_n_out = bt;
+        if (ms_out) *ms_out = best;
         return GBXC_OK;
     });
 }

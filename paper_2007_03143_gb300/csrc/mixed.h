@@ -55,12 +55,15 @@ struct MixedSchedule {
     int64_t *d_pofs = nullptr;         // per (chunk, batch): first P-slice row
     int64_t *d_pexp_ofs = nullptr;     // per (chunk, batch): first row-exponent entry
     int64_t max_prows = 0, max_pexp = 0;
+    int bn = 128;                      // N tile of the tcgen05 GEMMs: 128 or 64 functions
 };
 
 size_t mixed_row_bytes();
-void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks);
+// Tile widths the tcgen05 GEMMs are built for; `bn` below is one of them.
+bool mixed_tile_supported(int bn);
+void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, int bn, std::vector<int> &tasks);
 void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chunk_t0,
-                          const std::vector<int64_t> &chunk_t1, MixedSchedule &s);
+                          const std::vector<int64_t> &chunk_t1, int bn, MixedSchedule &s);
 void free_mixed_schedule(MixedSchedule &s);
 void free_mixed_resident(MixedResident &r);
 void free_mixed_ctx(MixedCtx &c);

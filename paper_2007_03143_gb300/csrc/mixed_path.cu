@@ -45,7 +45,6 @@ using slc::pow2f;
 using slc::scale2;
 using slc::slice5;
 using slc::exp_of;
-constexpr int BN = 128;         // N extent of one MMA (functions)
 constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
 // at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
@@ -297,24 +296,32 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
 // level 0).  The issue order is listed in issue_op().
 constexpr int XACC = 4;
 constexpr int BM = 128;                        // M extent of one MMA (points or functions)
-constexpr int NBUF = 512 / (XACC * BN);        // accumulator sets that fit in tensor memory
-constexpr int TMEM_COLS = NBUF * XACC * BN;    // 512 columns
-static_assert(NBUF >= 1 && NBUF <= 2, "one or two accumulator sets");
+constexpr int EPI_WARPS = 16;
+constexpr int GEMM_THREADS = 32 * (4 + EPI_WARPS);   // 4 control warps + the epilogue warps
 
-// One pipeline stage holds one 16-wide K step of every slice of both operands: the global
-// rows of 32 values are fetched as two 32-byte halves with the 32-byte swizzle.
-template <int SA, int SB, int STAGES>
-struct GemmSmem {
-    static constexpr int A_BYTES = SA * BM * 32;
-    static constexpr int B_BYTES = SB * BN * 32;
+// Geometry of the persistent GEMM for an N tile of BN functions: one pipeline stage holds
+// one 16-wide K step of every slice of both operands (the global rows of 32 values are
+// fetched as two 32-byte halves with the 32-byte swizzle); tensor memory holds NBUF
+// accumulator sets of 4 x BN columns.
+template <int BN_>
+struct GemmCfg {
+    static constexpr int BN = BN_;
+    static constexpr int NBUF = 512 / (XACC * BN);
+    static constexpr int TMEM_COLS = NBUF * XACC * BN;   // 512 columns
+    static constexpr int STAGES = BN == 128 ? 5 : 7;
+    static constexpr int EPI_COLS = BN / (EPI_WARPS / 4);  // columns per epilogue warp
+    static constexpr int A_BYTES = NSL * BM * 32;
+    static constexpr int B_BYTES = NSL * BN * 32;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int TOTAL = 1024 + STAGES * STAGE + 256;
+    static_assert(NBUF >= 1 && NBUF <= 2, "one or two accumulator sets");
+    static_assert(TOTAL <= 227 * 1024, "shared memory");
 };
 
 // The 15 MMAs of one 16-wide K step with compile-time operand offsets.  `first` is 0 only
 // for the first K step of a task: then the first product into each accumulator overwrites
 // it (levels 0, 1, 2, 3 start at ops 0, 1, 3, 6).
-template <int Q>
+template <int BN, int Q>
 __device__ __forceinline__ void issue_op(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first) {
     constexpr int A[15] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
     constexpr int B[15] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
@@ -327,15 +334,16 @@ __device__ __forceinline__ void issue_op(uint32_t tmem, uint64_t a0, uint64_t b0
     umma::mma_bf16(tmem + C[Q] * BN, ad, bd, idesc, acc);
 }
 
-template <int... Q>
+template <int BN, int... Q>
 __device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first,
                                           std::integer_sequence<int, Q...>) {
-    (issue_op<Q>(tmem, a0, b0, idesc, first), ...);
+    (issue_op<BN, Q>(tmem, a0, b0, idesc, first), ...);
 }
 
+template <int BN>
 __device__ __forceinline__ void issue_slice_mmas(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc,
                                                  uint32_t first) {
-    issue_ops(tmem, a0, b0, idesc, first, std::make_integer_sequence<int, 15>{});
+    issue_ops<BN>(tmem, a0, b0, idesc, first, std::make_integer_sequence<int, 15>{});
 }
 
 // ---------------------------------------------------------------- persistent GEMM
@@ -349,11 +357,6 @@ __device__ __forceinline__ void issue_slice_mmas(uint32_t tmem, uint64_t a0, uin
 // the MMAs of the next); tmem_full[b] (MMA -> epilogue) and tmem_empty[b] (epilogue -> MMA)
 // hand set b over.  The epilogue is kept short: a 4-term combine, power-of-two scaling
 // from exponent bits, one store or one float64 atomic per element.
-constexpr int EPI_WARPS = 16;
-constexpr int GEMM_THREADS = 32 * (4 + EPI_WARPS);   // 4 control warps + the epilogue warps
-constexpr int EPI_COLS = BN / (EPI_WARPS / 4);       // columns per epilogue warp
-constexpr int GEMM_STAGES = BN == 128 ? 5 : 7;
-using GL = GemmSmem<NSL, NSL, GEMM_STAGES>;
 
 struct XGeom {
     int64_t t, r0, pofs;
@@ -408,13 +411,16 @@ __device__ __forceinline__ double f2d_scaled(float f, int k) {
     return __longlong_as_double((long long)d);
 }
 
-// KIND 0: X^j = P^j Phi^j tiles (tasks: point tile, 64-function column chunk).
-// KIND 1: W^j = Z^T Phi tiles (tasks: batch, 128-row block, 64-column block, tile range).
-template <int KIND>
+// KIND 0: X^j = P^j Phi^j tiles (tasks: point tile, BN-function column chunk).
+// KIND 1: W^j = Z^T Phi tiles (tasks: batch, 128-row block, BN-column block, tile range).
+template <int KIND, int BN_>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_constant__ CUtensorMap ta,
                                                                    const __grid_constant__ CUtensorMap tb,
                                                                    ChunkArgs a, MixedArgs m, const int *tasks,
                                                                    int ntasks) {
+    using GL = GemmCfg<BN_>;
+    constexpr int BN = GL::BN, NBUF = GL::NBUF, TMEM_COLS = GL::TMEM_COLS, GEMM_STAGES = GL::STAGES,
+                  EPI_COLS = GL::EPI_COLS;
     extern __shared__ uint8_t smem_raw[];
     uint32_t base = umma::smem_u32(smem_raw);
     uint8_t *smem = smem_raw + (((base + 1023) & ~1023u) - base);
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     // descriptors of slice 0; every other slice is a fixed offset in 16-byte
                     // units (slice tiles BM x 32 B and BN x 32 B apart)
                     const uint64_t a0 = umma::desc_sw32(sa), b0 = umma::desc_sw32(sb);
-                    issue_slice_mmas(tacc, a0, b0, idesc, ks == 0 ? 0u : 1u);
+                    issue_slice_mmas<BN>(tacc, a0, b0, idesc, ks == 0 ? 0u : 1u);
                     umma::mma_commit(&empty[s]);
                 }
                 if (abort_flag) break;
@@ -817,8 +823,10 @@ cudaError_t grow(T *&p, size_t &cap, size_t need) {
 
 size_t mixed_row_bytes() { return (size_t)TILE * (8 * 4 + 2 * 4 + 3 * NSL * 2) + 8 + 16; }
 
-void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks) {
-    int mblk = (n + BM - 1) / BM, nblk = (n + BN - 1) / BN;
+bool mixed_tile_supported(int bn) { return bn == 128 || bn == 64; }
+
+void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, int bn, std::vector<int> &tasks) {
+    int mblk = (n + BM - 1) / BM, nblk = (n + bn - 1) / bn;
     for (int64_t k = s0; k < s1; k += VKS) {
         int64_t k1 = std::min<int64_t>(k + VKS, s1);
         for (int mb = 0; mb < mblk; ++mb)
@@ -833,8 +841,9 @@ void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> 
 }
 
 void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chunk_t0,
-                          const std::vector<int64_t> &chunk_t1, MixedSchedule &s) {
+                          const std::vector<int64_t> &chunk_t1, int bn, MixedSchedule &s) {
     free_mixed_schedule(s);
+    s.bn = bn;
     std::vector<int64_t> pofs, pexp;
     std::vector<int> xt;
     for (size_t c = 0; c < chunk_t0.size(); ++c) {
@@ -848,7 +857,7 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
         for (int64_t t = chunk_t0[c]; t < chunk_t1[c]; ++t) {
             int j = plan.tile_batch[t];
             int64_t n = plan.func_ptr[j + 1] - plan.func_ptr[j];
-            for (int nc = 0; (int64_t)nc * BN < n; ++nc) {
+            for (int nc = 0; (int64_t)nc * bn < n; ++nc) {
                 xt.push_back((int)t);
                 xt.push_back(nc);
             }
@@ -937,10 +946,11 @@ cudaError_t mixed_init(MixedCtx &c) {
     }
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_persistent<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             GL::TOTAL);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(gemm_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, GL::TOTAL);
+        const cudaFuncAttribute smem = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(gemm_persistent<0, 128>, smem, GemmCfg<128>::TOTAL);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<1, 128>, smem, GemmCfg<128>::TOTAL);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<0, 64>, smem, GemmCfg<64>::TOTAL);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<1, 64>, smem, GemmCfg<64>::TOTAL);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -1008,9 +1018,9 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     m.err = c.d_err;
     cudaError_t err = cudaSuccess;
     CUtensorMap tax = make_map(c, m.s.ax, 4 * a.rows, 4 * a.rows, NSL, BM, err);
-    CUtensorMap tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, BN, err);
+    CUtensorMap tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, s.bn, err);
     CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NSL, BM, err);
-    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NSL, BN, err);
+    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NSL, s.bn, err);
     if (err != cudaSuccess) return err;
     Profiler &P = *a.prof;
     P.begin(GBXC_K_PGATHER, st);
@@ -1023,8 +1033,11 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     int nx = (int)ch.nxtask;
     if (nx > 0) {
         P.begin(GBXC_K_XGEMM, st);
-        gemm_persistent<0><<<(unsigned)std::min(nx, c.num_sms), GEMM_THREADS, GL::TOTAL, st>>>(tax, tp, a, m,
-                                                                                                xtasks, nx);
+        const unsigned g = (unsigned)std::min(nx, c.num_sms);
+        if (s.bn == 64)
+            gemm_persistent<0, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(tax, tp, a, m, xtasks, nx);
+        else
+            gemm_persistent<0, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(tax, tp, a, m, xtasks, nx);
         P.end(GBXC_K_XGEMM, st);
     }
     P.begin(GBXC_K_RHO_Z, st);
@@ -1035,8 +1048,12 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     P.end(GBXC_K_SLICE, st);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, st);
-        gemm_persistent<1><<<(unsigned)std::min(a.nvtasks, c.num_sms), GEMM_THREADS, GL::TOTAL, st>>>(
-            tz, tph, a, m, a.vtasks, a.nvtasks);
+        const unsigned g = (unsigned)std::min(a.nvtasks, c.num_sms);
+        if (s.bn == 64)
+            gemm_persistent<1, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(tz, tph, a, m, a.vtasks, a.nvtasks);
+        else
+            gemm_persistent<1, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(tz, tph, a, m, a.vtasks,
+                                                                                   a.nvtasks);
         P.end(GBXC_K_VGEMM, st);
     }
     return cudaGetLastError();

@@ -61,6 +61,41 @@ def test_many_matches_single(setup, prec):
         assert abs(E2[k] - e) <= 1e-10
 
 
+@pytest.mark.parametrize("branches,tile_n", [(1, 64), (3, 64), (2, 128)])
+def test_many_schedules(setup, branches, tile_n):
+    # every schedule computes the same slice products in the same K order per element: only
+    # the order of the float64 V atomics changes
+    G, ctx, mols = setup
+    fns = ["pbe", "pbe", "slater", "pbe", "pbe", "slater"]
+    ids = [m[0] for m in mols]
+    G.gbxc_set_schedule(ctx.h, ids, "mixed", branches, tile_n)
+    Vs = [np.zeros((nbf, nbf)) for (_, nbf, _) in mols]
+    E, N = G.gbxc_integrate_many(ctx.h, ids, [m[2] for m in mols], fns, "mixed", Vs)
+    for k, ((mid, nbf, P), fn) in enumerate(zip(mols, fns)):
+        e, n, V = _alone(G, ctx, mid, nbf, P, fn, "mixed")
+        assert abs(E[k] - e) <= 1e-10 and abs(N[k] - n) <= 1e-10, k
+        assert np.max(np.abs(Vs[k] - V)) <= 1e-9, k
+        e64, _, V64 = _alone(G, ctx, mid, nbf, P, fn, "fp64")
+        assert abs(E[k] - e64) <= 1e-7 and np.max(np.abs(Vs[k] - V64)) <= 1e-6, k
+
+
+def test_autotune(setup):
+    G, ctx, mols = setup
+    fns = ["pbe"] * len(mols)
+    ids = [m[0] for m in mols]
+    Ps = [m[2] for m in mols]
+    w, t, ms = G.gbxc_autotune(ctx.h, ids, Ps, fns, "mixed")
+    assert w in (1, 2, 4, 6) and t in (64, 128) and ms > 0.0
+    E, _ = G.gbxc_integrate_many(ctx.h, ids, Ps, fns, "mixed")
+    for k, (mid, nbf, P) in enumerate(mols):
+        e, _, _ = _alone(G, ctx, mid, nbf, P, "pbe", "mixed")
+        assert abs(E[k] - e) <= 1e-10
+    w64, t64, ms64 = G.gbxc_autotune(ctx.h, ids, Ps, fns, "fp64")
+    assert w64 in (1, 2, 4, 6) and t64 == 128 and ms64 > 0.0
+    with pytest.raises(G.GbxcError):
+        G.gbxc_set_schedule(ctx.h, ids, "mixed", 2, 96)
+
+
 def test_serving_alone_equals_in_the_mix(setup):
     G, ctx, mols = setup
     rng = np.random.default_rng(0)
