@@ -264,21 +264,32 @@ def run_many(args):
     Ps = [torch.tensor(p[3], device="cuda") for p in pool]
     fns = ["pbe"] * len(pool)
     npts = sum(p[2] for p in pool)
-    res = {}
-    for prec in ("fp64", "mixed"):
+    res, tune = {}, {}
+
+    def timed(prec):
         for _ in range(args.warmup):
             G.gbxc_integrate_many(ctx.h, ids, Ps, fns, prec)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             E, N = G.gbxc_integrate_many(ctx.h, ids, Ps, fns, prec)
-        dt = (time.perf_counter() - t0) / args.steps
+        return (time.perf_counter() - t0) / args.steps, E
+
+    for prec in ("fp64", "mixed"):
+        dt0, _ = timed(prec)                       # default schedule: 8 branches, N tile 128
+        if args.no_autotune:
+            dt, E = dt0, _
+        else:
+            w, t, ms = G.gbxc_autotune(ctx.h, ids, Ps, fns, prec)
+            dt, E = timed(prec)
+            tune[prec] = {"branches": w, "tile_n": t, "tuned_device_ms": ms, "default_ms_per_step": dt0 * 1e3,
+                          "tuned_ms_per_step": dt * 1e3}
         res[prec] = {"value": npts / dt, "ms_per_step": dt * 1e3, "E": E}
     dE = float(np.max(np.abs(res["mixed"]["E"] - res["fp64"]["E"])))
     line = {"mode": "many", "metric": "grid pts/s, one CUDA-graph launch over many molecules", "unit": UNIT,
             "value": res["mixed"]["value"], "ms_per_step": res["mixed"]["ms_per_step"],
             "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"]},
-            "max_dE_xc_mixed_vs_fp64": dE, "n_molecules": len(pool), "waters": sizes, "npts": npts,
+            "max_dE_xc_mixed_vs_fp64": dE, "autotune": tune, "n_molecules": len(pool), "waters": sizes, "npts": npts,
             "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
             "timing": "wall clock around the call (inputs resident on the device)"}
     print(json.dumps(line))
@@ -398,6 +409,7 @@ def main():
     ap.add_argument("--scratch-mb", type=int, default=0, help="device scratch budget (0 = default)")
     ap.add_argument("--mode", default="single", choices=["single", "many", "serve"])
     ap.add_argument("--nmol", type=int, default=64)
+    ap.add_argument("--no-autotune", action="store_true", help="batching: keep the default schedule")
     ap.add_argument("--min-waters", type=int, default=1)
     ap.add_argument("--max-waters", type=int, default=8)
     ap.add_argument("--pool", type=int, default=16)
