@@ -537,23 +537,46 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             if (!umma::mbar_wait(drain, 0)) atomicOr(m.err, 4);
         }
     } else if (warp >= 4) {   // ---------------------------------------------- epilogue
+        // Per task, the epilogue warps first stage the column data of the task (X: P^j row
+        // exponents; V: global function indices and Phi group exponents) in shared memory,
+        // double-buffered by task parity, then meet at named barrier 1 (the 16 epilogue
+        // warps only).  Every epilogue warp visits every task and every barrier; after an
+        // abort the waits and the drain are skipped, never the barrier.
+        __shared__ int col_a[2][BN], col_b[2][BN];
         const int q = warp & 3, cpart = (warp - 4) >> 2;
         const int i = q * 32 + lane;
+        const int et = (warp - 4) * 32 + lane;   // 0 .. 511
         uint32_t tau = 0;
-        for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x, ++tau) {
-            const uint32_t b = tau % NBUF, use = tau / NBUF;
+        for (int k = blockIdx.x; k < ntasks; k += gridDim.x, ++tau) {
+            const uint32_t b = tau % NBUF, use = tau / NBUF, sb = tau & 1;
+            if (KIND == 0) {
+                XGeom g = x_geom(a, m, tasks, k);
+                if (et < BN) {
+                    const int mu = g.nc * BN + et;
+                    col_a[sb][et] = mu < g.n ? m.pexp[m.pexp_ofs[g.jl] + mu] : 0;
+                }
+            } else {
+                VGeom g = v_geom(a, tasks, k);
+                if (et < BN) {
+                    const int nu = g.nc * BN + et;
+                    const int64_t rg = a.plan.tile_row[g.tb] - a.row0;
+                    col_a[sb][et] = nu < g.n ? a.plan.func_idx[a.plan.func_ptr[g.j] + nu] : 0;
+                    col_b[sb][et] = nu < g.n ? m.s.fexp[rg + nu] : 0;
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
+            if (abort_flag) continue;
             if (!umma::mbar_wait(&tfull[b], use & 1)) {
                 atomicOr(m.err, 4);
                 abort_flag = 1;
-                break;
+                continue;
             }
             umma::fence_after_sync();
             __syncwarp();
             const uint32_t lane_base = tmem + b * (XACC * BN) + ((uint32_t)(q * 32) << 16);
             if (KIND == 0) {
                 XGeom g = x_geom(a, m, tasks, k);
-                int ei = m.s.pexp[(g.t - a.t0) * TILE + i];
-                const int *fexp = m.pexp + m.pexp_ofs[g.jl];
+                const int ei = m.s.pexp[(g.t - a.t0) * TILE + i];
 #pragma unroll 1
                 for (int c = cpart * EPI_COLS; c < (cpart + 1) * EPI_COLS; c += 16) {
                     if (g.nc * BN + c >= g.n) break;   // warp-uniform
@@ -565,10 +588,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     umma::tmem_wait_ld();
 #pragma unroll
                     for (int kk = 0; kk < 16; ++kk) {
-                        int mu = g.nc * BN + c + kk;
+                        const int mu = g.nc * BN + c + kk;
                         if (mu < g.n) {
                             df x = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
-                            const int sc = min(max(ei + fexp[mu], -252), 252);
+                            const int sc = min(max(ei + col_a[sb][c + kk], -252), 252);
                             const float s1 = pow2f(sc >> 1), s2 = pow2f(sc - (sc >> 1));
                             m.s.x[(size_t)(g.r0 + mu) * TILE + i] =
                                 make_float2(__fmul_rn(__fmul_rn(x.h, s1), s2), __fmul_rn(__fmul_rn(x.l, s1), s2));
@@ -580,11 +603,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                 // V = V_acc + V_acc^T is unchanged, and the 32 lanes of a warp (consecutive
                 // mu) then update neighbouring words of one row of V_acc
                 VGeom g = v_geom(a, tasks, k);
-                const int *F = a.plan.func_idx + a.plan.func_ptr[g.j];
-                int mu = g.mc * BM + i;
-                size_t colg = (mu < g.n) ? (size_t)F[mu] : 0;
-                int64_t rg = a.plan.tile_row[g.tb] - a.row0;   // group exponents on the first tile
-                int ez = (mu < g.n) ? m.s.zexp[rg + mu] : 0;
+                const int mu = g.mc * BM + i;
+                const size_t colg = (mu < g.n) ? (size_t)a.plan.func_idx[a.plan.func_ptr[g.j] + mu] : 0;
+                const int64_t rg = a.plan.tile_row[g.tb] - a.row0;   // group exponents on the first tile
+                const int ez = (mu < g.n) ? m.s.zexp[rg + mu] : 0;
 #pragma unroll 1
                 for (int c = cpart * EPI_COLS; c < (cpart + 1) * EPI_COLS; c += 16) {
                     if (g.nc * BN + c >= g.n) break;   // warp-uniform
@@ -597,11 +619,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     if (mu < g.n) {
 #pragma unroll
                         for (int kk = 0; kk < 16; ++kk) {
-                            int nu = g.nc * BN + c + kk;
+                            const int nu = g.nc * BN + c + kk;
                             if (nu < g.n) {
                                 df w = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
-                                int sc = ez + m.s.fexp[rg + nu];
-                                atomicAdd(&a.Vacc[(size_t)F[nu] * a.nbf + colg],
+                                const int sc = ez + col_b[sb][c + kk];
+                                atomicAdd(&a.Vacc[(size_t)col_a[sb][c + kk] * a.nbf + colg],
                                           f2d_scaled(w.h, sc) + f2d_scaled(w.l, sc));
                             }
                         }
