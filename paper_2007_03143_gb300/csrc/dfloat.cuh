@@ -4,14 +4,18 @@
 // Knuth's two-sum; every step uses the explicitly rounded intrinsics so no compiler
 // contraction can change it.
 //
-// df_exp_neg(t) = exp(-t) for t >= 0: Cody-Waite reduction t = k ln2 + r (|r| <= ln2/2,
-// ln2 in three float parts), Taylor series of exp(-r/8) to degree 7 (terms from y^4 on
-// summed in float32: |y| <= 0.0434 puts their rounding below 2^-47; coefficients 1/n! as df
-// below that), three squarings, scaling by 2^-k.  Relative error ~1e-13; results below
-// 2^-126 lose precision gradually and are zero from t = 87 on.
+// exp_neg(t, tab) = exp(-t) for t >= 0, table-driven after P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point arithmetic" (ACM TOMS
+// 15, 1989): t = k ln2/64 + r with |r| <= ln2/128 (ln2/64 in three float parts), exp(-r)
+// by its Taylor series to degree 5, times 2^(-(k mod 64)/64) from a 64-entry double-float
+// table (make_exp2_table) and 2^-floor(k/64).  Relative error ~1e-14; results below 2^-126
+// lose precision gradually and are zero from t = 87 on.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+
+#include <cuda_runtime.h>
 
 namespace gbxc {
 namespace dfl {
@@ -69,39 +73,40 @@ __device__ __forceinline__ double to_double(df a) { return (double)a.h + (double
 
 __device__ __forceinline__ df ldexp_df(df a, int k) { return {ldexpf(a.h, k), ldexpf(a.l, k)}; }
 
-// exp(-t), t >= 0 given as a df.
-__device__ __forceinline__ df exp_neg(df t) {
+// The table of exp_neg: tab[j] = 2^(-j/64) as (hi, lo), from the host's float64 exp2.
+inline void make_exp2_table(float2 *tab) {
+    for (int j = 0; j < 64; ++j) {
+        const double v = std::exp2(-(double)j / 64.0);
+        const float hi = (float)v;
+        tab[j] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
+// exp(-t), t >= 0 given as a df; `tab` from make_exp2_table (any memory space).
+__device__ __forceinline__ df exp_neg(df t, const float2 *tab) {
     if (!(t.h < 87.0f)) return {0.f, 0.f};
-    // ln 2 = C1 + C2 + C3; C1 has 15 significant bits so k*C1 is exact for k < 2^9
-    const float C1 = 0.693145751953125f;
-    const float C2 = 1.428606765e-06f;  // ln2 - C1, rounded
-    const float C3 = 5.497923148e-14f;  // ln2 - C1 - C2, rounded
-    float k = rintf(__fmul_rn(t.h, 1.442695022f));
-    // r = t - k ln2 in df
-    float a = __fsub_rn(t.h, __fmul_rn(k, C1));   // exact (Sterbenz / small k)
-    float p2 = __fmul_rn(k, C2);
-    float e2 = __fmaf_rn(k, C2, -p2);
+    // ln2/64 = C1 + C2 + C3; C1 has 11 significant bits so k*C1 is exact for k < 2^13
+    const float C1 = 0.01082611083984375f;
+    const float C2 = 4.3138566070e-06f;
+    const float C3 = -2.0164562565e-13f;
+    const float k = rintf(__fmul_rn(t.h, 92.33248138f));   // 64 / ln2
+    const float a = __fsub_rn(t.h, __fmul_rn(k, C1));       // exact (Sterbenz / k = 0)
+    const float p2 = __fmul_rn(k, C2);
+    const float e2 = __fmaf_rn(k, C2, -p2);
     df r = two_sum(a, -p2);
     r = add_f(r, __fsub_rn(t.l, e2));
     r = add_f(r, -__fmul_rn(k, C3));
-    // y = -r / 8, |y| <= 0.0434
-    df y = {ldexpf(-r.h, -3), ldexpf(-r.l, -3)};
-    // Taylor: 1 + y + y^2/2 + y^3/6 + y^4 (1/24 + y/120 + y^2/720 + y^3/5040) (Horner)
-    const df I2 = {0.5f, 0.f};
-    const df I3 = {1.666666716e-01f, -4.967053879e-09f};
-    float q = 1.984127011e-04f;                    // 1/7!
-    q = __fmaf_rn(q, y.h, 1.388888923e-03f);       // 1/6!
-    q = __fmaf_rn(q, y.h, 8.333333768e-03f);       // 1/5!
-    q = __fmaf_rn(q, y.h, 4.166666791e-02f);       // 1/4!
-    df s = add(mul_f(y, q), I3);
-    s = add(mul(s, y), I2);
-    s = add_f(mul(s, y), 1.0f);
-    s = add_f(mul(s, y), 1.0f);
-    s = mul(s, s);
-    s = mul(s, s);
-    s = mul(s, s);
-    // 2^-k with 0 <= k <= 126 (t < 87), from the exponent field
-    const float sc = __int_as_float((127 - (int)k) << 23);
+    // exp(-r) = 1 + r (-1 + r (1/2 - r q)), q = 1/6 - r/24 + r^2/120 in float32 (|r| <= 0.0055:
+    // its rounding enters below 2^-49); 1/2 - r q by two-sum, the two outer steps in df
+    float q = __fmaf_rn(r.h, 8.3333337680e-03f, -4.1666667908e-02f);
+    q = __fmaf_rn(q, r.h, 1.6666667163e-01f);
+    df w = two_sum(0.5f, -__fmul_rn(r.h, q));
+    w = add_f(mul(w, r), -1.0f);
+    df s = add_f(mul(w, r), 1.0f);
+    const int ki = (int)k;
+    const float2 T = tab[ki & 63];
+    s = mul(s, {T.x, T.y});
+    const float sc = __int_as_float((127 - (ki >> 6)) << 23);   // 2^-floor(k/64), k < 8040
     return {__fmul_rn(s.h, sc), __fmul_rn(s.l, sc)};
 }
 

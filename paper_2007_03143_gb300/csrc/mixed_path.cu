@@ -206,7 +206,15 @@ __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const
 // float32 pipe (exp(-alpha r^2) by dfl::exp_neg), stored as (hi, lo) pairs; then the
 // point's Ozaki slices of Phi, K-blocked by 32 functions.  Consecutive shells on one centre
 // share X, Y, Z and r^2.
-__global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells) {
+struct Exp2Table {
+    float2 v[64];   // 2^(-j/64) as (hi, lo): the table of dfl::exp_neg
+};
+
+__global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells,
+                                                     const __grid_constant__ Exp2Table e2t) {
+    __shared__ float2 tab[64];
+    if (threadIdx.x < 64) tab[threadIdx.x] = e2t.v[threadIdx.x];
+    __syncthreads();
     int64_t t = a.t0 + blockIdx.x;
     int i = threadIdx.x;
     int j = a.plan.tile_batch[t];
@@ -238,7 +246,7 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
         }
         df g = {0.f, 0.f}, h = {0.f, 0.f};
         for (int k = 0; k < sh.nprim; ++k) {
-            df ex = dfl::exp_neg(df_mul({sh.ah[k], sh.al[k]}, r2));
+            df ex = dfl::exp_neg(df_mul({sh.ah[k], sh.al[k]}, r2), tab);
             g = df_add(g, df_mul({sh.dh[k], sh.dl[k]}, ex));
             h = df_add(h, df_mul({sh.gh[k], sh.gl[k]}, ex));
         }
@@ -1049,7 +1057,12 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     pslice_kernel<<<dim3(ch.j1 - ch.j0 + 1, (ch.max_np + 3) / 4), 128, 0, st>>>(a, m);
     P.end(GBXC_K_PGATHER, st);
     P.begin(GBXC_K_COLLOC, st);
-    colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells);
+    static const Exp2Table e2t = [] {
+        Exp2Table x;
+        dfl::make_exp2_table(x.v);
+        return x;
+    }();
+    colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells, e2t);
     P.end(GBXC_K_COLLOC, st);
     const int *xtasks = s.d_xtasks + 2 * ch.xtask0;
     int nx = (int)ch.nxtask;
