@@ -1,0 +1,95 @@
+"""Degenerate and edge inputs through the C-ABI against the oracle (Algorithm 4, Eqs. rho/exc/
+vxc): zero density, densities straddling the rho < 1e-15 cut, single atoms (partition of unity
+with one centre), and batches capped at 16 points (nearly empty 128-point tiles)."""
+import numpy as np
+import pytest
+
+import xcinputs as X
+from oracle import integrate as I
+
+from gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(mol, spec, functional, P, forms=("fp64", "mixed")):
+    G = need_gpu()
+    basis = X.make_basis(mol)
+    ctx = G.Context(0)
+    try:
+        mid = ctx.load_molecule(mol, basis, spec)
+        out = {}
+        for f in forms:
+            V = np.zeros((basis.nbf, basis.nbf))
+            E, N = G.gbxc_integrate(ctx.h, mid, P, functional, f, V)
+            out[f] = (E, N, V)
+        return basis, out
+    finally:
+        ctx.close()
+
+
+def _oracle(mol, basis, spec, functional, P):
+    g = I.make_grid(mol.xyz, spec)
+    pl = I.make_plan(g, mol.xyz, basis, spec)
+    return I.integrate_method(g, basis, P, functional, pl)
+
+
+def _density(mol, nocc, seed):
+    basis = X.make_basis(mol)
+    return X.density_matrix(X.overlap_matrix(basis), nocc, seed)
+
+
+SPEC_SMALL = X.GridSpec(20, 8, 16, "ssf", 128)
+
+
+@pytest.mark.parametrize("functional", ["pbe", "slater"])
+def test_zero_density(functional):
+    mol = X.water_cluster(2, 9100)
+    nbf = X.make_basis(mol).nbf
+    _, out = _run(mol, SPEC_SMALL, functional, np.zeros((nbf, nbf)))
+    for f, (E, N, V) in out.items():
+        assert E == 0.0 and N == 0.0, f
+        assert not np.any(V), f
+
+
+@pytest.mark.parametrize("scale", [1e-12, 1e-6])
+def test_density_near_the_cut(scale):
+    # rho spans the 1e-15 threshold: points on either side of it contribute ~1e-20
+    mol = X.water_cluster(2, 9100)
+    P = scale * _density(mol, 10, 9101)
+    basis, out = _run(mol, SPEC_SMALL, "pbe", P)
+    ref = _oracle(mol, basis, SPEC_SMALL, "pbe", P)
+    E, N, V = out["fp64"]
+    assert abs(E - ref.E) <= 1e-9 * abs(ref.E) + 1e-18
+    assert abs(N - ref.N) <= 1e-9 * abs(ref.N) + 1e-18
+    assert np.max(np.abs(V - ref.V)) <= 1e-9 * np.max(np.abs(ref.V)) + 1e-18
+    Em, Nm, Vm = out["mixed"]
+    assert abs(Em - ref.E) <= 1e-7 * abs(ref.E) + 1e-18
+    assert np.max(np.abs(Vm - ref.V)) <= 1e-6 * np.max(np.abs(ref.V)) + 1e-18
+
+
+@pytest.mark.parametrize("Z,partition", [(8, "ssf"), (1, "becke"), (8, "becke")])
+def test_single_atom(Z, partition):
+    mol = X.single_atom(Z)
+    spec = X.GridSpec(30, 10, 20, partition, 256)
+    P = _density(mol, 4 if Z == 8 else 1, 9400 + Z)
+    basis, out = _run(mol, spec, "pbe", P)
+    ref = _oracle(mol, basis, spec, "pbe", P)
+    E, N, V = out["fp64"]
+    assert abs(E - ref.E) <= 1e-9 and abs(N - ref.N) <= 1e-9
+    assert np.max(np.abs(V - ref.V)) <= 1e-9
+    Em, Nm, Vm = out["mixed"]
+    assert abs(Em - ref.E) <= 1e-7 and np.max(np.abs(Vm - ref.V)) <= 1e-6
+
+
+def test_tiny_batches():
+    # at most 16 points per batch: every tile is mostly padding
+    mol = X.water_cluster(2, 9100)
+    spec = X.GridSpec(20, 8, 16, "ssf", 16)
+    P = _density(mol, 10, 9101)
+    basis, out = _run(mol, spec, "pbe", P)
+    ref = _oracle(mol, basis, spec, "pbe", P)
+    E, N, V = out["fp64"]
+    assert abs(E - ref.E) <= 1e-9 and np.max(np.abs(V - ref.V)) <= 1e-9
+    Em, Nm, Vm = out["mixed"]
+    assert abs(Em - ref.E) <= 1e-7 and np.max(np.abs(Vm - ref.V)) <= 1e-6
