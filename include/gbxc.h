@@ -139,6 +139,16 @@ int gbxc_load_basis(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, 
 int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
                    int *nbatch_out);
 
+/* The same as gbxc_load_grid with the grid expansion, the cuboid subdivision of every atom's
+ * points and Algorithm 1 on every leaf run as device kernels (the batch merge and layout stay
+ * on the host).  The resulting grid, batches and screening lists are identical, bit for bit,
+ * to gbxc_load_grid's.  The paper plans on the host and points to moving Algorithm 3's batch
+ * generation and screening to the GPU as the way to relieve its strong-scaling limit
+ * (Algorithm 3 discussion; Conclusion).  GBXC_EINVAL for a host-only context or a grid of
+ * 2^31 points or more. */
+int gbxc_load_grid_device(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
+                          int *nbatch_out);
+
 /* Sizes of the plan of `mol` (after gbxc_load_grid). */
 int gbxc_plan_info_get(gbxc_ctx *ctx, int mol, gbxc_plan_info *info);
 

@@ -34,7 +34,7 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
-            "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule"]
+            "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule", "gbxc_load_grid_device"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -81,6 +81,8 @@ def lib():
     L.gbxc_load_basis.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_int)]
     L.gbxc_load_grid.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
+    L.gbxc_load_grid_device.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
+    L.gbxc_load_grid_device.restype = c_int
     L.gbxc_plan_info_get.argtypes = [c_void_p, c_int, POINTER(PlanInfo)]
     L.gbxc_export_plan.argtypes = [c_void_p, c_int] + [c_void_p] * 10
     L.gbxc_integrate.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, pd, c_void_p, pd, c_void_p]
@@ -184,6 +186,14 @@ def gbxc_load_grid(ctx, mol, nrad, ntheta, nphi, partition, max_batch, eta=1e-10
     spec = GridSpec(nrad, ntheta, nphi, PARTITIONS.get(partition, partition), max_batch, eta, mk_alpha)
     npts, nb = c_longlong(), c_int()
     _check(ctx, lib().gbxc_load_grid(ctx, mol, ctypes.byref(spec), ctypes.byref(npts), ctypes.byref(nb)))
+    return npts.value, nb.value
+
+
+def gbxc_load_grid_device(ctx, mol, nrad, ntheta, nphi, partition, max_batch, eta=1e-10, mk_alpha=5.0):
+    """gbxc_load_grid with the planner's kernels on the device (identical plan)."""
+    spec = GridSpec(nrad, ntheta, nphi, PARTITIONS.get(partition, partition), max_batch, eta, mk_alpha)
+    npts, nb = c_longlong(), c_int()
+    _check(ctx, lib().gbxc_load_grid_device(ctx, mol, ctypes.byref(spec), ctypes.byref(npts), ctypes.byref(nb)))
     return npts.value, nb.value
 
 
@@ -343,10 +353,11 @@ class Context:
         except Exception:
             pass
 
-    def load_molecule(self, mol, basis, grid):
+    def load_molecule(self, mol, basis, grid, device_planner=False):
         """Register an ``xcinputs`` Molecule/Basis pair and build its grid; returns the id."""
         mid, nbf = gbxc_load_basis(self.h, mol.xyz, mol.Z, basis.atom, basis.L, basis.nprim,
                                    basis.alpha, basis.coeff)
-        gbxc_load_grid(self.h, mid, grid.nrad, grid.ntheta, grid.nphi, grid.partition,
-                       grid.max_batch, grid.eta, grid.mk_alpha)
+        load = gbxc_load_grid_device if device_planner else gbxc_load_grid
+        load(self.h, mid, grid.nrad, grid.ntheta, grid.nphi, grid.partition, grid.max_batch, grid.eta,
+             grid.mk_alpha)
         return mid

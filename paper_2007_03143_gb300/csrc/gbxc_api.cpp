@@ -950,8 +950,24 @@ int gbxc_load_basis(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, 
     });
 }
 
+namespace {
+int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out, int *nbatch_out,
+                   bool on_device);
+}
+
 int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
                    int *nbatch_out) {
+    return load_grid_impl(ctx, mol, spec, npts_out, nbatch_out, false);
+}
+
+int gbxc_load_grid_device(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
+                          int *nbatch_out) {
+    return load_grid_impl(ctx, mol, spec, npts_out, nbatch_out, true);
+}
+
+namespace {
+int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out, int *nbatch_out,
+                   bool on_device) {
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {
         REQUIRE(spec, "spec is NULL");
@@ -968,15 +984,24 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
             ctx->many.exec = nullptr;
             ctx->many.mols.clear();
         }
+        if (on_device) REQUIRE(!host_only, "the device planner needs a device context");
         free_grid(m);
         m.spec = *spec;
         std::vector<double> x, y, z, wq;
         std::vector<int> parent;
-        build_molecular_grid(m.xyz, *spec, x, y, z, wq, parent);
         std::vector<double> rcut(m.nshell);
         for (int s = 0; s < m.nshell; ++s)
             rcut[s] = shell_cutoff(m.shells[s].alpha, m.shells[s].nprim, spec->eta);
-        build_plan(m.xyz, m.shells, rcut, m.nbf, *spec, x, y, z, wq, parent, m.plan);
+        if (on_device) {
+            int status = 0;
+            check(device_plan(m.xyz, m.shells, rcut, *spec, x, y, z, wq, parent, m.plan, ctx->stream, &status),
+                  "device planner");
+            if (status == 1) return fail(ctx, GBXC_EINVAL, "grid too large for the device planner (>= 2^31 points)");
+            if (status == 2) return fail(ctx, GBXC_ECUDA, "device planner: cell stack overflow");
+        } else {
+            build_molecular_grid(m.xyz, *spec, x, y, z, wq, parent);
+            build_plan(m.xyz, m.shells, rcut, m.nbf, *spec, x, y, z, wq, parent, m.plan);
+        }
         m.work = 0.0;
         for (double wj : m.plan.work) m.work += wj;
         if (host_only) {
@@ -1028,6 +1053,8 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
         return GBXC_OK;
     });
 }
+
+}  // namespace
 
 int gbxc_plan_info_get(gbxc_ctx *ctx, int mol, gbxc_plan_info *info) {
     if (!ctx) return GBXC_EINVAL;

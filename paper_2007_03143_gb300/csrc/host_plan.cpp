@@ -162,15 +162,15 @@ double shell_cutoff(const double *alpha, int nprim, double eta) {
     return rc;
 }
 
-void build_molecular_grid(const std::vector<double> &xyz, const gbxc_grid_spec &spec,
-                          std::vector<double> &x, std::vector<double> &y, std::vector<double> &z,
-                          std::vector<double> &wq, std::vector<int> &parent) {
-    std::vector<double> r, wr, t, wt;
-    mura_knowles(spec.nrad, spec.mk_alpha, r, wr);
+void grid_tables(const gbxc_grid_spec &spec, GridTables &T) {
+    std::vector<double> t, wt;
+    mura_knowles(spec.nrad, spec.mk_alpha, T.r, T.wr);
     gauss_legendre(spec.ntheta, t, wt);
     int nt = spec.ntheta, np = spec.nphi;
-    std::vector<double> ux((size_t)nt * np), uy((size_t)nt * np), uz((size_t)nt * np),
-        wa((size_t)nt * np);
+    T.ux.assign((size_t)nt * np, 0.0);
+    T.uy.assign((size_t)nt * np, 0.0);
+    T.uz.assign((size_t)nt * np, 0.0);
+    T.wa.assign((size_t)nt * np, 0.0);
     std::vector<double> cphi(np), sphi(np);
     for (int b = 0; b < np; ++b) {
         cphi[b] = std::cos(2.0 * kPi * b / np);
@@ -181,13 +181,21 @@ void build_molecular_grid(const std::vector<double> &xyz, const gbxc_grid_spec &
         double st = std::sqrt(1.0 - t[a] * t[a]);
         for (int b = 0; b < np; ++b) {
             size_t k = (size_t)a * np + b;
-            ux[k] = st * cphi[b];
-            uy[k] = st * sphi[b];
-            uz[k] = t[a];
-            wa[k] = wt[a] * wphi;
+            T.ux[k] = st * cphi[b];
+            T.uy[k] = st * sphi[b];
+            T.uz[k] = t[a];
+            T.wa[k] = wt[a] * wphi;
         }
     }
-    size_t natoms = xyz.size() / 3, nang = (size_t)nt * np, npa = (size_t)spec.nrad * nang;
+}
+
+void build_molecular_grid(const std::vector<double> &xyz, const gbxc_grid_spec &spec,
+                          std::vector<double> &x, std::vector<double> &y, std::vector<double> &z,
+                          std::vector<double> &wq, std::vector<int> &parent) {
+    GridTables T;
+    grid_tables(spec, T);
+    const std::vector<double> &r = T.r, &wr = T.wr, &ux = T.ux, &uy = T.uy, &uz = T.uz, &wa = T.wa;
+    size_t natoms = xyz.size() / 3, nang = ux.size(), npa = (size_t)spec.nrad * nang;
     x.resize(natoms * npa);
     y.resize(natoms * npa);
     z.resize(natoms * npa);
@@ -237,11 +245,8 @@ void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &she
         subdivide(idx, c, 0, spec.max_batch, xyz, P, leaves);
         start = end;
     }
-    plan.nleaf = (int)leaves.size();
-    // 2. Algorithm 1 on each leaf's tight bounding box, 3. merge equal shell lists
-    std::map<std::vector<int>, int> key_to_batch;
-    std::vector<std::vector<int>> bshells;
-    std::vector<std::vector<int>> bleaves;
+    // 2. Algorithm 1 on each leaf's tight bounding box
+    std::vector<std::vector<int>> keeps(leaves.size());
     size_t nsh = shells.size();
     for (size_t l = 0; l < leaves.size(); ++l) {
         const auto &idx = leaves[l];
@@ -253,9 +258,25 @@ void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &she
                 W[d] = std::max(W[d], P[d][p]);
             }
         }
-        std::vector<int> keep;
         for (size_t s = 0; s < nsh; ++s)
-            if (cuboid_sphere(shells[s].c, rcut[s], V, W)) keep.push_back((int)s);
+            if (cuboid_sphere(shells[s].c, rcut[s], V, W)) keeps[l].push_back((int)s);
+    }
+    plan_from_leaves(natoms, shells, leaves, keeps, x, y, z, wq, parent, plan);
+}
+
+// 3. merge equal shell lists (first-occurrence order), 4. lay the points out batch by batch,
+// function lists, work estimate (Eq. batch_work), 5. 128-point tiles.
+void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
+                      const std::vector<std::vector<int64_t>> &leaves, const std::vector<std::vector<int>> &keeps,
+                      const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
+                      const std::vector<double> &wq, const std::vector<int> &parent, HostPlan &plan) {
+    size_t npts = x.size();
+    plan.nleaf = (int)leaves.size();
+    std::map<std::vector<int>, int> key_to_batch;
+    std::vector<std::vector<int>> bshells;
+    std::vector<std::vector<int>> bleaves;
+    for (size_t l = 0; l < leaves.size(); ++l) {
+        const std::vector<int> &keep = keeps[l];
         auto it = key_to_batch.find(keep);
         if (it == key_to_batch.end()) {
             key_to_batch.emplace(keep, (int)bshells.size());

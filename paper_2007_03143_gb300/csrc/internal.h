@@ -66,6 +66,12 @@ struct DevPlan {
 // Grid generation and planning on the host (host_plan.cpp).  Bitwise contract:
 // the same coordinates and the same batches as the reference CPU planner in the
 // same process (plain IEEE double arithmetic, no contraction, platform libm).
+// 1-D factors of the atomic grid: Mura-Knowles radii and weights (r^2 included), and the
+// angular product rule's unit vectors and weights.
+struct GridTables {
+    std::vector<double> r, wr, ux, uy, uz, wa;
+};
+void grid_tables(const gbxc_grid_spec &spec, GridTables &T);
 void build_molecular_grid(const std::vector<double> &xyz, const gbxc_grid_spec &spec,
                           std::vector<double> &x, std::vector<double> &y, std::vector<double> &z,
                           std::vector<double> &wq, std::vector<int> &parent);
@@ -77,6 +83,19 @@ void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &she
                 const std::vector<int> &parent, HostPlan &plan);
 
 inline int64_t pad_funcs(int64_t n) { return (n + FBLK - 1) / FBLK * FBLK; }
+// The planner as device kernels (device_plan.cu): the same grid and plan as
+// build_molecular_grid + build_plan, bit for bit.  *status: 0 done, 1 grid too large,
+// 2 internal stack overflow (cannot happen for depth <= 16).
+cudaError_t device_plan(const std::vector<double> &xyz, const std::vector<DevShell> &shells,
+                        const std::vector<double> &rcut, const gbxc_grid_spec &spec, std::vector<double> &x,
+                        std::vector<double> &y, std::vector<double> &z, std::vector<double> &wq,
+                        std::vector<int> &parent, HostPlan &plan, cudaStream_t s, int *status);
+// The planner's last steps, shared by the host and the device planner: merge leaves with
+// equal shell lists (first occurrence first), lay out points, functions, work and tiles.
+void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
+                      const std::vector<std::vector<int64_t>> &leaves, const std::vector<std::vector<int>> &keeps,
+                      const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
+                      const std::vector<double> &wq, const std::vector<int> &parent, HostPlan &plan);
 
 // Per-kernel-class launch counter and optional CUDA-event timer (profiler.cpp).
 // Kernel classes are the GBXC_K_* constants of gbxc.h.
