@@ -11,9 +11,11 @@
 //                    cell's points are split into its 27 or 8 children by a stable counting
 //                    scatter, which keeps every child's points in ascending order
 //   screen_leaves    tight box of each leaf, Algorithm 1 for every shell -> bit masks
+//   layout_points    the points of the merged batches in batch order, left on the device
 //
-// Merging leaves with equal shell lists and the batch layout run on the host
-// (plan_from_leaves, shared with the host planner).
+// Merging leaves with equal shell lists and the batch metadata (function lists, work, tiles)
+// run on the host, shared with the host planner (merge_leaves, batch_metadata); only leaf
+// ranges and shell masks cross to the host.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
@@ -305,6 +307,25 @@ __global__ void __launch_bounds__(PT) screen_leaves(const double *__restrict__ x
     }
 }
 
+// Points of the merged batches in batch order: leaf order[k] goes to out_ofs[k].
+__global__ void layout_points(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                              const double *__restrict__ wq, const int *__restrict__ parent, const int *__restrict__ idx,
+                              const int *__restrict__ lb, const int *__restrict__ le, const int *__restrict__ order,
+                              const int64_t *__restrict__ out_ofs, DevPoints out) {
+    const int l = order[blockIdx.x];
+    const int b = lb[l], n = le[l] - b;
+    const int64_t o = out_ofs[blockIdx.x];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int p = idx[b + t];
+        out.x[o + t] = x[p];
+        out.y[o + t] = y[p];
+        out.z[o + t] = z[p];
+        out.wq[o + t] = wq[p];
+        out.parent[o + t] = parent[p];
+        out.point_index[o + t] = p;
+    }
+}
+
 template <typename T>
 struct DevBuf {
     T *p = nullptr;
@@ -335,10 +356,10 @@ cudaError_t download(std::vector<T> &v, const T *p, size_t n, cudaStream_t s) {
 }  // namespace
 
 cudaError_t device_plan(const std::vector<double> &xyz, const std::vector<DevShell> &shells,
-                        const std::vector<double> &rcut, const gbxc_grid_spec &spec, std::vector<double> &x,
-                        std::vector<double> &y, std::vector<double> &z, std::vector<double> &wq,
-                        std::vector<int> &parent, HostPlan &plan, cudaStream_t s, int *status) {
+                        const std::vector<double> &rcut, const gbxc_grid_spec &spec, HostPlan &plan,
+                        DevPoints &out, cudaStream_t s, int *status) {
     *status = 0;
+    out = DevPoints{};
     const int natoms = (int)(xyz.size() / 3);
     GridTables T;
     grid_tables(spec, T);
@@ -348,8 +369,8 @@ cudaError_t device_plan(const std::vector<double> &xyz, const std::vector<DevShe
         return cudaSuccess;
     }
     DevBuf<double> d_atoms, d_r, d_wr, d_ux, d_uy, d_uz, d_wa, dx, dy, dz, dwq, d_cent, d_rcut;
-    DevBuf<int> d_parent, d_idx, d_tmp, d_lb, d_le, d_ln, d_err, d_fb, d_fe;
-    DevBuf<int64_t> d_lofs;
+    DevBuf<int> d_parent, d_idx, d_tmp, d_lb, d_le, d_ln, d_err, d_fb, d_fe, d_order;
+    DevBuf<int64_t> d_lofs, d_oofs;
     DevBuf<uint32_t> d_mask;
     DP_CHECK(upload(d_atoms, xyz, s));
     DP_CHECK(upload(d_r, T.r, s));
@@ -405,26 +426,60 @@ cudaError_t device_plan(const std::vector<double> &xyz, const std::vector<DevShe
         screen_leaves<<<(unsigned)nleaf, PT, 0, s>>>(dx.p, dy.p, dz.p, d_idx.p, d_fb.p, d_fe.p, d_cent.p, d_rcut.p,
                                                      nsh, nwords, d_mask.p);
     DP_CHECK(cudaGetLastError());
-    std::vector<int> fb, fe, idx;
+    std::vector<int> fb, fe;
     std::vector<uint32_t> mask;
-    DP_CHECK(download(x, dx.p, npts, s));
-    DP_CHECK(download(y, dy.p, npts, s));
-    DP_CHECK(download(z, dz.p, npts, s));
-    DP_CHECK(download(wq, dwq.p, npts, s));
-    DP_CHECK(download(parent, d_parent.p, npts, s));
-    DP_CHECK(download(idx, d_idx.p, npts, s));
     DP_CHECK(download(fb, d_fb.p, nleaf, s));
     DP_CHECK(download(fe, d_fe.p, nleaf, s));
     DP_CHECK(download(mask, d_mask.p, (size_t)nleaf * nwords, s));
     DP_CHECK(cudaStreamSynchronize(s));
-    std::vector<std::vector<int64_t>> leaves(nleaf);
-    std::vector<std::vector<int>> keeps(nleaf);
-    for (int64_t l = 0; l < nleaf; ++l) {
-        leaves[l].assign(idx.begin() + fb[l], idx.begin() + fe[l]);
+    // merge on the host (small: one shell list per leaf), then the points in batch order on
+    // the device
+    std::vector<std::vector<int>> keeps(nleaf), bshells, bleaves;
+    for (int64_t l = 0; l < nleaf; ++l)
         for (int k = 0; k < nsh; ++k)
             if (mask[l * nwords + (k >> 5)] >> (k & 31) & 1u) keeps[l].push_back(k);
+    merge_leaves(keeps, bshells, bleaves);
+    std::vector<int> order;
+    std::vector<int64_t> oofs, bsize;
+    int64_t pos = 0;
+    for (const auto &bl : bleaves) {
+        const int64_t p0 = pos;
+        for (int l : bl) {
+            order.push_back(l);
+            oofs.push_back(pos);
+            pos += fe[l] - fb[l];
+        }
+        bsize.push_back(pos - p0);
     }
-    plan_from_leaves((size_t)natoms, shells, leaves, keeps, x, y, z, wq, parent, plan);
+    DP_CHECK(upload(d_order, order, s));
+    DP_CHECK(upload(d_oofs, oofs, s));
+    DevPoints pts;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&pts.x, npts * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&pts.y, npts * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&pts.z, npts * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&pts.wq, npts * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&pts.parent, npts * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&pts.point_index, npts * sizeof(int64_t));
+    if (e == cudaSuccess && nleaf > 0)
+        layout_points<<<(unsigned)nleaf, PT, 0, s>>>(dx.p, dy.p, dz.p, dwq.p, d_parent.p, d_idx.p, d_fb.p, d_fe.p,
+                                                    d_order.p, d_oofs.p, pts);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(pts.x);
+        cudaFree(pts.y);
+        cudaFree(pts.z);
+        cudaFree(pts.wq);
+        cudaFree(pts.parent);
+        cudaFree(pts.point_index);
+        return e;
+    }
+    plan.x.clear(); plan.y.clear(); plan.z.clear(); plan.wq.clear();
+    plan.parent.clear(); plan.point_index.clear();
+    plan.nleaf = (int)nleaf;
+    batch_metadata((size_t)natoms, shells, bshells, bsize, plan);
+    out = pts;
     return cudaSuccess;
 }
 

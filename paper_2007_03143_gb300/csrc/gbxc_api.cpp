@@ -61,6 +61,7 @@ struct Molecule {
     DevPlan dev;
     std::vector<void *> dev_allocs;
     double *d_tileE = nullptr, *d_tileN = nullptr, *d_Eb = nullptr, *d_Nb = nullptr;
+    int64_t *d_point_index = nullptr;   // device-planned molecules: generation index of each point
     std::map<SchedKey, std::unique_ptr<Schedule>> scheds;
     MixedResident mixed_res;
     double work = 0.0;          // sum_j W_j, for balancing many molecules over graph branches
@@ -992,12 +993,15 @@ int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
         std::vector<double> rcut(m.nshell);
         for (int s = 0; s < m.nshell; ++s)
             rcut[s] = shell_cutoff(m.shells[s].alpha, m.shells[s].nprim, spec->eta);
+        DevPoints pts;
         if (on_device) {
             int status = 0;
-            check(device_plan(m.xyz, m.shells, rcut, *spec, x, y, z, wq, parent, m.plan, ctx->stream, &status),
-                  "device planner");
+            check(device_plan(m.xyz, m.shells, rcut, *spec, m.plan, pts, ctx->stream, &status), "device planner");
             if (status == 1) return fail(ctx, GBXC_EINVAL, "grid too large for the device planner (>= 2^31 points)");
             if (status == 2) return fail(ctx, GBXC_ECUDA, "device planner: cell stack overflow");
+            for (void *q : {(void *)pts.x, (void *)pts.y, (void *)pts.z, (void *)pts.wq, (void *)pts.parent,
+                            (void *)pts.point_index})
+                m.dev_allocs.push_back(q);
         } else {
             build_molecular_grid(m.xyz, *spec, x, y, z, wq, parent);
             build_plan(m.xyz, m.shells, rcut, m.nbf, *spec, x, y, z, wq, parent, m.plan);
@@ -1006,18 +1010,28 @@ int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
         for (double wj : m.plan.work) m.work += wj;
         if (host_only) {
             m.has_grid = true;
-            if (npts_out) *npts_out = (long long)m.plan.x.size();
+            if (npts_out) *npts_out = (long long)m.plan.npts;
             if (nbatch_out) *nbatch_out = m.plan.nbatch();
             return GBXC_OK;
         }
         cudaStream_t s = ctx->stream;
         HostPlan &P = m.plan;
-        m.dev.x = dev_upload(m, P.x, s);
-        m.dev.y = dev_upload(m, P.y, s);
-        m.dev.z = dev_upload(m, P.z, s);
-        m.dev.wq = dev_upload(m, P.wq, s);
-        m.dev.parent = dev_upload(m, P.parent, s);
-        m.dev.w = dev_alloc<double>(m, P.x.size());
+        if (on_device) {
+            m.dev.x = pts.x;
+            m.dev.y = pts.y;
+            m.dev.z = pts.z;
+            m.dev.wq = pts.wq;
+            m.dev.parent = pts.parent;
+            m.d_point_index = pts.point_index;
+        } else {
+            m.dev.x = dev_upload(m, P.x, s);
+            m.dev.y = dev_upload(m, P.y, s);
+            m.dev.z = dev_upload(m, P.z, s);
+            m.dev.wq = dev_upload(m, P.wq, s);
+            m.dev.parent = dev_upload(m, P.parent, s);
+            m.d_point_index = nullptr;
+        }
+        m.dev.w = dev_alloc<double>(m, P.npts);
         m.dev.shell_ptr = dev_upload(m, P.shell_ptr, s);
         m.dev.shell_idx = dev_upload(m, P.shell_idx, s);
         m.dev.func_ptr = dev_upload(m, P.func_ptr, s);
@@ -1041,14 +1055,14 @@ int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
         wa.atoms = m.d_atoms;
         wa.rnn = m.d_rnn;
         wa.w = m.dev.w;
-        wa.npts = (int64_t)P.x.size();
+        wa.npts = P.npts;
         wa.natoms = m.natoms;
         wa.scheme = spec->partition;
         wa.prof = &ctx->prof;
         check(launch_partition_weights(wa, s), "partition weights");
         check(cudaStreamSynchronize(s), "load_grid");
         m.has_grid = true;
-        if (npts_out) *npts_out = (long long)P.x.size();
+        if (npts_out) *npts_out = (long long)P.npts;
         if (nbatch_out) *nbatch_out = P.nbatch();
         return GBXC_OK;
     });
@@ -1067,7 +1081,7 @@ int gbxc_plan_info_get(gbxc_ctx *ctx, int mol, gbxc_plan_info *info) {
         info->nbf = m.nbf;
         if (!m.has_grid) return GBXC_OK;
         const HostPlan &P = m.plan;
-        info->npts = (long long)P.x.size();
+        info->npts = (long long)P.npts;
         info->nbatch = P.nbatch();
         info->nleaf = P.nleaf;
         info->nshell_entries = (long long)P.shell_idx.size();
@@ -1096,14 +1110,24 @@ int gbxc_export_plan(gbxc_ctx *ctx, int mol, double *x, double *y, double *z, do
         Molecule &m = get_mol(ctx, mol);
         if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
         const HostPlan &P = m.plan;
-        size_t n = P.x.size();
-        if (x) std::memcpy(x, P.x.data(), n * 8);
-        if (y) std::memcpy(y, P.y.data(), n * 8);
-        if (z) std::memcpy(z, P.z.data(), n * 8);
-        if (wq) std::memcpy(wq, P.wq.data(), n * 8);
-        if (parent) std::memcpy(parent, P.parent.data(), n * 4);
-        if (point_index)
-            for (size_t i = 0; i < n; ++i) point_index[i] = P.point_index[i];
+        size_t n = (size_t)P.npts;
+        if (P.x.size() == n) {
+            if (x) std::memcpy(x, P.x.data(), n * 8);
+            if (y) std::memcpy(y, P.y.data(), n * 8);
+            if (z) std::memcpy(z, P.z.data(), n * 8);
+            if (wq) std::memcpy(wq, P.wq.data(), n * 8);
+            if (parent) std::memcpy(parent, P.parent.data(), n * 4);
+            if (point_index)
+                for (size_t i = 0; i < n; ++i) point_index[i] = P.point_index[i];
+        } else {   // planned on the device: the point arrays live there only
+            if (x) check(cudaMemcpy(x, m.dev.x, n * 8, cudaMemcpyDeviceToHost), "copy x");
+            if (y) check(cudaMemcpy(y, m.dev.y, n * 8, cudaMemcpyDeviceToHost), "copy y");
+            if (z) check(cudaMemcpy(z, m.dev.z, n * 8, cudaMemcpyDeviceToHost), "copy z");
+            if (wq) check(cudaMemcpy(wq, m.dev.wq, n * 8, cudaMemcpyDeviceToHost), "copy wq");
+            if (parent) check(cudaMemcpy(parent, m.dev.parent, n * 4, cudaMemcpyDeviceToHost), "copy parent");
+            if (point_index)
+                check(cudaMemcpy(point_index, m.d_point_index, n * 8, cudaMemcpyDeviceToHost), "copy point index");
+        }
         if (batch_ptr)
             for (size_t i = 0; i < P.batch_ptr.size(); ++i) batch_ptr[i] = P.batch_ptr[i];
         if (shell_ptr)

@@ -264,18 +264,14 @@ void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &she
     plan_from_leaves(natoms, shells, leaves, keeps, x, y, z, wq, parent, plan);
 }
 
-// 3. merge equal shell lists (first-occurrence order), 4. lay the points out batch by batch,
-// function lists, work estimate (Eq. batch_work), 5. 128-point tiles.
-void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
-                      const std::vector<std::vector<int64_t>> &leaves, const std::vector<std::vector<int>> &keeps,
-                      const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
-                      const std::vector<double> &wq, const std::vector<int> &parent, HostPlan &plan) {
-    size_t npts = x.size();
-    plan.nleaf = (int)leaves.size();
+// 3. merge equal shell lists: leaves with identical lists form one batch, batches in order
+// of first occurrence, leaves in order within a batch.
+void merge_leaves(const std::vector<std::vector<int>> &keeps, std::vector<std::vector<int>> &bshells,
+                  std::vector<std::vector<int>> &bleaves) {
     std::map<std::vector<int>, int> key_to_batch;
-    std::vector<std::vector<int>> bshells;
-    std::vector<std::vector<int>> bleaves;
-    for (size_t l = 0; l < leaves.size(); ++l) {
+    bshells.clear();
+    bleaves.clear();
+    for (size_t l = 0; l < keeps.size(); ++l) {
         const std::vector<int> &keep = keeps[l];
         auto it = key_to_batch.find(keep);
         if (it == key_to_batch.end()) {
@@ -286,29 +282,21 @@ void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
             bleaves[it->second].push_back((int)l);
         }
     }
-    // 4. lay the points out batch by batch; function lists; work estimate (Eq. batch_work)
-    int nb = (int)bshells.size();
-    plan.x.clear(); plan.y.clear(); plan.z.clear(); plan.wq.clear();
-    plan.parent.clear(); plan.point_index.clear();
+}
+
+// 4. function lists and work estimate (Eq. batch_work) per batch, 5. 128-point tiles and the
+// slab row offsets of each tile (padded function count); batch sizes in batch order.
+void batch_metadata(size_t natoms, const std::vector<DevShell> &shells, const std::vector<std::vector<int>> &bshells,
+                    const std::vector<int64_t> &batch_size, HostPlan &plan) {
+    const int nb = (int)bshells.size();
     plan.batch_ptr.assign(1, 0);
     plan.shell_ptr.assign(1, 0);
     plan.shell_idx.clear();
     plan.func_ptr.assign(1, 0);
     plan.func_idx.clear();
     plan.work.clear();
-    plan.x.reserve(npts); plan.y.reserve(npts); plan.z.reserve(npts); plan.wq.reserve(npts);
-    plan.parent.reserve(npts); plan.point_index.reserve(npts);
     for (int j = 0; j < nb; ++j) {
-        for (int l : bleaves[j])
-            for (int64_t p : leaves[l]) {
-                plan.x.push_back(x[p]);
-                plan.y.push_back(y[p]);
-                plan.z.push_back(z[p]);
-                plan.wq.push_back(wq[p]);
-                plan.parent.push_back(parent[p]);
-                plan.point_index.push_back(p);
-            }
-        plan.batch_ptr.push_back((int64_t)plan.x.size());
+        plan.batch_ptr.push_back(plan.batch_ptr.back() + batch_size[j]);
         int64_t nfun = 0;
         for (int s : bshells[j]) {
             plan.shell_idx.push_back(s);
@@ -317,11 +305,11 @@ void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
         }
         plan.shell_ptr.push_back((int64_t)plan.shell_idx.size());
         plan.func_ptr.push_back((int64_t)plan.func_idx.size());
-        int64_t ng = plan.batch_ptr[j + 1] - plan.batch_ptr[j];
+        int64_t ng = batch_size[j];
         int64_t na = (int64_t)natoms;
         plan.work.push_back((double)(ng * (na * na + 9 * nfun + 2 * nfun * nfun + 3) + nfun * nfun));
     }
-    // 5. 128-point tiles and the slab row offsets of each tile (padded function count)
+    plan.npts = plan.batch_ptr.back();
     plan.tile_batch.clear(); plan.tile_first.clear(); plan.tile_count.clear();
     plan.tile_row.clear();
     plan.batch_tile.assign(1, 0);
@@ -339,6 +327,36 @@ void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
         plan.batch_tile.push_back((int64_t)plan.tile_batch.size());
     }
     plan.tile_row.push_back(row);   // total rows (one past the last tile)
+}
+
+// Steps 3-5 with the points laid out batch by batch on the host.
+void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
+                      const std::vector<std::vector<int64_t>> &leaves, const std::vector<std::vector<int>> &keeps,
+                      const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
+                      const std::vector<double> &wq, const std::vector<int> &parent, HostPlan &plan) {
+    size_t npts = x.size();
+    plan.nleaf = (int)leaves.size();
+    std::vector<std::vector<int>> bshells, bleaves;
+    merge_leaves(keeps, bshells, bleaves);
+    plan.x.clear(); plan.y.clear(); plan.z.clear(); plan.wq.clear();
+    plan.parent.clear(); plan.point_index.clear();
+    plan.x.reserve(npts); plan.y.reserve(npts); plan.z.reserve(npts); plan.wq.reserve(npts);
+    plan.parent.reserve(npts); plan.point_index.reserve(npts);
+    std::vector<int64_t> bsize;
+    for (size_t j = 0; j < bshells.size(); ++j) {
+        int64_t n0 = (int64_t)plan.x.size();
+        for (int l : bleaves[j])
+            for (int64_t p : leaves[l]) {
+                plan.x.push_back(x[p]);
+                plan.y.push_back(y[p]);
+                plan.z.push_back(z[p]);
+                plan.wq.push_back(wq[p]);
+                plan.parent.push_back(parent[p]);
+                plan.point_index.push_back(p);
+            }
+        bsize.push_back((int64_t)plan.x.size() - n0);
+    }
+    batch_metadata(natoms, shells, bshells, bsize, plan);
 }
 
 }  // namespace gbxc

@@ -43,6 +43,7 @@ struct HostPlan {
     std::vector<int> tile_count;
     std::vector<int64_t> tile_row;    // prefix sum of padded N_b^j over tiles (slab row offset)
     std::vector<int64_t> batch_tile;  // nbatch+1 into the tile arrays
+    int64_t npts = 0;                 // points (the arrays above may live on the device only)
     int nbatch() const { return (int)batch_ptr.size() - 1; }
     int64_t ntiles() const { return (int64_t)tile_batch.size(); }
 };
@@ -86,12 +87,23 @@ inline int64_t pad_funcs(int64_t n) { return (n + FBLK - 1) / FBLK * FBLK; }
 // The planner as device kernels (device_plan.cu): the same grid and plan as
 // build_molecular_grid + build_plan, bit for bit.  *status: 0 done, 1 grid too large,
 // 2 internal stack overflow (cannot happen for depth <= 16).
+// The point arrays in batch order stay on the device: x, y, z, wq, parent and point_index
+// are allocated here (cudaMalloc; the caller frees them) and the host plan's copies stay
+// empty (plan.npts holds the count).
+struct DevPoints {
+    double *x = nullptr, *y = nullptr, *z = nullptr, *wq = nullptr;
+    int *parent = nullptr;
+    int64_t *point_index = nullptr;
+};
 cudaError_t device_plan(const std::vector<double> &xyz, const std::vector<DevShell> &shells,
-                        const std::vector<double> &rcut, const gbxc_grid_spec &spec, std::vector<double> &x,
-                        std::vector<double> &y, std::vector<double> &z, std::vector<double> &wq,
-                        std::vector<int> &parent, HostPlan &plan, cudaStream_t s, int *status);
+                        const std::vector<double> &rcut, const gbxc_grid_spec &spec, HostPlan &plan,
+                        DevPoints &out, cudaStream_t s, int *status);
 // The planner's last steps, shared by the host and the device planner: merge leaves with
 // equal shell lists (first occurrence first), lay out points, functions, work and tiles.
+void merge_leaves(const std::vector<std::vector<int>> &keeps, std::vector<std::vector<int>> &bshells,
+                  std::vector<std::vector<int>> &bleaves);
+void batch_metadata(size_t natoms, const std::vector<DevShell> &shells, const std::vector<std::vector<int>> &bshells,
+                    const std::vector<int64_t> &batch_size, HostPlan &plan);
 void plan_from_leaves(size_t natoms, const std::vector<DevShell> &shells,
                       const std::vector<std::vector<int64_t>> &leaves, const std::vector<std::vector<int>> &keeps,
                       const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
