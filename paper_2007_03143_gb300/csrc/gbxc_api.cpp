@@ -437,6 +437,11 @@ Schedule &get_schedule(Molecule &m, int precision, int b0, int b1, size_t budget
     SchedKey key{precision, b0, b1, budget, tile_n};
     auto it = m.scheds.find(key);
     if (it != m.scheds.end()) return *it->second;
+    if (precision == GBXC_MIXED)
+        for (int j = b0; j < b1; ++j)
+            if (pad_funcs(m.plan.func_ptr[j + 1] - m.plan.func_ptr[j]) > mixed_max_functions())
+                throw ArgError{"a batch has more than " + std::to_string(mixed_max_functions()) +
+                               " significant functions: too many for the tensor-core form (use GBXC_FP64)"};
     auto sp = std::make_unique<Schedule>();
     Schedule &S = *sp;
     const HostPlan &P = m.plan;

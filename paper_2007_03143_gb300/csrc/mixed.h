@@ -49,9 +49,11 @@ struct MixedSchedule {
         int64_t pexp_rows;             // sum of padded N_b^j over the chunk's batches
         int max_np;
         int64_t xtask0, nxtask;        // X-contraction tasks (tile, N chunk) of the chunk
+        int64_t ptask0, nptask;        // P^j slicing tasks (batch, group of 8 rows) of the chunk
     };
     std::vector<Chunk> chunks;
     int *d_xtasks = nullptr;           // (tile, N chunk) pairs of every chunk
+    int *d_ptasks = nullptr;           // (batch within the chunk, first row) pairs of every chunk
     int64_t *d_pofs = nullptr;         // per (chunk, batch): first P-slice row
     int64_t *d_pexp_ofs = nullptr;     // per (chunk, batch): first row-exponent entry
     int64_t max_prows = 0, max_pexp = 0;
@@ -61,6 +63,8 @@ struct MixedSchedule {
 size_t mixed_row_bytes();
 // Tile widths the tcgen05 GEMMs are built for; `bn` below is one of them.
 bool mixed_tile_supported(int bn);
+// Largest padded N_b^j the tensor-core form takes (its exact accumulator levels need it).
+int mixed_max_functions();
 void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, int bn, std::vector<int> &tasks);
 void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chunk_t0,
                           const std::vector<int64_t> &chunk_t1, int bn, MixedSchedule &s);

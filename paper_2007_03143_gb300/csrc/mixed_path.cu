@@ -45,6 +45,7 @@ using slc::pow2f;
 using slc::scale2;
 using slc::slice5;
 using slc::exp_of;
+constexpr int MAX_NP = 1184;   // largest padded N_b^j: keeps the exact accumulator levels exact
 constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
 // at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
@@ -123,16 +124,19 @@ __global__ void p_to_df(const double *__restrict__ P, float *__restrict__ ph, fl
     pl[k] = d.l;
 }
 
-// One warp per row mu of P^j: row exponent, then the 5 slices of P^j[mu][nu] for every
-// K block of 32 nu's.  Rows and columns past N_b^j are written as zeros.
-__global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
-    int jl = blockIdx.x;
-    int j = m.j0 + jl;
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t f0 = a.plan.func_ptr[j];
-    int n = (int)(a.plan.func_ptr[j + 1] - f0);
-    int np = pad32(n);
-    int mu = blockIdx.y * 4 + warp;
+// One warp per row mu of P^j, four rows per block (tasks: batch, first row of four): the row
+// exponent from the maximum over the row, then the 5 slices of P^j[mu][nu] for every K block
+// of 32 nu's, one nu per lane (gathers and stores coalesced over the lanes).  Rows and
+// columns past N_b^j are written as zeros.
+constexpr int PS_ROWS = 4;
+__global__ void __launch_bounds__(32 * PS_ROWS) pslice_kernel(ChunkArgs a, MixedArgs m, const int *tasks) {
+    const int jl = tasks[2 * blockIdx.x], mu0 = tasks[2 * blockIdx.x + 1];
+    const int j = m.j0 + jl;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t f0 = a.plan.func_ptr[j];
+    const int n = (int)(a.plan.func_ptr[j + 1] - f0);
+    const int np = pad32(n);
+    const int mu = mu0 + warp;
     if (mu >= np) return;
     const int *F = a.plan.func_idx + f0;
     const size_t rowoff = (mu < n) ? (size_t)F[mu] * a.nbf : 0;
@@ -141,16 +145,16 @@ __global__ void __launch_bounds__(128) pslice_kernel(ChunkArgs a, MixedArgs m) {
         for (int nu = lane; nu < n; nu += 32) mx = fmaxf(mx, fabsf(m.ph[rowoff + F[nu]]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = exp_of(mx);
+    const int e = exp_of(mx);
     if (lane == 0) m.pexp[m.pexp_ofs[jl] + mu] = e;
-    int64_t pofs = m.pofs[jl];
+    const int64_t pofs = m.pofs[jl];
     for (int kb = 0; kb < np / 32; ++kb) {
-        int nu = kb * 32 + lane;
-        bool in = mu < n && nu < n;
-        float h = in ? m.ph[rowoff + F[nu]] : 0.f, l = in ? m.pl[rowoff + F[nu]] : 0.f;
+        const int nu = kb * 32 + lane;
+        const bool in = mu < n && nu < n;
+        const float h = in ? m.ph[rowoff + F[nu]] : 0.f, l = in ? m.pl[rowoff + F[nu]] : 0.f;
         float q[NSL];
         slice5(h, l, e, q);
-        size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + lane;
+        const size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + lane;
 #pragma unroll
         for (int s = 0; s < NSL; ++s) m.pslices[(size_t)s * m.pplane * 32 + o] = __float2bfloat16_rn(q[s]);
     }
@@ -659,7 +663,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     const float2 *phi = m.s.phi;
-    if (np > 1184) {   // the exponent scratch below holds 1184 rows; larger batches are rejected
+    if (np > MAX_NP) {   // the exponent scratch below holds MAX_NP rows; larger batches are rejected
         if (i == 0) atomicOr(m.err, 8);
         return;
     }
@@ -704,7 +708,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     // Z (Eq. z_mat) in double-float, written over X (each thread touches its own point);
     // maxima of |Z| and |Phi| per function row over the tile's points, kept as float bits
     // (non-negative floats order like their bit patterns) for the V-side slicing exponents
-    __shared__ int zmax[1184], fmx[1184];
+    __shared__ int zmax[MAX_NP], fmx[MAX_NP];
     for (int mu = i; mu < np; mu += TILE) {
         zmax[mu] = 0;
         fmx[mu] = 0;
@@ -855,6 +859,8 @@ size_t mixed_row_bytes() { return (size_t)TILE * (8 * 4 + 2 * 4 + 3 * NSL * 2) +
 
 bool mixed_tile_supported(int bn) { return bn == 128 || bn == 64; }
 
+int mixed_max_functions() { return MAX_NP; }
+
 void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, int bn, std::vector<int> &tasks) {
     int mblk = (n + BM - 1) / BM, nblk = (n + bn - 1) / bn;
     for (int64_t k = s0; k < s1; k += VKS) {
@@ -875,7 +881,7 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
     free_mixed_schedule(s);
     s.bn = bn;
     std::vector<int64_t> pofs, pexp;
-    std::vector<int> xt;
+    std::vector<int> xt, pt;
     for (size_t c = 0; c < chunk_t0.size(); ++c) {
         MixedSchedule::Chunk ch;
         ch.j0 = plan.tile_batch[chunk_t0[c]];
@@ -893,6 +899,15 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
             }
         }
         ch.nxtask = (int64_t)xt.size() / 2 - ch.xtask0;
+        ch.ptask0 = (int64_t)pt.size() / 2;
+        for (int j = ch.j0; j <= ch.j1; ++j) {
+            const int64_t np = pad_funcs(plan.func_ptr[j + 1] - plan.func_ptr[j]);
+            for (int64_t mu0 = 0; mu0 < np; mu0 += PS_ROWS) {
+                pt.push_back(j - ch.j0);
+                pt.push_back((int)mu0);
+            }
+        }
+        ch.nptask = (int64_t)pt.size() / 2 - ch.ptask0;
         for (int j = ch.j0; j <= ch.j1; ++j) {
             int64_t n = plan.func_ptr[j + 1] - plan.func_ptr[j];
             int64_t np = pad_funcs(n);
@@ -912,6 +927,10 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
         cudaMalloc(&s.d_xtasks, xt.size() * sizeof(int));
         cudaMemcpy(s.d_xtasks, xt.data(), xt.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
+    if (!pt.empty()) {
+        cudaMalloc(&s.d_ptasks, pt.size() * sizeof(int));
+        cudaMemcpy(s.d_ptasks, pt.data(), pt.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
     if (!pofs.empty()) {
         cudaMalloc(&s.d_pofs, pofs.size() * sizeof(int64_t));
         cudaMemcpy(s.d_pofs, pofs.data(), pofs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -922,6 +941,7 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
 
 void free_mixed_schedule(MixedSchedule &s) {
     cudaFree(s.d_xtasks);
+    cudaFree(s.d_ptasks);
     cudaFree(s.d_pofs);
     cudaFree(s.d_pexp_ofs);
     s = MixedSchedule{};
@@ -1054,7 +1074,8 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     if (err != cudaSuccess) return err;
     Profiler &P = *a.prof;
     P.begin(GBXC_K_PGATHER, st);
-    pslice_kernel<<<dim3(ch.j1 - ch.j0 + 1, (ch.max_np + 3) / 4), 128, 0, st>>>(a, m);
+    if (ch.nptask > 0)
+        pslice_kernel<<<(unsigned)ch.nptask, 32 * PS_ROWS, 0, st>>>(a, m, s.d_ptasks + 2 * ch.ptask0);
     P.end(GBXC_K_PGATHER, st);
     P.begin(GBXC_K_COLLOC, st);
     static const Exp2Table e2t = [] {
