@@ -57,3 +57,47 @@ def test_shell_subset_columns_are_sorted_global_functions():
     shells = [1, 4, 5, 8]
     cols = np.concatenate([np.arange(w.basis.func_offset[s], w.basis.func_offset[s + 1]) for s in shells])
     assert np.array_equal(C.collocate(p, w.basis, shells)[0], full[:, cols])
+
+
+# ---------------------------------------------------------------- pure (spherical) shells
+@pytest.mark.parametrize("L", [2, 3])
+def test_solid_harmonics_match_the_workload_table(L):
+    # the oracle's general closed form and the explicit table of the inputs are two
+    # independent derivations of the same functions
+    assert np.max(np.abs(C.solid_harmonic_matrix(L) - np.array(X.PURE_TABLE[L]))) < 1e-15
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_solid_harmonics_addition_theorem(L):
+    # Racah normalisation: sum_m S_Lm(r)^2 = r^(2L) at every point (Unsold)
+    T = C.solid_harmonic_matrix(L)
+    p = np.random.default_rng(L).normal(size=(50, 3))
+    mono = np.stack([p[:, 0] ** a * p[:, 1] ** b * p[:, 2] ** c for a, b, c in C.cart_components(L)], 1)
+    S = mono @ T.T
+    r2L = np.sum(p * p, 1) ** L
+    assert np.max(np.abs(np.sum(S * S, 1) / r2L - 1.0)) < 1e-13
+
+
+@pytest.mark.parametrize("L", [2, 3])
+def test_pure_shell_orthonormal(L):
+    # int chi_m chi_m' d^3r = delta_mm' with the x^L-normalised radial part: angular degree
+    # 2L <= 6 is exact on 8 x 16, the radial part to 1e-11 on 400 points
+    from oracle import quadrature as Q
+    b = X.make_basis(X.single_atom(), single_shell=(L, [3.0, 0.7, 0.15], [0.2, 0.5, 0.4]), pure=True)
+    assert b.nbf == 2 * L + 1
+    x, y, z, wq = Q.atom_grid(np.zeros(3), 400, 8, 16, 5.0)
+    phi = C.collocate(np.stack([x, y, z], 1), b)[0]
+    G = phi.T @ (wq[:, None] * phi)
+    assert np.max(np.abs(G - np.eye(2 * L + 1))) < 1e-10
+
+
+def test_pure_gradient_matches_finite_differences():
+    b = X.make_basis(X.single_atom(), single_shell=(3, [3.0, 0.7, 0.15], [0.2, 0.5, 0.4]), pure=True)
+    p = np.random.default_rng(7).normal(scale=1.2, size=(40, 3))
+    phi, gx, gy, gz = C.collocate(p, b)
+    h = 1e-5
+    for d, g in enumerate((gx, gy, gz)):
+        e = np.zeros(3)
+        e[d] = h
+        fd = (C.collocate(p + e, b)[0] - C.collocate(p - e, b)[0]) / (2 * h)
+        assert np.max(np.abs(fd - g)) < 1e-8 * max(1.0, np.abs(g).max())

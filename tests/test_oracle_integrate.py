@@ -143,3 +143,23 @@ def test_batch_order_invariance(water1_pbe):
     assert abs(a.E - b.E) < 1e-13 * abs(a.E)
     assert np.max(np.abs(a.V - b.V)) < 1e-13 * np.max(np.abs(a.V))
     assert np.allclose(a.E_batch, b.E_batch, rtol=0, atol=0)
+
+
+def test_pure_basis_V_is_dE_dP_and_traces():
+    w, g, pl = _setup("water2_pbe_small_sph")
+    assert w.basis.nbf == 48
+    assert _fd_error(w, g, pl, "pbe") < 1e-7
+    r = I.integrate_method(g, w.basis, w.P, "pbe", pl)
+    # the 20-point radial grid of this case integrates rho to 0.7% (as for the Cartesian basis)
+    assert abs(r.N - np.trace(w.P @ w.S)) < 1e-2 * r.N
+
+
+def test_pure_basis_definitional_equals_method():
+    w = X.make_workload("water2_pbe_small_sph")
+    spec = X.GridSpec(6, 4, 8, "ssf", 40, eta=1e-300)
+    g = I.make_grid(w.mol.xyz, spec)
+    pl = I.make_plan(g, w.mol.xyz, w.basis, spec)
+    D = I.integrate_definitional(g, w.basis, w.P, "pbe")
+    M = I.integrate_method(g, w.basis, w.P, "pbe", pl)
+    assert abs(D.E - M.E) < 1e-13 * abs(D.E)
+    assert np.max(np.abs(D.V - M.V)) < 1e-13 * np.max(np.abs(D.V))

@@ -53,6 +53,36 @@ def cart_components(L: int):
     return out
 
 
+# Pure (spherical) shells, L >= 2: the 2L+1 functions m = -L..L are the real solid harmonics
+# S_Lm in Racah normalisation (sphere norm equal to that of x^L) written in the Cartesian
+# components of the shell (order of cart_components).  This table defines the pure functions
+# of the synthetic workloads; it serves only the input generation here (the overlap matrix
+# that normalises the density).
+_S3, _S15 = math.sqrt(3.0), math.sqrt(15.0)
+_A, _B = math.sqrt(5.0 / 8.0), math.sqrt(3.0 / 8.0)
+PURE_TABLE = {
+    # xx, xy, xz, yy, yz, zz
+    2: [[0, _S3, 0, 0, 0, 0],                      # m = -2: sqrt3 xy
+        [0, 0, 0, 0, _S3, 0],                      # m = -1: sqrt3 yz
+        [-0.5, 0, 0, -0.5, 0, 1.0],                # m =  0: z^2 - (x^2 + y^2)/2
+        [0, 0, _S3, 0, 0, 0],                      # m =  1: sqrt3 xz
+        [_S3 / 2, 0, 0, -_S3 / 2, 0, 0]],          # m =  2: sqrt3/2 (x^2 - y^2)
+    # xxx, xxy, xxz, xyy, xyz, xzz, yyy, yyz, yzz, zzz
+    3: [[0, 3 * _A, 0, 0, 0, 0, -_A, 0, 0, 0],     # m = -3
+        [0, 0, 0, 0, _S15, 0, 0, 0, 0, 0],         # m = -2
+        [0, -_B, 0, 0, 0, 0, -_B, 0, 4 * _B, 0],   # m = -1
+        [0, 0, -1.5, 0, 0, 0, 0, -1.5, 0, 1.0],    # m =  0
+        [-_B, 0, 0, -_B, 0, 4 * _B, 0, 0, 0, 0],   # m =  1
+        [0, 0, _S15 / 2, 0, 0, 0, 0, -_S15 / 2, 0, 0],   # m =  2
+        [_A, 0, 0, -3 * _A, 0, 0, 0, 0, 0, 0]],    # m =  3
+}
+
+
+def nfunc(L: int, pure: int = 0) -> int:
+    """Functions of a shell: (L+1)(L+2)/2 Cartesian, or 2L+1 for a pure shell with L >= 2."""
+    return 2 * L + 1 if (pure and L >= 2) else ncart(L)
+
+
 def ncart(L: int) -> int:
     return (L + 1) * (L + 2) // 2
 
@@ -76,11 +106,14 @@ class Basis:
     coeff: np.ndarray     # (nshell, maxprim) float64, normalisation folded in
     center: np.ndarray    # (nshell, 3) float64, bohr (copy of the atom position)
     func_offset: np.ndarray = field(default=None)  # (nshell+1,) first function of each shell
+    pure: np.ndarray = field(default=None)         # (nshell,) int32: 1 = spherical shell (L >= 2)
 
     def __post_init__(self):
+        if self.pure is None:
+            self.pure = np.zeros(len(self.L), dtype=np.int32)
         if self.func_offset is None:
             off = np.zeros(len(self.L) + 1, dtype=np.int64)
-            off[1:] = np.cumsum([ncart(int(l)) for l in self.L])
+            off[1:] = np.cumsum([nfunc(int(l), int(p)) for l, p in zip(self.L, self.pure)])
             self.func_offset = off
 
     @property
@@ -184,12 +217,12 @@ def _normalise(L: int, a: np.ndarray, d: np.ndarray) -> np.ndarray:
     return c / math.sqrt(norm2)
 
 
-def make_basis(mol: Molecule, single_shell: tuple | None = None) -> Basis:
+def make_basis(mol: Molecule, single_shell: tuple | None = None, pure: bool = False) -> Basis:
     """Basis for a molecule from the element rules above.
 
     ``single_shell=(L, alphas, coeffs)`` instead puts exactly one shell with
     the given raw coefficients (normalised as above) on every atom, used by
-    closed-form tests.
+    closed-form tests.  ``pure=True`` makes every shell with L >= 2 spherical.
     """
     atom, Ls, nprim, alpha, coeff, center = [], [], [], [], [], []
     for A in range(mol.natoms):
@@ -211,9 +244,11 @@ def make_basis(mol: Molecule, single_shell: tuple | None = None) -> Basis:
     for s in range(len(Ls)):
         al[s, :nprim[s]] = alpha[s]
         co[s, :nprim[s]] = coeff[s]
-    return Basis(atom=np.array(atom, dtype=np.int32), L=np.array(Ls, dtype=np.int32),
+    Ls = np.array(Ls, dtype=np.int32)
+    return Basis(atom=np.array(atom, dtype=np.int32), L=Ls,
                  nprim=np.array(nprim, dtype=np.int32), alpha=al, coeff=co,
-                 center=np.array(center, dtype=np.float64))
+                 center=np.array(center, dtype=np.float64),
+                 pure=((Ls >= 2) & bool(pure)).astype(np.int32))
 
 
 def _overlap_1d_table(a, b, A, B, lmax: int):
@@ -243,7 +278,22 @@ def _overlap_1d_table(a, b, A, B, lmax: int):
 
 
 def overlap_matrix(basis: Basis) -> np.ndarray:
-    """Closed-form AO overlap S (used only to normalise the seeded density)."""
+    """Closed-form AO overlap S (used only to normalise the seeded density); pure shells
+    through PURE_TABLE applied to the Cartesian overlap."""
+    if np.any(basis.pure):
+        cart = Basis(atom=basis.atom, L=basis.L, nprim=basis.nprim, alpha=basis.alpha, coeff=basis.coeff,
+                     center=basis.center)
+        Sc = overlap_matrix(cart)
+        T = np.zeros((basis.nbf, cart.nbf))
+        for s in range(basis.nshell):
+            o, oc = basis.func_offset[s], cart.func_offset[s]
+            L = int(basis.L[s])
+            if basis.pure[s]:
+                T[o:o + 2 * L + 1, oc:oc + ncart(L)] = PURE_TABLE[L]
+            else:
+                T[o:o + ncart(L), oc:oc + ncart(L)] = np.eye(ncart(L))
+        S = T @ Sc @ T.T
+        return 0.5 * (S + S.T)
     nbf = basis.nbf
     lmax = int(basis.L.max())
     maxp = basis.alpha.shape[1]
@@ -316,10 +366,14 @@ WORKLOADS = {
     "water2_pbe_small": dict(n_waters=2, grid=GridSpec(20, 8, 16, "ssf", 128), functional="pbe"),
     "water3_pbe_small": dict(n_waters=3, grid=GridSpec(24, 10, 20, "ssf", 200), functional="pbe"),
     "water1_pbe_small": dict(n_waters=1, grid=GridSpec(30, 10, 20, "becke", 256), functional="pbe"),
+    # spherical d shells (O 3s2p1d: 14 functions; 24 per water)
+    "water2_pbe_small_sph": dict(n_waters=2, grid=GridSpec(20, 8, 16, "ssf", 128), functional="pbe", pure=True),
+    "water16_pbe_sph": dict(n_waters=16, grid=GridSpec(75, 16, 32, "ssf", 512), functional="pbe", pure=True),
 }
 
 _WORKLOAD_SEEDS = {"water1_slater": 1000, "water16_pbe": 2000, "water64_pbe": 3000,
-                   "water2_pbe_small": 9100, "water3_pbe_small": 9200, "water1_pbe_small": 9300}
+                   "water2_pbe_small": 9100, "water3_pbe_small": 9200, "water1_pbe_small": 9300,
+                   "water2_pbe_small_sph": 9100, "water16_pbe_sph": 2000}
 
 
 def make_workload(name: str, n_waters: int | None = None, seed: int | None = None) -> Workload:
@@ -327,7 +381,7 @@ def make_workload(name: str, n_waters: int | None = None, seed: int | None = Non
     nw = cfg["n_waters"] if n_waters is None else n_waters
     sd = _WORKLOAD_SEEDS[name] if seed is None else seed
     mol = water_cluster(nw, sd)
-    basis = make_basis(mol)
+    basis = make_basis(mol, pure=cfg.get("pure", False))
     S = overlap_matrix(basis)
     P = density_matrix(S, 5 * nw, sd + 1)
     return Workload(name=name, mol=mol, basis=basis, grid=cfg["grid"], functional=cfg["functional"],
