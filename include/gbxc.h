@@ -130,6 +130,17 @@ int gbxc_load_basis(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, 
                     const int *shell_atom, const int *shell_L, const int *shell_nprim,
                     const double *alpha, const double *coeff, int *mol_out, int *nbf_out);
 
+/* The same with spherical shells (the paper's cc-pVDZ runs, Sec. 3): shell_pure[s] != 0 makes
+ * a shell with L >= 2 carry the 2L+1 real solid harmonics S_Lm, m = -L..L, in Racah
+ * normalisation (sqrt(4 pi/(2L+1)) r^L Y_Lm, the same norm as x^L), as combinations of its
+ * Cartesian functions, e.g. for L = 2: sqrt3 xy, sqrt3 yz, z^2 - (x^2 + y^2)/2, sqrt3 xz,
+ * sqrt3/2 (x^2 - y^2).  Functions are numbered shell by shell as before, a pure shell
+ * contributing 2L+1.  shell_pure may be NULL (all Cartesian: gbxc_load_basis). */
+int gbxc_load_basis_pure(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, int nshell,
+                         const int *shell_atom, const int *shell_L, const int *shell_nprim,
+                         const int *shell_pure, const double *alpha, const double *coeff, int *mol_out,
+                         int *nbf_out);
+
 /* Build the molecular grid and the batch plan, and keep them on the device
  * (Sec. 2.2 and Algorithm 3; the paper reuses them across SCF iterations):
  * atomic grids, partition weights (computed on the GPU in float64), cuboid

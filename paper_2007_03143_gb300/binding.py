@@ -34,7 +34,8 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
-            "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule", "gbxc_load_grid_device"]
+            "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule", "gbxc_load_grid_device",
+            "gbxc_load_basis_pure"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -80,6 +81,9 @@ def lib():
     L.gbxc_last_error.restype = ctypes.c_char_p
     L.gbxc_load_basis.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_int)]
+    L.gbxc_load_basis_pure.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_int)]
+    L.gbxc_load_basis_pure.restype = c_int
     L.gbxc_load_grid.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
     L.gbxc_load_grid_device.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
     L.gbxc_load_grid_device.restype = c_int
@@ -161,8 +165,9 @@ def gbxc_last_error(ctx) -> str:
     return lib().gbxc_last_error(ctx).decode()
 
 
-def gbxc_load_basis(ctx, xyz, Z, shell_atom, shell_L, shell_nprim, alpha, coeff):
-    """Register a molecule; returns (mol_id, nbf).  alpha/coeff: (nshell, <=8) arrays."""
+def gbxc_load_basis(ctx, xyz, Z, shell_atom, shell_L, shell_nprim, alpha, coeff, pure=None):
+    """Register a molecule; returns (mol_id, nbf).  alpha/coeff: (nshell, <=8) arrays;
+    pure: optional per-shell flags (spherical shells for L >= 2)."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     Z = np.ascontiguousarray(Z, dtype=np.int32)
     sa = np.ascontiguousarray(shell_atom, dtype=np.int32)
@@ -176,9 +181,10 @@ def gbxc_load_basis(ctx, xyz, Z, shell_atom, shell_L, shell_nprim, alpha, coeff)
     al[:, :alpha.shape[1]] = alpha
     co[:, :coeff.shape[1]] = coeff
     mol, nbf = c_int(), c_int()
-    _check(ctx, lib().gbxc_load_basis(ctx, len(Z), xyz.ctypes.data, Z.ctypes.data, nsh, sa.ctypes.data,
-                                      sL.ctypes.data, sn.ctypes.data, al.ctypes.data, co.ctypes.data,
-                                      ctypes.byref(mol), ctypes.byref(nbf)))
+    sp = None if pure is None else np.ascontiguousarray(pure, dtype=np.int32)
+    _check(ctx, lib().gbxc_load_basis_pure(ctx, len(Z), xyz.ctypes.data, Z.ctypes.data, nsh, sa.ctypes.data,
+                                           sL.ctypes.data, sn.ctypes.data, None if sp is None else sp.ctypes.data,
+                                           al.ctypes.data, co.ctypes.data, ctypes.byref(mol), ctypes.byref(nbf)))
     return mol.value, nbf.value
 
 
@@ -356,7 +362,7 @@ class Context:
     def load_molecule(self, mol, basis, grid, device_planner=False):
         """Register an ``xcinputs`` Molecule/Basis pair and build its grid; returns the id."""
         mid, nbf = gbxc_load_basis(self.h, mol.xyz, mol.Z, basis.atom, basis.L, basis.nprim,
-                                   basis.alpha, basis.coeff)
+                                   basis.alpha, basis.coeff, getattr(basis, "pure", None))
         load = gbxc_load_grid_device if device_planner else gbxc_load_grid
         load(self.h, mid, grid.nrad, grid.ntheta, grid.nphi, grid.partition, grid.max_batch, grid.eta,
              grid.mk_alpha)

@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "solid_harmonics.cuh"
 #include "xc_functional.cuh"
 
 namespace gbxc {
@@ -40,6 +41,43 @@ __device__ __forceinline__ Slabs slabs_of(const ChunkArgs &a) {
 // k1: collocation.  One block per tile, one thread per point; a warp walks the
 // same shell list for 32 points (no divergence between shells).
 // --------------------------------------------------------------------------
+// A pure shell (L = 2 or 3): its Cartesian functions and gradients, then the 2L+1 real
+// solid harmonics of each component (solid_harmonics.cuh), written as rows row .. row + 2L.
+template <int L>
+__device__ __forceinline__ void pure_shell_f64(double X, double Y, double Z, double g, double h, const Slabs &S,
+                                               int64_t row0, int row, int i, bool live) {
+    constexpr int NC = (L + 1) * (L + 2) / 2, NO = 2 * L + 1;
+    double xp[L + 1], yp[L + 1], zp[L + 1];
+    xp[0] = yp[0] = zp[0] = 1.0;
+#pragma unroll
+    for (int k = 1; k <= L; ++k) {
+        xp[k] = xp[k - 1] * X;
+        yp[k] = yp[k - 1] * Y;
+        zp[k] = zp[k - 1] * Z;
+    }
+    double cv[4][NC];
+    int f = 0;
+#pragma unroll
+    for (int l = L; l >= 0; --l)
+#pragma unroll
+        for (int m = L - l; m >= 0; --m) {
+            const int n = L - l - m;
+            const double mono = xp[l] * yp[m] * zp[n];
+            cv[0][f] = mono * g;
+            cv[1][f] = (l > 0 ? l * xp[l > 0 ? l - 1 : 0] * yp[m] * zp[n] : 0.0) * g + mono * X * h;
+            cv[2][f] = (m > 0 ? m * xp[l] * yp[m > 0 ? m - 1 : 0] * zp[n] : 0.0) * g + mono * Y * h;
+            cv[3][f] = (n > 0 ? n * xp[l] * yp[m] * zp[n > 0 ? n - 1 : 0] : 0.0) * g + mono * Z * h;
+            ++f;
+        }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double o[NO];
+        sph::pure<L, sph::DoubleOps>(cv[c], o);
+#pragma unroll
+        for (int k = 0; k < NO; ++k) S.c[c][(size_t)(row0 + row + k) * TILE + i] = live ? o[k] : 0.0;
+    }
+}
+
 __global__ void __launch_bounds__(TILE) colloc_f64(ChunkArgs a) {
     int64_t t = a.t0 + blockIdx.x;
     int i = threadIdx.x;
@@ -62,6 +100,12 @@ __global__ void __launch_bounds__(TILE) colloc_f64(ChunkArgs a) {
             double e = exp(-sh.alpha[k] * r2);
             g += sh.coeff[k] * e;
             h += (-2.0 * sh.alpha[k] * sh.coeff[k]) * e;
+        }
+        if (sh.pure) {
+            if (sh.L == 2) pure_shell_f64<2>(X, Y, Z, g, h, S, row0, row, i, live);
+            else pure_shell_f64<3>(X, Y, Z, g, h, S, row0, row, i, live);
+            row += 2 * sh.L + 1;
+            continue;
         }
         double xp[GBXC_MAX_L + 2], yp[GBXC_MAX_L + 2], zp[GBXC_MAX_L + 2];
         xp[0] = yp[0] = zp[0] = 1.0;

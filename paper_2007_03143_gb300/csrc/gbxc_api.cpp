@@ -887,6 +887,14 @@ const char *gbxc_last_error(const gbxc_ctx *ctx) { return ctx ? ctx->err.c_str()
 int gbxc_load_basis(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, int nshell,
                     const int *shell_atom, const int *shell_L, const int *shell_nprim,
                     const double *alpha, const double *coeff, int *mol_out, int *nbf_out) {
+    return gbxc_load_basis_pure(ctx, natoms, xyz, Z, nshell, shell_atom, shell_L, shell_nprim, nullptr, alpha,
+                                coeff, mol_out, nbf_out);
+}
+
+int gbxc_load_basis_pure(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, int nshell,
+                         const int *shell_atom, const int *shell_L, const int *shell_nprim,
+                         const int *shell_pure, const double *alpha, const double *coeff, int *mol_out,
+                         int *nbf_out) {
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {
         REQUIRE(natoms > 0 && xyz && nshell > 0 && shell_atom && shell_L && shell_nprim && alpha &&
@@ -910,13 +918,14 @@ int gbxc_load_basis(gbxc_ctx *ctx, int natoms, const double *xyz, const int *Z, 
             sh.L = shell_L[s];
             sh.nprim = shell_nprim[s];
             sh.fofs = fofs;
+            sh.pure = (shell_pure && shell_pure[s] && sh.L >= 2) ? 1 : 0;
             for (int k = 0; k < sh.nprim; ++k) {
                 sh.alpha[k] = alpha[(size_t)s * GBXC_MAX_PRIM + k];
                 sh.coeff[k] = coeff[(size_t)s * GBXC_MAX_PRIM + k];
                 REQUIRE(sh.alpha[k] > 0 && std::isfinite(sh.alpha[k]), "exponents must be positive");
                 REQUIRE(std::isfinite(sh.coeff[k]), "coefficients must be finite");
             }
-            fofs += (sh.L + 1) * (sh.L + 2) / 2;
+            fofs += shell_nfunc(sh);
             m->shells.push_back(sh);
         }
         m->nbf = fofs;

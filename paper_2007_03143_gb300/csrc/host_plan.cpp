@@ -300,8 +300,8 @@ void batch_metadata(size_t natoms, const std::vector<DevShell> &shells, const st
         int64_t nfun = 0;
         for (int s : bshells[j]) {
             plan.shell_idx.push_back(s);
-            for (int c = 0; c < ncart(shells[s].L); ++c) plan.func_idx.push_back(shells[s].fofs + c);
-            nfun += ncart(shells[s].L);
+            for (int c = 0; c < shell_nfunc(shells[s]); ++c) plan.func_idx.push_back(shells[s].fofs + c);
+            nfun += shell_nfunc(shells[s]);
         }
         plan.shell_ptr.push_back((int64_t)plan.shell_idx.size());
         plan.func_ptr.push_back((int64_t)plan.func_idx.size());

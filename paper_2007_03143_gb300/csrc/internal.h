@@ -18,7 +18,8 @@ constexpr int FBLK = 32;         // function padding granule (one 64-byte K bloc
 // One contracted Cartesian shell (Eq. gau_cart), as the kernels read it.
 struct DevShell {
     double c[3];
-    int L, nprim, fofs, pad;
+    int L, nprim, fofs;
+    int pure;   // 1: the 2L+1 real solid harmonics (L >= 2) instead of the Cartesian functions
     double alpha[GBXC_MAX_PRIM];
     double coeff[GBXC_MAX_PRIM];
 };
@@ -84,6 +85,8 @@ void build_plan(const std::vector<double> &xyz, const std::vector<DevShell> &she
                 const std::vector<int> &parent, HostPlan &plan);
 
 inline int64_t pad_funcs(int64_t n) { return (n + FBLK - 1) / FBLK * FBLK; }
+// Functions of a shell: (L+1)(L+2)/2 Cartesian, or 2L+1 real solid harmonics when pure.
+inline int shell_nfunc(const DevShell &s) { return s.pure ? 2 * s.L + 1 : (s.L + 1) * (s.L + 2) / 2; }
 // The planner as device kernels (device_plan.cu): the same grid and plan as
 // build_molecular_grid + build_plan, bit for bit.  *status: 0 done, 1 grid too large,
 // 2 internal stack overflow (cannot happen for depth <= 16).

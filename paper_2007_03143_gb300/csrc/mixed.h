@@ -32,11 +32,12 @@ struct DfShell {
     float ah[GBXC_MAX_PRIM], al[GBXC_MAX_PRIM];       // exponents alpha
     float dh[GBXC_MAX_PRIM], dl[GBXC_MAX_PRIM];       // coefficients d
     float gh[GBXC_MAX_PRIM], gl[GBXC_MAX_PRIM];       // -2 alpha d (gradient coefficients)
-    int L, nprim, fofs, pad;
+    int L, nprim, fofs, pure;
 };
 // Per-molecule resident state of the mixed form.
 struct MixedResident {
     DfShell *d_shells = nullptr;
+    bool has_pure = false;   // any spherical shell: the collocation with the pure-shell path
 };
 cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResident &r);
 // Per-schedule state of the mixed form: for every chunk the batch range and the row

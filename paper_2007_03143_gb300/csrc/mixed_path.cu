@@ -34,6 +34,7 @@
 #include "mixed.h"
 #include "dfloat.cuh"
 #include "slicing.cuh"
+#include "solid_harmonics.cuh"
 #include "umma.cuh"
 #include "xc_functional.cuh"
 
@@ -206,6 +207,66 @@ __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const
         }
 }
 
+// Double-float arithmetic for the pure-shell combinations (solid_harmonics.cuh).
+struct DfOps {
+    __device__ static df add(df a, df b) { return dfl::add(a, b); }
+    __device__ static df sub(df a, df b) { return dfl::sub(a, b); }
+    __device__ static df scale(df a, double k) {
+        const float kh = (float)k;
+        return dfl::mul(a, {kh, (float)(k - (double)kh)});
+    }
+};
+
+// A pure shell (L = 2 or 3), one component at a time (value, d/dx, d/dy, d/dz): the
+// Cartesian values of that component, then its 2L+1 real solid harmonics, written as rows
+// o, o + TILE, ... (the same formulas as colloc_shell for each component).
+template <int L>
+__device__ __forceinline__ void colloc_pure_shell(df X, df Y, df Z, df g, df h, const MixedSlabs &sl, size_t plane,
+                                                  size_t o, bool live, float &mx) {
+    constexpr int NC = (L + 1) * (L + 2) / 2, NO = 2 * L + 1;
+    df xp[L + 1], yp[L + 1], zp[L + 1];
+    xp[0] = yp[0] = zp[0] = {1.f, 0.f};
+#pragma unroll
+    for (int k = 1; k <= L; ++k) {
+        xp[k] = df_mul(xp[k - 1], X);
+        yp[k] = df_mul(yp[k - 1], Y);
+        zp[k] = df_mul(zp[k - 1], Z);
+    }
+    const df R[4] = {g, df_mul(X, h), df_mul(Y, h), df_mul(Z, h)};
+#pragma unroll
+    for (int comp = 0; comp < 4; ++comp) {
+        df cv[NC], out[NO];
+        int f = 0;
+#pragma unroll
+        for (int l = L; l >= 0; --l)
+#pragma unroll
+            for (int mm = L - l; mm >= 0; --mm) {
+                const int nn = L - l - mm;
+                const df ym_zn = df_mul(yp[mm], zp[nn]);
+                df v = df_mul(df_mul(xp[l], ym_zn), R[comp]);
+                if (comp == 1 && l > 0)
+                    v = df_add(v, df_mul(dfl::mul_f(df_mul(xp[l > 0 ? l - 1 : 0], ym_zn), (float)l), g));
+                if (comp == 2 && mm > 0)
+                    v = df_add(v, df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm > 0 ? mm - 1 : 0]), zp[nn]), (float)mm), g));
+                if (comp == 3 && nn > 0)
+                    v = df_add(v, df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm]), zp[nn > 0 ? nn - 1 : 0]), (float)nn), g));
+                cv[f++] = v;
+            }
+        sph::pure<L, DfOps>(cv, out);
+#pragma unroll
+        for (int k = 0; k < NO; ++k) {
+            const size_t of = o + (size_t)k * TILE;
+            if (comp == 0) {
+                sl.phi[of] = live ? make_float2(out[k].h, out[k].l) : make_float2(0.f, 0.f);
+                if (live) mx = fmaxf(mx, fabsf(out[k].h));
+            } else {
+                sl.ghi[(comp - 1) * plane + of] = live ? out[k].h : 0.f;
+                sl.glo[(comp - 1) * plane + of] = live ? out[k].l : 0.f;
+            }
+        }
+    }
+}
+
 // Thread per point; Eq. gau_cart and its gradient in double-float arithmetic on the
 // float32 pipe (exp(-alpha r^2) by dfl::exp_neg), stored as (hi, lo) pairs; then the
 // point's Ozaki slices of Phi, K-blocked by 32 functions.  Consecutive shells on one centre
@@ -214,7 +275,8 @@ struct Exp2Table {
     float2 v[64];   // 2^(-j/64) as (hi, lo): the table of dfl::exp_neg
 };
 
-__global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells,
+template <bool HAS_PURE>   // instantiated without the pure-shell path for Cartesian bases
+__global__ void __launch_bounds__(TILE, HAS_PURE ? 7 : 1) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells,
                                                      const __grid_constant__ Exp2Table e2t) {
     __shared__ float2 tab[64];
     if (threadIdx.x < 64) tab[threadIdx.x] = e2t.v[threadIdx.x];
@@ -255,6 +317,14 @@ __global__ void __launch_bounds__(TILE) colloc_mixed(ChunkArgs a, MixedArgs m, c
             h = df_add(h, df_mul({sh.gh[k], sh.gl[k]}, ex));
         }
         const size_t o = (size_t)(r0 + row) * TILE + i;
+        if constexpr (HAS_PURE) {
+            if (sh.pure) {   // L = 2 or 3
+                if (sh.L == 2) colloc_pure_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, mx);
+                else colloc_pure_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, mx);
+                row += 2 * sh.L + 1;
+                continue;
+            }
+        }
         switch (sh.L) {
             case 0: colloc_shell<0>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 1; break;
             case 1: colloc_shell<1>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 3; break;
@@ -954,6 +1024,7 @@ void free_mixed_resident(MixedResident &r) {
 
 cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResident &r) {
     std::vector<DfShell> h(shells.size());
+    r.has_pure = false;
     auto split = [](double v, float &hi, float &lo) {
         hi = (float)v;
         lo = (float)(v - (double)hi);
@@ -971,6 +1042,8 @@ cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResid
         o.L = d.L;
         o.nprim = d.nprim;
         o.fofs = d.fofs;
+        o.pure = d.pure;
+        if (d.pure) r.has_pure = true;
     }
     cudaFree(r.d_shells);
     r.d_shells = nullptr;
@@ -1083,7 +1156,10 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
         dfl::make_exp2_table(x.v);
         return x;
     }();
-    colloc_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells, e2t);
+    if (r.has_pure)
+        colloc_mixed<true><<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells, e2t);
+    else
+        colloc_mixed<false><<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells, e2t);
     P.end(GBXC_K_COLLOC, st);
     const int *xtasks = s.d_xtasks + 2 * ch.xtask0;
     int nx = (int)ch.nxtask;

@@ -12,7 +12,7 @@ from gpu_common import Loaded
 
 pytestmark = pytest.mark.gpu
 
-SMALL = ["water1_slater", "water1_pbe_small", "water2_pbe_small", "water3_pbe_small"]
+SMALL = ["water1_slater", "water1_pbe_small", "water2_pbe_small", "water3_pbe_small", "water2_pbe_small_sph"]
 
 
 @pytest.fixture(scope="module", params=SMALL)

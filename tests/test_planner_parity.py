@@ -18,7 +18,7 @@ def _lib_plan(w):
     ctx = G.gbxc_create(-1)
     try:
         b = w.basis
-        mid, nbf = G.gbxc_load_basis(ctx, w.mol.xyz, w.mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff)
+        mid, nbf = G.gbxc_load_basis(ctx, w.mol.xyz, w.mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff, b.pure)
         assert nbf == b.nbf
         g = w.grid
         G.gbxc_load_grid(ctx, mid, g.nrad, g.ntheta, g.nphi, g.partition, g.max_batch, g.eta, g.mk_alpha)
@@ -39,7 +39,7 @@ def _lib_plan(w):
 
 
 @pytest.mark.parametrize("name", ["water1_slater", "water2_pbe_small", "water3_pbe_small",
-                                  "water1_pbe_small", "water16_pbe"])
+                                  "water1_pbe_small", "water16_pbe", "water2_pbe_small_sph"])
 def test_plan_bit_exact(name):
     w = X.make_workload(name)
     info, L = _lib_plan(w)
@@ -72,7 +72,7 @@ def test_host_context_rejects_integration():
     ctx = G.gbxc_create(-1)
     try:
         b = w.basis
-        mid, nbf = G.gbxc_load_basis(ctx, w.mol.xyz, w.mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff)
+        mid, nbf = G.gbxc_load_basis(ctx, w.mol.xyz, w.mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff, b.pure)
         with pytest.raises(G.GbxcError):
             G.gbxc_integrate(ctx, mid, w.P)
         with pytest.raises(G.GbxcError):
