@@ -276,7 +276,7 @@ struct Exp2Table {
 };
 
 template <bool HAS_PURE>   // instantiated without the pure-shell path for Cartesian bases
-__global__ void __launch_bounds__(TILE, HAS_PURE ? 7 : 1) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells,
+__global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m, const DfShell *__restrict__ shells,
                                                      const __grid_constant__ Exp2Table e2t) {
     __shared__ float2 tab[64];
     if (threadIdx.x < 64) tab[threadIdx.x] = e2t.v[threadIdx.x];
