@@ -140,3 +140,66 @@ def integrate_method(grid: Grid, basis, P, functional: str, plan: planner.Plan,
             Nb[j] += n
             V[np.ix_(F, F)] += Vj                                   # Eq. vxc_inc
     return Result(float(np.sum(Eb)), float(np.sum(Nb)), V, Eb, Nb)
+
+
+# ---------------------------------------------------------------- spin-unrestricted
+@dataclass
+class ResultUKS:
+    E: float
+    N: float
+    Va: np.ndarray
+    Vb: np.ndarray
+    E_batch: np.ndarray | None = None
+    N_batch: np.ndarray | None = None
+
+
+def integrate_batch_uks(pts, w, phi_args, Paj, Pbj, fn):
+    """One batch of the spin-unrestricted extension (Sec. 2.1): Eqs. x_mat, eval_local_den,
+    eval_local_den_grad per spin, the polarised functional, then per spin
+    Z^s = 1/2 w v_s phi + w (2 s_ss grad rho_s + s_ab grad rho_s') . grad phi and
+    V^s = Z^sT phi + phi^T Z^s (Eqs. z_mat, vxc_batch)."""
+    phi, gx, gy, gz = phi_args
+    rho, grad = [], []
+    for Pj in (Paj, Pbj):
+        X = phi @ Pj
+        rho.append(np.sum(phi * X, axis=1))
+        grad.append([2.0 * np.sum(g * X, axis=1) for g in (gx, gy, gz)])
+    dot = lambda u, v: u[0] * v[0] + u[1] * v[1] + u[2] * v[2]          # noqa: E731
+    saa, sab, sbb = dot(grad[0], grad[0]), dot(grad[0], grad[1]), dot(grad[1], grad[1])
+    f, va, vb, s_aa, s_ab, s_bb = fn(rho[0], rho[1], saa, sab, sbb)
+    V = []
+    for v, s_ss, own, other in ((va, s_aa, grad[0], grad[1]), (vb, s_bb, grad[1], grad[0])):
+        c = [w * (2.0 * s_ss * own[d] + s_ab * other[d]) for d in range(3)]
+        Z = (0.5 * w * v)[:, None] * phi + c[0][:, None] * gx + c[1][:, None] * gy + c[2][:, None] * gz
+        V.append(Z.T @ phi + phi.T @ Z)
+    return float(np.sum(w * f)), float(np.sum(w * (rho[0] + rho[1]))), V[0], V[1]
+
+
+def integrate_method_uks(grid: Grid, basis, Pa, Pb, functional: str, plan: planner.Plan,
+                         batches=None) -> ResultUKS:
+    """Spin-unrestricted method-equivalent mode over the merged batches of ``plan``."""
+    from . import functionals_pol
+    fn = functionals_pol.FUNCTIONALS_POL[functional]
+    nbf = basis.nbf
+    Va = np.zeros((nbf, nbf))
+    Vb = np.zeros((nbf, nbf))
+    nb = len(plan.batch_points)
+    sel = range(nb) if batches is None else batches
+    Eb = np.zeros(nb)
+    Nb = np.zeros(nb)
+    for j in sel:
+        idx = plan.batch_points[j]
+        F = plan.batch_funcs[j]
+        if len(F) == 0:
+            continue
+        Paj, Pbj = Pa[np.ix_(F, F)], Pb[np.ix_(F, F)]
+        for s in range(0, len(idx), CHUNK):
+            ii = idx[s:s + CHUNK]
+            pts = np.stack([grid.x[ii], grid.y[ii], grid.z[ii]], axis=1)
+            cols = collocation.collocate(pts, basis, plan.batch_shells[j])
+            e, n, Vaj, Vbj = integrate_batch_uks(pts, grid.w[ii], cols, Paj, Pbj, fn)
+            Eb[j] += e
+            Nb[j] += n
+            Va[np.ix_(F, F)] += Vaj
+            Vb[np.ix_(F, F)] += Vbj
+    return ResultUKS(float(np.sum(Eb)), float(np.sum(Nb)), Va, Vb, Eb, Nb)

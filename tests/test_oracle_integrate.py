@@ -163,3 +163,40 @@ def test_pure_basis_definitional_equals_method():
     M = I.integrate_method(g, w.basis, w.P, "pbe", pl)
     assert abs(D.E - M.E) < 1e-13 * abs(D.E)
     assert np.max(np.abs(D.V - M.V)) < 1e-13 * np.max(np.abs(D.V))
+
+
+# ---------------------------------------------------------------- spin-unrestricted
+def _spin_densities(w, na, nb, seed):
+    # P_s = C_s C_s^T with C_s^T S C_s = I (na alpha, nb beta orbitals, separately seeded):
+    # positive semidefinite, so rho_a, rho_b >= 0 everywhere
+    return 0.5 * X.density_matrix(w.S, na, seed), 0.5 * X.density_matrix(w.S, nb, seed + 1)
+
+
+@pytest.mark.parametrize("functional", ["slater", "pbe"])
+def test_uks_equal_spins_reduce_to_rks(water1_pbe, functional):
+    w, g, pl = water1_pbe
+    r = I.integrate_method(g, w.basis, w.P, functional, pl)
+    u = I.integrate_method_uks(g, w.basis, 0.5 * w.P, 0.5 * w.P, functional, pl)
+    assert abs(u.E - r.E) < 1e-12 * abs(r.E) and abs(u.N - r.N) < 1e-12 * r.N
+    assert np.max(np.abs(u.Va - r.V)) < 1e-11 * np.max(np.abs(r.V))
+    assert np.max(np.abs(u.Vb - r.V)) < 1e-11 * np.max(np.abs(r.V))
+
+
+@pytest.mark.parametrize("functional", ["slater", "pbe"])
+def test_uks_V_is_dE_dP_per_spin(water1_pbe, functional):
+    w, g, pl = water1_pbe
+    Pa, Pb = _spin_densities(w, 5, 4, 500)
+    u = I.integrate_method_uks(g, w.basis, Pa, Pb, functional, pl)
+    rng = np.random.default_rng(6)
+    d = rng.normal(size=w.P.shape)
+    d = 0.5 * (d + d.T)
+    h = 1e-5   # the central difference converges as h^2 (2e-7 relative at h = 1e-4, 2e-9 at 1e-5)
+    for spin in (0, 1):
+        Pp = [Pa.copy(), Pb.copy()]
+        Pm = [Pa.copy(), Pb.copy()]
+        Pp[spin] += h * d
+        Pm[spin] -= h * d
+        fd = (I.integrate_method_uks(g, w.basis, *Pp, functional, pl).E
+              - I.integrate_method_uks(g, w.basis, *Pm, functional, pl).E) / (2 * h)
+        V = u.Va if spin == 0 else u.Vb
+        assert abs(fd - np.sum(V * d)) < 1e-7 * abs(fd), spin
