@@ -191,6 +191,20 @@ int gbxc_export_plan(gbxc_ctx *ctx, int mol, double *x, double *y, double *z, do
 int gbxc_integrate(gbxc_ctx *ctx, int mol, const double *P, int functional, int precision,
                    double *Exc, double *Vxc, double *Nel, void *stream);
 
+/* Spin-unrestricted integration (the extension the paper notes for its method, Sec. 2.1):
+ * spin densities rho_s = sum P^s_mu,nu phi_mu phi_nu from P^a and P^b, the spin-polarised
+ * functional f(rho_a, rho_b, sigma_aa, sigma_ab, sigma_bb) (Slater exchange by spin scaling;
+ * PBE exchange by spin scaling and PBE correlation with the PW92 spin interpolation), and
+ * V^s = dE_xc/dP^s through Z^s = 1/2 w v_s Phi + w (2 s_ss grad rho_s + s_ab grad rho_s') .
+ * grad Phi.  With P^a = P^b = P/2 the result equals gbxc_integrate's with P (V^a = V^b = V).
+ *   Pa, Pb      nbf x nbf spin density matrices (host or device, symmetric)
+ *   precision   GBXC_FP64 (the tensor-core form is not built for this variant: GBXC_EINVAL)
+ *   Exc, Nel    E_xc and the total electron count (may be NULL)
+ *   Va, Vb      nbf x nbf outputs, host or device (may be NULL)
+ *   stream      as gbxc_integrate */
+int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *Pb, int functional, int precision,
+                       double *Exc, double *Va, double *Vb, double *Nel, void *stream);
+
 /* As gbxc_integrate, restricted to merged batches [batch_begin, batch_end),
  * the device subset step of Algorithm 2.  E_batch and N_batch (host, may be
  * NULL) receive each batch's contribution, nbatch entries, zero outside the

@@ -35,7 +35,7 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
             "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule", "gbxc_load_grid_device",
-            "gbxc_load_basis_pure"]
+            "gbxc_load_basis_pure", "gbxc_integrate_uks"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -84,6 +84,9 @@ def lib():
     L.gbxc_load_basis_pure.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_int)]
     L.gbxc_load_basis_pure.restype = c_int
+    L.gbxc_integrate_uks.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, pd, c_void_p, c_void_p,
+                                     pd, c_void_p]
+    L.gbxc_integrate_uks.restype = c_int
     L.gbxc_load_grid.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
     L.gbxc_load_grid_device.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
     L.gbxc_load_grid_device.restype = c_int
@@ -231,6 +234,20 @@ def gbxc_integrate(ctx, mol, P, functional="pbe", precision="fp64", V=None, stre
     _check(ctx, lib().gbxc_integrate(ctx, mol, pP, FUNCTIONALS.get(functional, functional),
                                      PRECISIONS.get(precision, precision), ctypes.byref(E), pV,
                                      ctypes.byref(N), st))
+    return E.value, N.value
+
+
+def gbxc_integrate_uks(ctx, mol, Pa, Pb, functional="pbe", precision="fp64", Va=None, Vb=None, stream=None):
+    """Spin-unrestricted integration; returns (E_xc, N_el); fills Va, Vb if given."""
+    pA, kA, _ = _ptr(Pa)
+    pB, kB, _ = _ptr(Pb)
+    pVa, kVa, _ = _ptr(Va)
+    pVb, kVb, _ = _ptr(Vb)
+    st = _stream_for(stream, Pa, Va)
+    E, N = c_double(), c_double()
+    _check(ctx, lib().gbxc_integrate_uks(ctx, mol, pA, pB, FUNCTIONALS.get(functional, functional),
+                                         PRECISIONS.get(precision, precision), ctypes.byref(E), pVa, pVb,
+                                         ctypes.byref(N), st))
     return E.value, N.value
 
 

@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(TILE) colloc_f64(ChunkArgs a) {
 // --------------------------------------------------------------------------
 constexpr int XB_R = 64, XB_K = 16;
 
-__global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a) {
+// X = P^j Phi^j from density P into slab plane `out` (4, or 5 for the second spin).
+__global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a, const double *__restrict__ P, int out) {
     int64_t t = a.t0 + blockIdx.x;
     int rb = blockIdx.y;
     int j = a.plan.tile_batch[t];
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a) {
     Slabs S = slabs_of(a);
     int64_t row0 = a.plan.tile_row[t] - a.row0;
     const double *Phi = S.c[0] + (size_t)row0 * TILE;
-    double *Xo = S.c[4] + (size_t)row0 * TILE;
+    double *Xo = S.c[out] + (size_t)row0 * TILE;
 
     __shared__ double As[XB_K][XB_R + 1];
     __shared__ double Bs[XB_K][TILE];
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a) {
             int kk = e / XB_R, rr = e % XB_R;
             int k = k0 + kk;
             int fr = Frow[rr];
-            As[kk][rr] = (fr >= 0 && k < n) ? a.P[(size_t)fr * a.nbf + F[k]] : 0.0;
+            As[kk][rr] = (fr >= 0 && k < n) ? P[(size_t)fr * a.nbf + F[k]] : 0.0;
         }
         for (int e = tid; e < XB_K * TILE; e += 256) {
             int kk = e / TILE, c = e % TILE;
@@ -262,13 +263,88 @@ __global__ void __launch_bounds__(TILE) rho_xc_z_f64(ChunkArgs a) {
 }
 
 // --------------------------------------------------------------------------
+// k45, spin-unrestricted (the extension of Sec. 2.1): X^a in plane 4 and X^b in plane 5 give
+// rho_s and grad rho_s per spin; the spin-polarised functional; then per spin
+// Z^s = 1/2 w v_s Phi + w (2 s_ss grad rho_s + s_ab grad rho_s') . grad Phi over X^s.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE) rho_xc_z_uks_f64(ChunkArgs a) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int64_t row0 = a.plan.tile_row[t] - a.row0;
+    Slabs S = slabs_of(a);
+    size_t base = (size_t)row0 * TILE + i;
+    double rho[2] = {0.0, 0.0}, g[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int r = 0; r < n; ++r) {
+        size_t o = base + (size_t)r * TILE;
+        const double p0 = S.c[0][o], p1 = S.c[1][o], p2 = S.c[2][o], p3 = S.c[3][o];
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            const double xv = S.c[4 + sp][o];
+            rho[sp] = fma(p0, xv, rho[sp]);
+            g[sp][0] = fma(p1, xv, g[sp][0]);
+            g[sp][1] = fma(p2, xv, g[sp][1]);
+            g[sp][2] = fma(p3, xv, g[sp][2]);
+        }
+    }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) g[sp][d] *= 2.0;
+    double e = 0.0, nn = 0.0, ca[2] = {0.0, 0.0}, cb[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    if (i < cnt) {
+        const double w = a.plan.w[a.plan.tile_first[t] + i];
+        const double saa = g[0][0] * g[0][0] + g[0][1] * g[0][1] + g[0][2] * g[0][2];
+        const double sab = g[0][0] * g[1][0] + g[0][1] * g[1][1] + g[0][2] * g[1][2];
+        const double sbb = g[1][0] * g[1][0] + g[1][1] * g[1][1] + g[1][2] * g[1][2];
+        double f, va, vb, s_aa, s_ab, s_bb;
+        xc::evaluate_pol<double>(a.functional, rho[0], rho[1], saa, sab, sbb, f, va, vb, s_aa, s_ab, s_bb);
+        e = w * f;
+        nn = w * (rho[0] + rho[1]);
+        ca[0] = 0.5 * w * va;
+        ca[1] = 0.5 * w * vb;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cb[0][d] = w * (2.0 * s_aa * g[0][d] + s_ab * g[1][d]);
+            cb[1][d] = w * (2.0 * s_bb * g[1][d] + s_ab * g[0][d]);
+        }
+    }
+    for (int r = 0; r < n; ++r) {
+        size_t o = base + (size_t)r * TILE;
+        const double p0 = S.c[0][o], p1 = S.c[1][o], p2 = S.c[2][o], p3 = S.c[3][o];
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp)
+            S.c[4 + sp][o] = ca[sp] * p0 + cb[sp][0] * p1 + cb[sp][1] * p2 + cb[sp][2] * p3;
+    }
+    __shared__ double re[TILE], rn[TILE];
+    re[i] = e;
+    rn[i] = nn;
+    __syncthreads();
+    for (int st = TILE / 2; st > 0; st >>= 1) {
+        if (i < st) {
+            re[i] += re[i + st];
+            rn[i] += rn[i + st];
+        }
+        __syncthreads();
+    }
+    if (i == 0) {
+        a.tileE[t] = re[0];
+        a.tileN[t] = rn[0];
+    }
+}
+
+// --------------------------------------------------------------------------
 // k6: W^j[mu][nu] = sum_i Z[mu][i] Phi[nu][i] over tiles [t0, t1) of batch j,
 // 64 x 64 output block per CTA (256 threads, 4 x 4 each), then
 // V_acc[F_mu][F_nu] += W (float64 atomics).
 // --------------------------------------------------------------------------
 constexpr int VB = 64, VK = 16;
 
-__global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a) {
+// W = Z^T Phi from slab plane `zp` (5, or 4 for the first spin of the unrestricted form),
+// scattered into Vacc.
+__global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a, int zp, double *__restrict__ Vacc) {
     const int *task = a.vtasks + 5 * blockIdx.x;
     int j = task[0], mb = task[1], nb = task[2];
     int64_t tb = task[3], te = task[4];
@@ -288,7 +364,7 @@ __global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a) {
         for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
     for (int64_t t = tb; t < te; ++t) {
         int64_t row0 = a.plan.tile_row[t] - a.row0;
-        const double *Zs = S.c[5] + (size_t)row0 * TILE;
+        const double *Zs = S.c[zp] + (size_t)row0 * TILE;
         const double *Ps = S.c[0] + (size_t)row0 * TILE;
         int cnt = a.plan.tile_count[t];
         for (int k0 = 0; k0 < cnt; k0 += VK) {
@@ -323,7 +399,7 @@ __global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             int nr = n0 + tx * 4 + v;
-            if (nr < n) atomicAdd(&a.Vacc[rowg + F[nr]], acc[u][v]);
+            if (nr < n) atomicAdd(&Vacc[rowg + F[nr]], acc[u][v]);
         }
     }
 }
@@ -449,15 +525,39 @@ cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s) {
     P.end(GBXC_K_COLLOC, s);
     dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
     P.begin(GBXC_K_XGEMM, s);
-    xgemm_f64<<<xg, 256, 0, s>>>(a);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 4);
     P.end(GBXC_K_XGEMM, s);
     P.begin(GBXC_K_RHO_Z, s);
     rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     P.end(GBXC_K_RHO_Z, s);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, s);
-        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a);
+        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 5, a.Vacc);
         P.end(GBXC_K_VGEMM, s);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_chunk_uks(const ChunkArgs &a, const double *Pb, double *Vacc_b, cudaStream_t s) {
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    Profiler &P = *a.prof;
+    P.begin(GBXC_K_COLLOC, s);
+    colloc_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    P.end(GBXC_K_COLLOC, s);
+    dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
+    P.begin(GBXC_K_XGEMM, s);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 4);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, Pb, 5);
+    P.end(GBXC_K_XGEMM, s, 2);
+    P.begin(GBXC_K_RHO_Z, s);
+    rho_xc_z_uks_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    P.end(GBXC_K_RHO_Z, s);
+    if (a.nvtasks > 0) {
+        P.begin(GBXC_K_VGEMM, s);
+        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 4, a.Vacc);
+        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 5, Vacc_b);
+        P.end(GBXC_K_VGEMM, s, 2);
     }
     return cudaGetLastError();
 }
@@ -485,10 +585,16 @@ cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s) {
     if (nt <= 0) return cudaSuccess;
     colloc_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
-    xgemm_f64<<<xg, 256, 0, s>>>(a);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 4);
     rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     unsigned nblk = (unsigned)((a.max_nfunc + VB - 1) / VB);
     vgemm_f64_tile<<<dim3((unsigned)nt, nblk, nblk), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(const double *Vacc, double *V, int nbf, cudaStream_t s) {
+    int64_t nn = (int64_t)nbf * nbf;
+    if (nn > 0) symmetrize<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Vacc, V, nbf);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,8 @@ struct Workspace {
     double *tileE = nullptr, *tileN = nullptr, *Eb = nullptr, *Nb = nullptr;
     size_t tile_cap = 0, batch_cap = 0;
     MixedCtx mixed;
+    double *d_P2 = nullptr, *d_Vacc2 = nullptr, *d_V2 = nullptr;   // second spin (unrestricted)
+    size_t mat2_cap = 0;
 };
 
 // First-fit allocator over one device allocation (the paper's preallocated device arena
@@ -296,6 +298,9 @@ void free_workspace(Workspace &w) {
         cudaFree(w.tileN);
         cudaFree(w.Eb);
         cudaFree(w.Nb);
+        cudaFree(w.d_P2);
+        cudaFree(w.d_Vacc2);
+        cudaFree(w.d_V2);
         free_mixed_ctx(w.mixed);
     }
     w = Workspace{};
@@ -1163,6 +1168,89 @@ int gbxc_integrate(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
         if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
         return integrate_impl(ctx, mol, P, functional, precision, 0, m.plan.nbatch(), Exc, Vxc,
                               Nel, nullptr, nullptr, stream);
+    });
+}
+
+int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *Pb, int functional, int precision,
+                       double *Exc, double *Va, double *Vb, double *Nel, void *stream) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(ctx->device >= 0, "integration needs a device context");
+        Molecule &m = get_mol(ctx, mol);
+        if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
+        REQUIRE(Pa && Pb, "P is NULL");
+        REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "unknown functional");
+        REQUIRE(precision == GBXC_FP64, "the spin-unrestricted form is built for GBXC_FP64");
+        const int nb = m.plan.nbatch();
+        cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+        const size_t nn = (size_t)m.nbf * m.nbf;
+        Workspace &w = ctx->ws;
+        const Schedule &S = get_schedule(m, GBXC_FP64, 0, nb, scratch_budget(ctx));
+        reserve(w, m, S, GBXC_FP64);
+        if (nn > w.mat2_cap || !w.d_P2) {
+            size_t c0 = w.mat2_cap, c1 = w.mat2_cap, c2 = w.mat2_cap;
+            grow_buf(w.d_P2, c0, nn, "P_b");
+            grow_buf(w.d_Vacc2, c1, nn, "V_acc_b");
+            grow_buf(w.d_V2, c2, nn, "V_b");
+            w.mat2_cap = nn;
+        }
+        const double *dPa = Pa, *dPb = Pb;
+        if (!is_device_ptr(Pa)) {
+            check(cudaMemcpyAsync(w.d_P, Pa, nn * 8, cudaMemcpyHostToDevice, s), "copy P_a");
+            dPa = w.d_P;
+        }
+        if (!is_device_ptr(Pb)) {
+            check(cudaMemcpyAsync(w.d_P2, Pb, nn * 8, cudaMemcpyHostToDevice, s), "copy P_b");
+            dPb = w.d_P2;
+        }
+        double *dVa = (Va && is_device_ptr(Va)) ? Va : w.d_V;
+        double *dVb = (Vb && is_device_ptr(Vb)) ? Vb : w.d_V2;
+        check(cudaMemsetAsync(w.d_Vacc, 0, nn * 8, s), "zero V_a");
+        check(cudaMemsetAsync(w.d_Vacc2, 0, nn * 8, s), "zero V_b");
+        for (const auto &c : S.chunks) {
+            ChunkArgs a;
+            a.plan = m.dev;
+            a.shells = m.d_shells;
+            a.nbf = m.nbf;
+            a.t0 = c.t0;
+            a.t1 = c.t1;
+            a.row0 = c.row0;
+            a.rows = c.rows;
+            a.max_nfunc = c.max_nfunc;
+            a.functional = functional;
+            a.P = dPa;
+            a.Vacc = w.d_Vacc;
+            a.tileE = w.tileE;
+            a.tileN = w.tileN;
+            a.scratch = w.scratch;
+            a.vtasks = S.d_tasks ? S.d_tasks + 5 * c.task0 : nullptr;
+            a.nvtasks = (int)c.ntask;
+            a.prof = &ctx->prof;
+            check(launch_fp64_chunk_uks(a, dPb, w.d_Vacc2, s), "unrestricted chunk");
+        }
+        FinishArgs f;
+        f.Vacc = w.d_Vacc;
+        f.V = Va ? dVa : nullptr;
+        f.nbf = m.nbf;
+        f.tileE = w.tileE;
+        f.tileN = w.tileN;
+        f.batch_tile = m.dev.batch_tile;
+        f.b0 = 0;
+        f.b1 = nb;
+        f.Eb = w.Eb;
+        f.Nb = w.Nb;
+        f.tot = w.d_tot;
+        f.prof = &ctx->prof;
+        check(launch_finish(f, s), "finish");
+        if (Vb) check(launch_symmetrize(w.d_Vacc2, dVb, m.nbf, s), "symmetrise V_b");
+        double tot[2];
+        check(cudaMemcpyAsync(tot, w.d_tot, 16, cudaMemcpyDeviceToHost, s), "copy E");
+        if (Va && dVa != Va) check(cudaMemcpyAsync(Va, dVa, nn * 8, cudaMemcpyDeviceToHost, s), "copy V_a");
+        if (Vb && dVb != Vb) check(cudaMemcpyAsync(Vb, dVb, nn * 8, cudaMemcpyDeviceToHost, s), "copy V_b");
+        check(cudaStreamSynchronize(s), "integrate unrestricted");
+        if (Exc) *Exc = tot[0];
+        if (Nel) *Nel = tot[1];
+        return GBXC_OK;
     });
 }
 

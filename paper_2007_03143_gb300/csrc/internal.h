@@ -166,6 +166,8 @@ struct ChunkArgs {
     Profiler *prof;
 };
 cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s);
+// Spin-unrestricted chunk: a.P / a.Vacc carry spin a, Pb / Vacc_b spin b.
+cudaError_t launch_fp64_chunk_uks(const ChunkArgs &a, const double *Pb, double *Vacc_b, cudaStream_t s);
 
 struct FinishArgs {
     const double *Vacc;
@@ -185,5 +187,7 @@ cudaError_t launch_finish(const FinishArgs &a, cudaStream_t s);
 cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
 cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s);
 cudaError_t launch_symmetrize_inplace(double *V, int nbf, cudaStream_t s);
+// V = V_acc + V_acc^T
+cudaError_t launch_symmetrize(const double *Vacc, double *V, int nbf, cudaStream_t s);
 
 }  // namespace gbxc

@@ -117,5 +117,147 @@ __device__ __forceinline__ void evaluate(int fn, T rho, T sigma, T &f, T &vrho, 
     }
 }
 
+// ---------------------------------------------------------------- spin-polarised forms
+// Arguments rho_a, rho_b, sigma_aa, sigma_ab, sigma_bb; results f and its derivatives
+// va, vb (rho_a, rho_b), saa, sab, sbb (the three sigmas).
+//
+// Exchange by spin scaling, f = f(2 rho_a, 4 sigma_aa)/2 + f(2 rho_b, 4 sigma_bb)/2.
+// PBE correlation with the PW92 spin interpolation (Perdew and Wang 1992):
+//   eps_c = e0 + alpha_c f(zeta)(1 - zeta^4)/f''(0) + (e1 - e0) f(zeta) zeta^4,
+//   f(zeta) = ((1+zeta)^(4/3) + (1-zeta)^(4/3) - 2)/(2^(4/3) - 2),
+//   e0, e1, -alpha_c = G(r_s) with PW92's three parameter sets,
+//   H = gamma phi^3 ln(1 + (beta/gamma) Y(t^2, A)), phi = ((1+zeta)^(2/3) + (1-zeta)^(2/3))/2,
+//   t^2 = pi sigma/(16 (3 pi^2)^(1/3) rho^(7/3) phi^2), A = (beta/gamma)/(exp(-eps_c/(gamma phi^3)) - 1),
+// with rho = rho_a + rho_b, zeta = (rho_a - rho_b)/rho clamped to |zeta| <= 1 - 1e-10 and
+// sigma = sigma_aa + 2 sigma_ab + sigma_bb; zero below rho = kRhoMin.
+constexpr double kZetaMax = 1.0 - 1e-10;
+constexpr double kFzDen = 0.5198420997897464;          // 2^(4/3) - 2
+constexpr double kFpp0 = 1.7099209341613653;           // 8 / (9 (2^(4/3) - 2))
+// PW92's parameter sets: 0 = e0 (paramagnetic), 1 = e1 (ferromagnetic), 2 = -alpha_c
+template <int K>
+struct PwSet;
+template <>
+struct PwSet<0> {
+    static constexpr double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
+};
+template <>
+struct PwSet<1> {
+    static constexpr double A = 0.015545, a1 = 0.20548, b1 = 14.1189, b2 = 6.1977, b3 = 3.3662, b4 = 0.62517;
+};
+template <>
+struct PwSet<2> {
+    static constexpr double A = 0.016887, a1 = 0.11125, b1 = 10.357, b2 = 3.6231, b3 = 0.88026, b4 = 0.49671;
+};
+
+template <int K, typename T>
+__device__ __forceinline__ void pw_G(T rs, T &g, T &dg) {
+    using p = PwSet<K>;
+    T srs = m_sqrt(rs);
+    T Q = T(p::b1) * srs + T(p::b2) * rs + T(p::b3) * rs * srs + T(p::b4) * rs * rs;
+    T dQ = T(0.5 * p::b1) / srs + T(p::b2) + T(1.5 * p::b3) * srs + T(2.0 * p::b4) * rs;
+    T lg = m_log1p(T(1) / (T(2.0 * p::A) * Q));
+    g = T(-2.0 * p::A) * (T(1) + T(p::a1) * rs) * lg;
+    dg = T(-2.0 * p::A * p::a1) * lg + T(2.0 * p::A) * (T(1) + T(p::a1) * rs) * dQ / (Q * (T(2.0 * p::A) * Q + T(1)));
+}
+
+template <typename T>
+__device__ __forceinline__ void pbe_c_pol(T ra, T rb, T saa, T sab, T sbb, T &f, T &va, T &vb, T &s_aa, T &s_ab,
+                                          T &s_bb) {
+    const T rho = ra + rb;
+    if (!(rho >= T(kRhoMin))) {
+        f = va = vb = s_aa = s_ab = s_bb = T(0);
+        return;
+    }
+    T zeta = (ra - rb) / rho;
+    zeta = zeta > T(kZetaMax) ? T(kZetaMax) : (zeta < T(-kZetaMax) ? T(-kZetaMax) : zeta);
+    const T sig = saa + T(2) * sab + sbb;
+    const T r13 = m_cbrt(rho);
+    const T rs = T(kRsScale) / r13;
+    T e0, de0, e1, de1, mac, dmac;
+    pw_G<0>(rs, e0, de0);
+    pw_G<1>(rs, e1, de1);
+    pw_G<2>(rs, mac, dmac);
+    const T opz = T(1) + zeta, omz = T(1) - zeta;
+    const T co = m_cbrt(opz), cm = m_cbrt(omz);
+    const T fz = (opz * co + omz * cm - T(2)) / T(kFzDen);
+    const T dfz = T(4.0 / 3.0) * (co - cm) / T(kFzDen);
+    const T z2 = zeta * zeta, z3 = z2 * zeta, z4 = z2 * z2;
+    const T eps = e0 - mac * fz * (T(1) - z4) / T(kFpp0) + (e1 - e0) * fz * z4;
+    const T deps_drs = de0 - dmac * fz * (T(1) - z4) / T(kFpp0) + (de1 - de0) * fz * z4;
+    const T deps_dz = -mac * (dfz * (T(1) - z4) - T(4) * z3 * fz) / T(kFpp0) + (e1 - e0) * (dfz * z4 + T(4) * z3 * fz);
+    const T deps_drho = deps_drs * (-rs / (T(3) * rho));
+    const T phi = T(0.5) * (co * co + cm * cm);
+    const T dphi = T(1.0 / 3.0) * (T(1) / co - T(1) / cm);
+    const T phi2 = phi * phi, phi3 = phi2 * phi;
+    const T Em1 = m_expm1(-eps / (T(kGamma) * phi3));
+    const T E = Em1 + T(1);
+    const T A = T(kBeta / kGamma) / Em1;
+    const T dA_deps = A * A * E / (T(kBeta) * phi3);
+    const T dA_dphi = T(-3) * A * A * E * eps / (T(kBeta) * phi3 * phi);
+    const T du_dsig = T(kT2Scale) / (rho * rho * r13 * phi2);
+    const T u = sig * du_dsig;   // t^2
+    const T Au = A * u;
+    const T num = u + Au * u;
+    const T den = T(1) + Au + Au * Au;
+    const T inv_den2 = T(1) / (den * den);
+    const T Y = num / den;
+    const T dY_du = ((T(1) + T(2) * Au) * den - num * (A + T(2) * A * Au)) * inv_den2;
+    const T dY_dA = (u * u * den - num * (u + T(2) * Au * u)) * inv_den2;
+    const T Lg = m_log1p(T(kBeta / kGamma) * Y);
+    const T dL_dY = T(kBeta / kGamma) / (T(1) + T(kBeta / kGamma) * Y);
+    const T gp3 = T(kGamma) * phi3;
+    const T H = gp3 * Lg;
+    const T du_drho = T(-7.0 / 3.0) * u / rho;
+    const T du_dphi = T(-2) * u / phi;
+    const T dH_drho = gp3 * dL_dY * (dY_du * du_drho + dY_dA * dA_deps * deps_drho);
+    const T dH_dz = T(3) * T(kGamma) * phi2 * dphi * Lg +
+                    gp3 * dL_dY * (dY_du * du_dphi * dphi + dY_dA * (dA_deps * deps_dz + dA_dphi * dphi));
+    const T dH_dsig = gp3 * dL_dY * dY_du * du_dsig;
+    f = rho * (eps + H);
+    const T df_drho = eps + H + rho * (deps_drho + dH_drho);
+    const T df_dz = rho * (deps_dz + dH_dz);
+    va = df_drho + (T(1) - zeta) / rho * df_dz;
+    vb = df_drho - (T(1) + zeta) / rho * df_dz;
+    s_aa = s_bb = rho * dH_dsig;
+    s_ab = T(2) * rho * dH_dsig;
+}
+
+// one spin channel of a spin-scaled exchange
+template <typename T>
+__device__ __forceinline__ void exchange_channel(int fn, T r, T s, T &f, T &v, T &vs) {
+    T ff = T(0), vr = T(0), vsg = T(0);
+    if (T(2) * r >= T(kRhoMin)) {
+        if (fn == GBXC_SLATER) slater(T(2) * r, ff, vr, vsg);
+        else pbe_x(T(2) * r, T(4) * s, ff, vr, vsg);
+    }
+    f = T(0.5) * ff;
+    v = vr;
+    vs = T(2) * vsg;
+}
+
+template <typename T>
+__device__ __forceinline__ void evaluate_pol(int fn, T ra, T rb, T saa, T sab, T sbb, T &f, T &va, T &vb, T &s_aa,
+                                             T &s_ab, T &s_bb) {
+    T fa, fb, xa, xb, xsa, xsb;
+    exchange_channel(fn, ra, saa, fa, xa, xsa);
+    exchange_channel(fn, rb, sbb, fb, xb, xsb);
+    f = fa + fb;
+    va = xa;
+    vb = xb;
+    s_aa = xsa;
+    s_ab = T(0);
+    s_bb = xsb;
+    if (fn == GBXC_PBE) {
+        T fc, ca, cb, csa, csab, csb;
+        pbe_c_pol(ra, rb, saa, sab, sbb, fc, ca, cb, csa, csab, csb);
+        f += fc;
+        va += ca;
+        vb += cb;
+        s_aa += csa;
+        s_ab += csab;
+        s_bb += csb;
+    }
+}
+
 }  // namespace xc
 }  // namespace gbxc
