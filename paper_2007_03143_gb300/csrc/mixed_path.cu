@@ -162,6 +162,24 @@ __global__ void __launch_bounds__(32 * PS_ROWS) pslice_kernel(ChunkArgs a, Mixed
 }
 
 // ---------------------------------------------------------------- collocation
+// x^a y^b z^c from the power tables (index >= 1; the zeroth powers are never read); `one`
+// tells that all exponents are 0, i.e. the value is exactly 1 and need not multiply anything.
+__device__ __forceinline__ df pow3(const df *xp, const df *yp, const df *zp, int a, int b, int c, bool &one) {
+    one = (a == 0 && b == 0 && c == 0);
+    df r{1.f, 0.f};
+    bool have = false;
+    if (a > 0) {
+        r = xp[a];
+        have = true;
+    }
+    if (b > 0) {
+        r = have ? df_mul(r, yp[b]) : yp[b];
+        have = true;
+    }
+    if (c > 0) r = have ? df_mul(r, zp[c]) : zp[c];
+    return r;
+}
+
 // The (L+1)(L+2)/2 Cartesian functions of one shell at one point (Eq. gau_cart) and their
 // gradients, from X, Y, Z = r - A and the radial sums g = sum_k d_k e_k and
 // h = sum_k (-2 alpha_k d_k) e_k (e_k = exp(-alpha_k r^2)):
@@ -185,16 +203,32 @@ __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const
 #pragma unroll
         for (int mm = L - l; mm >= 0; --mm) {
             const int nn = L - l - mm;
-            const df ym_zn = df_mul(yp[mm], zp[nn]);
-            const df mono = df_mul(xp[l], ym_zn);
+            // after unrolling every exponent is a constant: factors equal to 1 are skipped
+            bool one;
+            const df mono = pow3(xp, yp, zp, l, mm, nn, one);
             df v[4];
-            v[0] = df_mul(mono, g);
-            v[1] = df_mul(mono, Xh);
-            v[2] = df_mul(mono, Yh);
-            v[3] = df_mul(mono, Zh);
-            if (l > 0) v[1] = df_add(v[1], df_mul(dfl::mul_f(df_mul(xp[l - 1], ym_zn), (float)l), g));
-            if (mm > 0) v[2] = df_add(v[2], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm - 1]), zp[nn]), (float)mm), g));
-            if (nn > 0) v[3] = df_add(v[3], df_mul(dfl::mul_f(df_mul(df_mul(xp[l], yp[mm]), zp[nn - 1]), (float)nn), g));
+            v[0] = one ? g : df_mul(mono, g);
+            v[1] = one ? Xh : df_mul(mono, Xh);
+            v[2] = one ? Yh : df_mul(mono, Yh);
+            v[3] = one ? Zh : df_mul(mono, Zh);
+            if (l > 0) {
+                const df b = pow3(xp, yp, zp, l - 1, mm, nn, one);
+                df t = one ? g : df_mul(b, g);
+                if (l > 1) t = dfl::mul_f(t, (float)l);
+                v[1] = df_add(v[1], t);
+            }
+            if (mm > 0) {
+                const df b = pow3(xp, yp, zp, l, mm - 1, nn, one);
+                df t = one ? g : df_mul(b, g);
+                if (mm > 1) t = dfl::mul_f(t, (float)mm);
+                v[2] = df_add(v[2], t);
+            }
+            if (nn > 0) {
+                const df b = pow3(xp, yp, zp, l, mm, nn - 1, one);
+                df t = one ? g : df_mul(b, g);
+                if (nn > 1) t = dfl::mul_f(t, (float)nn);
+                v[3] = df_add(v[3], t);
+            }
             const size_t of = o + (size_t)f * TILE;
             sl.phi[of] = live ? make_float2(v[0].h, v[0].l) : make_float2(0.f, 0.f);
 #pragma unroll
