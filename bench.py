@@ -50,6 +50,22 @@ def _rank_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def _max_over_ranks(x, world, device=None):
+    """The maximum of x over the ranks: a replica job's time is that of its slowest rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, world, steps, seconds):
+    """Whole-job throughput of `world` replicas that each process units_per_rank per step."""
+    return world * units_per_rank * steps / seconds
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -479,11 +495,7 @@ def main():
         G.gbxc_profile_enable(ctx.h, False)
         ms = [a.elapsed_time(b) for a, b in ev]
         total = sum(ms)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = _max_over_ranks(total, world, dev)
         return dict(E=E, N=N, V=V_dev.cpu().numpy(), ms=ms, total_ms=total, prof=prof, clocks=clocks)
 
     forms = [f for f in args.forms.split(",") if f]
@@ -508,7 +520,7 @@ def main():
         valid = list(ok)
     head = min(valid, key=lambda f: ok[f]["total_ms"])
     R = ok[head]
-    value = world * npts * args.steps / (R["total_ms"] / 1e3)
+    value = _job_rate(npts, world, args.steps, R["total_ms"] / 1e3)
     ms_sorted = sorted(R["ms"])
     p50 = statistics.median(ms_sorted)
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
@@ -539,12 +551,8 @@ def main():
         G.gbxc_integrate(ctx.h, mid, P_host, w.functional, head, V_host)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * npts * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = _max_over_ranks(e2e_s, world, dev)
+    e2e = {"value": _job_rate(npts, world, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": nbf * nbf * 8, "d2h_bytes_per_step": nbf * nbf * 8 + 16}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
