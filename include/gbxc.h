@@ -70,20 +70,33 @@ extern "C" {
 
 typedef struct gbxc_ctx gbxc_ctx;
 
+#define GBXC_ANGULAR_PRODUCT 0  /* Gauss-Legendre in cos(theta) x trapezoid in phi */
+#define GBXC_ANGULAR_LEBEDEV 1  /* Lebedev-Laikov rule (Sec. 2.2) */
+
 /* Atomic quadrature and batching parameters (Sec. 2.2).
  *   nrad      Mura-Knowles radial points per atom
- *   ntheta    Gauss-Legendre nodes in cos(theta)
- *   nphi      trapezoid nodes in phi (angular grid = ntheta * nphi points)
+ *   ntheta    product rule: Gauss-Legendre nodes in cos(theta);
+ *             Lebedev rule: its number of points, one of 6 14 26 38 50 86 110 146 170
+ *             194 302 590 (degrees 3 ... 41; the paper's FG grid uses 302, UFG 590)
+ *   nphi      product rule: trapezoid nodes in phi (angular grid = ntheta * nphi points);
+ *             ignored for a Lebedev rule
  *   partition GBXC_BECKE or GBXC_SSF
  *   max_batch batch threshold of the cuboid subdivision (the paper uses 512)
  *   eta       screening tolerance of Eq. rcut (the paper uses 1e-10)
- *   mk_alpha  Mura-Knowles radial scale (same for every element)        */
+ *   mk_alpha  Mura-Knowles radial scale (same for every element)
+ *   angular   GBXC_ANGULAR_PRODUCT (0, the default of a zeroed struct) or
+ *             GBXC_ANGULAR_LEBEDEV.  A Lebedev rule's points are its octahedral orbits
+ *             expanded in a fixed order: orbits a1 (1,0,0), a2 (s,s,0), a3 (t,t,t),
+ *             b (l,l,m), c (p,q,0), d (r,s,u), each kind by ascending generator; within
+ *             an orbit the coordinate permutations in lexicographic order, for each the
+ *             sign patterns +++, ++-, +-+, ..., ---, first occurrences only.          */
 typedef struct {
     int nrad, ntheta, nphi;
     int partition;
     int max_batch;
     double eta;
     double mk_alpha;
+    int angular;
 } gbxc_grid_spec;
 
 /* Sizes of a loaded molecule's plan. */
@@ -198,7 +211,9 @@ int gbxc_integrate(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
  * V^s = dE_xc/dP^s through Z^s = 1/2 w v_s Phi + w (2 s_ss grad rho_s + s_ab grad rho_s') .
  * grad Phi.  With P^a = P^b = P/2 the result equals gbxc_integrate's with P (V^a = V^b = V).
  *   Pa, Pb      nbf x nbf spin density matrices (host or device, symmetric)
- *   precision   GBXC_FP64 (the tensor-core form is not built for this variant: GBXC_EINVAL)
+ *   precision   GBXC_FP64, or GBXC_MIXED: the tensor-core form (both X contractions and both
+ *               V contractions on the sliced bf16 operands; the densities and the
+ *               spin-polarised functional in float64 from double-float sums)
  *   Exc, Nel    E_xc and the total electron count (may be NULL)
  *   Va, Vb      nbf x nbf outputs, host or device (may be NULL)
  *   stream      as gbxc_integrate */

@@ -31,7 +31,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import collocation, functionals, partition, planner, quadrature
+from . import collocation, functionals, lebedev, partition, planner, quadrature
 
 CHUNK = 8192
 
@@ -57,7 +57,11 @@ class Result:
 
 def make_grid(xyz, spec, weights: bool = True) -> Grid:
     """Total quadrature Q with partitioned weights w_i = p_A(r_i) w^q_i (Eq. num_int)."""
-    x, y, z, wq, par = quadrature.molecular_grid(xyz, spec.nrad, spec.ntheta, spec.nphi, spec.mk_alpha)
+    angular = None
+    if getattr(spec, "angular", "product") == "lebedev":
+        angular = lebedev.angular_rule(spec.ntheta)
+    x, y, z, wq, par = quadrature.molecular_grid(xyz, spec.nrad, spec.ntheta, spec.nphi, spec.mk_alpha,
+                                                 angular)
     w = None
     if weights:
         w = np.empty_like(wq)

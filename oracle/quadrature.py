@@ -95,15 +95,16 @@ def angular_product(ntheta: int, nphi: int):
             np.ascontiguousarray(w).reshape(-1))
 
 
-def atom_grid(center, nrad: int, ntheta: int, nphi: int, mk_alpha: float):
-    """Quadrature points of one atom, ordered radial-major then theta then phi.
+def atom_grid(center, nrad: int, ntheta: int, nphi: int, mk_alpha: float, angular=None):
+    """Quadrature points of one atom, ordered radial-major then angular point.
 
     Coordinate = R + r_k * u (product first, then the sum); weight =
-    w_rad_k * w_ang (the unmodified weights w^q of Eq. num_int).
-    Returns x, y, z, wq as float64 arrays of length nrad*ntheta*nphi.
+    w_rad_k * w_ang (the unmodified weights w^q of Eq. num_int).  The angular rule is the
+    product rule (theta-major) unless `angular` = (ux, uy, uz, wa) gives another one.
+    Returns x, y, z, wq as float64 arrays of length nrad * (angular points).
     """
     r, wr = mura_knowles(nrad, mk_alpha)
-    ux, uy, uz, wa = angular_product(ntheta, nphi)
+    ux, uy, uz, wa = angular if angular is not None else angular_product(ntheta, nphi)
     x = center[0] + r[:, None] * ux[None, :]
     y = center[1] + r[:, None] * uy[None, :]
     z = center[2] + r[:, None] * uz[None, :]
@@ -111,14 +112,14 @@ def atom_grid(center, nrad: int, ntheta: int, nphi: int, mk_alpha: float):
     return x.reshape(-1), y.reshape(-1), z.reshape(-1), wq.reshape(-1)
 
 
-def molecular_grid(xyz, nrad: int, ntheta: int, nphi: int, mk_alpha: float):
+def molecular_grid(xyz, nrad: int, ntheta: int, nphi: int, mk_alpha: float, angular=None):
     """Union of the atomic grids (the total quadrature Q), atom-major.
 
     Returns x, y, z, wq (float64) and the parent atom index (int32) per point.
     """
     xs, ys, zs, ws, par = [], [], [], [], []
     for A in range(len(xyz)):
-        x, y, z, wq = atom_grid(xyz[A], nrad, ntheta, nphi, mk_alpha)
+        x, y, z, wq = atom_grid(xyz[A], nrad, ntheta, nphi, mk_alpha, angular)
         xs.append(x)
         ys.append(y)
         zs.append(z)

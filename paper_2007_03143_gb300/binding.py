@@ -23,12 +23,14 @@ GBXC_OK, GBXC_EINVAL, GBXC_ENOMEM, GBXC_ECUDA, GBXC_ETIMEOUT, GBXC_ENOTREADY, GB
 GBXC_BECKE, GBXC_SSF = 0, 1
 GBXC_SLATER, GBXC_PBE = 0, 1
 GBXC_FP64, GBXC_MIXED = 0, 1
+GBXC_ANGULAR_PRODUCT, GBXC_ANGULAR_LEBEDEV = 0, 1
 GBXC_MAX_PRIM = 8
 GBXC_MAX_L = 3
 
 FUNCTIONALS = {"slater": GBXC_SLATER, "pbe": GBXC_PBE}
 PARTITIONS = {"becke": GBXC_BECKE, "ssf": GBXC_SSF}
 PRECISIONS = {"fp64": GBXC_FP64, "mixed": GBXC_MIXED}
+ANGULAR = {"product": GBXC_ANGULAR_PRODUCT, "lebedev": GBXC_ANGULAR_LEBEDEV}
 
 EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis", "gbxc_load_grid",
             "gbxc_plan_info_get", "gbxc_export_plan", "gbxc_integrate", "gbxc_integrate_batches",
@@ -52,7 +54,7 @@ class GbxcError(RuntimeError):
 
 class GridSpec(ctypes.Structure):
     _fields_ = [("nrad", c_int), ("ntheta", c_int), ("nphi", c_int), ("partition", c_int),
-                ("max_batch", c_int), ("eta", c_double), ("mk_alpha", c_double)]
+                ("max_batch", c_int), ("eta", c_double), ("mk_alpha", c_double), ("angular", c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -191,16 +193,24 @@ def gbxc_load_basis(ctx, xyz, Z, shell_atom, shell_L, shell_nprim, alpha, coeff,
     return mol.value, nbf.value
 
 
-def gbxc_load_grid(ctx, mol, nrad, ntheta, nphi, partition, max_batch, eta=1e-10, mk_alpha=5.0):
-    spec = GridSpec(nrad, ntheta, nphi, PARTITIONS.get(partition, partition), max_batch, eta, mk_alpha)
+def _grid_spec(nrad, ntheta, nphi, partition, max_batch, eta, mk_alpha, angular):
+    return GridSpec(nrad, ntheta, nphi, PARTITIONS.get(partition, partition), max_batch, eta, mk_alpha,
+                    ANGULAR.get(angular, angular))
+
+
+def gbxc_load_grid(ctx, mol, nrad, ntheta, nphi, partition, max_batch, eta=1e-10, mk_alpha=5.0,
+                   angular="product"):
+    """angular: "product" (ntheta x nphi) or "lebedev" (the rule of ntheta points)."""
+    spec = _grid_spec(nrad, ntheta, nphi, partition, max_batch, eta, mk_alpha, angular)
     npts, nb = c_longlong(), c_int()
     _check(ctx, lib().gbxc_load_grid(ctx, mol, ctypes.byref(spec), ctypes.byref(npts), ctypes.byref(nb)))
     return npts.value, nb.value
 
 
-def gbxc_load_grid_device(ctx, mol, nrad, ntheta, nphi, partition, max_batch, eta=1e-10, mk_alpha=5.0):
+def gbxc_load_grid_device(ctx, mol, nrad, ntheta, nphi, partition, max_batch, eta=1e-10, mk_alpha=5.0,
+                          angular="product"):
     """gbxc_load_grid with the planner's kernels on the device (identical plan)."""
-    spec = GridSpec(nrad, ntheta, nphi, PARTITIONS.get(partition, partition), max_batch, eta, mk_alpha)
+    spec = _grid_spec(nrad, ntheta, nphi, partition, max_batch, eta, mk_alpha, angular)
     npts, nb = c_longlong(), c_int()
     _check(ctx, lib().gbxc_load_grid_device(ctx, mol, ctypes.byref(spec), ctypes.byref(npts), ctypes.byref(nb)))
     return npts.value, nb.value
@@ -382,5 +392,5 @@ class Context:
                                    basis.alpha, basis.coeff, getattr(basis, "pure", None))
         load = gbxc_load_grid_device if device_planner else gbxc_load_grid
         load(self.h, mid, grid.nrad, grid.ntheta, grid.nphi, grid.partition, grid.max_batch, grid.eta,
-             grid.mk_alpha)
+             grid.mk_alpha, getattr(grid, "angular", "product"))
         return mid

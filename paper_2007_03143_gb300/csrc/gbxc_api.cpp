@@ -991,7 +991,13 @@ int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {
         REQUIRE(spec, "spec is NULL");
-        REQUIRE(spec->nrad > 0 && spec->ntheta > 0 && spec->nphi > 0, "grid sizes must be positive");
+        REQUIRE(spec->angular == GBXC_ANGULAR_PRODUCT || spec->angular == GBXC_ANGULAR_LEBEDEV,
+                "unknown angular rule");
+        if (spec->angular == GBXC_ANGULAR_LEBEDEV)
+            REQUIRE(spec->nrad > 0 && lebedev_supported(spec->ntheta),
+                    "no Lebedev rule of that many points (6 14 26 38 50 86 110 146 170 194 302 590)");
+        else
+            REQUIRE(spec->nrad > 0 && spec->ntheta > 0 && spec->nphi > 0, "grid sizes must be positive");
         REQUIRE(spec->partition == GBXC_BECKE || spec->partition == GBXC_SSF, "unknown partition");
         REQUIRE(spec->max_batch > 0, "max_batch must be positive");
         REQUIRE(spec->eta > 0 && spec->eta < 1 && spec->mk_alpha > 0, "bad eta or mk_alpha");
@@ -1180,13 +1186,14 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
         if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
         REQUIRE(Pa && Pb, "P is NULL");
         REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "unknown functional");
-        REQUIRE(precision == GBXC_FP64, "the spin-unrestricted form is built for GBXC_FP64");
+        REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
         const int nb = m.plan.nbatch();
         cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
         const size_t nn = (size_t)m.nbf * m.nbf;
         Workspace &w = ctx->ws;
-        const Schedule &S = get_schedule(m, GBXC_FP64, 0, nb, scratch_budget(ctx));
-        reserve(w, m, S, GBXC_FP64);
+        const Schedule &S = get_schedule(m, precision, 0, nb, scratch_budget(ctx));
+        reserve(w, m, S, precision);
+        if (precision == GBXC_MIXED) check(mixed_reserve_uks(w.mixed, S.max_rows, m.nbf), "mixed spin buffers");
         if (nn > w.mat2_cap || !w.d_P2) {
             size_t c0 = w.mat2_cap, c1 = w.mat2_cap, c2 = w.mat2_cap;
             grow_buf(w.d_P2, c0, nn, "P_b");
@@ -1207,7 +1214,9 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
         double *dVb = (Vb && is_device_ptr(Vb)) ? Vb : w.d_V2;
         check(cudaMemsetAsync(w.d_Vacc, 0, nn * 8, s), "zero V_a");
         check(cudaMemsetAsync(w.d_Vacc2, 0, nn * 8, s), "zero V_b");
-        for (const auto &c : S.chunks) {
+        if (precision == GBXC_MIXED) check(mixed_begin_uks(w.mixed, dPa, dPb, m.nbf, s), "mixed begin");
+        for (size_t ci = 0; ci < S.chunks.size(); ++ci) {
+            const auto &c = S.chunks[ci];
             ChunkArgs a;
             a.plan = m.dev;
             a.shells = m.d_shells;
@@ -1226,7 +1235,11 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
             a.vtasks = S.d_tasks ? S.d_tasks + 5 * c.task0 : nullptr;
             a.nvtasks = (int)c.ntask;
             a.prof = &ctx->prof;
-            check(launch_fp64_chunk_uks(a, dPb, w.d_Vacc2, s), "unrestricted chunk");
+            if (precision == GBXC_FP64)
+                check(launch_fp64_chunk_uks(a, dPb, w.d_Vacc2, s), "unrestricted chunk");
+            else
+                check(launch_mixed_chunk_uks(a, w.mixed, m.mixed_res, S.mixed, (int)ci, w.d_Vacc2, s),
+                      "unrestricted mixed chunk");
         }
         FinishArgs f;
         f.Vacc = w.d_Vacc;
@@ -1248,6 +1261,12 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
         if (Va && dVa != Va) check(cudaMemcpyAsync(Va, dVa, nn * 8, cudaMemcpyDeviceToHost, s), "copy V_a");
         if (Vb && dVb != Vb) check(cudaMemcpyAsync(Vb, dVb, nn * 8, cudaMemcpyDeviceToHost, s), "copy V_b");
         check(cudaStreamSynchronize(s), "integrate unrestricted");
+        if (precision == GBXC_MIXED) {
+            int werr = 0;
+            check(mixed_read_error(w.mixed, &werr, s), "mixed status");
+            if (werr) return fail(ctx, GBXC_ETIMEOUT, "a bounded tensor-core pipeline wait expired (code " +
+                                                          std::to_string(werr) + ")");
+        }
         if (Exc) *Exc = tot[0];
         if (Nel) *Nel = tot[1];
         return GBXC_OK;

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <map>
 #include <numeric>
+#include <stdexcept>
 
 #include "internal.h"
 
@@ -162,9 +163,67 @@ double shell_cutoff(const double *alpha, int nprim, double eta) {
     return rc;
 }
 
+namespace {
+struct LebedevOrbit {
+    int kind;       // 0 a1, 1 a2, 2 a3, 3 b, 4 c, 5 d
+    double g[3];    // generator
+    double w;       // weight of each point (the rule sums to 4 pi)
+};
+struct LebedevRuleIndex {
+    int n, degree, first, count;
+};
+#include "lebedev_rules.inc"
+
+const LebedevRuleIndex *find_lebedev(int n) {
+    for (const LebedevRuleIndex &r : kLebedevRules)
+        if (r.n == n) return &r;
+    return nullptr;
+}
+
+// The octahedral orbits of a Lebedev-Laikov rule expanded to points: for each orbit, the
+// permutations of the generator's coordinates in lexicographic order and for each the sign
+// patterns +++, ++-, ..., --- (a set bit negates; the first coordinate is the high bit),
+// keeping the first occurrence of every point (a zero never takes a sign).
+void lebedev_points(const LebedevRuleIndex &rule, GridTables &T) {
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    T.ux.clear();
+    T.uy.clear();
+    T.uz.clear();
+    T.wa.clear();
+    for (int o = rule.first; o < rule.first + rule.count; ++o) {
+        const LebedevOrbit &orb = kLebedevOrbits[o];
+        size_t begin = T.ux.size();
+        for (const auto &pm : perms)
+            for (int sg = 0; sg < 8; ++sg) {
+                double v[3];
+                for (int k = 0; k < 3; ++k) {
+                    double c = orb.g[pm[k]];
+                    v[k] = ((sg >> (2 - k)) & 1) && c != 0.0 ? -c : c;
+                }
+                bool seen = false;
+                for (size_t q = begin; q < T.ux.size() && !seen; ++q)
+                    seen = T.ux[q] == v[0] && T.uy[q] == v[1] && T.uz[q] == v[2];
+                if (seen) continue;
+                T.ux.push_back(v[0]);
+                T.uy.push_back(v[1]);
+                T.uz.push_back(v[2]);
+                T.wa.push_back(orb.w);
+            }
+    }
+}
+}  // namespace
+
+bool lebedev_supported(int n) { return find_lebedev(n) != nullptr; }
+
 void grid_tables(const gbxc_grid_spec &spec, GridTables &T) {
     std::vector<double> t, wt;
     mura_knowles(spec.nrad, spec.mk_alpha, T.r, T.wr);
+    if (spec.angular == GBXC_ANGULAR_LEBEDEV) {
+        const LebedevRuleIndex *rule = find_lebedev(spec.ntheta);
+        if (!rule) throw std::invalid_argument("no Lebedev rule of that many points");
+        lebedev_points(*rule, T);
+        return;
+    }
     gauss_legendre(spec.ntheta, t, wt);
     int nt = spec.ntheta, np = spec.nphi;
     T.ux.assign((size_t)nt * np, 0.0);

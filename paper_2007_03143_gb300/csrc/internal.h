@@ -74,6 +74,8 @@ struct GridTables {
     std::vector<double> r, wr, ux, uy, uz, wa;
 };
 void grid_tables(const gbxc_grid_spec &spec, GridTables &T);
+// True when a Lebedev-Laikov rule of n points is tabulated (lebedev_rules.inc).
+bool lebedev_supported(int n);
 void build_molecular_grid(const std::vector<double> &xyz, const gbxc_grid_spec &spec,
                           std::vector<double> &x, std::vector<double> &y, std::vector<double> &z,
                           std::vector<double> &wq, std::vector<int> &parent);

@@ -23,6 +23,13 @@ struct MixedCtx {
     size_t pexp_cap = 0;
     float *pdf = nullptr;              // P as double-float planes (hi, lo)
     size_t pdf_cap = 0;
+    // spin-unrestricted form: P_b's planes, the second X/Z slab and its Z exponents
+    float *pdf2 = nullptr;
+    size_t pdf2_cap = 0;
+    float2 *x2 = nullptr;
+    size_t x2_cap = 0;
+    int *zexp2 = nullptr;
+    size_t zexp2_cap = 0;
     int num_sms = 0;                   // persistent-GEMM grid size
     int *d_err = nullptr;
 };
@@ -81,6 +88,13 @@ size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf);
 cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st);
 cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
                                const MixedSchedule &s, int chunk_index, cudaStream_t st);
+// Spin-unrestricted form: buffers for chunks of up to max_rows slab rows, the per-call
+// preparation of P_a and P_b, and one chunk (a.Vacc receives W^j of spin a, Vacc_b spin b's).
+cudaError_t mixed_reserve_uks(MixedCtx &c, int64_t max_rows, int nbf);
+size_t mixed_reserve_uks_bytes(int64_t max_rows, int nbf);
+cudaError_t mixed_begin_uks(MixedCtx &c, const double *Pa, const double *Pb, int nbf, cudaStream_t st);
+cudaError_t launch_mixed_chunk_uks(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
+                                   const MixedSchedule &s, int chunk_index, double *Vacc_b, cudaStream_t st);
 // Device error word of the mixed kernels (nonzero after a bounded wait expired).
 cudaError_t mixed_read_error(MixedCtx &c, int *err, cudaStream_t st);
 

@@ -867,6 +867,135 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     }
 }
 
+// ---------------------------------------------------------------- spin-unrestricted rho, functional, Z
+// The same two passes for the two spin densities (X_a in the slab, X_b in x2): rho_s and
+// grad rho_s in double-float, the spin-polarised functional in float64, then
+// Z^s = 1/2 w v_s Phi + w (2 s_ss grad rho_s + s_ab grad rho_s') . grad Phi over X_s, with the
+// per-tile maxima of |Z^a| (zexp), |Z^b| (zexp2) and |Phi| (fexp) for the V-side slicing.
+__global__ void __launch_bounds__(TILE) rho_z_mixed_uks(ChunkArgs a, MixedArgs m, float2 *__restrict__ x2,
+                                                         int *__restrict__ zexp2) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int np = pad32(n);
+    int64_t r0 = a.plan.tile_row[t] - a.row0;
+    const size_t plane = (size_t)m.rows * TILE;
+    const float2 *phi = m.s.phi;
+    if (np > MAX_NP) {
+        if (i == 0) atomicOr(m.err, 8);
+        return;
+    }
+    df rho[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    df g[2][3] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
+#pragma unroll 2
+    for (int mu = 0; mu < n; ++mu) {
+        size_t o = (size_t)(r0 + mu) * TILE + i;
+        const float2 xa = m.s.x[o], xb = x2[o], f0 = phi[o];
+        const df gr[3] = {{m.s.ghi[o], m.s.glo[o]},
+                          {m.s.ghi[plane + o], m.s.glo[plane + o]},
+                          {m.s.ghi[2 * plane + o], m.s.glo[2 * plane + o]}};
+        const df xs[2] = {{xa.x, xa.y}, {xb.x, xb.y}};
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            rho[sp] = df_add(rho[sp], df_mul({f0.x, f0.y}, xs[sp]));
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g[sp][d] = df_add(g[sp][d], df_mul(gr[d], xs[sp]));
+        }
+    }
+    double r[2], gd[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+        r[sp] = df_to_d(rho[sp]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gd[sp][d] = 2.0 * df_to_d(g[sp][d]);
+    }
+    double e = 0.0, nn = 0.0, ca[2] = {0.0, 0.0}, cb[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    if (i < cnt) {
+        const double w = a.plan.w[a.plan.tile_first[t] + i];
+        const double saa = gd[0][0] * gd[0][0] + gd[0][1] * gd[0][1] + gd[0][2] * gd[0][2];
+        const double sab = gd[0][0] * gd[1][0] + gd[0][1] * gd[1][1] + gd[0][2] * gd[1][2];
+        const double sbb = gd[1][0] * gd[1][0] + gd[1][1] * gd[1][1] + gd[1][2] * gd[1][2];
+        double f, va, vb, s_aa, s_ab, s_bb;
+        xc::evaluate_pol<double>(a.functional, r[0], r[1], saa, sab, sbb, f, va, vb, s_aa, s_ab, s_bb);
+        e = w * f;
+        nn = w * (r[0] + r[1]);
+        ca[0] = 0.5 * w * va;
+        ca[1] = 0.5 * w * vb;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cb[0][d] = w * (2.0 * s_aa * gd[0][d] + s_ab * gd[1][d]);
+            cb[1][d] = w * (2.0 * s_bb * gd[1][d] + s_ab * gd[0][d]);
+        }
+    }
+    __shared__ int zmax[2][MAX_NP], fmx[MAX_NP];
+    for (int mu = i; mu < np; mu += TILE) {
+        zmax[0][mu] = 0;
+        zmax[1][mu] = 0;
+        fmx[mu] = 0;
+    }
+    __syncthreads();
+    df cz[2], cg[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+        cz[sp] = d_to_df(ca[sp]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cg[sp][d] = d_to_df(cb[sp][d]);
+    }
+    int lane = i & 31;
+    float2 *zout[2] = {m.s.x, x2};
+#pragma unroll 2
+    for (int mu = 0; mu < n; ++mu) {
+        size_t o = (size_t)(r0 + mu) * TILE + i;
+        const float2 f0 = phi[o];
+        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
+        float az[2];
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            df z = df_mul(cz[sp], {f0.x, f0.y});
+            z = df_add(z, dfl::mul_f(cg[sp][0], h1));
+            z = df_add(z, dfl::mul_f(cg[sp][1], h2));
+            z = df_add(z, dfl::mul_f(cg[sp][2], h3));
+            zout[sp][o] = make_float2(z.h, z.l);
+            az[sp] = fabsf(z.h);
+        }
+        float ap = fabsf(f0.x);
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) {
+            az[0] = fmaxf(az[0], __shfl_xor_sync(0xffffffffu, az[0], q));
+            az[1] = fmaxf(az[1], __shfl_xor_sync(0xffffffffu, az[1], q));
+            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
+        }
+        if (lane == 0) {
+            atomicMax(&zmax[0][mu], __float_as_int(az[0]));
+            atomicMax(&zmax[1][mu], __float_as_int(az[1]));
+            atomicMax(&fmx[mu], __float_as_int(ap));
+        }
+    }
+    __syncthreads();
+    for (int mu = i; mu < n; mu += TILE) {
+        m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[0][mu]));
+        zexp2[r0 + mu] = exp_of(__int_as_float(zmax[1][mu]));
+        m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu]));
+    }
+    __shared__ double re[TILE], rn[TILE];
+    re[i] = e;
+    rn[i] = nn;
+    __syncthreads();
+    for (int st = TILE / 2; st > 0; st >>= 1) {
+        if (i < st) {
+            re[i] += re[i + st];
+            rn[i] += rn[i + st];
+        }
+        __syncthreads();
+    }
+    if (i == 0) {
+        a.tileE[t] = re[0];
+        a.tileN[t] = rn[0];
+    }
+}
+
 // ---------------------------------------------------------------- V-side slicing
 // Thread per point.  The K group of the tile (the V task it belongs to) shares one
 // exponent per function for Z and one for Phi: the maximum of the per-tile exponents.
@@ -1088,6 +1217,9 @@ cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResid
 
 void free_mixed_ctx(MixedCtx &c) {
     cudaFree(c.pdf);
+    cudaFree(c.pdf2);
+    cudaFree(c.x2);
+    cudaFree(c.zexp2);
     cudaFree(c.pslices);
     cudaFree(c.pexp);
     cudaFree(c.d_err);
@@ -1147,6 +1279,28 @@ cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st) 
     return cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
 }
 
+cudaError_t mixed_reserve_uks(MixedCtx &c, int64_t max_rows, int nbf) {
+    const size_t rows = (size_t)std::max<int64_t>(max_rows, 1);
+    cudaError_t e = grow(c.x2, c.x2_cap, rows * TILE);
+    if (e != cudaSuccess) return e;
+    e = grow(c.zexp2, c.zexp2_cap, rows);
+    if (e != cudaSuccess) return e;
+    return grow(c.pdf2, c.pdf2_cap, (size_t)std::max<int64_t>(2 * (int64_t)nbf * nbf, 1));
+}
+
+size_t mixed_reserve_uks_bytes(int64_t max_rows, int nbf) {
+    const size_t rows = (size_t)std::max<int64_t>(max_rows, 1);
+    return rows * TILE * 8 + rows * 4 + (size_t)2 * nbf * nbf * 4;
+}
+
+cudaError_t mixed_begin_uks(MixedCtx &c, const double *Pa, const double *Pb, int nbf, cudaStream_t st) {
+    cudaError_t e = mixed_begin(c, Pa, nbf, st);
+    if (e != cudaSuccess) return e;
+    int64_t nn = (int64_t)nbf * nbf;
+    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Pb, c.pdf2, c.pdf2 + nn, nn);
+    return cudaGetLastError();
+}
+
 cudaError_t mixed_read_error(MixedCtx &c, int *err, cudaStream_t st) {
     *err = 0;
     if (!c.d_err) return cudaSuccess;
@@ -1155,12 +1309,9 @@ cudaError_t mixed_read_error(MixedCtx &c, int *err, cudaStream_t st) {
     return cudaStreamSynchronize(st);
 }
 
-cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r, const MixedSchedule &s,
-                               int chunk_index, cudaStream_t st) {
-    if (!r.d_shells) return cudaErrorInvalidValue;
-    int64_t nt = a.t1 - a.t0;
-    if (nt <= 0) return cudaSuccess;
-    const MixedSchedule::Chunk &ch = s.chunks[chunk_index];
+namespace {
+MixedArgs chunk_mixed_args(const ChunkArgs &a, MixedCtx &c, const MixedSchedule &s,
+                           const MixedSchedule::Chunk &ch, const float *pdf) {
     MixedArgs m;
     m.s = mixed_slabs(a.scratch, a.rows);
     m.rows = a.rows;
@@ -1170,20 +1321,37 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     m.pslices = reinterpret_cast<__nv_bfloat16 *>(c.pslices);
     m.pplane = std::max<int64_t>(s.max_prows, 1);
     m.pexp = c.pexp;
-    m.ph = c.pdf;
-    m.pl = c.pdf + (size_t)a.nbf * a.nbf;
+    m.ph = pdf;
+    m.pl = pdf + (size_t)a.nbf * a.nbf;
     m.err = c.d_err;
-    cudaError_t err = cudaSuccess;
-    CUtensorMap tax = make_map(c, m.s.ax, 4 * a.rows, 4 * a.rows, NSL, BM, err);
-    CUtensorMap tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, s.bn, err);
-    CUtensorMap tz = make_map(c, m.s.vz, 4 * a.rows, 4 * a.rows, NSL, BM, err);
-    CUtensorMap tph = make_map(c, m.s.vphi, 4 * a.rows, 4 * a.rows, NSL, s.bn, err);
-    if (err != cudaSuccess) return err;
+    return m;
+}
+
+struct ChunkMaps {
+    CUtensorMap tax, tp, tz, tph;
+};
+
+ChunkMaps chunk_maps(MixedCtx &c, const MixedArgs &m, const MixedSchedule &s, const MixedSchedule::Chunk &ch,
+                     cudaError_t &err) {
+    ChunkMaps q;
+    q.tax = make_map(c, m.s.ax, 4 * m.rows, 4 * m.rows, NSL, BM, err);
+    q.tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, s.bn, err);
+    q.tz = make_map(c, m.s.vz, 4 * m.rows, 4 * m.rows, NSL, BM, err);
+    q.tph = make_map(c, m.s.vphi, 4 * m.rows, 4 * m.rows, NSL, s.bn, err);
+    return q;
+}
+
+void run_pslice(const ChunkArgs &a, const MixedArgs &m, const MixedSchedule &s, const MixedSchedule::Chunk &ch,
+                cudaStream_t st) {
     Profiler &P = *a.prof;
     P.begin(GBXC_K_PGATHER, st);
     if (ch.nptask > 0)
         pslice_kernel<<<(unsigned)ch.nptask, 32 * PS_ROWS, 0, st>>>(a, m, s.d_ptasks + 2 * ch.ptask0);
     P.end(GBXC_K_PGATHER, st);
+}
+
+void run_colloc(const ChunkArgs &a, const MixedArgs &m, const MixedResident &r, int64_t nt, cudaStream_t st) {
+    Profiler &P = *a.prof;
     P.begin(GBXC_K_COLLOC, st);
     static const Exp2Table e2t = [] {
         Exp2Table x;
@@ -1195,33 +1363,94 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     else
         colloc_mixed<false><<<(unsigned)nt, TILE, 0, st>>>(a, m, r.d_shells, e2t);
     P.end(GBXC_K_COLLOC, st);
+}
+
+void run_xgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c, const MixedSchedule &s,
+               const MixedSchedule::Chunk &ch, cudaStream_t st) {
     const int *xtasks = s.d_xtasks + 2 * ch.xtask0;
     int nx = (int)ch.nxtask;
-    if (nx > 0) {
-        P.begin(GBXC_K_XGEMM, st);
-        const unsigned g = (unsigned)std::min(nx, c.num_sms);
-        if (s.bn == 64)
-            gemm_persistent<0, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(tax, tp, a, m, xtasks, nx);
-        else
-            gemm_persistent<0, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(tax, tp, a, m, xtasks, nx);
-        P.end(GBXC_K_XGEMM, st);
-    }
-    P.begin(GBXC_K_RHO_Z, st);
-    rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
-    P.end(GBXC_K_RHO_Z, st);
+    if (nx <= 0) return;
+    Profiler &P = *a.prof;
+    P.begin(GBXC_K_XGEMM, st);
+    const unsigned g = (unsigned)std::min(nx, c.num_sms);
+    if (s.bn == 64)
+        gemm_persistent<0, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tax, q.tp, a, m, xtasks, nx);
+    else
+        gemm_persistent<0, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(q.tax, q.tp, a, m, xtasks, nx);
+    P.end(GBXC_K_XGEMM, st);
+}
+
+void run_slice_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c,
+                     const MixedSchedule &s, int64_t nt, cudaStream_t st) {
+    Profiler &P = *a.prof;
     P.begin(GBXC_K_SLICE, st);
     slice_v<<<(unsigned)nt, TILE, 0, st>>>(a, m);
     P.end(GBXC_K_SLICE, st);
-    if (a.nvtasks > 0) {
-        P.begin(GBXC_K_VGEMM, st);
-        const unsigned g = (unsigned)std::min(a.nvtasks, c.num_sms);
-        if (s.bn == 64)
-            gemm_persistent<1, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(tz, tph, a, m, a.vtasks, a.nvtasks);
-        else
-            gemm_persistent<1, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(tz, tph, a, m, a.vtasks,
-                                                                                   a.nvtasks);
-        P.end(GBXC_K_VGEMM, st);
-    }
+    if (a.nvtasks <= 0) return;
+    P.begin(GBXC_K_VGEMM, st);
+    const unsigned g = (unsigned)std::min(a.nvtasks, c.num_sms);
+    if (s.bn == 64)
+        gemm_persistent<1, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tz, q.tph, a, m, a.vtasks, a.nvtasks);
+    else
+        gemm_persistent<1, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(q.tz, q.tph, a, m, a.vtasks,
+                                                                               a.nvtasks);
+    P.end(GBXC_K_VGEMM, st);
+}
+}  // namespace
+
+cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r, const MixedSchedule &s,
+                               int chunk_index, cudaStream_t st) {
+    if (!r.d_shells) return cudaErrorInvalidValue;
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    const MixedSchedule::Chunk &ch = s.chunks[chunk_index];
+    MixedArgs m = chunk_mixed_args(a, c, s, ch, c.pdf);
+    cudaError_t err = cudaSuccess;
+    const ChunkMaps q = chunk_maps(c, m, s, ch, err);
+    if (err != cudaSuccess) return err;
+    run_pslice(a, m, s, ch, st);
+    run_colloc(a, m, r, nt, st);
+    run_xgemm(a, m, q, c, s, ch, st);
+    Profiler &P = *a.prof;
+    P.begin(GBXC_K_RHO_Z, st);
+    rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    P.end(GBXC_K_RHO_Z, st);
+    run_slice_vgemm(a, m, q, c, s, nt, st);
+    return cudaGetLastError();
+}
+
+// Spin-unrestricted chunk: one collocation; P_a's slices and X_a (into the slab), then P_b's
+// slices and X_b (into x2), both densities and the spin-polarised functional in one kernel
+// (Z_a over X_a, Z_b over X_b), then slicing and W^j per spin, spin b with x2 and zexp2 in
+// place of the slab's X/Z plane and exponents.  The Phi slices of the second slicing are
+// the same values as the first's.
+cudaError_t launch_mixed_chunk_uks(const ChunkArgs &a, MixedCtx &c, MixedResident &r, const MixedSchedule &s,
+                                   int chunk_index, double *Vacc_b, cudaStream_t st) {
+    if (!r.d_shells || !c.x2 || !c.zexp2 || !c.pdf2) return cudaErrorInvalidValue;
+    if ((size_t)a.rows > c.zexp2_cap || (size_t)a.rows * TILE > c.x2_cap) return cudaErrorInvalidValue;
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    const MixedSchedule::Chunk &ch = s.chunks[chunk_index];
+    MixedArgs ma = chunk_mixed_args(a, c, s, ch, c.pdf);
+    MixedArgs mb = chunk_mixed_args(a, c, s, ch, c.pdf2);
+    mb.s.x = c.x2;
+    mb.s.zexp = c.zexp2;
+    cudaError_t err = cudaSuccess;
+    const ChunkMaps q = chunk_maps(c, ma, s, ch, err);
+    if (err != cudaSuccess) return err;
+    run_pslice(a, ma, s, ch, st);
+    run_colloc(a, ma, r, nt, st);
+    run_xgemm(a, ma, q, c, s, ch, st);
+    run_pslice(a, mb, s, ch, st);
+    run_xgemm(a, mb, q, c, s, ch, st);
+    Profiler &P = *a.prof;
+    P.begin(GBXC_K_RHO_Z, st);
+    rho_z_mixed_uks<<<(unsigned)nt, TILE, 0, st>>>(a, ma, c.x2, c.zexp2);
+    P.end(GBXC_K_RHO_Z, st);
+    run_slice_vgemm(a, ma, q, c, s, nt, st);
+    ChunkArgs ab = a;
+    ab.Vacc = Vacc_b;
+    run_slice_vgemm(ab, mb, q, c, s, nt, st);
     return cudaGetLastError();
 }
 

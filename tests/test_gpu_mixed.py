@@ -12,7 +12,8 @@ from gpu_common import Loaded
 
 pytestmark = pytest.mark.gpu
 
-SMALL = ["water1_slater", "water1_pbe_small", "water2_pbe_small", "water3_pbe_small", "water2_pbe_small_sph"]
+SMALL = ["water1_slater", "water1_pbe_small", "water2_pbe_small", "water3_pbe_small", "water2_pbe_small_sph",
+         "water2_pbe_small_leb"]
 
 
 @pytest.fixture(scope="module", params=SMALL)

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 TOL_E = 1e-9
 TOL_V = 1e-9
 
-SMALL = ["water1_slater", "water1_pbe_small", "water2_pbe_small", "water3_pbe_small", "water2_pbe_small_sph"]
+SMALL = ["water1_slater", "water1_pbe_small", "water2_pbe_small", "water3_pbe_small", "water2_pbe_small_sph",
+         "water2_pbe_small_leb"]
 
 
 @pytest.fixture(scope="module", params=SMALL)

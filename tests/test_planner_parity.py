@@ -21,7 +21,8 @@ def _lib_plan(w):
         mid, nbf = G.gbxc_load_basis(ctx, w.mol.xyz, w.mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff, b.pure)
         assert nbf == b.nbf
         g = w.grid
-        G.gbxc_load_grid(ctx, mid, g.nrad, g.ntheta, g.nphi, g.partition, g.max_batch, g.eta, g.mk_alpha)
+        G.gbxc_load_grid(ctx, mid, g.nrad, g.ntheta, g.nphi, g.partition, g.max_batch, g.eta, g.mk_alpha,
+                         g.angular)
         info = G.gbxc_plan_info_get(ctx, mid)
         n, nb = info["npts"], info["nbatch"]
         out = dict(x=np.empty(n), y=np.empty(n), z=np.empty(n), wq=np.empty(n),
@@ -39,7 +40,8 @@ def _lib_plan(w):
 
 
 @pytest.mark.parametrize("name", ["water1_slater", "water2_pbe_small", "water3_pbe_small",
-                                  "water1_pbe_small", "water16_pbe", "water2_pbe_small_sph"])
+                                  "water1_pbe_small", "water16_pbe", "water2_pbe_small_sph",
+                                  "water2_pbe_small_leb", "water16_pbe_fg"])
 def test_plan_bit_exact(name):
     w = X.make_workload(name)
     info, L = _lib_plan(w)

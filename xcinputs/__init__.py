@@ -342,6 +342,7 @@ class GridSpec:
     max_batch: int
     eta: float = 1e-10
     mk_alpha: float = 5.0
+    angular: str = "product"  # "product": ntheta x nphi; "lebedev": the rule of ntheta points
 
 
 @dataclass
@@ -369,11 +370,17 @@ WORKLOADS = {
     # spherical d shells (O 3s2p1d: 14 functions; 24 per water)
     "water2_pbe_small_sph": dict(n_waters=2, grid=GridSpec(20, 8, 16, "ssf", 128), functional="pbe", pure=True),
     "water16_pbe_sph": dict(n_waters=16, grid=GridSpec(75, 16, 32, "ssf", 512), functional="pbe", pure=True),
+    # Lebedev-Laikov angular rules: a small case, and the paper's FG grid (75 x 302)
+    "water2_pbe_small_leb": dict(n_waters=2, grid=GridSpec(20, 110, 0, "ssf", 128, angular="lebedev"),
+                                 functional="pbe"),
+    "water16_pbe_fg": dict(n_waters=16, grid=GridSpec(75, 302, 0, "ssf", 512, angular="lebedev"),
+                           functional="pbe"),
 }
 
 _WORKLOAD_SEEDS = {"water1_slater": 1000, "water16_pbe": 2000, "water64_pbe": 3000,
                    "water2_pbe_small": 9100, "water3_pbe_small": 9200, "water1_pbe_small": 9300,
-                   "water2_pbe_small_sph": 9100, "water16_pbe_sph": 2000}
+                   "water2_pbe_small_sph": 9100, "water16_pbe_sph": 2000,
+                   "water2_pbe_small_leb": 9100, "water16_pbe_fg": 2000}
 
 
 def make_workload(name: str, n_waters: int | None = None, seed: int | None = None) -> Workload:
