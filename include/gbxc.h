@@ -173,6 +173,13 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
 int gbxc_load_grid_device(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
                           int *nbatch_out);
 
+/* Release everything the library holds for `mol` (basis, grid, partition weights, plan,
+ * schedules and cached graphs that include it); the id is not reused.  The boundary's
+ * counterpart of load_basis/load_grid (the resident per-molecule state of Sec. 2.3's
+ * device memory management).  GBXC_ENOENT for an unknown id, GBXC_ENOTREADY while the
+ * request server has requests queued or in flight. */
+int gbxc_unload(gbxc_ctx *ctx, int mol);
+
 /* Sizes of the plan of `mol` (after gbxc_load_grid). */
 int gbxc_plan_info_get(gbxc_ctx *ctx, int mol, gbxc_plan_info *info);
 

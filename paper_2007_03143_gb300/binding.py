@@ -37,7 +37,7 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
             "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule", "gbxc_load_grid_device",
-            "gbxc_load_basis_pure", "gbxc_integrate_uks"]
+            "gbxc_load_basis_pure", "gbxc_integrate_uks", "gbxc_unload"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -92,6 +92,8 @@ def lib():
     L.gbxc_load_grid.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
     L.gbxc_load_grid_device.argtypes = [c_void_p, c_int, POINTER(GridSpec), POINTER(c_longlong), POINTER(c_int)]
     L.gbxc_load_grid_device.restype = c_int
+    L.gbxc_unload.argtypes = [c_void_p, c_int]
+    L.gbxc_unload.restype = c_int
     L.gbxc_plan_info_get.argtypes = [c_void_p, c_int, POINTER(PlanInfo)]
     L.gbxc_export_plan.argtypes = [c_void_p, c_int] + [c_void_p] * 10
     L.gbxc_integrate.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, pd, c_void_p, pd, c_void_p]
@@ -214,6 +216,10 @@ def gbxc_load_grid_device(ctx, mol, nrad, ntheta, nphi, partition, max_batch, et
     npts, nb = c_longlong(), c_int()
     _check(ctx, lib().gbxc_load_grid_device(ctx, mol, ctypes.byref(spec), ctypes.byref(npts), ctypes.byref(nb)))
     return npts.value, nb.value
+
+
+def gbxc_unload(ctx, mol):
+    _check(ctx, lib().gbxc_unload(ctx, mol))
 
 
 def gbxc_plan_info_get(ctx, mol) -> dict:

@@ -287,6 +287,18 @@ void free_grid(Molecule &m) {
     m.has_grid = false;
 }
 
+// Every device allocation a loaded molecule holds (basis, grid, plan, schedules, buffers).
+void free_molecule(Molecule &m) {
+    free_grid(m);
+    cudaFree(m.d_shells);
+    free_mixed_resident(m.mixed_res);
+    cudaFree(m.d_atoms);
+    cudaFree(m.d_rnn);
+    cudaFree(m.many_P);
+    cudaFree(m.many_V);
+    cudaFree(m.many_tot);
+}
+
 void free_workspace(Workspace &w) {
     if (w.owns) {
         cudaFree(w.scratch);
@@ -869,22 +881,37 @@ void gbxc_destroy(gbxc_ctx *ctx) {
     for (auto e : ctx->many.join) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
-    for (auto &kv : ctx->mols) {
-        Molecule &m = *kv.second;
-        free_grid(m);
-        cudaFree(m.d_shells);
-        free_mixed_resident(m.mixed_res);
-        cudaFree(m.d_atoms);
-        cudaFree(m.d_rnn);
-        cudaFree(m.many_P);
-        cudaFree(m.many_V);
-        cudaFree(m.many_tot);
-    }
+    for (auto &kv : ctx->mols) free_molecule(*kv.second);
     ctx->mols.clear();
     free_workspace(ctx->ws);
     ctx->prof.release();
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+}
+
+int gbxc_unload(gbxc_ctx *ctx, int mol) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        auto it = ctx->mols.find(mol);
+        if (it == ctx->mols.end()) return fail(ctx, GBXC_ENOENT, "unknown molecule id");
+        if (server_busy(ctx)) return fail(ctx, GBXC_ENOTREADY, "requests are in flight; wait for them first");
+        if (ctx->device >= 0) {
+            check(cudaStreamSynchronize(ctx->stream), "sync");
+            if (ctx->many.exec &&
+                std::find(ctx->many.mols.begin(), ctx->many.mols.end(), mol) != ctx->many.mols.end()) {
+                cudaGraphExecDestroy(ctx->many.exec);   // the cached graph reads this molecule's buffers
+                ctx->many.exec = nullptr;
+                ctx->many.mols.clear();
+            }
+            for (auto t = ctx->tuned.begin(); t != ctx->tuned.end();) {
+                const std::vector<int> &ids = t->first.first;
+                t = std::find(ids.begin(), ids.end(), mol) != ids.end() ? ctx->tuned.erase(t) : std::next(t);
+            }
+        }
+        free_molecule(*it->second);
+        ctx->mols.erase(it);
+        return GBXC_OK;
+    });
 }
 
 const char *gbxc_last_error(const gbxc_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }

@@ -93,3 +93,29 @@ def test_tiny_batches():
     assert abs(E - ref.E) <= 1e-9 and np.max(np.abs(V - ref.V)) <= 1e-9
     Em, Nm, Vm = out["mixed"]
     assert abs(Em - ref.E) <= 1e-7 and np.max(np.abs(Vm - ref.V)) <= 1e-6
+
+
+def test_unload_releases_a_molecule_and_its_cached_graph():
+    """After gbxc_unload the id is refused, the batching graph that held it is rebuilt for the
+    remaining molecules, and their results do not change."""
+    G = need_gpu()
+    ws = [X.make_workload("water1_pbe_small"), X.make_workload("water2_pbe_small")]
+    ctx = G.Context(0)
+    try:
+        ids = [ctx.load_molecule(w.mol, w.basis, w.grid) for w in ws]
+        V1 = np.zeros((ws[1].basis.nbf,) * 2)
+        E1, N1 = G.gbxc_integrate(ctx.h, ids[1], ws[1].P, "pbe", "mixed", V1)
+        E, N = G.gbxc_integrate_many(ctx.h, ids, [w.P for w in ws], ["pbe", "pbe"], "mixed")
+        G.gbxc_unload(ctx.h, ids[0])
+        with pytest.raises(G.GbxcError):
+            G.gbxc_integrate(ctx.h, ids[0], ws[0].P, "pbe", "mixed", None)
+        with pytest.raises(G.GbxcError):
+            G.gbxc_integrate_many(ctx.h, ids, [w.P for w in ws], ["pbe", "pbe"], "mixed")
+        E2, N2 = G.gbxc_integrate_many(ctx.h, ids[1:], [ws[1].P], ["pbe"], "mixed")
+        assert abs(E2[0] - E1) <= 1e-10 * abs(E1) and abs(E[1] - E1) <= 1e-10 * abs(E1)
+        V2 = np.zeros_like(V1)
+        E3, _ = G.gbxc_integrate(ctx.h, ids[1], ws[1].P, "pbe", "mixed", V2)
+        # E is summed in a fixed order; V through float64 atomics (order-dependent rounding)
+        assert E3 == E1 and np.max(np.abs(V2 - V1)) <= 1e-12 * np.max(np.abs(V1))
+    finally:
+        ctx.close()
