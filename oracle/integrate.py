@@ -207,3 +207,55 @@ def integrate_method_uks(grid: Grid, basis, Pa, Pb, functional: str, plan: plann
             Va[np.ix_(F, F)] += Vaj
             Vb[np.ix_(F, F)] += Vbj
     return ResultUKS(float(np.sum(Eb)), float(np.sum(Nb)), Va, Vb, Eb, Nb)
+
+
+# ---------------------------------------------------------------- meta-GGA
+def integrate_batch_mgga(pts, w, phi_args, Pj, fn, return_tau=False):
+    """One batch with a meta-GGA f(rho, sigma, tau): X as in Eq. x_mat, and per gradient
+    component k the contraction Y^k = (d_k Phi) P^j, so that
+    tau_i = 1/2 sum_k sum_mu d_k Phi_i,mu Y^k_i,mu; V^j gains the term
+    sum_k (1/4 w vtau d_k Phi)^T d_k Phi + its transpose."""
+    phi, gx, gy, gz = phi_args
+    X = phi @ Pj
+    rho = np.sum(phi * X, axis=1)
+    grad = [2.0 * np.sum(g * X, axis=1) for g in (gx, gy, gz)]
+    sigma = grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]
+    tau = 0.5 * sum(np.sum(g * (g @ Pj), axis=1) for g in (gx, gy, gz))
+    f, vr, vs, vt = fn(rho, sigma, tau)
+    a = 0.5 * w * vr
+    b = 2.0 * w * vs
+    Z = a[:, None] * phi + b[:, None] * (grad[0][:, None] * gx + grad[1][:, None] * gy
+                                         + grad[2][:, None] * gz)
+    c = 0.25 * w * vt
+    W = Z.T @ phi + sum((c[:, None] * g).T @ g for g in (gx, gy, gz))
+    Vj = W + W.T
+    out = (float(np.sum(w * f)), float(np.sum(w * rho)), Vj)
+    return out + ((rho, sigma, tau),) if return_tau else out
+
+
+def integrate_method_mgga(grid: Grid, basis, P, functional: str, plan: planner.Plan,
+                          batches=None) -> Result:
+    """Meta-GGA method-equivalent mode over the merged batches of ``plan``."""
+    from . import functionals_mgga
+    fn = functionals_mgga.FUNCTIONALS_MGGA[functional]
+    nbf = basis.nbf
+    V = np.zeros((nbf, nbf))
+    nb = len(plan.batch_points)
+    sel = range(nb) if batches is None else batches
+    Eb = np.zeros(nb)
+    Nb = np.zeros(nb)
+    for j in sel:
+        idx = plan.batch_points[j]
+        F = plan.batch_funcs[j]
+        if len(F) == 0:
+            continue
+        Pj = P[np.ix_(F, F)]
+        for s in range(0, len(idx), CHUNK):
+            ii = idx[s:s + CHUNK]
+            pts = np.stack([grid.x[ii], grid.y[ii], grid.z[ii]], axis=1)
+            cols = collocation.collocate(pts, basis, plan.batch_shells[j])
+            e, n, Vj = integrate_batch_mgga(pts, grid.w[ii], cols, Pj, fn)
+            Eb[j] += e
+            Nb[j] += n
+            V[np.ix_(F, F)] += Vj
+    return Result(float(np.sum(Eb)), float(np.sum(Nb)), V, Eb, Nb)
