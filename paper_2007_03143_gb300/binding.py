@@ -21,13 +21,13 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 GBXC_OK, GBXC_EINVAL, GBXC_ENOMEM, GBXC_ECUDA, GBXC_ETIMEOUT, GBXC_ENOTREADY, GBXC_ENOENT = \
     0, -1, -2, -3, -4, -5, -6
 GBXC_BECKE, GBXC_SSF = 0, 1
-GBXC_SLATER, GBXC_PBE = 0, 1
+GBXC_SLATER, GBXC_PBE, GBXC_MVS_X = 0, 1, 2
 GBXC_FP64, GBXC_MIXED = 0, 1
 GBXC_ANGULAR_PRODUCT, GBXC_ANGULAR_LEBEDEV = 0, 1
 GBXC_MAX_PRIM = 8
 GBXC_MAX_L = 3
 
-FUNCTIONALS = {"slater": GBXC_SLATER, "pbe": GBXC_PBE}
+FUNCTIONALS = {"slater": GBXC_SLATER, "pbe": GBXC_PBE, "mvs_x": GBXC_MVS_X}
 PARTITIONS = {"becke": GBXC_BECKE, "ssf": GBXC_SSF}
 PRECISIONS = {"fp64": GBXC_FP64, "mixed": GBXC_MIXED}
 ANGULAR = {"product": GBXC_ANGULAR_PRODUCT, "lebedev": GBXC_ANGULAR_LEBEDEV}

@@ -24,7 +24,10 @@
 namespace gbxc {
 namespace {
 
-constexpr int NCOMP = 6;  // Phi, Phi_x, Phi_y, Phi_z, X, Z
+// planes: Phi, Phi_x, Phi_y, Phi_z, then X / Z (4), a second X / Z (5: the other spin, or Z
+// of the spin-restricted form), and for the meta-GGA Y^k = (d_k Phi) P^j, later
+// W^k = 1/4 w vtau d_k Phi, in planes 5, 6, 7
+constexpr int NCOMP = 8;
 
 struct Slabs {
     double *c[NCOMP];
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(TILE) colloc_f64(ChunkArgs a) {
 constexpr int XB_R = 64, XB_K = 16;
 
 // X = P^j Phi^j from density P into slab plane `out` (4, or 5 for the second spin).
-__global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a, const double *__restrict__ P, int out) {
+__global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a, const double *__restrict__ P, int in, int out) {
     int64_t t = a.t0 + blockIdx.x;
     int rb = blockIdx.y;
     int j = a.plan.tile_batch[t];
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a, const double *__re
     const int *F = a.plan.func_idx + f0;
     Slabs S = slabs_of(a);
     int64_t row0 = a.plan.tile_row[t] - a.row0;
-    const double *Phi = S.c[0] + (size_t)row0 * TILE;
+    const double *Phi = S.c[in] + (size_t)row0 * TILE;
     double *Xo = S.c[out] + (size_t)row0 * TILE;
 
     __shared__ double As[XB_K][XB_R + 1];
@@ -336,15 +339,87 @@ __global__ void __launch_bounds__(TILE) rho_xc_z_uks_f64(ChunkArgs a) {
 }
 
 // --------------------------------------------------------------------------
+// k45, meta-GGA (the extension of Sec. 2.1): rho and grad rho from X (plane 4), the kinetic
+// energy density tau = 1/2 sum_k sum_mu d_k Phi Y^k from Y^k = (d_k Phi) P^j (planes 5-7),
+// the meta-GGA functional, then Z over X (plane 4) and W^k = 1/4 w vtau d_k Phi over Y^k,
+// so that V^j = Z^T Phi + sum_k W^k^T d_k Phi plus the transpose.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE) rho_xc_z_mgga_f64(ChunkArgs a) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int64_t row0 = a.plan.tile_row[t] - a.row0;
+    Slabs S = slabs_of(a);
+    size_t base = (size_t)row0 * TILE + i;
+    double rho = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, tau = 0.0;
+    for (int r = 0; r < n; ++r) {
+        size_t o = base + (size_t)r * TILE;
+        const double xv = S.c[4][o], p1 = S.c[1][o], p2 = S.c[2][o], p3 = S.c[3][o];
+        rho = fma(S.c[0][o], xv, rho);
+        gx = fma(p1, xv, gx);
+        gy = fma(p2, xv, gy);
+        gz = fma(p3, xv, gz);
+        tau = fma(p1, S.c[5][o], tau);
+        tau = fma(p2, S.c[6][o], tau);
+        tau = fma(p3, S.c[7][o], tau);
+    }
+    gx *= 2.0;
+    gy *= 2.0;
+    gz *= 2.0;
+    tau *= 0.5;
+    double e = 0.0, nn = 0.0, ca = 0.0, bx = 0.0, by = 0.0, bz = 0.0, ct = 0.0;
+    if (i < cnt) {
+        const double w = a.plan.w[a.plan.tile_first[t] + i];
+        const double sigma = gx * gx + gy * gy + gz * gz;
+        double f, vr, vs, vt;
+        xc::mvs_x(rho, sigma, tau, f, vr, vs, vt);
+        e = w * f;
+        nn = w * rho;
+        ca = 0.5 * w * vr;
+        const double b = 2.0 * w * vs;
+        bx = b * gx;
+        by = b * gy;
+        bz = b * gz;
+        ct = 0.25 * w * vt;
+    }
+    for (int r = 0; r < n; ++r) {
+        size_t o = base + (size_t)r * TILE;
+        const double p1 = S.c[1][o], p2 = S.c[2][o], p3 = S.c[3][o];
+        S.c[4][o] = ca * S.c[0][o] + bx * p1 + by * p2 + bz * p3;
+        S.c[5][o] = ct * p1;
+        S.c[6][o] = ct * p2;
+        S.c[7][o] = ct * p3;
+    }
+    __shared__ double re[TILE], rn[TILE];
+    re[i] = e;
+    rn[i] = nn;
+    __syncthreads();
+    for (int st = TILE / 2; st > 0; st >>= 1) {
+        if (i < st) {
+            re[i] += re[i + st];
+            rn[i] += rn[i + st];
+        }
+        __syncthreads();
+    }
+    if (i == 0) {
+        a.tileE[t] = re[0];
+        a.tileN[t] = rn[0];
+    }
+}
+
+// --------------------------------------------------------------------------
 // k6: W^j[mu][nu] = sum_i Z[mu][i] Phi[nu][i] over tiles [t0, t1) of batch j,
 // 64 x 64 output block per CTA (256 threads, 4 x 4 each), then
 // V_acc[F_mu][F_nu] += W (float64 atomics).
 // --------------------------------------------------------------------------
 constexpr int VB = 64, VK = 16;
 
-// W = Z^T Phi from slab plane `zp` (5, or 4 for the first spin of the unrestricted form),
+// W = Z^T Phi from slab planes `zp` (5, or 4 for the first spin of the unrestricted form and
+// the meta-GGA's Z, 5-7 for its W^k) and `pp` (Phi, or d_k Phi for the meta-GGA terms),
 // scattered into Vacc.
-__global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a, int zp, double *__restrict__ Vacc) {
+__global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a, int zp, int pp, double *__restrict__ Vacc) {
     const int *task = a.vtasks + 5 * blockIdx.x;
     int j = task[0], mb = task[1], nb = task[2];
     int64_t tb = task[3], te = task[4];
@@ -365,7 +440,7 @@ __global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a, int zp, double *__
     for (int64_t t = tb; t < te; ++t) {
         int64_t row0 = a.plan.tile_row[t] - a.row0;
         const double *Zs = S.c[zp] + (size_t)row0 * TILE;
-        const double *Ps = S.c[0] + (size_t)row0 * TILE;
+        const double *Ps = S.c[pp] + (size_t)row0 * TILE;
         int cnt = a.plan.tile_count[t];
         for (int k0 = 0; k0 < cnt; k0 += VK) {
             for (int e = tid; e < VK * VB; e += 256) {
@@ -525,14 +600,14 @@ cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s) {
     P.end(GBXC_K_COLLOC, s);
     dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
     P.begin(GBXC_K_XGEMM, s);
-    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 4);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 0, 4);
     P.end(GBXC_K_XGEMM, s);
     P.begin(GBXC_K_RHO_Z, s);
     rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     P.end(GBXC_K_RHO_Z, s);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, s);
-        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 5, a.Vacc);
+        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 5, 0, a.Vacc);
         P.end(GBXC_K_VGEMM, s);
     }
     return cudaGetLastError();
@@ -547,17 +622,39 @@ cudaError_t launch_fp64_chunk_uks(const ChunkArgs &a, const double *Pb, double *
     P.end(GBXC_K_COLLOC, s);
     dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
     P.begin(GBXC_K_XGEMM, s);
-    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 4);
-    xgemm_f64<<<xg, 256, 0, s>>>(a, Pb, 5);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 0, 4);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, Pb, 0, 5);
     P.end(GBXC_K_XGEMM, s, 2);
     P.begin(GBXC_K_RHO_Z, s);
     rho_xc_z_uks_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     P.end(GBXC_K_RHO_Z, s);
     if (a.nvtasks > 0) {
         P.begin(GBXC_K_VGEMM, s);
-        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 4, a.Vacc);
-        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 5, Vacc_b);
+        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 4, 0, a.Vacc);
+        vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 5, 0, Vacc_b);
         P.end(GBXC_K_VGEMM, s, 2);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_chunk_mgga(const ChunkArgs &a, cudaStream_t s) {
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    Profiler &P = *a.prof;
+    P.begin(GBXC_K_COLLOC, s);
+    colloc_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    P.end(GBXC_K_COLLOC, s);
+    dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
+    P.begin(GBXC_K_XGEMM, s);
+    for (int k = 0; k < 4; ++k) xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, k, 4 + k);   // X, then Y^x, Y^y, Y^z
+    P.end(GBXC_K_XGEMM, s, 4);
+    P.begin(GBXC_K_RHO_Z, s);
+    rho_xc_z_mgga_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
+    P.end(GBXC_K_RHO_Z, s);
+    if (a.nvtasks > 0) {
+        P.begin(GBXC_K_VGEMM, s);
+        for (int k = 0; k < 4; ++k) vgemm_f64<<<(unsigned)a.nvtasks, 256, 0, s>>>(a, 4 + k, k, a.Vacc);
+        P.end(GBXC_K_VGEMM, s, 4);
     }
     return cudaGetLastError();
 }
@@ -585,7 +682,7 @@ cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s) {
     if (nt <= 0) return cudaSuccess;
     colloc_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     dim3 xg((unsigned)nt, (unsigned)((a.max_nfunc + XB_R - 1) / XB_R));
-    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 4);
+    xgemm_f64<<<xg, 256, 0, s>>>(a, a.P, 0, 4);
     rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     unsigned nblk = (unsigned)((a.max_nfunc + VB - 1) / VB);
     vgemm_f64_tile<<<dim3((unsigned)nt, nblk, nblk), 256, 0, s>>>(a);

@@ -542,7 +542,9 @@ void enqueue(Workspace &w, Molecule &m, const Schedule &S, const double *dP, int
         a.vtasks = S.d_tasks ? S.d_tasks + 5 * c.task0 : nullptr;
         a.nvtasks = (int)c.ntask;
         a.prof = prof;
-        if (precision == GBXC_FP64)
+        if (precision == GBXC_FP64 && functional == GBXC_MVS_X)
+            check(launch_fp64_chunk_mgga(a, s), "fp64 meta-GGA chunk");
+        else if (precision == GBXC_FP64)
             check(launch_fp64_chunk(a, s), "fp64 chunk");
         else
             check(launch_mixed_chunk(a, w.mixed, m.mixed_res, S.mixed, (int)ci, s), "mixed chunk");
@@ -575,8 +577,9 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     Molecule &m = get_mol(ctx, mol);
     if (!m.has_grid) throw ArgError{"molecule has no grid (call gbxc_load_grid first)"};
     REQUIRE(P, "P is NULL");
-    REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "unknown functional");
+    REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE || functional == GBXC_MVS_X, "unknown functional");
     REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
+    REQUIRE(functional != GBXC_MVS_X || precision == GBXC_FP64, "the meta-GGA is built for GBXC_FP64 only");
     int nb = m.plan.nbatch();
     REQUIRE(0 <= b0 && b0 <= b1 && b1 <= nb, "batch range out of bounds");
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
@@ -801,7 +804,7 @@ void server_stop(gbxc_ctx *ctx) {
 // kernel-facing helpers shared with the float64 path
 // ---------------------------------------------------------------------------
 namespace gbxc {
-size_t fp64_row_bytes() { return (size_t)6 * TILE * sizeof(double); }
+size_t fp64_row_bytes() { return (size_t)8 * TILE * sizeof(double); }
 
 void append_fp64_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &tasks) {
     const int VB = 64, KS = 16;

@@ -170,6 +170,9 @@ struct ChunkArgs {
 cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s);
 // Spin-unrestricted chunk: a.P / a.Vacc carry spin a, Pb / Vacc_b spin b.
 cudaError_t launch_fp64_chunk_uks(const ChunkArgs &a, const double *Pb, double *Vacc_b, cudaStream_t s);
+// Meta-GGA chunk (a.functional is a meta-GGA): X and the three Y^k = (d_k Phi) P^j, rho, tau,
+// the functional, Z and W^k, and four V contractions into a.Vacc.
+cudaError_t launch_fp64_chunk_mgga(const ChunkArgs &a, cudaStream_t s);
 
 struct FinishArgs {
     const double *Vacc;

@@ -259,5 +259,43 @@ __device__ __forceinline__ void evaluate_pol(int fn, T ra, T rb, T saa, T sab, T
     }
 }
 
+// ---- meta-GGA: MVS exchange (Sun, Perdew and Ruzsinszky 2015), spin-restricted, float64.
+//   f = C_x rho^(4/3) (1 + kappa0 f_a(alpha)) / (1 + b s^4)^(1/8),
+//   f_a = (1 - alpha) / ((1 + e1 alpha^2)^2 + c1 alpha^4)^(1/4),
+//   alpha = (tau - sigma/(8 rho)) / tau_unif, tau_unif = (3/10)(3 pi^2)^(2/3) rho^(5/3),
+//   kappa0 = 0.174, e1 = -1.6665, c1 = 0.7438, b = 0.0233;
+// returns f and its derivatives with respect to rho, sigma and tau (zero below kRhoMin).
+constexpr double kMvsKappa0 = 0.174, kMvsE1 = -1.6665, kMvsC1 = 0.7438, kMvsB = 0.0233;
+constexpr double kTauUnif = 2.871234000188191;        // (3/10)(3 pi^2)^(2/3)
+
+__device__ __forceinline__ void mvs_x(double rho, double sigma, double tau, double &f, double &vrho, double &vsigma,
+                                      double &vtau) {
+    f = vrho = vsigma = vtau = 0.0;
+    if (!(rho >= kRhoMin)) return;
+    const double r13 = cbrt(rho), r53 = rho * r13 * r13;
+    const double u = kS2Scale * sigma / (r53 * rho);                 // s^2
+    const double at = 1.0 / (kTauUnif * r53);                        // d alpha / d tau
+    const double al = (tau - sigma / (8.0 * rho)) * at;
+    const double q = 1.0 + kMvsE1 * al * al;
+    const double D = q * q + kMvsC1 * al * al * al * al;
+    const double D14 = sqrt(sqrt(D));                                 // D^(1/4)
+    const double fa = (1.0 - al) / D14;
+    const double dD = 4.0 * kMvsE1 * al * q + 4.0 * kMvsC1 * al * al * al;
+    const double dfa = -1.0 / D14 - 0.25 * (1.0 - al) * dD / (D * D14);
+    const double p = 1.0 + kMvsB * u * u;
+    const double g = 1.0 / sqrt(sqrt(sqrt(p)));                       // p^(-1/8)
+    const double dg = -0.25 * kMvsB * u * g / p;
+    const double F = (1.0 + kMvsKappa0 * fa) * g;
+    const double Fu = (1.0 + kMvsKappa0 * fa) * dg;
+    const double Fa = kMvsKappa0 * dfa * g;
+    const double ur = -(8.0 / 3.0) * u / rho, us = kS2Scale / (r53 * rho);
+    const double as = -at / (8.0 * rho), ar = sigma / (8.0 * rho * rho) * at - (5.0 / 3.0) * al / rho;
+    const double e0 = kCx * rho * r13;
+    f = e0 * F;
+    vrho = (4.0 / 3.0) * kCx * r13 * F + e0 * (Fu * ur + Fa * ar);
+    vsigma = e0 * (Fu * us + Fa * as);
+    vtau = e0 * Fa * at;
+}
+
 }  // namespace xc
 }  // namespace gbxc

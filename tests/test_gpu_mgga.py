@@ -1,0 +1,56 @@
+"""The meta-GGA (MVS exchange with the kinetic energy density tau; the meta-GGA extension of
+Sec. 2.1) through the C-ABI, float64 form, against the oracle: |dE| <= 1e-9 Eh, |dN| <= 1e-9,
+max |dV_ij| <= 1e-9 on small cases; sampled batches of the 16-water workload; and the calls
+that do not take it refuse it."""
+import numpy as np
+import pytest
+
+from oracle import integrate as I
+
+from gpu_common import Loaded
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", params=["water1_pbe_small", "water2_pbe_small", "water2_pbe_small_sph",
+                                        "water2_pbe_small_leb"])
+def loaded(request):
+    L = Loaded(request.param)
+    yield L
+    L.close()
+
+
+def test_mgga_matches_oracle(loaded):
+    g, pl = loaded.oracle()
+    ref = I.integrate_method_mgga(g, loaded.w.basis, loaded.w.P, "mvs_x", pl)
+    E, N, V = loaded.integrate("fp64", functional="mvs_x")
+    assert abs(E - ref.E) <= 1e-9 and abs(N - ref.N) <= 1e-9
+    assert np.max(np.abs(V - ref.V)) <= 1e-9
+    assert np.array_equal(V, V.T)
+
+
+def test_mgga_refused_where_not_built(loaded):
+    G, h, mid, P = loaded.G, loaded.ctx.h, loaded.mid, loaded.w.P
+    with pytest.raises(G.GbxcError):
+        G.gbxc_integrate(h, mid, P, "mvs_x", "mixed", None)
+    with pytest.raises(G.GbxcError):
+        G.gbxc_integrate_uks(h, mid, 0.5 * P, 0.5 * P, "mvs_x", "fp64")
+    with pytest.raises(G.GbxcError):
+        G.gbxc_integrate_many(h, [mid], [P], ["mvs_x"], "fp64")
+
+
+def test_mgga_full_size_sampled_batches():
+    L = Loaded("water16_pbe")
+    try:
+        g, pl = L.oracle()
+        nb = L.info["nbatch"]
+        rng = np.random.default_rng(5)
+        sel = sorted(set(rng.choice(nb, size=10, replace=False).tolist()) | {0, nb - 1})
+        ref = I.integrate_method_mgga(g, L.w.basis, L.w.P, "mvs_x", pl, batches=sel)
+        Eb, Nb = np.zeros(nb), np.zeros(nb)
+        E, N = L.G.gbxc_integrate_batches(L.ctx.h, L.mid, L.w.P, "mvs_x", "fp64", 0, nb, None, Eb, Nb)
+        assert np.max(np.abs(Eb[sel] - ref.E_batch[sel])) <= 1e-9
+        assert np.max(np.abs(Nb[sel] - ref.N_batch[sel])) <= 1e-9
+        assert abs(E - np.sum(Eb)) <= 1e-9 and abs(N - 160.0) < 1e-2
+    finally:
+        L.close()
