@@ -55,8 +55,10 @@ constexpr double kFp32RhoMin = 1e300;
 // ---------------------------------------------------------------- scratch layout
 struct MixedSlabs {
     float2 *phi;            // [rows][128]: Phi as (hi, lo) pairs
-    float *ghi, *glo;       // 3 planes each [rows][128]: hi and lo words of dPhi/dx, /dy, /dz
-                            // (the Z pass reads the hi words alone)
+    float *ghi;             // 3 planes [rows][128]: hi words of dPhi/dx, /dy, /dz
+    __nv_bfloat16 *glo;     // 3 planes [rows][128]: their lo words rounded to bf16 (hi + lo
+                            // then carries about 32 bits, enough for grad rho; the Z pass
+                            // reads the hi words alone)
     float2 *x;              // 1 plane [rows][128]: X (later Z) as (hi, lo)
     __nv_bfloat16 *ax;      // 5 planes [4 rows][32]: Phi slices, K-blocked per tile
     __nv_bfloat16 *vz;      // 5 planes [4 rows][32]: Z slices, point-blocked per tile
@@ -73,8 +75,8 @@ __host__ __device__ inline MixedSlabs mixed_slabs(void *base, int64_t rows) {
     p += (size_t)2 * rows * TILE * 4;
     s.ghi = reinterpret_cast<float *>(p);
     p += (size_t)3 * rows * TILE * 4;
-    s.glo = reinterpret_cast<float *>(p);
-    p += (size_t)3 * rows * TILE * 4;
+    s.glo = reinterpret_cast<__nv_bfloat16 *>(p);
+    p += (size_t)3 * rows * TILE * 2;
     s.x = reinterpret_cast<float2 *>(p);
     p += (size_t)2 * rows * TILE * 4;
     s.ax = reinterpret_cast<__nv_bfloat16 *>(p);
@@ -234,7 +236,7 @@ __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 sl.ghi[c * plane + of] = live ? v[c + 1].h : 0.f;
-                sl.glo[c * plane + of] = live ? v[c + 1].l : 0.f;
+                sl.glo[c * plane + of] = __float2bfloat16_rn(live ? v[c + 1].l : 0.f);
             }
             if (live) mx = fmaxf(mx, fabsf(v[0].h));
             ++f;
@@ -295,7 +297,7 @@ __device__ __forceinline__ void colloc_pure_shell(df X, df Y, df Z, df g, df h, 
                 if (live) mx = fmaxf(mx, fabsf(out[k].h));
             } else {
                 sl.ghi[(comp - 1) * plane + of] = live ? out[k].h : 0.f;
-                sl.glo[(comp - 1) * plane + of] = live ? out[k].l : 0.f;
+                sl.glo[(comp - 1) * plane + of] = __float2bfloat16_rn(live ? out[k].l : 0.f);
             }
         }
     }
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             m.s.ghi[c * plane + o] = 0.f;
-            m.s.glo[c * plane + o] = 0.f;
+            m.s.glo[c * plane + o] = __float2bfloat16_rn(0.f);
         }
     }
     int e = exp_of(mx);
@@ -777,7 +779,8 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
         const float2 xv = m.s.x[o], f0 = phi[o];
         const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
-        const float l1 = m.s.glo[o], l2 = m.s.glo[plane + o], l3 = m.s.glo[2 * plane + o];
+        const float l1 = __bfloat162float(m.s.glo[o]), l2 = __bfloat162float(m.s.glo[plane + o]),
+                    l3 = __bfloat162float(m.s.glo[2 * plane + o]);
         df x{xv.x, xv.y};
         rho = df_add(rho, df_mul({f0.x, f0.y}, x));
         gx = df_add(gx, df_mul({h1, l1}, x));
@@ -893,9 +896,9 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed_uks(ChunkArgs a, MixedArgs m
     for (int mu = 0; mu < n; ++mu) {
         size_t o = (size_t)(r0 + mu) * TILE + i;
         const float2 xa = m.s.x[o], xb = x2[o], f0 = phi[o];
-        const df gr[3] = {{m.s.ghi[o], m.s.glo[o]},
-                          {m.s.ghi[plane + o], m.s.glo[plane + o]},
-                          {m.s.ghi[2 * plane + o], m.s.glo[2 * plane + o]}};
+        const df gr[3] = {{m.s.ghi[o], __bfloat162float(m.s.glo[o])},
+                          {m.s.ghi[plane + o], __bfloat162float(m.s.glo[plane + o])},
+                          {m.s.ghi[2 * plane + o], __bfloat162float(m.s.glo[2 * plane + o])}};
         const df xs[2] = {{xa.x, xa.y}, {xb.x, xb.y}};
 #pragma unroll
         for (int sp = 0; sp < 2; ++sp) {
@@ -1088,7 +1091,7 @@ cudaError_t grow(T *&p, size_t &cap, size_t need) {
 
 }  // namespace
 
-size_t mixed_row_bytes() { return (size_t)TILE * (8 * 4 + 2 * 4 + 3 * NSL * 2) + 8 + 16; }
+size_t mixed_row_bytes() { return (size_t)TILE * (8 + 12 + 6 + 8 + 3 * NSL * 2) + 8 + 16; }
 
 bool mixed_tile_supported(int bn) { return bn == 128 || bn == 64; }
 
