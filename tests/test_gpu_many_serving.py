@@ -157,3 +157,24 @@ def test_serving_rejects_bad_requests(setup):
         assert np.isfinite(E)
     finally:
         G.gbxc_serve_stop(ctx.h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_many_heterogeneous_molecules(prec):
+    """Cartesian and spherical bases, product and Lebedev-Laikov grids in one graph launch:
+    each molecule's result equals its own gbxc_integrate."""
+    G = need_gpu()
+    ctx = G.Context(0)
+    try:
+        ws = [X.make_workload(n) for n in ("water2_pbe_small", "water2_pbe_small_sph", "water2_pbe_small_leb",
+                                           "water1_slater")]
+        ids = [ctx.load_molecule(w.mol, w.basis, w.grid) for w in ws]
+        fns = [w.functional for w in ws]
+        ref = [_alone(G, ctx, mid, w.basis.nbf, w.P, fn, prec) for mid, w, fn in zip(ids, ws, fns)]
+        Vs = [np.zeros((w.basis.nbf,) * 2) for w in ws]
+        E, N = G.gbxc_integrate_many(ctx.h, ids, [w.P for w in ws], fns, prec, Vs)
+        for k in range(len(ws)):
+            assert abs(E[k] - ref[k][0]) <= 1e-10 and abs(N[k] - ref[k][1]) <= 1e-10, k
+            assert np.max(np.abs(Vs[k] - ref[k][2])) <= 1e-9, k
+    finally:
+        ctx.close()

@@ -19,7 +19,7 @@ def _spins(w, na, nb, seed):
 
 
 @pytest.fixture(scope="module", params=["water1_slater", "water1_pbe_small", "water2_pbe_small",
-                                        "water2_pbe_small_sph"])
+                                        "water2_pbe_small_sph", "water2_pbe_small_leb"])
 def loaded(request):
     L = Loaded(request.param)
     yield L
