@@ -50,7 +50,7 @@ extern "C" {
 #define GBXC_MVS_X 2        /* MVS exchange, a meta-GGA in rho, sigma and the kinetic energy
                                density tau = 1/2 sum P grad phi . grad phi (the meta-GGA
                                extension of Sec. 2.1); gbxc_integrate and
-                               gbxc_integrate_batches in GBXC_FP64 only */
+                               gbxc_integrate_batches, both precisions */
 
 /* arithmetic of the integration */
 #define GBXC_FP64 0         /* every step in float64 */
@@ -206,7 +206,7 @@ int gbxc_export_plan(gbxc_ctx *ctx, int mol, double *x, double *y, double *z, do
  * batch of the plan; Eqs. x_mat, eval_local_den, eval_local_den_grad,
  * eval_xc_batch, exc_batch, z_mat, vxc_batch, vxc_inc).
  *   P          nbf x nbf symmetric density matrix, host or device; read as given
- *   functional GBXC_SLATER, GBXC_PBE, or GBXC_MVS_X (meta-GGA; GBXC_FP64 only)
+ *   functional GBXC_SLATER, GBXC_PBE, or GBXC_MVS_X (meta-GGA)
  *   precision  GBXC_FP64 or GBXC_MIXED
  *   Exc, Nel   host scalars (may be NULL)
  *   Vxc        nbf x nbf output, host or device (may be NULL); exactly symmetric

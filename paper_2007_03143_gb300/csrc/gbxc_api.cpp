@@ -546,6 +546,8 @@ void enqueue(Workspace &w, Molecule &m, const Schedule &S, const double *dP, int
             check(launch_fp64_chunk_mgga(a, s), "fp64 meta-GGA chunk");
         else if (precision == GBXC_FP64)
             check(launch_fp64_chunk(a, s), "fp64 chunk");
+        else if (functional == GBXC_MVS_X)
+            check(launch_mixed_chunk_mgga(a, w.mixed, m.mixed_res, S.mixed, (int)ci, s), "mixed meta-GGA chunk");
         else
             check(launch_mixed_chunk(a, w.mixed, m.mixed_res, S.mixed, (int)ci, s), "mixed chunk");
     }
@@ -579,7 +581,6 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     REQUIRE(P, "P is NULL");
     REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE || functional == GBXC_MVS_X, "unknown functional");
     REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
-    REQUIRE(functional != GBXC_MVS_X || precision == GBXC_FP64, "the meta-GGA is built for GBXC_FP64 only");
     int nb = m.plan.nbatch();
     REQUIRE(0 <= b0 && b0 <= b1 && b1 <= nb, "batch range out of bounds");
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
@@ -587,6 +588,8 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     Workspace &w = ctx->ws;
     const Schedule &S = get_schedule(m, precision, b0, b1, scratch_budget(ctx));
     reserve(w, m, S, precision);
+    if (precision == GBXC_MIXED && functional == GBXC_MVS_X)
+        check(mixed_reserve_mgga(w.mixed, S.max_rows), "mixed meta-GGA buffers");
     const double *dP = P;
     if (!is_device_ptr(P)) {
         check(cudaMemcpyAsync(w.d_P, P, nn * 8, cudaMemcpyHostToDevice, s), "copy P");

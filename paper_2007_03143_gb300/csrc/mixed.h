@@ -30,6 +30,14 @@ struct MixedCtx {
     size_t x2_cap = 0;
     int *zexp2 = nullptr;
     size_t zexp2_cap = 0;
+    // meta-GGA: slices of d_k Phi, the Y^k / W^k planes and their exponents, for chunks of
+    // up to mgga_rows slab rows
+    uint16_t *ax_g = nullptr;          // 3 x 5 planes x rows x 128 bf16
+    float2 *y_g = nullptr;             // 3 planes x rows x 128
+    int *pexp_g = nullptr;             // 3 x 4 rows point exponents
+    int *wexp_g = nullptr, *gexp_g = nullptr;   // 3 x rows each
+    size_t ax_g_cap = 0, y_g_cap = 0, pexp_g_cap = 0, wexp_g_cap = 0, gexp_g_cap = 0;
+    int64_t mgga_rows = 0;
     int num_sms = 0;                   // persistent-GEMM grid size
     int *d_err = nullptr;
 };
@@ -95,6 +103,12 @@ size_t mixed_reserve_uks_bytes(int64_t max_rows, int nbf);
 cudaError_t mixed_begin_uks(MixedCtx &c, const double *Pa, const double *Pb, int nbf, cudaStream_t st);
 cudaError_t launch_mixed_chunk_uks(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
                                    const MixedSchedule &s, int chunk_index, double *Vacc_b, cudaStream_t st);
+// Meta-GGA form (a.functional a meta-GGA): buffers for chunks of up to max_rows slab rows, and
+// one chunk: X and Y^k = (d_k Phi) P^j on tcgen05, rho, grad rho, tau, the functional, Z and
+// W^k, then the four V terms Z^T Phi + sum_k W^k^T d_k Phi into a.Vacc.
+cudaError_t mixed_reserve_mgga(MixedCtx &c, int64_t max_rows);
+cudaError_t launch_mixed_chunk_mgga(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
+                                    const MixedSchedule &s, int chunk_index, cudaStream_t st);
 // Device error word of the mixed kernels (nonzero after a bounded wait expired).
 cudaError_t mixed_read_error(MixedCtx &c, int *err, cudaStream_t st);
 

@@ -370,7 +370,6 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
     }
     for (; row < np; ++row) {
         size_t o = (size_t)(r0 + row) * TILE + i;
-#pragma unroll
         m.s.phi[o] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -999,13 +998,195 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed_uks(ChunkArgs a, MixedArgs m
     }
 }
 
+// ---------------------------------------------------------------- meta-GGA (tensor-core form)
+// The meta-GGA's kinetic energy density needs Y^k = (d_k Phi) P^j for k = x, y, z: the X
+// contraction again with d_k Phi as its A operand.  grad_slices cuts d_k Phi (hi words and
+// bf16 lo words) into the K-blocked Ozaki slices the collocation writes for Phi, with per
+// point exponents of max_mu |d_k Phi|: component k's slices at ax_g + k NSL plane, its
+// exponents at pexp_g + k 4 rows (the stride of the slab's own point exponents).
+__global__ void __launch_bounds__(TILE) grad_slices(ChunkArgs a, MixedArgs m, __nv_bfloat16 *__restrict__ ax_g,
+                                                    int *__restrict__ pexp_g) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int np = pad32(n);
+    int64_t r0 = a.plan.tile_row[t] - a.row0;
+    const size_t plane = (size_t)m.rows * TILE;
+    for (int k = 0; k < 3; ++k) {
+        const float *gh = m.s.ghi + (size_t)k * plane;
+        const __nv_bfloat16 *gl = m.s.glo + (size_t)k * plane;
+        float mx = 0.f;
+        for (int mu = 0; mu < n; ++mu) mx = fmaxf(mx, fabsf(gh[(size_t)(r0 + mu) * TILE + i]));
+        const int e = exp_of(mx);
+        pexp_g[(size_t)k * 4 * m.rows + (t - a.t0) * TILE + i] = e;
+        __nv_bfloat16 *ax = ax_g + (size_t)k * NSL * plane;
+        for (int kb = 0; kb < np / 32; ++kb) {
+            const size_t orow = (size_t)(4 * r0 + (int64_t)kb * TILE + i) * 32;
+#pragma unroll 1
+            for (int c8 = 0; c8 < 32; c8 += 8) {
+                uint32_t w[NSL][4];
+#pragma unroll
+                for (int pr = 0; pr < 4; ++pr) {
+                    size_t o = (size_t)(r0 + kb * 32 + c8 + 2 * pr) * TILE + i;
+                    float q0[NSL], q1[NSL];
+                    slice5(gh[o], __bfloat162float(gl[o]), e, q0);
+                    slice5(gh[o + TILE], __bfloat162float(gl[o + TILE]), e, q1);
+#pragma unroll
+                    for (int s = 0; s < NSL; ++s) {
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(q0[s], q1[s]);
+                        w[s][pr] = *reinterpret_cast<uint32_t *>(&b2);
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < NSL; ++s)
+                    *reinterpret_cast<uint4 *>(ax + (size_t)s * plane + orow + c8) =
+                        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+            }
+        }
+    }
+}
+
+// rho, grad rho and tau = 1/2 sum_k sum_mu d_k Phi Y^k in double-float (X in the slab, Y^k
+// in y_g + k plane), the meta-GGA functional in float64, then Z over X and
+// W^k = 1/4 w vtau d_k Phi over Y^k, with the per-tile maxima of |Z| (zexp), |Phi| (fexp),
+// |W^k| (wexp_g + k rows) and |d_k Phi| (gexp_g + k rows) for the V-side slicing.
+__global__ void __launch_bounds__(TILE) rho_z_mixed_mgga(ChunkArgs a, MixedArgs m, float2 *__restrict__ y_g,
+                                                          int *__restrict__ wexp_g, int *__restrict__ gexp_g) {
+    int64_t t = a.t0 + blockIdx.x;
+    int i = threadIdx.x;
+    int j = a.plan.tile_batch[t];
+    int cnt = a.plan.tile_count[t];
+    int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    int np = pad32(n);
+    int64_t r0 = a.plan.tile_row[t] - a.row0;
+    const size_t plane = (size_t)m.rows * TILE;
+    const float2 *phi = m.s.phi;
+    if (np > MAX_NP) {
+        if (i == 0) atomicOr(m.err, 8);
+        return;
+    }
+    df rho{0.f, 0.f}, tau{0.f, 0.f}, gr[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 2
+    for (int mu = 0; mu < n; ++mu) {
+        size_t o = (size_t)(r0 + mu) * TILE + i;
+        const float2 xv = m.s.x[o], f0 = phi[o];
+        const df x{xv.x, xv.y};
+        rho = df_add(rho, df_mul({f0.x, f0.y}, x));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const df gk{m.s.ghi[k * plane + o], __bfloat162float(m.s.glo[k * plane + o])};
+            const float2 yv = y_g[k * plane + o];
+            gr[k] = df_add(gr[k], df_mul(gk, x));
+            tau = df_add(tau, df_mul(gk, {yv.x, yv.y}));
+        }
+    }
+    const double r = df_to_d(rho), ta = 0.5 * df_to_d(tau);
+    const double dx = 2.0 * df_to_d(gr[0]), dy = 2.0 * df_to_d(gr[1]), dz = 2.0 * df_to_d(gr[2]);
+    double e = 0.0, nn = 0.0, ca_d = 0.0, bx_d = 0.0, by_d = 0.0, bz_d = 0.0, ct_d = 0.0;
+    if (i < cnt) {
+        const double w = a.plan.w[a.plan.tile_first[t] + i];
+        double f, vr, vs, vt;
+        xc::mvs_x(r, dx * dx + dy * dy + dz * dz, ta, f, vr, vs, vt);
+        e = w * f;
+        nn = w * r;
+        ca_d = 0.5 * w * vr;
+        const double b = 2.0 * w * vs;
+        bx_d = b * dx;
+        by_d = b * dy;
+        bz_d = b * dz;
+        ct_d = 0.25 * w * vt;
+    }
+    __shared__ int zmax[MAX_NP], fmx[MAX_NP], wmax[3][MAX_NP], gmax[3][MAX_NP];
+    for (int mu = i; mu < np; mu += TILE) {
+        zmax[mu] = 0;
+        fmx[mu] = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            wmax[k][mu] = 0;
+            gmax[k][mu] = 0;
+        }
+    }
+    __syncthreads();
+    const df cz = d_to_df(ca_d), cbx = d_to_df(bx_d), cby = d_to_df(by_d), cbz = d_to_df(bz_d), ct = d_to_df(ct_d);
+    const int lane = i & 31;
+#pragma unroll 2
+    for (int mu = 0; mu < n; ++mu) {
+        size_t o = (size_t)(r0 + mu) * TILE + i;
+        const float2 f0 = phi[o];
+        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
+        df z = df_mul(cz, {f0.x, f0.y});
+        z = df_add(z, dfl::mul_f(cbx, h1));
+        z = df_add(z, dfl::mul_f(cby, h2));
+        z = df_add(z, dfl::mul_f(cbz, h3));
+        m.s.x[o] = make_float2(z.h, z.l);
+        float az = fabsf(z.h), ap = fabsf(f0.x), aw[3], ag[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float hk = m.s.ghi[k * plane + o];
+            const df wk = df_mul(ct, {hk, __bfloat162float(m.s.glo[k * plane + o])});
+            y_g[k * plane + o] = make_float2(wk.h, wk.l);
+            aw[k] = fabsf(wk.h);
+            ag[k] = fabsf(hk);
+        }
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) {
+            az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
+            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                aw[k] = fmaxf(aw[k], __shfl_xor_sync(0xffffffffu, aw[k], q));
+                ag[k] = fmaxf(ag[k], __shfl_xor_sync(0xffffffffu, ag[k], q));
+            }
+        }
+        if (lane == 0) {
+            atomicMax(&zmax[mu], __float_as_int(az));
+            atomicMax(&fmx[mu], __float_as_int(ap));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                atomicMax(&wmax[k][mu], __float_as_int(aw[k]));
+                atomicMax(&gmax[k][mu], __float_as_int(ag[k]));
+            }
+        }
+    }
+    __syncthreads();
+    for (int mu = i; mu < n; mu += TILE) {
+        m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[mu]));
+        m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu]));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            wexp_g[(size_t)k * m.rows + r0 + mu] = exp_of(__int_as_float(wmax[k][mu]));
+            gexp_g[(size_t)k * m.rows + r0 + mu] = exp_of(__int_as_float(gmax[k][mu]));
+        }
+    }
+    __shared__ double re[TILE], rn[TILE];
+    re[i] = e;
+    rn[i] = nn;
+    __syncthreads();
+    for (int st = TILE / 2; st > 0; st >>= 1) {
+        if (i < st) {
+            re[i] += re[i + st];
+            rn[i] += rn[i + st];
+        }
+        __syncthreads();
+    }
+    if (i == 0) {
+        a.tileE[t] = re[0];
+        a.tileN[t] = rn[0];
+    }
+}
+
 // ---------------------------------------------------------------- V-side slicing
 // Thread per point.  The K group of the tile (the V task it belongs to) shares one
 // exponent per function for Z and one for Phi: the maximum of the per-tile exponents.
 // The group's first tile stores those maxima for the V epilogue over its own per-tile
 // entries; a reader in another block that sees the new value takes the same maximum, so
 // no ordering between the blocks of a group is needed.
-__global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
+// GRAD: the meta-GGA's terms W^k^T d_k Phi, with W^k in the X/Z plane (m.s.x) and d_k Phi read
+// from its hi words `gh` and bf16 lo words `gl` instead of Phi.
+template <bool GRAD>
+__global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m, const float *__restrict__ gh,
+                                                const __nv_bfloat16 *__restrict__ gl) {
     int64_t t = a.t0 + blockIdx.x;
     int j = a.plan.tile_batch[t];
     int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
@@ -1030,10 +1211,27 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m) {
         const size_t o = (size_t)(r0 + mu) * TILE + 8 * pg;
         const float4 *zs = reinterpret_cast<const float4 *>(m.s.x + o);
         const float4 *fs = reinterpret_cast<const float4 *>(m.s.phi + o);
+        float gfh[8], gfl[8];
+        if constexpr (GRAD) {
+            const float4 h0 = *reinterpret_cast<const float4 *>(gh + o), h1 = *reinterpret_cast<const float4 *>(gh + o + 4);
+            const uint4 lw = *reinterpret_cast<const uint4 *>(gl + o);
+            const uint32_t lu[4] = {lw.x, lw.y, lw.z, lw.w};
+            gfh[0] = h0.x; gfh[1] = h0.y; gfh[2] = h0.z; gfh[3] = h0.w;
+            gfh[4] = h1.x; gfh[5] = h1.y; gfh[6] = h1.z; gfh[7] = h1.w;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lu[q]));
+                gfl[2 * q] = f.x;
+                gfl[2 * q + 1] = f.y;
+            }
+        }
         uint32_t wz[NSL][4], wp[NSL][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {   // points 2q, 2q + 1 as (hi, lo, hi, lo)
-            const float4 z4 = zs[q], f4 = fs[q];
+            const float4 z4 = zs[q];
+            float4 f4;
+            if constexpr (GRAD) f4 = make_float4(gfh[2 * q], gfl[2 * q], gfh[2 * q + 1], gfl[2 * q + 1]);
+            else f4 = fs[q];
             float a0[NSL], a1[NSL], b0[NSL], b1[NSL];
             slice5(z4.x, z4.y, ez, a0);
             slice5(z4.z, z4.w, ez, a1);
@@ -1223,6 +1421,11 @@ void free_mixed_ctx(MixedCtx &c) {
     cudaFree(c.pdf2);
     cudaFree(c.x2);
     cudaFree(c.zexp2);
+    cudaFree(c.ax_g);
+    cudaFree(c.y_g);
+    cudaFree(c.pexp_g);
+    cudaFree(c.wexp_g);
+    cudaFree(c.gexp_g);
     cudaFree(c.pslices);
     cudaFree(c.pexp);
     cudaFree(c.d_err);
@@ -1294,6 +1497,17 @@ cudaError_t mixed_reserve_uks(MixedCtx &c, int64_t max_rows, int nbf) {
 size_t mixed_reserve_uks_bytes(int64_t max_rows, int nbf) {
     const size_t rows = (size_t)std::max<int64_t>(max_rows, 1);
     return rows * TILE * 8 + rows * 4 + (size_t)2 * nbf * nbf * 4;
+}
+
+cudaError_t mixed_reserve_mgga(MixedCtx &c, int64_t max_rows) {
+    const size_t rows = (size_t)std::max<int64_t>(max_rows, 1);
+    cudaError_t e = grow(c.ax_g, c.ax_g_cap, (size_t)3 * NSL * rows * TILE);
+    if (e == cudaSuccess) e = grow(c.y_g, c.y_g_cap, (size_t)3 * rows * TILE);
+    if (e == cudaSuccess) e = grow(c.pexp_g, c.pexp_g_cap, (size_t)3 * 4 * rows);
+    if (e == cudaSuccess) e = grow(c.wexp_g, c.wexp_g_cap, (size_t)3 * rows);
+    if (e == cudaSuccess) e = grow(c.gexp_g, c.gexp_g_cap, (size_t)3 * rows);
+    c.mgga_rows = e == cudaSuccess ? (int64_t)rows : 0;
+    return e;
 }
 
 cudaError_t mixed_begin_uks(MixedCtx &c, const double *Pa, const double *Pb, int nbf, cudaStream_t st) {
@@ -1383,12 +1597,21 @@ void run_xgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, Mixed
     P.end(GBXC_K_XGEMM, st);
 }
 
+void run_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c, const MixedSchedule &s,
+               cudaStream_t st);
+
 void run_slice_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c,
                      const MixedSchedule &s, int64_t nt, cudaStream_t st) {
     Profiler &P = *a.prof;
     P.begin(GBXC_K_SLICE, st);
-    slice_v<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    slice_v<false><<<(unsigned)nt, TILE, 0, st>>>(a, m, nullptr, nullptr);
     P.end(GBXC_K_SLICE, st);
+    run_vgemm(a, m, q, c, s, st);
+}
+
+void run_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c, const MixedSchedule &s,
+               cudaStream_t st) {
+    Profiler &P = *a.prof;
     if (a.nvtasks <= 0) return;
     P.begin(GBXC_K_VGEMM, st);
     const unsigned g = (unsigned)std::min(a.nvtasks, c.num_sms);
@@ -1419,6 +1642,59 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
     P.end(GBXC_K_RHO_Z, st);
     run_slice_vgemm(a, m, q, c, s, nt, st);
+    return cudaGetLastError();
+}
+
+// Meta-GGA chunk: the collocation, then the slices of d_k Phi; X and the three Y^k on the
+// same P^j slices (Y^k through the X/Z plane of a per-component copy of the slab view); the
+// rho/tau/functional/Z/W^k kernel; the V term Z^T Phi as in the spin-restricted form, then
+// each W^k^T d_k Phi with its own slicing (W^k from its Y^k plane, d_k Phi from the gradient
+// planes) into the same V_acc.
+cudaError_t launch_mixed_chunk_mgga(const ChunkArgs &a, MixedCtx &c, MixedResident &r, const MixedSchedule &s,
+                                    int chunk_index, cudaStream_t st) {
+    if (!r.d_shells || !c.ax_g || !c.y_g || !c.pexp_g || !c.wexp_g || !c.gexp_g) return cudaErrorInvalidValue;
+    if (a.rows > c.mgga_rows) return cudaErrorInvalidValue;
+    int64_t nt = a.t1 - a.t0;
+    if (nt <= 0) return cudaSuccess;
+    const MixedSchedule::Chunk &ch = s.chunks[chunk_index];
+    MixedArgs m = chunk_mixed_args(a, c, s, ch, c.pdf);
+    cudaError_t err = cudaSuccess;
+    const ChunkMaps q = chunk_maps(c, m, s, ch, err);
+    const size_t plane = (size_t)a.rows * TILE;
+    __nv_bfloat16 *axg = reinterpret_cast<__nv_bfloat16 *>(c.ax_g);
+    CUtensorMap tg[3];
+    for (int k = 0; k < 3; ++k)
+        tg[k] = make_map(c, axg + (size_t)k * NSL * plane, 4 * a.rows, 4 * a.rows, NSL, BM, err);
+    if (err != cudaSuccess) return err;
+    Profiler &P = *a.prof;
+    run_pslice(a, m, s, ch, st);
+    run_colloc(a, m, r, nt, st);
+    P.begin(GBXC_K_COLLOC, st);
+    grad_slices<<<(unsigned)nt, TILE, 0, st>>>(a, m, axg, c.pexp_g);
+    P.end(GBXC_K_COLLOC, st);
+    run_xgemm(a, m, q, c, s, ch, st);
+    for (int k = 0; k < 3; ++k) {
+        MixedArgs mk = m;
+        mk.s.pexp = c.pexp_g + (size_t)k * 4 * a.rows;
+        mk.s.x = c.y_g + (size_t)k * plane;
+        ChunkMaps qk = q;
+        qk.tax = tg[k];
+        run_xgemm(a, mk, qk, c, s, ch, st);
+    }
+    P.begin(GBXC_K_RHO_Z, st);
+    rho_z_mixed_mgga<<<(unsigned)nt, TILE, 0, st>>>(a, m, c.y_g, c.wexp_g, c.gexp_g);
+    P.end(GBXC_K_RHO_Z, st);
+    run_slice_vgemm(a, m, q, c, s, nt, st);
+    for (int k = 0; k < 3; ++k) {
+        MixedArgs mk = m;
+        mk.s.x = c.y_g + (size_t)k * plane;
+        mk.s.zexp = c.wexp_g + (size_t)k * a.rows;
+        mk.s.fexp = c.gexp_g + (size_t)k * a.rows;
+        P.begin(GBXC_K_SLICE, st);
+        slice_v<true><<<(unsigned)nt, TILE, 0, st>>>(a, mk, m.s.ghi + (size_t)k * plane, m.s.glo + (size_t)k * plane);
+        P.end(GBXC_K_SLICE, st);
+        run_vgemm(a, mk, q, c, s, st);
+    }
     return cudaGetLastError();
 }
 
