@@ -39,9 +39,18 @@ import xcinputs as X  # noqa: E402
 METRIC = "grid pts/s for E_xc+V_xc at |ΔE_xc|≤1e-6 Eh vs FP64 form; p50/p99 latency"
 UNIT = "grid pts/s"
 WORKLOAD = "water16_pbe"
-WORKLOAD_DESC = ("16-water cluster (48 atoms, 10 A box), 400 Cartesian Gaussians (O 3s2p1d, H 2s1p, "
-                 "3 primitives), PBE, SSF partition, Mura-Knowles 75 x Gauss-Legendre 16 x trapezoid 32, "
-                 "batches <= 512 points, eta = 1e-10")
+def describe(w):
+    """The workload in words, from its own parameters."""
+    g = w.grid
+    nw = w.mol.n_waters
+    ang = (f"Lebedev-Laikov {g.ntheta}" if getattr(g, "angular", "product") == "lebedev"
+           else f"Gauss-Legendre {g.ntheta} x trapezoid {g.nphi}")
+    kind = "spherical" if getattr(w.basis, "pure", None) is not None and any(w.basis.pure) else "Cartesian"
+    box = 10.0 * (nw / 16.0) ** (1.0 / 3.0)
+    return (f"{nw}-water cluster ({3 * nw} atoms, {box:.3g} A box), {w.basis.nbf} {kind} Gaussians "
+            f"(O 3s2p1d, H 2s1p, 3 primitives), {w.functional.upper() if w.functional == 'pbe' else 'Slater'}, "
+            f"{g.partition.upper() if g.partition == 'ssf' else 'Becke'} partition, Mura-Knowles {g.nrad} x {ang}, "
+            f"batches <= {g.max_batch} points, eta = {g.eta:g}")
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (alu bound)
 
 
@@ -243,7 +252,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "name": args.workload},
+            "data": "synthetic", "config": {"workload": describe(w), "name": args.workload},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -559,7 +568,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": R["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if head == "fp64" else "bf16x3+f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "name": args.workload, "npts": npts, "nbf": nbf,
+            "config": {"workload": describe(w), "name": args.workload, "npts": npts, "nbf": nbf,
                        "nbatch": info["nbatch"], "sum_mn2": info["sum_mn2"], "form": head,
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -81,7 +81,8 @@ typedef struct gbxc_ctx gbxc_ctx;
  *   nrad      Mura-Knowles radial points per atom
  *   ntheta    product rule: Gauss-Legendre nodes in cos(theta);
  *             Lebedev rule: its number of points, one of 6 14 26 38 50 86 110 146 170
- *             194 302 590 (degrees 3 ... 41; the paper's FG grid uses 302, UFG 590)
+ *             194 302 590 974 (degrees 3 ... 53; the paper's FG, UFG and SFG grids use
+ *             302, 590 and 974)
  *   nphi      product rule: trapezoid nodes in phi (angular grid = ntheta * nphi points);
  *             ignored for a Lebedev rule
  *   partition GBXC_BECKE or GBXC_SSF

@@ -1028,7 +1028,7 @@ int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
                 "unknown angular rule");
         if (spec->angular == GBXC_ANGULAR_LEBEDEV)
             REQUIRE(spec->nrad > 0 && lebedev_supported(spec->ntheta),
-                    "no Lebedev rule of that many points (6 14 26 38 50 86 110 146 170 194 302 590)");
+                    "no Lebedev rule of that many points (6 14 26 38 50 86 110 146 170 194 302 590 974)");
         else
             REQUIRE(spec->nrad > 0 && spec->ntheta > 0 && spec->nphi > 0, "grid sizes must be positive");
         REQUIRE(spec->partition == GBXC_BECKE || spec->partition == GBXC_SSF, "unknown partition");

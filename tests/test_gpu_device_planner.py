@@ -21,7 +21,7 @@ def _plan(G, ctx, w, device):
 
 @pytest.mark.parametrize("name", ["water1_slater", "water1_pbe_small", "water2_pbe_small", "water3_pbe_small",
                                   "water16_pbe", "water64_pbe", "water2_pbe_small_sph",
-                                  "water2_pbe_small_leb", "water16_pbe_fg"])
+                                  "water2_pbe_small_leb", "water16_pbe_fg", "water2_pbe_small_974"])
 def test_device_plan_identical(name):
     G = need_gpu()
     w = X.make_workload(name)

@@ -119,3 +119,21 @@ def test_unload_releases_a_molecule_and_its_cached_graph():
         assert E3 == E1 and np.max(np.abs(V2 - V1)) <= 1e-12 * np.max(np.abs(V1))
     finally:
         ctx.close()
+
+
+def test_974_point_grid_mixed_against_float64():
+    """The 974-point Lebedev-Laikov rule (pinned by exactness in the CPU tests; the oracle does
+    not build it): the tensor-core form against the float64 form on it."""
+    G = need_gpu()
+    w = X.make_workload("water2_pbe_small_974")
+    ctx = G.Context(0)
+    try:
+        mid = ctx.load_molecule(w.mol, w.basis, w.grid)
+        nbf = w.basis.nbf
+        V64, Vm = np.zeros((nbf, nbf)), np.zeros((nbf, nbf))
+        E64, N64 = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", "fp64", V64)
+        Em, Nm = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", "mixed", Vm)
+        assert abs(Em - E64) <= 1e-7 and abs(Nm - N64) <= 1e-8
+        assert np.max(np.abs(Vm - V64)) <= 1e-6
+    finally:
+        ctx.close()

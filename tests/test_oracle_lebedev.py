@@ -148,18 +148,25 @@ def _library_unit_rule(G, n):
     return ex["x"][o] / r[0], ex["y"][o] / r[0], ex["z"][o] / r[0], ex["wq"][o] / wr[0]
 
 
-def test_library_590_rule_pinned_directly():
-    """The 590-point rule (degree 41), which the oracle does not build: every Y_lm with
-    l <= 41 integrated exactly, l = 42 not, positive weights summing to 4 pi."""
+@pytest.mark.parametrize("n,p", [(590, 41), (974, 53)])
+def test_library_large_rules_pinned_directly(n, p):
+    """The 590- and 974-point rules (degrees 41 and 53; the paper's UFG and SFG grids), which
+    the oracle does not build: every Y_lm with l <= p integrated exactly, l = p + 1 not,
+    positive weights summing to 4 pi, octahedral orbits."""
     G = pytest.importorskip("paper_2007_03143_gb300")
     try:
         G.lib()
     except G.LibraryMissing as e:
         pytest.skip(str(e))
-    ux, uy, uz, w = _library_unit_rule(G, 590)
-    assert len(w) == 590 and np.all(w > 0) and abs(np.sum(w) - 4 * math.pi) < 1e-13
-    err = _harmonic_errors(ux, uy, uz, w, 42)
-    assert np.max(err[:42]) < 2e-14 and err[42] > 1e-4
+    ux, uy, uz, w = _library_unit_rule(G, n)
+    assert len(w) == n and np.all(w > 0) and abs(np.sum(w) - 4 * math.pi) < 1e-13
+    err = _harmonic_errors(ux, uy, uz, w, p + 1)
+    assert np.max(err[:p + 1]) < 2e-14 and err[p + 1] > 1e-4
+    pts = {(round(a, 12), round(b, 12), round(c, 12)) for a, b, c in zip(ux, uy, uz)}
+    for a, b, c in list(pts)[:50]:
+        for perm in itertools.permutations((a, b, c)):
+            for sg in itertools.product((1, -1), repeat=3):
+                assert tuple(round(sg[k] * perm[k], 12) + 0.0 for k in range(3)) in pts
 
 
 def test_library_rejects_unknown_lebedev_size():

@@ -375,12 +375,21 @@ WORKLOADS = {
                                  functional="pbe"),
     "water16_pbe_fg": dict(n_waters=16, grid=GridSpec(75, 302, 0, "ssf", 512, angular="lebedev"),
                            functional="pbe"),
+    # the paper's UFG (99 x 590) and SFG (175 x 974) grids on the 16-water cluster
+    "water16_pbe_ufg": dict(n_waters=16, grid=GridSpec(99, 590, 0, "ssf", 512, angular="lebedev"),
+                            functional="pbe"),
+    "water16_pbe_sfg": dict(n_waters=16, grid=GridSpec(175, 974, 0, "ssf", 512, angular="lebedev"),
+                            functional="pbe"),
+    # the 974-point rule (the paper's SFG angular grid) on a small radial grid
+    "water2_pbe_small_974": dict(n_waters=2, grid=GridSpec(20, 974, 0, "ssf", 128, angular="lebedev"),
+                                 functional="pbe"),
 }
 
 _WORKLOAD_SEEDS = {"water1_slater": 1000, "water16_pbe": 2000, "water64_pbe": 3000,
                    "water2_pbe_small": 9100, "water3_pbe_small": 9200, "water1_pbe_small": 9300,
                    "water2_pbe_small_sph": 9100, "water16_pbe_sph": 2000,
-                   "water2_pbe_small_leb": 9100, "water16_pbe_fg": 2000}
+                   "water2_pbe_small_leb": 9100, "water16_pbe_fg": 2000, "water2_pbe_small_974": 9100,
+                   "water16_pbe_ufg": 2000, "water16_pbe_sfg": 2000}
 
 
 def make_workload(name: str, n_waters: int | None = None, seed: int | None = None) -> Workload:
