@@ -50,7 +50,6 @@ constexpr int MAX_NP = 1184;   // largest padded N_b^j: keeps the exact accumula
 constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
 // at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
-constexpr double kFp32RhoMin = 1e300;
 
 // ---------------------------------------------------------------- scratch layout
 struct MixedSlabs {
@@ -794,15 +793,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
         double w = a.plan.w[a.plan.tile_first[t] + i];
         double sigma = dx * dx + dy * dy + dz * dz;
         double f, vr, vs;
-        if (r >= kFp32RhoMin) {
-            float ff, fr, fs;
-            xc::evaluate<float>(a.functional, (float)r, (float)sigma, ff, fr, fs);
-            f = ff;
-            vr = fr;
-            vs = fs;
-        } else {
-            xc::evaluate<double>(a.functional, r, sigma, f, vr, vs);
-        }
+        xc::evaluate<double>(a.functional, r, sigma, f, vr, vs);
         e = w * f;
         nn = w * r;
         ca_d = 0.5 * w * vr;

@@ -1,6 +1,6 @@
 // Spin-restricted exchange-correlation functionals on the device, templated on
-// the arithmetic type (double for the float64 form, float for the bulk of the
-// mixed form).  Each returns the energy per volume f = rho*eps and the first
+// the arithmetic type (both forms evaluate them in double: float32 PBE was measured
+// too inaccurate for the mixed form's bound).  Each returns the energy per volume f = rho*eps and the first
 // derivatives vrho = df/drho and vsigma = df/dsigma with sigma = |grad rho|^2,
 // the reading of Eqs. zvec_r / z_mat under which V_xc = dE_xc/dP.
 //
