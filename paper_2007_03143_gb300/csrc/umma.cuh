@@ -52,14 +52,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of `bar`; false if it did not complete within kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for phase `parity` of `bar`; false if it did not complete within `cycles` clocks.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, long long cycles) {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > cycles) return false;
     }
     return true;
+}
+
+// Wait for phase `parity` of `bar`; false if it did not complete within kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, kWaitCycles);
 }
 
 // ---------------------------------------------------------------- TMA
