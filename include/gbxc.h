@@ -212,7 +212,8 @@ int gbxc_export_plan(gbxc_ctx *ctx, int mol, double *x, double *y, double *z, do
  *   Exc, Nel   host scalars (may be NULL)
  *   Vxc        nbf x nbf output, host or device (may be NULL); exactly symmetric
  *   stream     cudaStream_t to run on (NULL = the context's own stream); the call
- *              returns after the results are complete                        */
+ *              returns after the results are complete
+ * GBXC_EINVAL when P holds a NaN or an infinity (checked on the device).      */
 int gbxc_integrate(gbxc_ctx *ctx, int mol, const double *P, int functional, int precision,
                    double *Exc, double *Vxc, double *Nel, void *stream);
 

@@ -482,6 +482,16 @@ __global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a, int zp, int pp, do
 // --------------------------------------------------------------------------
 // finish: V = V_acc + V_acc^T; per-batch and total E, N in a fixed order.
 // --------------------------------------------------------------------------
+// flag <- 1 if any of P[0 .. n) is a NaN or an infinity (a density that the functionals'
+// rho >= RHO_MIN test would otherwise drop point by point without a trace)
+__global__ void nonfinite_flag(const double *__restrict__ P, int64_t n, double *flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(P[i])) {
+            *flag = 1.0;
+            return;
+        }
+}
+
 __global__ void symmetrize(const double *__restrict__ Vacc, double *__restrict__ V, int nbf) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)nbf * nbf) return;
@@ -686,6 +696,16 @@ cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s) {
     rho_xc_z_f64<<<(unsigned)nt, TILE, 0, s>>>(a);
     unsigned nblk = (unsigned)((a.max_nfunc + VB - 1) / VB);
     vgemm_f64_tile<<<dim3((unsigned)nt, nblk, nblk), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double *P, int64_t n, double *flag, bool reset, cudaStream_t s) {
+    if (reset) {
+        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (n > 0)
+        nonfinite_flag<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(P, n, flag);
     return cudaGetLastError();
 }
 

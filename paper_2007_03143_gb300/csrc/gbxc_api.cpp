@@ -373,7 +373,7 @@ void reserve(Workspace &w, const Molecule &m, const Schedule &S, int precision) 
         w.mat_cap = nn;
     }
     size_t one = 2;
-    if (!w.d_tot) grow_buf(w.d_tot, one, 2, "totals");
+    if (!w.d_tot) grow_buf(w.d_tot, one, 3, "totals");   // E, N and the non-finite-P flag
     size_t nt = (size_t)m.plan.ntiles(), nb = (size_t)std::max(m.plan.nbatch(), 1);
     if (nt > w.tile_cap || !w.tileE) {
         size_t c0 = w.tile_cap, c1 = w.tile_cap;
@@ -596,13 +596,17 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
         dP = w.d_P;
     }
     double *dV = (Vxc && is_device_ptr(Vxc)) ? Vxc : w.d_V;
+    ctx->prof.begin(GBXC_K_FINISH, s);
+    check(launch_check_finite(dP, (int64_t)nn, w.d_tot + 2, true, s), "check P");
+    ctx->prof.end(GBXC_K_FINISH, s);
     enqueue(w, m, S, dP, functional, precision, b0, b1, Vxc ? dV : nullptr, Eb || Nb, s, &ctx->prof);
-    double tot[2];
-    check(cudaMemcpyAsync(tot, w.d_tot, 16, cudaMemcpyDeviceToHost, s), "copy E");
+    double tot[3];
+    check(cudaMemcpyAsync(tot, w.d_tot, 24, cudaMemcpyDeviceToHost, s), "copy E");
     if (Vxc && dV != Vxc) check(cudaMemcpyAsync(Vxc, dV, nn * 8, cudaMemcpyDeviceToHost, s), "copy V");
     if (Eb) check(cudaMemcpyAsync(Eb, w.Eb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Eb");
     if (Nb) check(cudaMemcpyAsync(Nb, w.Nb, nb * 8, cudaMemcpyDeviceToHost, s), "copy Nb");
     check(cudaStreamSynchronize(s), "integrate");
+    if (tot[2] != 0.0) return fail(ctx, GBXC_EINVAL, "P contains a NaN or an infinity");
     if (precision == GBXC_MIXED) {
         int werr = 0;
         check(mixed_read_error(w.mixed, &werr, s), "mixed status");
@@ -1243,6 +1247,8 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
             check(cudaMemcpyAsync(w.d_P2, Pb, nn * 8, cudaMemcpyHostToDevice, s), "copy P_b");
             dPb = w.d_P2;
         }
+        check(launch_check_finite(dPa, (int64_t)nn, w.d_tot + 2, true, s), "check P_a");
+        check(launch_check_finite(dPb, (int64_t)nn, w.d_tot + 2, false, s), "check P_b");
         double *dVa = (Va && is_device_ptr(Va)) ? Va : w.d_V;
         double *dVb = (Vb && is_device_ptr(Vb)) ? Vb : w.d_V2;
         check(cudaMemsetAsync(w.d_Vacc, 0, nn * 8, s), "zero V_a");
@@ -1289,11 +1295,12 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
         f.prof = &ctx->prof;
         check(launch_finish(f, s), "finish");
         if (Vb) check(launch_symmetrize(w.d_Vacc2, dVb, m.nbf, s), "symmetrise V_b");
-        double tot[2];
-        check(cudaMemcpyAsync(tot, w.d_tot, 16, cudaMemcpyDeviceToHost, s), "copy E");
+        double tot[3];
+        check(cudaMemcpyAsync(tot, w.d_tot, 24, cudaMemcpyDeviceToHost, s), "copy E");
         if (Va && dVa != Va) check(cudaMemcpyAsync(Va, dVa, nn * 8, cudaMemcpyDeviceToHost, s), "copy V_a");
         if (Vb && dVb != Vb) check(cudaMemcpyAsync(Vb, dVb, nn * 8, cudaMemcpyDeviceToHost, s), "copy V_b");
         check(cudaStreamSynchronize(s), "integrate unrestricted");
+        if (tot[2] != 0.0) return fail(ctx, GBXC_EINVAL, "P_a or P_b contains a NaN or an infinity");
         if (precision == GBXC_MIXED) {
             int werr = 0;
             check(mixed_read_error(w.mixed, &werr, s), "mixed status");

@@ -194,5 +194,7 @@ cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s);
 cudaError_t launch_symmetrize_inplace(double *V, int nbf, cudaStream_t s);
 // V = V_acc + V_acc^T
 cudaError_t launch_symmetrize(const double *Vacc, double *V, int nbf, cudaStream_t s);
+// *flag <- 1.0 if P[0 .. n) holds a NaN or an infinity (zeroed first when reset).
+cudaError_t launch_check_finite(const double *P, int64_t n, double *flag, bool reset, cudaStream_t s);
 
 }  // namespace gbxc

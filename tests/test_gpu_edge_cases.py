@@ -137,3 +137,53 @@ def test_974_point_grid_mixed_against_float64():
         assert np.max(np.abs(Vm - V64)) <= 1e-6
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_work_order_invariance(form):
+    """Race check by work order: the same integration with a small scratch budget (many chunks,
+    a different order of the V atomics and of the launches) agrees with the one-chunk result:
+    E and N bit for bit (fixed-order sums); V to 1e-12 relative in float64 (atomics order
+    only), 1e-9 in the mixed form (a batch cut by a chunk boundary also gets other V-side
+    slicing groups, hence other roundings)."""
+    G = need_gpu()
+    w = X.make_workload("water3_pbe_small")
+    nbf = w.basis.nbf
+    out = []
+    for scratch in (0, 24 << 20):
+        ctx = G.Context(0, scratch)
+        try:
+            mid = ctx.load_molecule(w.mol, w.basis, w.grid)
+            V = np.zeros((nbf, nbf))
+            E, N = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", form, V)
+            out.append((E, N, V))
+        finally:
+            ctx.close()
+    (E0, N0, V0), (E1, N1, V1) = out
+    assert E0 == E1 and N0 == N1
+    assert np.max(np.abs(V1 - V0)) <= (1e-12 if form == "fp64" else 1e-9) * np.max(np.abs(V0))
+
+
+def test_nan_in_P_is_refused_and_the_next_call_is_clean():
+    """Host-side injection of a NaN (and an infinity) in P: the call is refused with
+    GBXC_EINVAL after a device-side check, instead of the functionals' density test silently
+    dropping the affected points; the next call with a valid P gives the normal result."""
+    G = need_gpu()
+    w = X.make_workload("water1_pbe_small")
+    nbf = w.basis.nbf
+    ctx = G.Context(0)
+    try:
+        mid = ctx.load_molecule(w.mol, w.basis, w.grid)
+        E0, N0 = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", "mixed", None)
+        for bad in (np.nan, np.inf):
+            Pbad = w.P.copy()
+            Pbad[3, 5] = Pbad[5, 3] = bad
+            for form in ("fp64", "mixed"):
+                with pytest.raises(G.GbxcError):
+                    G.gbxc_integrate(ctx.h, mid, Pbad, "pbe", form, None)
+            with pytest.raises(G.GbxcError):
+                G.gbxc_integrate_uks(ctx.h, mid, 0.5 * w.P, 0.5 * Pbad, "pbe", "fp64")
+        E1, N1 = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", "mixed", None)
+        assert E1 == E0 and N1 == N0
+    finally:
+        ctx.close()
