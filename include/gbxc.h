@@ -178,6 +178,18 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
 int gbxc_load_grid_device(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
                           int *nbatch_out);
 
+/* Plan files (checkpoint / resume of the resident grid): gbxc_save_plan writes the grid spec,
+ * the points in batch order (x, y, z, w^q, parent atom, generation index) and the merged
+ * batches with their shell lists of `mol` to `path`; gbxc_load_plan reads such a file for a
+ * molecule with the same atoms and basis (checked by a hash) and makes it the molecule's
+ * grid without re-planning (the partition weights are recomputed on the device; the
+ * paper reuses grids and plans across SCF iterations, Sec. 2.2).  The file layout is the
+ * host's native one.  GBXC_EINVAL for I/O errors, a foreign or corrupt file (every size,
+ * pointer and index is validated before the molecule's grid is replaced), GBXC_ENOTREADY
+ * for a molecule without a grid (save) or while requests are in flight (load). */
+int gbxc_save_plan(gbxc_ctx *ctx, int mol, const char *path);
+int gbxc_load_plan(gbxc_ctx *ctx, int mol, const char *path, long long *npts_out, int *nbatch_out);
+
 /* Release everything the library holds for `mol` (basis, grid, partition weights, plan,
  * schedules and cached graphs that include it); the id is not reused.  The boundary's
  * counterpart of load_basis/load_grid (the resident per-molecule state of Sec. 2.3's

@@ -37,7 +37,7 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
             "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule", "gbxc_load_grid_device",
-            "gbxc_load_basis_pure", "gbxc_integrate_uks", "gbxc_unload"]
+            "gbxc_load_basis_pure", "gbxc_integrate_uks", "gbxc_unload", "gbxc_save_plan", "gbxc_load_plan"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -94,6 +94,10 @@ def lib():
     L.gbxc_load_grid_device.restype = c_int
     L.gbxc_unload.argtypes = [c_void_p, c_int]
     L.gbxc_unload.restype = c_int
+    L.gbxc_save_plan.argtypes = [c_void_p, c_int, ctypes.c_char_p]
+    L.gbxc_save_plan.restype = c_int
+    L.gbxc_load_plan.argtypes = [c_void_p, c_int, ctypes.c_char_p, POINTER(c_longlong), POINTER(c_int)]
+    L.gbxc_load_plan.restype = c_int
     L.gbxc_plan_info_get.argtypes = [c_void_p, c_int, POINTER(PlanInfo)]
     L.gbxc_export_plan.argtypes = [c_void_p, c_int] + [c_void_p] * 10
     L.gbxc_integrate.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, pd, c_void_p, pd, c_void_p]
@@ -220,6 +224,17 @@ def gbxc_load_grid_device(ctx, mol, nrad, ntheta, nphi, partition, max_batch, et
 
 def gbxc_unload(ctx, mol):
     _check(ctx, lib().gbxc_unload(ctx, mol))
+
+
+def gbxc_save_plan(ctx, mol, path):
+    _check(ctx, lib().gbxc_save_plan(ctx, mol, os.fsencode(path)))
+
+
+def gbxc_load_plan(ctx, mol, path):
+    """Make the plan file at `path` the grid of `mol`; returns (npts, nbatch)."""
+    npts, nb = c_longlong(), c_int()
+    _check(ctx, lib().gbxc_load_plan(ctx, mol, os.fsencode(path), ctypes.byref(npts), ctypes.byref(nb)))
+    return npts.value, nb.value
 
 
 def gbxc_plan_info_get(ctx, mol) -> dict:

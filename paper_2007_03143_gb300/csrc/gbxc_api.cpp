@@ -899,6 +899,163 @@ void gbxc_destroy(gbxc_ctx *ctx) {
     delete ctx;
 }
 
+// ---------------------------------------------------------------------------
+// plan files: the grid and merged batches of a molecule, reloaded without re-planning
+// ---------------------------------------------------------------------------
+namespace {
+constexpr char kPlanMagic[8] = {'G', 'B', 'X', 'C', 'P', 'L', 'A', 'N'};
+constexpr uint32_t kPlanVersion = 1;
+
+// FNV-1a over everything the plan depends on: atoms, shells (centres, L, primitives, purity)
+uint64_t molecule_hash(const Molecule &m) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    };
+    mix(&m.natoms, sizeof(m.natoms));
+    mix(m.xyz.data(), m.xyz.size() * sizeof(double));
+    mix(&m.nshell, sizeof(m.nshell));
+    for (const DevShell &sh : m.shells) {
+        mix(sh.c, sizeof(sh.c));
+        mix(&sh.L, sizeof(sh.L));
+        mix(&sh.nprim, sizeof(sh.nprim));
+        mix(&sh.pure, sizeof(sh.pure));
+        mix(sh.alpha, sizeof(double) * sh.nprim);
+    }
+    return h;
+}
+
+int finish_grid(gbxc_ctx *ctx, Molecule &m, const gbxc_grid_spec *spec, bool host_only, bool on_device,
+                DevPoints &pts, long long *npts_out, int *nbatch_out);
+
+struct PlanHeader {
+    char magic[8];
+    uint32_t version, reserved;
+    uint64_t hash;
+    gbxc_grid_spec spec;
+    int64_t npts, nbatch, nleaf, nshell_entries;
+};
+}  // namespace
+
+int gbxc_save_plan(gbxc_ctx *ctx, int mol, const char *path) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(path, "path is NULL");
+        Molecule &m = get_mol(ctx, mol);
+        if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
+        const HostPlan &P = m.plan;
+        const size_t n = (size_t)P.npts;
+        std::vector<double> x(n), y(n), z(n), wq(n);
+        std::vector<int> parent(n);
+        std::vector<long long> pidx(n);
+        int rc = gbxc_export_plan(ctx, mol, x.data(), y.data(), z.data(), wq.data(), nullptr, parent.data(),
+                                  pidx.data(), nullptr, nullptr, nullptr);
+        if (rc != GBXC_OK) return rc;
+        PlanHeader h;
+        std::memset(&h, 0, sizeof(h));
+        std::memcpy(h.magic, kPlanMagic, 8);
+        h.version = kPlanVersion;
+        h.hash = molecule_hash(m);
+        h.spec = m.spec;
+        h.npts = P.npts;
+        h.nbatch = P.nbatch();
+        h.nleaf = P.nleaf;
+        h.nshell_entries = (int64_t)P.shell_idx.size();
+        FILE *f = std::fopen(path, "wb");
+        if (!f) return fail(ctx, GBXC_EINVAL, std::string("cannot open ") + path + " for writing");
+        bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+        auto put = [&](const void *p, size_t bytes) { ok = ok && (bytes == 0 || std::fwrite(p, bytes, 1, f) == 1); };
+        put(x.data(), n * 8);
+        put(y.data(), n * 8);
+        put(z.data(), n * 8);
+        put(wq.data(), n * 8);
+        put(parent.data(), n * 4);
+        put(pidx.data(), n * 8);
+        put(P.batch_ptr.data(), P.batch_ptr.size() * 8);
+        put(P.shell_ptr.data(), P.shell_ptr.size() * 8);
+        put(P.shell_idx.data(), P.shell_idx.size() * 4);
+        ok = (std::fclose(f) == 0) && ok;
+        if (!ok) return fail(ctx, GBXC_EINVAL, std::string("writing ") + path + " failed");
+        return GBXC_OK;
+    });
+}
+
+int gbxc_load_plan(gbxc_ctx *ctx, int mol, const char *path, long long *npts_out, int *nbatch_out) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(path, "path is NULL");
+        Molecule &m = get_mol(ctx, mol);
+        bool host_only = ctx->device < 0;
+        if (server_busy(ctx)) return fail(ctx, GBXC_ENOTREADY, "requests are in flight; wait for them first");
+        FILE *f = std::fopen(path, "rb");
+        if (!f) return fail(ctx, GBXC_EINVAL, std::string("cannot open ") + path);
+        std::unique_ptr<FILE, int (*)(FILE *)> guard(f, std::fclose);
+        PlanHeader h;
+        if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kPlanMagic, 8) != 0 ||
+            h.version != kPlanVersion)
+            return fail(ctx, GBXC_EINVAL, "not a plan file of this version");
+        if (h.hash != molecule_hash(m)) return fail(ctx, GBXC_EINVAL, "the plan belongs to another molecule or basis");
+        REQUIRE(h.npts >= 0 && h.nbatch >= 0 && h.nshell_entries >= 0 && h.npts < (int64_t(1) << 40) &&
+                    h.nbatch <= h.npts + 1 && h.nshell_entries <= h.nbatch * (int64_t)m.nshell,
+                "corrupt plan sizes");
+        const size_t n = (size_t)h.npts, nb = (size_t)h.nbatch;
+        HostPlan P;
+        P.x.resize(n);
+        P.y.resize(n);
+        P.z.resize(n);
+        P.wq.resize(n);
+        P.parent.resize(n);
+        P.point_index.resize(n);
+        std::vector<int64_t> bptr(nb + 1), sptr(nb + 1);
+        std::vector<int> sidx((size_t)h.nshell_entries);
+        bool ok = true;
+        auto get = [&](void *p, size_t bytes) { ok = ok && (bytes == 0 || std::fread(p, bytes, 1, f) == 1); };
+        get(P.x.data(), n * 8);
+        get(P.y.data(), n * 8);
+        get(P.z.data(), n * 8);
+        get(P.wq.data(), n * 8);
+        get(P.parent.data(), n * 4);
+        get(P.point_index.data(), n * 8);
+        get(bptr.data(), (nb + 1) * 8);
+        get(sptr.data(), (nb + 1) * 8);
+        get(sidx.data(), sidx.size() * 4);
+        if (!ok) return fail(ctx, GBXC_EINVAL, "plan file is truncated");
+        // validate before anything is replaced
+        REQUIRE(bptr[0] == 0 && bptr[nb] == h.npts && sptr[0] == 0 && sptr[nb] == h.nshell_entries,
+                "corrupt batch pointers");
+        for (size_t j = 0; j < nb; ++j)
+            REQUIRE(bptr[j] <= bptr[j + 1] && sptr[j] <= sptr[j + 1], "corrupt batch pointers");
+        for (int s : sidx) REQUIRE(s >= 0 && s < m.nshell, "shell index out of range");
+        for (size_t i = 0; i < n; ++i)
+            REQUIRE(P.parent[i] >= 0 && P.parent[i] < m.natoms && P.point_index[i] >= 0 &&
+                        P.point_index[i] < h.npts,
+                    "corrupt point data");
+        std::vector<std::vector<int>> bshells(nb);
+        std::vector<int64_t> bsize(nb);
+        for (size_t j = 0; j < nb; ++j) {
+            bshells[j].assign(sidx.begin() + sptr[j], sidx.begin() + sptr[j + 1]);
+            bsize[j] = bptr[j + 1] - bptr[j];
+        }
+        batch_metadata((size_t)m.natoms, m.shells, bshells, bsize, P);
+        P.nleaf = (int)h.nleaf;
+        if (!host_only) {
+            check(cudaStreamSynchronize(ctx->stream), "sync");
+            if (ctx->many.exec &&
+                std::find(ctx->many.mols.begin(), ctx->many.mols.end(), mol) != ctx->many.mols.end()) {
+                cudaGraphExecDestroy(ctx->many.exec);
+                ctx->many.exec = nullptr;
+                ctx->many.mols.clear();
+            }
+        }
+        free_grid(m);
+        m.spec = h.spec;
+        m.plan = std::move(P);
+        DevPoints none;
+        return finish_grid(ctx, m, &m.spec, host_only, false, none, npts_out, nbatch_out);
+    });
+}
+
 int gbxc_unload(gbxc_ctx *ctx, int mol) {
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {
@@ -1023,6 +1180,71 @@ int gbxc_load_grid_device(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, lo
 }
 
 namespace {
+// The plan of `m` is built (m.plan; device-planned point arrays in *pts when on_device):
+// upload it, compute the partition weights on the device, mark the grid loaded.
+int finish_grid(gbxc_ctx *ctx, Molecule &m, const gbxc_grid_spec *spec, bool host_only, bool on_device,
+                DevPoints &pts, long long *npts_out, int *nbatch_out) {
+    m.work = 0.0;
+    for (double wj : m.plan.work) m.work += wj;
+    if (host_only) {
+        m.has_grid = true;
+        if (npts_out) *npts_out = (long long)m.plan.npts;
+        if (nbatch_out) *nbatch_out = m.plan.nbatch();
+        return GBXC_OK;
+    }
+    cudaStream_t s = ctx->stream;
+    HostPlan &P = m.plan;
+    if (on_device) {
+        m.dev.x = pts.x;
+        m.dev.y = pts.y;
+        m.dev.z = pts.z;
+        m.dev.wq = pts.wq;
+        m.dev.parent = pts.parent;
+        m.d_point_index = pts.point_index;
+    } else {
+        m.dev.x = dev_upload(m, P.x, s);
+        m.dev.y = dev_upload(m, P.y, s);
+        m.dev.z = dev_upload(m, P.z, s);
+        m.dev.wq = dev_upload(m, P.wq, s);
+        m.dev.parent = dev_upload(m, P.parent, s);
+        m.d_point_index = nullptr;
+    }
+    m.dev.w = dev_alloc<double>(m, P.npts);
+    m.dev.shell_ptr = dev_upload(m, P.shell_ptr, s);
+    m.dev.shell_idx = dev_upload(m, P.shell_idx, s);
+    m.dev.func_ptr = dev_upload(m, P.func_ptr, s);
+    m.dev.func_idx = dev_upload(m, P.func_idx, s);
+    m.dev.tile_batch = dev_upload(m, P.tile_batch, s);
+    m.dev.tile_first = dev_upload(m, P.tile_first, s);
+    m.dev.tile_count = dev_upload(m, P.tile_count, s);
+    m.dev.tile_row = dev_upload(m, P.tile_row, s);
+    m.dev.batch_tile = dev_upload(m, P.batch_tile, s);
+    m.dev.batch_ptr = dev_upload(m, P.batch_ptr, s);
+    m.d_tileE = dev_alloc<double>(m, P.ntiles());
+    m.d_tileN = dev_alloc<double>(m, P.ntiles());
+    m.d_Eb = dev_alloc<double>(m, P.nbatch());
+    m.d_Nb = dev_alloc<double>(m, P.nbatch());
+    WeightsArgs wa;
+    wa.x = m.dev.x;
+    wa.y = m.dev.y;
+    wa.z = m.dev.z;
+    wa.wq = m.dev.wq;
+    wa.parent = m.dev.parent;
+    wa.atoms = m.d_atoms;
+    wa.rnn = m.d_rnn;
+    wa.w = m.dev.w;
+    wa.npts = P.npts;
+    wa.natoms = m.natoms;
+    wa.scheme = spec->partition;
+    wa.prof = &ctx->prof;
+    check(launch_partition_weights(wa, s), "partition weights");
+    check(cudaStreamSynchronize(s), "load_grid");
+    m.has_grid = true;
+    if (npts_out) *npts_out = (long long)P.npts;
+    if (nbatch_out) *nbatch_out = P.nbatch();
+    return GBXC_OK;
+}
+
 int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out, int *nbatch_out,
                    bool on_device) {
     if (!ctx) return GBXC_EINVAL;
@@ -1068,65 +1290,7 @@ int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
             build_molecular_grid(m.xyz, *spec, x, y, z, wq, parent);
             build_plan(m.xyz, m.shells, rcut, m.nbf, *spec, x, y, z, wq, parent, m.plan);
         }
-        m.work = 0.0;
-        for (double wj : m.plan.work) m.work += wj;
-        if (host_only) {
-            m.has_grid = true;
-            if (npts_out) *npts_out = (long long)m.plan.npts;
-            if (nbatch_out) *nbatch_out = m.plan.nbatch();
-            return GBXC_OK;
-        }
-        cudaStream_t s = ctx->stream;
-        HostPlan &P = m.plan;
-        if (on_device) {
-            m.dev.x = pts.x;
-            m.dev.y = pts.y;
-            m.dev.z = pts.z;
-            m.dev.wq = pts.wq;
-            m.dev.parent = pts.parent;
-            m.d_point_index = pts.point_index;
-        } else {
-            m.dev.x = dev_upload(m, P.x, s);
-            m.dev.y = dev_upload(m, P.y, s);
-            m.dev.z = dev_upload(m, P.z, s);
-            m.dev.wq = dev_upload(m, P.wq, s);
-            m.dev.parent = dev_upload(m, P.parent, s);
-            m.d_point_index = nullptr;
-        }
-        m.dev.w = dev_alloc<double>(m, P.npts);
-        m.dev.shell_ptr = dev_upload(m, P.shell_ptr, s);
-        m.dev.shell_idx = dev_upload(m, P.shell_idx, s);
-        m.dev.func_ptr = dev_upload(m, P.func_ptr, s);
-        m.dev.func_idx = dev_upload(m, P.func_idx, s);
-        m.dev.tile_batch = dev_upload(m, P.tile_batch, s);
-        m.dev.tile_first = dev_upload(m, P.tile_first, s);
-        m.dev.tile_count = dev_upload(m, P.tile_count, s);
-        m.dev.tile_row = dev_upload(m, P.tile_row, s);
-        m.dev.batch_tile = dev_upload(m, P.batch_tile, s);
-        m.dev.batch_ptr = dev_upload(m, P.batch_ptr, s);
-        m.d_tileE = dev_alloc<double>(m, P.ntiles());
-        m.d_tileN = dev_alloc<double>(m, P.ntiles());
-        m.d_Eb = dev_alloc<double>(m, P.nbatch());
-        m.d_Nb = dev_alloc<double>(m, P.nbatch());
-        WeightsArgs wa;
-        wa.x = m.dev.x;
-        wa.y = m.dev.y;
-        wa.z = m.dev.z;
-        wa.wq = m.dev.wq;
-        wa.parent = m.dev.parent;
-        wa.atoms = m.d_atoms;
-        wa.rnn = m.d_rnn;
-        wa.w = m.dev.w;
-        wa.npts = P.npts;
-        wa.natoms = m.natoms;
-        wa.scheme = spec->partition;
-        wa.prof = &ctx->prof;
-        check(launch_partition_weights(wa, s), "partition weights");
-        check(cudaStreamSynchronize(s), "load_grid");
-        m.has_grid = true;
-        if (npts_out) *npts_out = (long long)P.npts;
-        if (nbatch_out) *nbatch_out = P.nbatch();
-        return GBXC_OK;
+        return finish_grid(ctx, m, spec, host_only, on_device, pts, npts_out, nbatch_out);
     });
 }
 

@@ -187,3 +187,28 @@ def test_nan_in_P_is_refused_and_the_next_call_is_clean():
         assert E1 == E0 and N1 == N0
     finally:
         ctx.close()
+
+
+def test_plan_file_reload_integrates_identically(tmp_path):
+    """A plan saved from a device-planned molecule and loaded into a fresh copy of it (no
+    planning) integrates to the same E_xc and N_el bit for bit and the same V to 1e-12."""
+    G = need_gpu()
+    w = X.make_workload("water2_pbe_small")
+    nbf = w.basis.nbf
+    ctx = G.Context(0)
+    try:
+        a = ctx.load_molecule(w.mol, w.basis, w.grid, device_planner=True)
+        path = str(tmp_path / "w2.plan")
+        G.gbxc_save_plan(ctx.h, a, path)
+        b, _ = G.gbxc_load_basis(ctx.h, w.mol.xyz, w.mol.Z, w.basis.atom, w.basis.L, w.basis.nprim,
+                                 w.basis.alpha, w.basis.coeff)
+        G.gbxc_load_plan(ctx.h, b, path)
+        out = []
+        for mid in (a, b):
+            V = np.zeros((nbf, nbf))
+            E, N = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", "mixed", V)
+            out.append((E, N, V))
+        assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+        assert np.max(np.abs(out[0][2] - out[1][2])) <= 1e-12 * np.max(np.abs(out[0][2]))
+    finally:
+        ctx.close()
