@@ -1,6 +1,8 @@
 """Degenerate and edge inputs through the C-ABI against the oracle (Algorithm 4, Eqs. rho/exc/
 vxc): zero density, densities straddling the rho < 1e-15 cut, single atoms (partition of unity
-with one centre), and batches capped at 16 points (nearly empty 128-point tiles)."""
+with one centre), batches capped at 16 points (nearly empty 128-point tiles), tiny shapes
+(n = 1, 3, 6 functions; m = 1, 31, 33 points); plus the library's own edge behaviour (unload,
+the 974-point grid, work-order invariance, non-finite P, plan files)."""
 import numpy as np
 import pytest
 
@@ -212,3 +214,36 @@ def test_plan_file_reload_integrates_identically(tmp_path):
         assert np.max(np.abs(out[0][2] - out[1][2])) <= 1e-12 * np.max(np.abs(out[0][2]))
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("L", [0, 1, 2])
+@pytest.mark.parametrize("m", [1, 31, 33])
+def test_tiny_shapes(L, m):
+    """Tiny shapes: one atom with one shell (n = 1, 3 or 6 functions) and a grid of m points on
+    one ray (m = 1: a single point; 31 and 33: one short of and one past a 32-point warp), so
+    the only batch is a nearly empty tile."""
+    G = need_gpu()
+    mol = X.single_atom(8)
+    basis = X.make_basis(mol, single_shell=(L, [5.0, 1.0, 0.3], [0.3, 0.5, 0.4]))
+    spec = X.GridSpec(m, 1, 1, "becke", 512)
+    S = X.overlap_matrix(basis)
+    P = X.density_matrix(S, 1, 9500 + 10 * L + m)
+    ctx = G.Context(0)
+    try:
+        mid = ctx.load_molecule(mol, basis, spec)
+        info = G.gbxc_plan_info_get(ctx.h, mid)
+        assert info["npts"] == m and info["nbatch"] == 1
+        out = {}
+        for f in ("fp64", "mixed"):
+            V = np.zeros((basis.nbf, basis.nbf))
+            E, N = G.gbxc_integrate(ctx.h, mid, P, "pbe", f, V)
+            out[f] = (E, N, V)
+    finally:
+        ctx.close()
+    g = I.make_grid(mol.xyz, spec)
+    pl = I.make_plan(g, mol.xyz, basis, spec)
+    ref = I.integrate_method(g, basis, P, "pbe", pl)
+    E, N, V = out["fp64"]
+    assert abs(E - ref.E) <= 1e-9 and abs(N - ref.N) <= 1e-9 and np.max(np.abs(V - ref.V)) <= 1e-9
+    Em, Nm, Vm = out["mixed"]
+    assert abs(Em - ref.E) <= 1e-7 and np.max(np.abs(Vm - ref.V)) <= 1e-6
