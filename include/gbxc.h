@@ -178,6 +178,16 @@ int gbxc_load_grid(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
 int gbxc_load_grid_device(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long *npts_out,
                           int *nbatch_out);
 
+/* Tracing and test hook: integrate batch `batch` alone (as gbxc_integrate_batches) and copy
+ * its per-point intermediates out of the scratch slabs, point-major m x n row-major (m points
+ * of the batch in batch order, n its functions in the batch's function order; both from
+ * gbxc_export_plan / gbxc_plan_info_get): Phi and dPhi/dx, dPhi/dy, dPhi/dz as collocated
+ * (Eq. gau_cart and its gradient), and Z (Eq. z_mat) as formed for the V contraction, in
+ * float64 (double-float pairs summed for the mixed form).  Any output may be NULL.
+ * functional GBXC_SLATER or GBXC_PBE; GBXC_EINVAL if the batch needs more than one chunk. */
+int gbxc_debug_batch(gbxc_ctx *ctx, int mol, int batch, const double *P, int functional, int precision,
+                     double *phi, double *gx, double *gy, double *gz, double *z);
+
 /* Plan files (checkpoint / resume of the resident grid): gbxc_save_plan writes the grid spec,
  * the points in batch order (x, y, z, w^q, parent atom, generation index) and the merged
  * batches with their shell lists of `mol` to `path`; gbxc_load_plan reads such a file for a

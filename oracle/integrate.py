@@ -119,6 +119,25 @@ def integrate_batch(pts, w, phi_args, Pj, fn):
     return float(np.sum(eps_w)), float(np.sum(w * rho)), Vj
 
 
+def batch_intermediates(grid: Grid, basis, P, functional: str, plan: planner.Plan, j: int):
+    """Phi, grad Phi and Z (Eqs. gau_cart, x_mat ... z_mat) of merged batch j, point-major
+    (points in the plan's batch order, functions in the batch's function order)."""
+    fn = functionals.FUNCTIONALS[functional]
+    idx = plan.batch_points[j]
+    F = plan.batch_funcs[j]
+    pts = np.stack([grid.x[idx], grid.y[idx], grid.z[idx]], axis=1)
+    phi, gx, gy, gz = collocation.collocate(pts, basis, plan.batch_shells[j])
+    X = phi @ P[np.ix_(F, F)]
+    rho = np.sum(phi * X, axis=1)
+    grad = [2.0 * np.sum(g * X, axis=1) for g in (gx, gy, gz)]
+    sigma = grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]
+    f, vr, vs = fn(rho, sigma)
+    w = grid.w[idx]
+    Z = (0.5 * w * vr)[:, None] * phi + (2.0 * w * vs)[:, None] * (grad[0][:, None] * gx + grad[1][:, None] * gy
+                                                                 + grad[2][:, None] * gz)
+    return phi, gx, gy, gz, Z
+
+
 def integrate_method(grid: Grid, basis, P, functional: str, plan: planner.Plan,
                      batches=None) -> Result:
     """Method-equivalent mode over the merged batches of ``plan`` (or a subset)."""

@@ -37,7 +37,8 @@ EXPORTED = ["gbxc_create", "gbxc_destroy", "gbxc_last_error", "gbxc_load_basis",
             "gbxc_profile_enable", "gbxc_profile_read", "gbxc_integrate_fp64_noalloc",
             "gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
             "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule", "gbxc_load_grid_device",
-            "gbxc_load_basis_pure", "gbxc_integrate_uks", "gbxc_unload", "gbxc_save_plan", "gbxc_load_plan"]
+            "gbxc_load_basis_pure", "gbxc_integrate_uks", "gbxc_unload", "gbxc_save_plan", "gbxc_load_plan",
+            "gbxc_debug_batch"]
 KERNEL_CLASSES = ["weights", "colloc", "xgemm", "rho_z", "vgemm", "finish", "pgather", "graph", "vslice"]
 GBXC_NKERNEL = len(KERNEL_CLASSES)
 
@@ -94,6 +95,8 @@ def lib():
     L.gbxc_load_grid_device.restype = c_int
     L.gbxc_unload.argtypes = [c_void_p, c_int]
     L.gbxc_unload.restype = c_int
+    L.gbxc_debug_batch.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int, c_int] + [c_void_p] * 5
+    L.gbxc_debug_batch.restype = c_int
     L.gbxc_save_plan.argtypes = [c_void_p, c_int, ctypes.c_char_p]
     L.gbxc_save_plan.restype = c_int
     L.gbxc_load_plan.argtypes = [c_void_p, c_int, ctypes.c_char_p, POINTER(c_longlong), POINTER(c_int)]
@@ -224,6 +227,15 @@ def gbxc_load_grid_device(ctx, mol, nrad, ntheta, nphi, partition, max_batch, et
 
 def gbxc_unload(ctx, mol):
     _check(ctx, lib().gbxc_unload(ctx, mol))
+
+
+def gbxc_debug_batch(ctx, mol, batch, P, functional, precision, m, n):
+    """Phi, grad Phi (3) and Z of one batch as m x n float64 arrays (see gbxc.h)."""
+    out = [np.zeros((m, n)) for _ in range(5)]
+    pP, kP, _ = _ptr(P)
+    _check(ctx, lib().gbxc_debug_batch(ctx, mol, batch, pP, FUNCTIONALS.get(functional, functional),
+                                       PRECISIONS.get(precision, precision), *[o.ctypes.data for o in out]))
+    return out
 
 
 def gbxc_save_plan(ctx, mol, path):

@@ -1489,6 +1489,62 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
     });
 }
 
+int gbxc_debug_batch(gbxc_ctx *ctx, int mol, int batch, const double *P, int functional, int precision,
+                     double *phi, double *gx, double *gy, double *gz, double *z) {
+    if (!ctx) return GBXC_EINVAL;
+    return guarded(ctx, [&] {
+        REQUIRE(ctx->device >= 0, "needs a device context");
+        Molecule &m = get_mol(ctx, mol);
+        if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
+        REQUIRE(batch >= 0 && batch < m.plan.nbatch(), "batch out of range");
+        REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "spin-restricted LDA/GGA only");
+        double E, N;
+        int rc = integrate_impl(ctx, mol, P, functional, precision, batch, batch + 1, &E, nullptr, &N, nullptr,
+                                nullptr, nullptr);
+        if (rc != GBXC_OK) return rc;
+        const Schedule &S = get_schedule(m, precision, batch, batch + 1, scratch_budget(ctx));
+        REQUIRE(S.chunks.size() == 1, "the batch does not fit one chunk");
+        const Schedule::Chunk &c = S.chunks[0];
+        const size_t plane = (size_t)c.rows * TILE;
+        std::vector<char> slab((size_t)c.rows * row_bytes(precision));
+        check(cudaMemcpy(slab.data(), ctx->ws.scratch, slab.size(), cudaMemcpyDeviceToHost), "copy slabs");
+        // value of component comp (0 Phi, 1-3 grad Phi, 4 Z) at slab element e
+        auto value = [&](int comp, size_t e) -> double {
+            if (precision == GBXC_FP64) {
+                const int planes[5] = {0, 1, 2, 3, 5};
+                return reinterpret_cast<const double *>(slab.data())[(size_t)planes[comp] * plane + e];
+            }
+            const MixedSlabOffsets o = mixed_slab_offsets(c.rows);
+            auto bf = [](uint16_t b) {
+                uint32_t u = (uint32_t)b << 16;
+                float f;
+                std::memcpy(&f, &u, 4);
+                return (double)f;
+            };
+            if (comp == 0 || comp == 4) {
+                const float *f = reinterpret_cast<const float *>(slab.data() + (comp == 0 ? o.phi : o.x));
+                return (double)f[2 * e] + (double)f[2 * e + 1];
+            }
+            const float *h = reinterpret_cast<const float *>(slab.data() + o.ghi);
+            const uint16_t *l = reinterpret_cast<const uint16_t *>(slab.data() + o.glo);
+            return (double)h[(size_t)(comp - 1) * plane + e] + bf(l[(size_t)(comp - 1) * plane + e]);
+        };
+        const HostPlan &Pl = m.plan;
+        const int64_t n = Pl.func_ptr[batch + 1] - Pl.func_ptr[batch];
+        double *outs[5] = {phi, gx, gy, gz, z};
+        for (int64_t t = Pl.batch_tile[batch]; t < Pl.batch_tile[batch + 1]; ++t) {
+            const int64_t r0 = Pl.tile_row[t] - c.row0;
+            for (int i = 0; i < Pl.tile_count[t]; ++i) {
+                const int64_t p = Pl.tile_first[t] + i - Pl.batch_ptr[batch];
+                for (int64_t mu = 0; mu < n; ++mu)
+                    for (int comp = 0; comp < 5; ++comp)
+                        if (outs[comp]) outs[comp][p * n + mu] = value(comp, (size_t)(r0 + mu) * TILE + i);
+            }
+        }
+        return GBXC_OK;
+    });
+}
+
 int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int functional, double *Vxc,
                                 double *EN, void *stream) {
     if (!ctx) return GBXC_EINVAL;

@@ -77,6 +77,13 @@ struct MixedSchedule {
 };
 
 size_t mixed_row_bytes();
+// Byte offsets, within a chunk's scratch of `rows` slab rows, of the mixed form's planes that
+// hold per-point values: Phi (float2 hi/lo), grad Phi hi words (3 float planes), their lo words
+// (3 bf16 planes) and X / Z (float2 hi/lo); each plane is rows x 128 points.
+struct MixedSlabOffsets {
+    size_t phi, ghi, glo, x;
+};
+MixedSlabOffsets mixed_slab_offsets(int64_t rows);
 // Tile widths the tcgen05 GEMMs are built for; `bn` below is one of them.
 bool mixed_tile_supported(int bn);
 // Largest padded N_b^j the tensor-core form takes (its exact accumulator levels need it).

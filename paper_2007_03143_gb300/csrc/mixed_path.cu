@@ -1280,6 +1280,16 @@ cudaError_t grow(T *&p, size_t &cap, size_t need) {
 
 }  // namespace
 
+MixedSlabOffsets mixed_slab_offsets(int64_t rows) {
+    const size_t plane = (size_t)rows * TILE;
+    MixedSlabOffsets o;
+    o.phi = 0;
+    o.ghi = o.phi + plane * 8;
+    o.glo = o.ghi + 3 * plane * 4;
+    o.x = o.glo + 3 * plane * 2;
+    return o;
+}
+
 size_t mixed_row_bytes() { return (size_t)TILE * (8 + 12 + 6 + 8 + 3 * NSL * 2) + 8 + 16; }
 
 bool mixed_tile_supported(int bn) { return bn == 128 || bn == 64; }
