@@ -55,6 +55,8 @@ struct Molecule {
     std::vector<DevShell> shells;
     DevShell *d_shells = nullptr;
     double *d_atoms = nullptr, *d_rnn = nullptr;
+    int *d_nbr = nullptr;           // natoms x (natoms - 1) neighbours of each atom by distance
+    double *d_nbr_r = nullptr;      // and their distances
     bool has_grid = false;
     gbxc_grid_spec spec{};
     HostPlan plan;
@@ -294,6 +296,8 @@ void free_molecule(Molecule &m) {
     free_mixed_resident(m.mixed_res);
     cudaFree(m.d_atoms);
     cudaFree(m.d_rnn);
+    cudaFree(m.d_nbr);
+    cudaFree(m.d_nbr_r);
     cudaFree(m.many_P);
     cudaFree(m.many_V);
     cudaFree(m.many_tot);
@@ -1156,6 +1160,29 @@ int gbxc_load_basis_pure(gbxc_ctx *ctx, int natoms, const double *xyz, const int
         check(cudaMalloc(&m->d_rnn, sizeof(double) * natoms), "cudaMalloc rnn");
         check(cudaMemcpy(m->d_rnn, rnn.data(), sizeof(double) * natoms, cudaMemcpyHostToDevice),
               "upload rnn");
+        // neighbour lists by distance (ties by index) for the SSF screening of the weights
+        const size_t nn1 = (size_t)natoms * (size_t)std::max(natoms - 1, 0);
+        std::vector<int> nbr(std::max<size_t>(nn1, 1), 0);
+        std::vector<double> nbr_r(std::max<size_t>(nn1, 1), 0.0);
+        for (int a = 0; a < natoms; ++a) {
+            std::vector<std::pair<double, int>> d;
+            for (int b = 0; b < natoms; ++b) {
+                if (a == b) continue;
+                double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
+                       dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+                d.emplace_back(std::sqrt(dx * dx + dy * dy + dz * dz), b);
+            }
+            std::sort(d.begin(), d.end());
+            for (size_t k = 0; k < d.size(); ++k) {
+                nbr[(size_t)a * (natoms - 1) + k] = d[k].second;
+                nbr_r[(size_t)a * (natoms - 1) + k] = d[k].first;
+            }
+        }
+        check(cudaMalloc(&m->d_nbr, sizeof(int) * nbr.size()), "cudaMalloc neighbours");
+        check(cudaMemcpy(m->d_nbr, nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice), "upload neighbours");
+        check(cudaMalloc(&m->d_nbr_r, sizeof(double) * nbr_r.size()), "cudaMalloc neighbour distances");
+        check(cudaMemcpy(m->d_nbr_r, nbr_r.data(), sizeof(double) * nbr_r.size(), cudaMemcpyHostToDevice),
+              "upload neighbour distances");
         int id = ctx->next_id++;
         *mol_out = id;
         if (nbf_out) *nbf_out = m->nbf;
@@ -1232,6 +1259,8 @@ int finish_grid(gbxc_ctx *ctx, Molecule &m, const gbxc_grid_spec *spec, bool hos
     wa.parent = m.dev.parent;
     wa.atoms = m.d_atoms;
     wa.rnn = m.d_rnn;
+    wa.nbr = m.d_nbr;
+    wa.nbr_r = m.d_nbr_r;
     wa.w = m.dev.w;
     wa.npts = P.npts;
     wa.natoms = m.natoms;

@@ -143,6 +143,8 @@ struct WeightsArgs {
     const int *parent;
     const double *atoms;      // natoms x 3
     const double *rnn;        // natoms nearest-neighbour distances
+    const int *nbr;           // natoms x (natoms - 1): the other atoms of each atom by distance
+    const double *nbr_r;      // their distances
     double *w;
     int64_t npts;
     int natoms;

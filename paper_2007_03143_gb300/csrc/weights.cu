@@ -7,9 +7,14 @@
 // P_B(r) = prod_{C != B} s(mu_BC), mu_BC = (|r-R_B| - |r-R_C|)/R_BC,
 // p_A = P_A / sum_B P_B.
 //
-// The natoms^2 loop is screened in the SSF case with an exact rule: if some
-// atom C has mu_BC >= a then s(mu_BC) = 0 and P_B = 0, so B is skipped once
-// that is seen for the atom C nearest to the point.
+// The natoms^2 loop is screened in the SSF case by two exact rules (the skipped factors are
+// exactly 0 or 1; only the order of the products changes).  (1) P_B = 0 when mu_Bn >= a for
+// the atom n nearest to the point.  (2) By the triangle inequality |r-R_C| >= R_BC - |r-R_B|,
+// so mu_BC <= 2|r-R_B|/R_BC - 1, which is <= -a (s = 1 exactly) once R_BC >= 2|r-R_B|/(1-a):
+// the factors of P_B are taken over B's neighbours in order of distance (lists built on the
+// host per molecule) and stop there.  The outer loop over B stays in atom order, so the
+// threads of a warp take the same B together (a candidate list per point, from the nearest
+// atom's neighbours, was measured slower: divergent).
 #include <cstdint>
 
 #include "internal.h"
@@ -63,7 +68,7 @@ __global__ void partition_weights_kernel(WeightsArgs a) {
         p = 1.0;
     } else if (a.scheme == GBXC_SSF && dist(A) < 0.5 * (1.0 - kSsfA) * a.rnn[A]) {
         p = 1.0;
-    } else {
+    } else if (a.scheme == GBXC_SSF) {
         int nearest = 0;
         double dn = dist(0);
         for (int k = 1; k < a.natoms; ++k) {
@@ -71,23 +76,33 @@ __global__ void partition_weights_kernel(WeightsArgs a) {
             if (d < dn) { dn = d; nearest = k; }
         }
         double sum = 0.0, pa = 0.0;
+        for (int B = 0; B < a.natoms; ++B) {   // every thread of a warp visits the same B
+            const double dB = dist(B);
+            double PB = 1.0;
+            if (B != nearest && (dB - dn) / rab(B, nearest) >= kSsfA) {
+                PB = 0.0;
+            } else {
+                const int *nb = a.nbr + (size_t)B * (a.natoms - 1);
+                const double *nr = a.nbr_r + (size_t)B * (a.natoms - 1);
+                const double lim = 2.0 * dB / (1.0 - kSsfA);
+                for (int k = 0; k < a.natoms - 1 && PB != 0.0; ++k) {
+                    const double R = nr[k];
+                    if (R >= lim) break;          // every further factor is exactly 1
+                    PB *= ssf_s((dB - dist(nb[k])) / R);
+                }
+            }
+            sum += PB;
+            if (B == A) pa = PB;
+        }
+        p = pa / sum;
+    } else {   // Becke: every pair
+        double sum = 0.0, pa = 0.0;
         for (int B = 0; B < a.natoms; ++B) {
             double dB = dist(B);
             double PB = 1.0;
-            if (a.scheme == GBXC_SSF) {
-                if (B != nearest && (dB - dn) / rab(B, nearest) >= kSsfA) {
-                    PB = 0.0;
-                } else {
-                    for (int C = 0; C < a.natoms && PB != 0.0; ++C) {
-                        if (C == B) continue;
-                        PB *= ssf_s((dB - dist(C)) / rab(B, C));
-                    }
-                }
-            } else {
-                for (int C = 0; C < a.natoms; ++C) {
-                    if (C == B) continue;
-                    PB *= becke_s((dB - dist(C)) / rab(B, C));
-                }
+            for (int C = 0; C < a.natoms; ++C) {
+                if (C == B) continue;
+                PB *= becke_s((dB - dist(C)) / rab(B, C));
             }
             sum += PB;
             if (B == A) pa = PB;
