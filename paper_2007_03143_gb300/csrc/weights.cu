@@ -42,9 +42,13 @@ __device__ __forceinline__ double ssf_s(double mu) {
     return 0.5 * (1.0 - g);
 }
 
+// CACHE: the point's distances to every atom are computed once into shared memory
+// ([atom][thread], so the threads of a warp read one row) and the SSF pair loops read them.
+template <bool CACHE>
 __global__ void partition_weights_kernel(WeightsArgs a) {
     extern __shared__ double sm[];
     double *ax = sm, *ay = sm + a.natoms, *az = sm + 2 * a.natoms;
+    double *dc = sm + 3 * a.natoms;   // CACHE: natoms x blockDim.x
     for (int k = threadIdx.x; k < a.natoms; k += blockDim.x) {
         ax[k] = a.atoms[3 * k];
         ay[k] = a.atoms[3 * k + 1];
@@ -55,9 +59,13 @@ __global__ void partition_weights_kernel(WeightsArgs a) {
     if (i >= a.npts) return;
     double px = a.x[i], py = a.y[i], pz = a.z[i];
     int A = a.parent[i];
-    auto dist = [&](int k) {
+    auto dist0 = [&](int k) {
         double dx = px - ax[k], dy = py - ay[k], dz = pz - az[k];
         return sqrt(dx * dx + dy * dy + dz * dz);
+    };
+    auto dist = [&](int k) {
+        if constexpr (CACHE) return dc[(size_t)k * blockDim.x + threadIdx.x];
+        else return dist0(k);
     };
     auto rab = [&](int k, int l) {
         double dx = ax[k] - ax[l], dy = ay[k] - ay[l], dz = az[k] - az[l];
@@ -66,13 +74,15 @@ __global__ void partition_weights_kernel(WeightsArgs a) {
     double p;
     if (a.natoms == 1) {
         p = 1.0;
-    } else if (a.scheme == GBXC_SSF && dist(A) < 0.5 * (1.0 - kSsfA) * a.rnn[A]) {
+    } else if (a.scheme == GBXC_SSF && dist0(A) < 0.5 * (1.0 - kSsfA) * a.rnn[A]) {
         p = 1.0;
     } else if (a.scheme == GBXC_SSF) {
         int nearest = 0;
-        double dn = dist(0);
+        double dn = dist0(0);
+        if constexpr (CACHE) dc[threadIdx.x] = dn;
         for (int k = 1; k < a.natoms; ++k) {
-            double d = dist(k);
+            double d = dist0(k);
+            if constexpr (CACHE) dc[(size_t)k * blockDim.x + threadIdx.x] = d;
             if (d < dn) { dn = d; nearest = k; }
         }
         double sum = 0.0, pa = 0.0;
@@ -98,11 +108,11 @@ __global__ void partition_weights_kernel(WeightsArgs a) {
     } else {   // Becke: every pair
         double sum = 0.0, pa = 0.0;
         for (int B = 0; B < a.natoms; ++B) {
-            double dB = dist(B);
+            double dB = dist0(B);
             double PB = 1.0;
             for (int C = 0; C < a.natoms; ++C) {
                 if (C == B) continue;
-                PB *= becke_s((dB - dist(C)) / rab(B, C));
+                PB *= becke_s((dB - dist0(C)) / rab(B, C));
             }
             sum += PB;
             if (B == A) pa = PB;
@@ -117,11 +127,21 @@ __global__ void partition_weights_kernel(WeightsArgs a) {
 cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s) {
     if (a.npts == 0) return cudaSuccess;
     if (a.natoms > kMaxAtomsSmem) return cudaErrorInvalidValue;
+    // SSF with the distance cache when 128 threads' distances fit in 200 KB (up to 195 atoms)
+    const size_t cache = sizeof(double) * (size_t)a.natoms * 128;
+    const bool use_cache = a.scheme == GBXC_SSF && cache <= (size_t)200 * 1024;
     int threads = 128;
     int64_t blocks = (a.npts + threads - 1) / threads;
-    size_t smem = sizeof(double) * 3 * a.natoms;
+    size_t smem = sizeof(double) * 3 * a.natoms + (use_cache ? cache : 0);
     if (a.prof) a.prof->begin(GBXC_K_WEIGHTS, s);
-    partition_weights_kernel<<<(unsigned)blocks, threads, smem, s>>>(a);
+    if (use_cache) {
+        cudaError_t e = cudaFuncSetAttribute(partition_weights_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        partition_weights_kernel<true><<<(unsigned)blocks, threads, smem, s>>>(a);
+    } else {
+        partition_weights_kernel<false><<<(unsigned)blocks, threads, smem, s>>>(a);
+    }
     if (a.prof) a.prof->end(GBXC_K_WEIGHTS, s);
     return cudaGetLastError();
 }
