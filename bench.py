@@ -168,13 +168,15 @@ def _traffic(kernel, form):
 # Per-unit work of each kernel class (the unit is one batch's (point, function) element, or
 # 2 m n^2 flops for a contraction).  Contractions: algorithmic flops 2 m n^2 each; the mixed
 # form issues 15 bf16 slice products per term, so its tensor work is 15 x 2 m n^2.
-# Streaming steps: the bytes of the step's inputs and outputs at the precision the form
-# carries (double-float = 8 B per value in the mixed form, float64 = 8 B):
-#   colloc  writes Phi and grad Phi (4 values) [+ 5 bf16 Phi slices in the mixed form]
-#   rho_z   reads Phi, grad Phi, X (5 values), writes Z (1 value)
-#   vslice  reads Z and Phi (2 values), writes 10 bf16 slices
+# Streaming steps: the bytes of the step's inputs and outputs at the widths the form stores
+# them (float64 form: 8 B per value; mixed form: Phi as a float pair, 8 B, grad Phi as a float
+# hi word plus a bf16 lo word, 6 B per component, bf16 slices 2 B):
+#   colloc  writes Phi and grad Phi [+ 5 bf16 Phi slices in the mixed form]
+#   rho_z   float64: reads Phi, grad Phi, X, writes Z; mixed: reads Phi, grad Phi, X
+#           (Z is formed in the slicing kernel from per-point coefficients)
+#   vslice  mixed: reads Phi and the grad Phi hi words, writes 5 Z and 5 Phi bf16 slices
 STREAM_BYTES = {"fp64": {"colloc": 32, "rho_z": 48},
-                "mixed": {"colloc": 32 + 10, "rho_z": 48, "vslice": 16 + 20}}
+                "mixed": {"colloc": 8 + 18 + 10, "rho_z": 8 + 18 + 8, "vslice": 8 + 12 + 20}}
 
 
 def roofline(kind, ms, form, info, peaks, peak_src):

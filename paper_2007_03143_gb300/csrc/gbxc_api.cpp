@@ -1528,6 +1528,12 @@ int gbxc_debug_batch(gbxc_ctx *ctx, int mol, int batch, const double *P, int fun
         REQUIRE(batch >= 0 && batch < m.plan.nbatch(), "batch out of range");
         REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "spin-restricted LDA/GGA only");
         double E, N;
+        // the mixed form forms Z inside its slicing kernel; keep_z makes it leave Z in the slab
+        struct KeepZ {
+            MixedCtx &c;
+            explicit KeepZ(MixedCtx &x) : c(x) { c.keep_z = 1; }
+            ~KeepZ() { c.keep_z = 0; }
+        } keep(ctx->ws.mixed);
         int rc = integrate_impl(ctx, mol, P, functional, precision, batch, batch + 1, &E, nullptr, &N, nullptr,
                                 nullptr, nullptr);
         if (rc != GBXC_OK) return rc;

@@ -39,6 +39,7 @@ struct MixedCtx {
     size_t ax_g_cap = 0, y_g_cap = 0, pexp_g_cap = 0, wexp_g_cap = 0, gexp_g_cap = 0;
     int64_t mgga_rows = 0;
     int num_sms = 0;                   // persistent-GEMM grid size
+    int keep_z = 0;                    // spin-restricted chunks also leave Z in the X plane
     int *d_err = nullptr;
 };
 // A shell with every constant split into a double-float pair (hi + lo).

@@ -19,9 +19,10 @@
 // partition weights, the functional and all E/N/V accumulation in float64.
 //
 // Kernels per chunk of tiles: pslice (P^j row slices), colloc (Phi, grad Phi, Phi slices),
-// xgemm (tcgen05), rho_z (rho, grad rho, functional, E/N partials, Z in double-float and
-// per-tile exponent maxima), slice_v (Z and Phi slices per V task), vgemm (tcgen05,
-// scatter into V_acc with float64 atomics).
+// xgemm (tcgen05), rho (rho, grad rho, functional, E/N partials, per-point Z coefficients),
+// z_slice (Z in double-float, group exponent maxima, Z and Phi slices per V task), vgemm
+// (tcgen05, scatter into V_acc with float64 atomics).  The spin-unrestricted and meta-GGA
+// forms form Z in their rho kernels (two passes over Phi) and slice it with slice_v.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -103,6 +104,7 @@ struct MixedArgs {
     int *pexp;                   // row exponents of P^j
     const float *ph, *pl;        // P as double-float planes (nbf x nbf each)
     int *err;
+    int keep_z;                  // z_slice also writes Z over X (per-batch debugging copy)
 };
 
 __device__ __forceinline__ int pad32(int n) { return (n + 31) & ~31; }
@@ -756,8 +758,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
     if (warp == 2) umma::tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// ---------------------------------------------------------------- rho, functional, Z
-__global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
+// ---------------------------------------------------------------- rho, functional (spin-restricted)
+// rho and grad rho (Eqs. eval_local_den, eval_local_den_grad) in double-float over the batch's
+// functions, the functional and the tile's E/N partials (Eq. exc_batch) in float64.  Z (Eq.
+// z_mat) is not formed here: the per-point coefficients a_i = 1/2 w vrho and
+// b_i = 2 w vsigma grad rho go, as float64, to the first four rows of the tile's X plane (X is
+// dead once rho is formed; a tile has at least FBLK = 32 rows), and z_slice forms Z from them
+// while slicing it, so Z never travels through memory.  Thread i reads and writes column i
+// only, so the overwrite needs no barrier.
+__global__ void __launch_bounds__(TILE) rho_mixed(ChunkArgs a, MixedArgs m) {
     int64_t t = a.t0 + blockIdx.x;
     int i = threadIdx.x;
     int j = a.plan.tile_batch[t];
@@ -767,7 +776,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     const float2 *phi = m.s.phi;
-    if (np > MAX_NP) {   // the exponent scratch below holds MAX_NP rows; larger batches are rejected
+    if (np > MAX_NP) {   // the exponent scratch holds MAX_NP rows; larger batches are rejected
         if (i == 0) atomicOr(m.err, 8);
         return;
     }
@@ -788,7 +797,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     double r = df_to_d(rho);
     double dx = 2.0 * df_to_d(gx), dy = 2.0 * df_to_d(gy), dz = 2.0 * df_to_d(gz);
     double e = 0.0, nn = 0.0;
-    double ca_d = 0.0, bx_d = 0.0, by_d = 0.0, bz_d = 0.0;
+    double coef[4] = {0.0, 0.0, 0.0, 0.0};
     if (i < cnt) {
         double w = a.plan.w[a.plan.tile_first[t] + i];
         double sigma = dx * dx + dy * dy + dz * dz;
@@ -796,53 +805,15 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
         xc::evaluate<double>(a.functional, r, sigma, f, vr, vs);
         e = w * f;
         nn = w * r;
-        ca_d = 0.5 * w * vr;
+        coef[0] = 0.5 * w * vr;
         double b = 2.0 * w * vs;
-        bx_d = b * dx;
-        by_d = b * dy;
-        bz_d = b * dz;
+        coef[1] = b * dx;
+        coef[2] = b * dy;
+        coef[3] = b * dz;
     }
-    // Z (Eq. z_mat) in double-float, written over X (each thread touches its own point);
-    // maxima of |Z| and |Phi| per function row over the tile's points, kept as float bits
-    // (non-negative floats order like their bit patterns) for the V-side slicing exponents
-    __shared__ int zmax[MAX_NP], fmx[MAX_NP];
-    for (int mu = i; mu < np; mu += TILE) {
-        zmax[mu] = 0;
-        fmx[mu] = 0;
-    }
-    __syncthreads();
-    df cz = d_to_df(ca_d), cbx = d_to_df(bx_d), cby = d_to_df(by_d), cbz = d_to_df(bz_d);
-    int lane = i & 31;
-    // rows >= N_b^j of the V operands are never used (they only feed discarded outputs)
-#pragma unroll 2
-    for (int mu = 0; mu < n; ++mu) {
-        size_t o = (size_t)(r0 + mu) * TILE + i;
-        // the gradient terms take the hi words only (dropping the low words moved max|dV|
-        // against float64 from 9.2e-8 to 9.4e-8 on the 16-water workload), while rho and
-        // grad rho above use both words: without them |dE_xc| grew from 7e-10 to 6e-8 Eh
-        const float2 f0 = phi[o];
-        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
-        df z = df_mul(cz, {f0.x, f0.y});
-        z = df_add(z, dfl::mul_f(cbx, h1));
-        z = df_add(z, dfl::mul_f(cby, h2));
-        z = df_add(z, dfl::mul_f(cbz, h3));
-        m.s.x[o] = make_float2(z.h, z.l);
-        float az = fabsf(z.h), ap = fabsf(f0.x);
+    double *cz = reinterpret_cast<double *>(m.s.x);
 #pragma unroll
-        for (int q = 16; q > 0; q >>= 1) {
-            az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
-            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
-        }
-        if (lane == 0) {
-            atomicMax(&zmax[mu], __float_as_int(az));
-            atomicMax(&fmx[mu], __float_as_int(ap));
-        }
-    }
-    __syncthreads();
-    for (int mu = i; mu < n; mu += TILE) {
-        m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[mu]));
-        m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu]));
-    }
+    for (int q = 0; q < 4; ++q) cz[(size_t)(r0 + q) * TILE + i] = coef[q];
     __shared__ double re[TILE], rn[TILE];
     re[i] = e;
     rn[i] = nn;
@@ -857,6 +828,148 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed(ChunkArgs a, MixedArgs m) {
     if (i == 0) {
         a.tileE[t] = re[0];
         a.tileN[t] = rn[0];
+    }
+}
+
+// ---------------------------------------------------------------- Z and the V-side slices (spin-restricted)
+// Per K group (the up to VKS tiles of one batch that form one V task) and function row mu:
+// Z_i,mu = a_i Phi_i,mu + b_i . grad Phi_i,mu (Eq. z_mat, double-float, gradient hi words),
+// the exponents of max |Z| and max |Phi| per tile, their maximum over the group, and the bf16
+// slices of Z and Phi in the layout of slice_v; the group exponents go to the group's first
+// tile for the V epilogue.  The block's eight 16-thread slots cover G2 tiles (the group size
+// rounded up to a power of two) for 8 / G2 rows at a time, 8 points per thread, so Z and Phi
+// stay in registers while the slots exchange their tile exponents through shared memory (one
+// barrier per step, double-buffered): every element is read once.  The blocks of a group's
+// tiles share its rows (row step k to block k mod group size), so the grid keeps one block per
+// tile.  With keep_z the values of Z are also written over X for the per-batch debugging copy;
+// the group's first block then does every row, because those writes cover the coefficient rows
+// the other blocks read.
+// Shared-memory slot of point p's coefficient: an XOR of p's octet bits (p >> 4) into its low
+// three bits, so the 16 threads of a slot (points 8 pg + k, one k) read 16 distinct bank pairs
+// instead of two.
+__device__ __forceinline__ int cf_slot(int p) { return p ^ ((p >> 4) & 7); }
+
+__global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
+    const int64_t t = a.t0 + blockIdx.x;
+    const int j = a.plan.tile_batch[t];
+    const int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
+    const int np = pad32(n);
+    const int64_t s0 = a.plan.batch_tile[j] > a.t0 ? a.plan.batch_tile[j] : a.t0;
+    const int64_t s1 = a.plan.batch_tile[j + 1] < a.t1 ? a.plan.batch_tile[j + 1] : a.t1;
+    const int64_t g0 = s0 + (t - s0) / VKS * VKS;
+    const int ng = (int)((g0 + VKS < s1 ? g0 + VKS : s1) - g0);
+    const int ub = (int)(t - g0), nblk = m.keep_z ? 1 : ng;
+    if (ub >= nblk) return;   // block-uniform
+    const int64_t rg = a.plan.tile_row[g0] - a.row0;
+    const size_t plane = (size_t)m.rows * TILE;
+    // the group's per-point coefficients (a, b_x, b_y, b_z) as double-float pairs
+    __shared__ float2 cf[VKS][4][TILE];
+    __shared__ int64_t trow[VKS];
+    __shared__ int red[2][8][2];   // per step parity and slot: tile exponents of |Z|, |Phi|
+    const double *cz = reinterpret_cast<const double *>(m.s.x);
+    for (int u = 0; u < ng; ++u) {
+        const int64_t ru = a.plan.tile_row[g0 + u] - a.row0;
+        if (threadIdx.x == 0) trow[u] = ru;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const df c = d_to_df(cz[(size_t)(ru + q) * TILE + threadIdx.x]);
+            cf[u][q][cf_slot(threadIdx.x)] = make_float2(c.h, c.l);
+        }
+    }
+    __syncthreads();
+    const int lg = ng > 4 ? 3 : ng > 2 ? 2 : ng > 1 ? 1 : 0;   // G2 = 2^lg tiles per row
+    const int R = 8 >> lg;                                       // rows per step
+    const int slot = threadIdx.x >> 4, pg = threadIdx.x & 15;
+    const int u = slot & ((1 << lg) - 1), rr = slot >> lg;
+    const int pk = pg >> 2, col = (pg & 3) * 8;
+    const int64_t ru = u < ng ? trow[u] : 0;
+    int par = 0;
+    for (int c = ub; c * R < n; c += nblk, par ^= 1) {
+        const int mu = c * R + rr;
+        const bool act = u < ng && mu < n;
+        float zh[8], zl[8], fh[8], fl[8];
+        float az = 0.f, ap = 0.f;
+        const size_t o = (size_t)(ru + mu) * TILE + 8 * pg;
+        if (act) {
+            const float4 *fs = reinterpret_cast<const float4 *>(m.s.phi + o);
+            const float4 *h1 = reinterpret_cast<const float4 *>(m.s.ghi + o);
+            const float4 *h2 = reinterpret_cast<const float4 *>(m.s.ghi + plane + o);
+            const float4 *h3 = reinterpret_cast<const float4 *>(m.s.ghi + 2 * plane + o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {   // points 2q, 2q + 1
+                const float4 f4 = fs[q];
+                const float4 a1 = h1[q >> 1], a2 = h2[q >> 1], a3 = h3[q >> 1];
+                const float gxs[2] = {(q & 1) ? a1.z : a1.x, (q & 1) ? a1.w : a1.y};
+                const float gys[2] = {(q & 1) ? a2.z : a2.x, (q & 1) ? a2.w : a2.y};
+                const float gzs[2] = {(q & 1) ? a3.z : a3.x, (q & 1) ? a3.w : a3.y};
+                fh[2 * q] = f4.x;
+                fl[2 * q] = f4.y;
+                fh[2 * q + 1] = f4.z;
+                fl[2 * q + 1] = f4.w;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int e = 2 * q + k, sp = cf_slot(8 * pg + e);
+                    const float2 c0 = cf[u][0][sp], c1 = cf[u][1][sp], c2 = cf[u][2][sp], c3 = cf[u][3][sp];
+                    df z = df_mul({c0.x, c0.y}, {fh[e], fl[e]});
+                    z = df_add(z, dfl::mul_f({c1.x, c1.y}, gxs[k]));
+                    z = df_add(z, dfl::mul_f({c2.x, c2.y}, gys[k]));
+                    z = df_add(z, dfl::mul_f({c3.x, c3.y}, gzs[k]));
+                    zh[e] = z.h;
+                    zl[e] = z.l;
+                    az = fmaxf(az, fabsf(z.h));
+                    ap = fmaxf(ap, fabsf(fh[e]));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 8; q > 0; q >>= 1) {   // over the 16 threads of the slot (one tile row)
+            az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
+            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
+        }
+        if (pg == 0) {
+            red[par][slot][0] = act ? exp_of(az) : -1000;
+            red[par][slot][1] = act ? exp_of(ap) : -1000;
+        }
+        __syncthreads();
+        int ez = -1000, ep = -1000;
+        for (int v = 0; v < (1 << lg); ++v) {
+            ez = max(ez, red[par][(rr << lg) + v][0]);
+            ep = max(ep, red[par][(rr << lg) + v][1]);
+        }
+        if (!act) continue;
+        if (m.keep_z) {
+            float4 *zo = reinterpret_cast<float4 *>(m.s.x + o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zo[q] = make_float4(zh[2 * q], zl[2 * q], zh[2 * q + 1], zl[2 * q + 1]);
+        }
+        uint32_t wz[NSL][4], wp[NSL][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {   // points 2q, 2q + 1
+            float a0[NSL], a1[NSL], b0[NSL], b1[NSL];
+            slice5(zh[2 * q], zl[2 * q], ez, a0);
+            slice5(zh[2 * q + 1], zl[2 * q + 1], ez, a1);
+            slice5(fh[2 * q], fl[2 * q], ep, b0);
+            slice5(fh[2 * q + 1], fl[2 * q + 1], ep, b1);
+#pragma unroll
+            for (int sl = 0; sl < NSL; ++sl) {
+                __nv_bfloat162 bz = __floats2bfloat162_rn(a0[sl], a1[sl]);
+                __nv_bfloat162 bp = __floats2bfloat162_rn(b0[sl], b1[sl]);
+                wz[sl][q] = *reinterpret_cast<uint32_t *>(&bz);
+                wp[sl][q] = *reinterpret_cast<uint32_t *>(&bp);
+            }
+        }
+        const size_t orow = (size_t)(4 * ru + (int64_t)pk * np + mu) * 32 + col;
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) {
+            *reinterpret_cast<uint4 *>(m.s.vz + (size_t)sl * plane + orow) =
+                make_uint4(wz[sl][0], wz[sl][1], wz[sl][2], wz[sl][3]);
+            *reinterpret_cast<uint4 *>(m.s.vphi + (size_t)sl * plane + orow) =
+                make_uint4(wp[sl][0], wp[sl][1], wp[sl][2], wp[sl][3]);
+        }
+        if (u == 0 && pg == 0) {
+            m.s.zexp[rg + mu] = ez;
+            m.s.fexp[rg + mu] = ep;
+        }
     }
 }
 
@@ -1542,6 +1655,7 @@ MixedArgs chunk_mixed_args(const ChunkArgs &a, MixedCtx &c, const MixedSchedule 
     m.ph = pdf;
     m.pl = pdf + (size_t)a.nbf * a.nbf;
     m.err = c.d_err;
+    m.keep_z = c.keep_z;
     return m;
 }
 
@@ -1640,9 +1754,12 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     run_xgemm(a, m, q, c, s, ch, st);
     Profiler &P = *a.prof;
     P.begin(GBXC_K_RHO_Z, st);
-    rho_z_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    rho_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
     P.end(GBXC_K_RHO_Z, st);
-    run_slice_vgemm(a, m, q, c, s, nt, st);
+    P.begin(GBXC_K_SLICE, st);
+    z_slice<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    P.end(GBXC_K_SLICE, st);
+    run_vgemm(a, m, q, c, s, st);
     return cudaGetLastError();
 }
 
