@@ -510,6 +510,15 @@ __device__ __forceinline__ VGeom v_geom(const ChunkArgs &a, const int *tasks, in
     return g;
 }
 
+// 16-wide K steps of a task.  Steps that cover only zero padding are skipped, their products
+// being exact zeros: for X the functions past N_b^j (the P^j and Phi slices of the rows up to
+// the 32-padded count are zero), for W the points past the count of the task's last tile (the
+// only tile of a batch that can be partial; Z is zero there).
+__device__ __forceinline__ int x_ksteps(const XGeom &g) { return (g.n + 15) >> 4; }
+__device__ __forceinline__ int v_ksteps(const ChunkArgs &a, const VGeom &g) {
+    return (int)(g.te - g.tb - 1) * 8 + ((a.plan.tile_count[g.te - 1] + 15) >> 4);
+}
+
 // The four level accumulators as an unnormalised pair: levels 0 + 1 by two-sum (exact), levels
 // 2-4 added to the low word (|v2| + |v3| < 2^-13 of level 0, so the rounding stays below 2^-37)
 __device__ __forceinline__ df combine4(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
@@ -579,10 +588,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                 int nks;   // 16-wide K steps: two per stored block of 32
                 if (KIND == 0) {
                     xg = x_geom(a, m, tasks, k);
-                    nks = xg.np / 16;
+                    nks = x_ksteps(xg);
                 } else {
                     vg = v_geom(a, tasks, k);
-                    nks = (int)(vg.te - vg.tb) * 8;
+                    nks = v_ksteps(a, vg);
                 }
                 for (int ks = 0; ks < nks; ++ks, ++gk) {
                     const int kb = ks >> 1, kx = (ks & 1) * 16;
@@ -616,11 +625,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                 int nks, ncols;
                 if (KIND == 0) {
                     XGeom g = x_geom(a, m, tasks, k);
-                    nks = g.np / 16;
+                    nks = x_ksteps(g);
                     ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
                 } else {
                     VGeom g = v_geom(a, tasks, k);
-                    nks = (int)(g.te - g.tb) * 8;
+                    nks = v_ksteps(a, g);
                     ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
                 }
                 const uint32_t idesc = umma::idesc_bf16(BM, ncols);
@@ -781,18 +790,20 @@ __global__ void __launch_bounds__(TILE) rho_mixed(ChunkArgs a, MixedArgs m) {
         return;
     }
     df rho{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
+    if (i < cnt) {   // padding points contribute nothing (their coefficients stay zero)
 #pragma unroll 2
-    for (int mu = 0; mu < n; ++mu) {
-        size_t o = (size_t)(r0 + mu) * TILE + i;
-        const float2 xv = m.s.x[o], f0 = phi[o];
-        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
-        const float l1 = __bfloat162float(m.s.glo[o]), l2 = __bfloat162float(m.s.glo[plane + o]),
-                    l3 = __bfloat162float(m.s.glo[2 * plane + o]);
-        df x{xv.x, xv.y};
-        rho = df_add(rho, df_mul({f0.x, f0.y}, x));
-        gx = df_add(gx, df_mul({h1, l1}, x));
-        gy = df_add(gy, df_mul({h2, l2}, x));
-        gz = df_add(gz, df_mul({h3, l3}, x));
+        for (int mu = 0; mu < n; ++mu) {
+            size_t o = (size_t)(r0 + mu) * TILE + i;
+            const float2 xv = m.s.x[o], f0 = phi[o];
+            const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
+            const float l1 = __bfloat162float(m.s.glo[o]), l2 = __bfloat162float(m.s.glo[plane + o]),
+                        l3 = __bfloat162float(m.s.glo[2 * plane + o]);
+            df x{xv.x, xv.y};
+            rho = df_add(rho, df_mul({f0.x, f0.y}, x));
+            gx = df_add(gx, df_mul({h1, l1}, x));
+            gy = df_add(gy, df_mul({h2, l2}, x));
+            gz = df_add(gz, df_mul({h3, l3}, x));
+        }
     }
     double r = df_to_d(rho);
     double dx = 2.0 * df_to_d(gx), dy = 2.0 * df_to_d(gy), dz = 2.0 * df_to_d(gz);
@@ -865,11 +876,15 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
     // the group's per-point coefficients (a, b_x, b_y, b_z) as double-float pairs
     __shared__ float2 cf[VKS][4][TILE];
     __shared__ int64_t trow[VKS];
+    __shared__ int tcnt[VKS];
     __shared__ int red[2][8][2];   // per step parity and slot: tile exponents of |Z|, |Phi|
     const double *cz = reinterpret_cast<const double *>(m.s.x);
     for (int u = 0; u < ng; ++u) {
         const int64_t ru = a.plan.tile_row[g0 + u] - a.row0;
-        if (threadIdx.x == 0) trow[u] = ru;
+        if (threadIdx.x == 0) {
+            trow[u] = ru;
+            tcnt[u] = a.plan.tile_count[g0 + u];
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const df c = d_to_df(cz[(size_t)(ru + q) * TILE + threadIdx.x]);
@@ -883,14 +898,21 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
     const int u = slot & ((1 << lg) - 1), rr = slot >> lg;
     const int pk = pg >> 2, col = (pg & 3) * 8;
     const int64_t ru = u < ng ? trow[u] : 0;
+    // padding points (past the tile's count) have Z = 0 and Phi = 0: a thread whose 8 points
+    // are all padding loads nothing, and stores its (zero) slices only if the V contraction
+    // reads them, i.e. below the count rounded up to its 16-point K steps
+    const int cu = u < ng ? tcnt[u] : 0;
+    const bool live8 = 8 * pg < cu, need8 = 8 * pg < ((cu + 15) & ~15);
     int par = 0;
     for (int c = ub; c * R < n; c += nblk, par ^= 1) {
         const int mu = c * R + rr;
         const bool act = u < ng && mu < n;
         float zh[8], zl[8], fh[8], fl[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) zh[e] = zl[e] = fh[e] = fl[e] = 0.f;
         float az = 0.f, ap = 0.f;
         const size_t o = (size_t)(ru + mu) * TILE + 8 * pg;
-        if (act) {
+        if (act && live8) {
             const float4 *fs = reinterpret_cast<const float4 *>(m.s.phi + o);
             const float4 *h1 = reinterpret_cast<const float4 *>(m.s.ghi + o);
             const float4 *h2 = reinterpret_cast<const float4 *>(m.s.ghi + plane + o);
@@ -937,7 +959,7 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
             ep = max(ep, red[par][(rr << lg) + v][1]);
         }
         if (!act) continue;
-        if (m.keep_z) {
+        if (m.keep_z && live8) {
             float4 *zo = reinterpret_cast<float4 *>(m.s.x + o);
 #pragma unroll
             for (int q = 0; q < 4; ++q) zo[q] = make_float4(zh[2 * q], zl[2 * q], zh[2 * q + 1], zl[2 * q + 1]);
@@ -959,12 +981,14 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
             }
         }
         const size_t orow = (size_t)(4 * ru + (int64_t)pk * np + mu) * 32 + col;
+        if (need8) {
 #pragma unroll
-        for (int sl = 0; sl < NSL; ++sl) {
-            *reinterpret_cast<uint4 *>(m.s.vz + (size_t)sl * plane + orow) =
-                make_uint4(wz[sl][0], wz[sl][1], wz[sl][2], wz[sl][3]);
-            *reinterpret_cast<uint4 *>(m.s.vphi + (size_t)sl * plane + orow) =
-                make_uint4(wp[sl][0], wp[sl][1], wp[sl][2], wp[sl][3]);
+            for (int sl = 0; sl < NSL; ++sl) {
+                *reinterpret_cast<uint4 *>(m.s.vz + (size_t)sl * plane + orow) =
+                    make_uint4(wz[sl][0], wz[sl][1], wz[sl][2], wz[sl][3]);
+                *reinterpret_cast<uint4 *>(m.s.vphi + (size_t)sl * plane + orow) =
+                    make_uint4(wp[sl][0], wp[sl][1], wp[sl][2], wp[sl][3]);
+            }
         }
         if (u == 0 && pg == 0) {
             m.s.zexp[rg + mu] = ez;
