@@ -21,8 +21,9 @@
 // Kernels per chunk of tiles: pslice (P^j row slices), colloc (Phi, grad Phi, Phi slices),
 // xgemm (tcgen05), rho (rho, grad rho, functional, E/N partials, per-point Z coefficients),
 // z_slice (Z in double-float, group exponent maxima, Z and Phi slices per V task), vgemm
-// (tcgen05, scatter into V_acc with float64 atomics).  The spin-unrestricted and meta-GGA
-// forms form Z in their rho kernels (two passes over Phi) and slice it with slice_v.
+// (tcgen05, scatter into V_acc with float64 atomics).  The spin-unrestricted form runs z_slice
+// once per spin; the meta-GGA form forms Z and W^k in its rho kernel (two passes over Phi) and
+// slices them with slice_v.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -997,13 +998,13 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
     }
 }
 
-// ---------------------------------------------------------------- spin-unrestricted rho, functional, Z
-// The same two passes for the two spin densities (X_a in the slab, X_b in x2): rho_s and
-// grad rho_s in double-float, the spin-polarised functional in float64, then
-// Z^s = 1/2 w v_s Phi + w (2 s_ss grad rho_s + s_ab grad rho_s') . grad Phi over X_s, with the
-// per-tile maxima of |Z^a| (zexp), |Z^b| (zexp2) and |Phi| (fexp) for the V-side slicing.
-__global__ void __launch_bounds__(TILE) rho_z_mixed_uks(ChunkArgs a, MixedArgs m, float2 *__restrict__ x2,
-                                                         int *__restrict__ zexp2) {
+// ---------------------------------------------------------------- spin-unrestricted rho, functional
+// Both spin densities and their gradients in double-float over X_a (in the slab) and X_b (in
+// x2), the spin-polarised functional in float64, the tile's E/N partials, and per spin the
+// coefficients of Z^s = 1/2 w v_s Phi + w (2 s_ss grad rho_s + s_ab grad rho_s') . grad Phi:
+// spin a's in the first four rows of the tile's X_a plane, spin b's in those of x2, as in
+// rho_mixed, so that z_slice forms and slices each Z^s in turn.  Padding points load nothing.
+__global__ void __launch_bounds__(TILE) rho_mixed_uks(ChunkArgs a, MixedArgs m, float2 *__restrict__ x2) {
     int64_t t = a.t0 + blockIdx.x;
     int i = threadIdx.x;
     int j = a.plan.tile_batch[t];
@@ -1019,19 +1020,21 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed_uks(ChunkArgs a, MixedArgs m
     }
     df rho[2] = {{0.f, 0.f}, {0.f, 0.f}};
     df g[2][3] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
+    if (i < cnt) {
 #pragma unroll 2
-    for (int mu = 0; mu < n; ++mu) {
-        size_t o = (size_t)(r0 + mu) * TILE + i;
-        const float2 xa = m.s.x[o], xb = x2[o], f0 = phi[o];
-        const df gr[3] = {{m.s.ghi[o], __bfloat162float(m.s.glo[o])},
-                          {m.s.ghi[plane + o], __bfloat162float(m.s.glo[plane + o])},
-                          {m.s.ghi[2 * plane + o], __bfloat162float(m.s.glo[2 * plane + o])}};
-        const df xs[2] = {{xa.x, xa.y}, {xb.x, xb.y}};
+        for (int mu = 0; mu < n; ++mu) {
+            size_t o = (size_t)(r0 + mu) * TILE + i;
+            const float2 xa = m.s.x[o], xb = x2[o], f0 = phi[o];
+            const df gr[3] = {{m.s.ghi[o], __bfloat162float(m.s.glo[o])},
+                              {m.s.ghi[plane + o], __bfloat162float(m.s.glo[plane + o])},
+                              {m.s.ghi[2 * plane + o], __bfloat162float(m.s.glo[2 * plane + o])}};
+            const df xs[2] = {{xa.x, xa.y}, {xb.x, xb.y}};
 #pragma unroll
-        for (int sp = 0; sp < 2; ++sp) {
-            rho[sp] = df_add(rho[sp], df_mul({f0.x, f0.y}, xs[sp]));
+            for (int sp = 0; sp < 2; ++sp) {
+                rho[sp] = df_add(rho[sp], df_mul({f0.x, f0.y}, xs[sp]));
 #pragma unroll
-            for (int d = 0; d < 3; ++d) g[sp][d] = df_add(g[sp][d], df_mul(gr[d], xs[sp]));
+                for (int d = 0; d < 3; ++d) g[sp][d] = df_add(g[sp][d], df_mul(gr[d], xs[sp]));
+            }
         }
     }
     double r[2], gd[2][3];
@@ -1041,7 +1044,7 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed_uks(ChunkArgs a, MixedArgs m
 #pragma unroll
         for (int d = 0; d < 3; ++d) gd[sp][d] = 2.0 * df_to_d(g[sp][d]);
     }
-    double e = 0.0, nn = 0.0, ca[2] = {0.0, 0.0}, cb[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    double e = 0.0, nn = 0.0, coef[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
     if (i < cnt) {
         const double w = a.plan.w[a.plan.tile_first[t] + i];
         const double saa = gd[0][0] * gd[0][0] + gd[0][1] * gd[0][1] + gd[0][2] * gd[0][2];
@@ -1051,63 +1054,19 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed_uks(ChunkArgs a, MixedArgs m
         xc::evaluate_pol<double>(a.functional, r[0], r[1], saa, sab, sbb, f, va, vb, s_aa, s_ab, s_bb);
         e = w * f;
         nn = w * (r[0] + r[1]);
-        ca[0] = 0.5 * w * va;
-        ca[1] = 0.5 * w * vb;
+        coef[0][0] = 0.5 * w * va;
+        coef[1][0] = 0.5 * w * vb;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            cb[0][d] = w * (2.0 * s_aa * gd[0][d] + s_ab * gd[1][d]);
-            cb[1][d] = w * (2.0 * s_bb * gd[1][d] + s_ab * gd[0][d]);
+            coef[0][d + 1] = w * (2.0 * s_aa * gd[0][d] + s_ab * gd[1][d]);
+            coef[1][d + 1] = w * (2.0 * s_bb * gd[1][d] + s_ab * gd[0][d]);
         }
     }
-    __shared__ int zmax[2][MAX_NP], fmx[MAX_NP];
-    for (int mu = i; mu < np; mu += TILE) {
-        zmax[0][mu] = 0;
-        zmax[1][mu] = 0;
-        fmx[mu] = 0;
-    }
-    __syncthreads();
-    df cz[2], cg[2][3];
+    double *cza = reinterpret_cast<double *>(m.s.x), *czb = reinterpret_cast<double *>(x2);
 #pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
-        cz[sp] = d_to_df(ca[sp]);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) cg[sp][d] = d_to_df(cb[sp][d]);
-    }
-    int lane = i & 31;
-    float2 *zout[2] = {m.s.x, x2};
-#pragma unroll 2
-    for (int mu = 0; mu < n; ++mu) {
-        size_t o = (size_t)(r0 + mu) * TILE + i;
-        const float2 f0 = phi[o];
-        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
-        float az[2];
-#pragma unroll
-        for (int sp = 0; sp < 2; ++sp) {
-            df z = df_mul(cz[sp], {f0.x, f0.y});
-            z = df_add(z, dfl::mul_f(cg[sp][0], h1));
-            z = df_add(z, dfl::mul_f(cg[sp][1], h2));
-            z = df_add(z, dfl::mul_f(cg[sp][2], h3));
-            zout[sp][o] = make_float2(z.h, z.l);
-            az[sp] = fabsf(z.h);
-        }
-        float ap = fabsf(f0.x);
-#pragma unroll
-        for (int q = 16; q > 0; q >>= 1) {
-            az[0] = fmaxf(az[0], __shfl_xor_sync(0xffffffffu, az[0], q));
-            az[1] = fmaxf(az[1], __shfl_xor_sync(0xffffffffu, az[1], q));
-            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
-        }
-        if (lane == 0) {
-            atomicMax(&zmax[0][mu], __float_as_int(az[0]));
-            atomicMax(&zmax[1][mu], __float_as_int(az[1]));
-            atomicMax(&fmx[mu], __float_as_int(ap));
-        }
-    }
-    __syncthreads();
-    for (int mu = i; mu < n; mu += TILE) {
-        m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[0][mu]));
-        zexp2[r0 + mu] = exp_of(__int_as_float(zmax[1][mu]));
-        m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu]));
+    for (int q = 0; q < 4; ++q) {
+        cza[(size_t)(r0 + q) * TILE + i] = coef[0][q];
+        czb[(size_t)(r0 + q) * TILE + i] = coef[1][q];
     }
     __shared__ double re[TILE], rn[TILE];
     re[i] = e;
@@ -1842,9 +1801,9 @@ cudaError_t launch_mixed_chunk_mgga(const ChunkArgs &a, MixedCtx &c, MixedReside
 
 // Spin-unrestricted chunk: one collocation; P_a's slices and X_a (into the slab), then P_b's
 // slices and X_b (into x2), both densities and the spin-polarised functional in one kernel
-// (Z_a over X_a, Z_b over X_b), then slicing and W^j per spin, spin b with x2 and zexp2 in
-// place of the slab's X/Z plane and exponents.  The Phi slices of the second slicing are
-// the same values as the first's.
+// (the Z^a coefficients over X_a, the Z^b coefficients over X_b), then z_slice and W^j per
+// spin, spin b with x2 and zexp2 in place of the slab's X plane and Z exponents.  The Phi
+// slices of the second slicing are the same values as the first's.
 cudaError_t launch_mixed_chunk_uks(const ChunkArgs &a, MixedCtx &c, MixedResident &r, const MixedSchedule &s,
                                    int chunk_index, double *Vacc_b, cudaStream_t st) {
     if (!r.d_shells || !c.x2 || !c.zexp2 || !c.pdf2) return cudaErrorInvalidValue;
@@ -1866,12 +1825,18 @@ cudaError_t launch_mixed_chunk_uks(const ChunkArgs &a, MixedCtx &c, MixedResiden
     run_xgemm(a, mb, q, c, s, ch, st);
     Profiler &P = *a.prof;
     P.begin(GBXC_K_RHO_Z, st);
-    rho_z_mixed_uks<<<(unsigned)nt, TILE, 0, st>>>(a, ma, c.x2, c.zexp2);
+    rho_mixed_uks<<<(unsigned)nt, TILE, 0, st>>>(a, ma, c.x2);
     P.end(GBXC_K_RHO_Z, st);
-    run_slice_vgemm(a, ma, q, c, s, nt, st);
+    P.begin(GBXC_K_SLICE, st);
+    z_slice<<<(unsigned)nt, TILE, 0, st>>>(a, ma);
+    P.end(GBXC_K_SLICE, st);
+    run_vgemm(a, ma, q, c, s, st);
     ChunkArgs ab = a;
     ab.Vacc = Vacc_b;
-    run_slice_vgemm(ab, mb, q, c, s, nt, st);
+    P.begin(GBXC_K_SLICE, st);
+    z_slice<<<(unsigned)nt, TILE, 0, st>>>(ab, mb);
+    P.end(GBXC_K_SLICE, st);
+    run_vgemm(ab, mb, q, c, s, st);
     return cudaGetLastError();
 }
 
