@@ -348,13 +348,20 @@ int gbxc_serve_stats(gbxc_ctx *ctx, long long *queued, long long *running, long 
  *   Vxc  nbf x nbf DEVICE output; used as the accumulator, then symmetrised in place
  *   EN   2 doubles of DEVICE memory: {E_xc, N_el}
  *   stream  cudaStream_t (NULL = the context's stream)
+ * P, Vxc and EN must be memory of the context's device (or managed memory); a buffer of
+ * another device is refused with GBXC_EINVAL.
  * The work is queued on `stream` and the call returns without waiting: results are
- * ready when the stream reaches this point.  The first call on a device resolves the
- * static array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Calls share the one static array, so calls whose work overlaps
- * on the GPU (different streams, or different contexts on one device) race and must
- * not be issued concurrently.  A batch whose tile needs more than 64 MiB of float64
- * slabs (more than about 10,900 padded functions) is rejected with GBXC_ENOMEM. */
+ * ready when the stream reaches this point.  Because the call returns before the device
+ * has looked at P, a NaN or an infinity in P cannot be reported by the return code; the
+ * device checks P and then writes NaN to both E_xc and N_el, so such a result never looks
+ * valid.  The first call on a device resolves the static array's device address
+ * (cudaGetSymbolAddress) and caches it for the life of the process; make that first call
+ * before any stream capture.  Calls share the one static array, and calls on the same
+ * molecule also share its per-tile and per-batch E and N partial sums (allocated when the
+ * grid was loaded), so calls whose work overlaps on the GPU (different streams, or
+ * different contexts on one device) race and must not be issued concurrently.  A batch
+ * whose tile needs more than 64 MiB of float64 slabs (more than about 10,900 padded
+ * functions) is rejected with GBXC_ENOMEM. */
 int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int functional, double *Vxc,
                                 double *EN, void *stream);
 

@@ -15,6 +15,7 @@
 //
 // On this GPU float64 runs at a small fraction of float32 and tensor rates, so
 // these kernels are bound by the float64 pipe; they are the precision anchor.
+#include <atomic>
 #include <cstdint>
 
 #include "internal.h"
@@ -492,6 +493,15 @@ __global__ void nonfinite_flag(const double *__restrict__ P, int64_t n, double *
         }
 }
 
+// {E, N} <- NaN when the flag is set: the allocation-free call returns before its status could
+// report a non-finite P, so the results themselves carry it.
+__global__ void poison_if_flagged(const double *__restrict__ flag, double *EN) {
+    if (threadIdx.x == 0 && *flag != 0.0) {
+        EN[0] = __longlong_as_double(0x7ff8000000000000LL);
+        EN[1] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+}
+
 __global__ void symmetrize(const double *__restrict__ Vacc, double *__restrict__ V, int nbf) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)nbf * nbf) return;
@@ -541,6 +551,7 @@ __global__ void total_sums(FinishArgs a) {
 // cudaGetSymbolAddress, once per device, with that device current.
 // --------------------------------------------------------------------------
 constexpr size_t kNoallocScratchBytes = (size_t)64 << 20;
+constexpr size_t kNoallocFlagBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 // W^j over one tile (K = its 128 points) for the 64 x 64 block (blockIdx.y, blockIdx.z),
@@ -669,21 +680,24 @@ cudaError_t launch_fp64_chunk_mgga(const ChunkArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t noalloc_scratch(void **ptr, size_t *bytes) {
-    // one cached address per device; the first call on a device resolves it
-    static void *cache[64] = {};
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes, double **flag) {
+    // one cached address per device, kept for the life of the process; the first call on a
+    // device resolves it (threads racing on that first call store the same value)
+    static std::atomic<void *> cache[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!cache[dev]) {
-        void *p = nullptr;
+    void *p = cache[dev].load(std::memory_order_acquire);
+    if (!p) {
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        cache[dev] = p;
+        cache[dev].store(p, std::memory_order_release);
     }
-    *ptr = cache[dev];
-    *bytes = kNoallocScratchBytes;
+    // the first 256 bytes hold the non-finite-P flag, the rest the slabs
+    *flag = static_cast<double *>(p);
+    *ptr = static_cast<unsigned char *>(p) + kNoallocFlagBytes;
+    *bytes = kNoallocScratchBytes - kNoallocFlagBytes;
     return cudaSuccess;
 }
 
@@ -706,6 +720,11 @@ cudaError_t launch_check_finite(const double *P, int64_t n, double *flag, bool r
     }
     if (n > 0)
         nonfinite_flag<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(P, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poison_if_flagged(const double *flag, double *EN, cudaStream_t s) {
+    poison_if_flagged<<<1, 32, 0, s>>>(flag, EN);
     return cudaGetLastError();
 }
 

@@ -332,6 +332,19 @@ bool is_device_ptr(const void *p) {
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Device memory that lives on another GPU than `device` (managed memory is reachable from
+// every device and does not count).  Kernels of a context run on its own device only, so
+// such a buffer is refused instead of being read over the interconnect or faulting.
+bool on_other_device(const void *p, int device) {
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice && attr.device != device;
+}
+
 Molecule &get_mol(gbxc_ctx *ctx, int mol) {
     auto it = ctx->mols.find(mol);
     if (it == ctx->mols.end()) throw ArgError{"unknown molecule id " + std::to_string(mol)};
@@ -583,6 +596,8 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     Molecule &m = get_mol(ctx, mol);
     if (!m.has_grid) throw ArgError{"molecule has no grid (call gbxc_load_grid first)"};
     REQUIRE(P, "P is NULL");
+    REQUIRE(!on_other_device(P, ctx->device) && (!Vxc || !on_other_device(Vxc, ctx->device)),
+            "P or Vxc is memory of another device");
     REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE || functional == GBXC_MVS_X, "unknown functional");
     REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
     int nb = m.plan.nbatch();
@@ -1415,6 +1430,8 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
         Molecule &m = get_mol(ctx, mol);
         if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
         REQUIRE(Pa && Pb, "P is NULL");
+        for (const void *q : {(const void *)Pa, (const void *)Pb, (const void *)Va, (const void *)Vb})
+            REQUIRE(!q || !on_other_device(q, ctx->device), "a buffer is memory of another device");
         REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "unknown functional");
         REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
         const int nb = m.plan.nbatch();
@@ -1589,11 +1606,15 @@ int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int fun
         REQUIRE(P && Vxc && EN, "P, Vxc and EN must be device pointers");
         REQUIRE(is_device_ptr(P) && is_device_ptr(Vxc) && is_device_ptr(EN),
                 "P, Vxc and EN must be device pointers");
+        REQUIRE(!on_other_device(P, ctx->device) && !on_other_device(Vxc, ctx->device) &&
+                    !on_other_device(EN, ctx->device),
+                "P, Vxc and EN must be memory of the context's device");
         Molecule &m = get_mol(ctx, mol);
         if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
         void *scratch = nullptr;
         size_t cap = 0;
-        check(noalloc_scratch(&scratch, &cap), "static scratch address");
+        double *flag = nullptr;
+        check(noalloc_scratch(&scratch, &cap, &flag), "static scratch address");
         const HostPlan &H = m.plan;
         int64_t max_rows = (int64_t)(cap / fp64_row_bytes());
         for (int64_t t = 0; t < H.ntiles(); ++t)
@@ -1602,6 +1623,7 @@ int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int fun
         cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
         size_t nn = (size_t)m.nbf * m.nbf;
         check(cudaMemsetAsync(Vxc, 0, nn * 8, s), "zero V");
+        check(launch_check_finite(P, (int64_t)nn, flag, true, s), "check P");
         int64_t t = 0, nt = H.ntiles();
         while (t < nt) {
             ChunkArgs a;
@@ -1645,6 +1667,7 @@ int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int fun
         f.tot = EN;
         f.prof = &quiet;
         check(launch_finish(f, s), "finish");
+        check(launch_poison_if_flagged(flag, EN, s), "non-finite P");
         return GBXC_OK;
     });
 }

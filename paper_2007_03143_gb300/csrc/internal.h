@@ -189,9 +189,11 @@ struct FinishArgs {
 };
 cudaError_t launch_finish(const FinishArgs &a, cudaStream_t s);
 
-// Allocation-free float64 variant: the static device scratch (address and size), one chunk
-// of the float64 pipeline with per-tile V tasks, and the in-place V + V^T.
-cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
+// Allocation-free float64 variant: the static device scratch (slab address and size, and the
+// address of its non-finite-P flag), one chunk of the float64 pipeline with per-tile V tasks,
+// the in-place V + V^T, and {E, N} <- NaN if the flag is set.
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes, double **flag);
+cudaError_t launch_poison_if_flagged(const double *flag, double *EN, cudaStream_t s);
 cudaError_t launch_fp64_chunk_noalloc(const ChunkArgs &a, cudaStream_t s);
 cudaError_t launch_symmetrize_inplace(double *V, int nbf, cudaStream_t s);
 // V = V_acc + V_acc^T
