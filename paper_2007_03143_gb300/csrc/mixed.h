@@ -1,6 +1,6 @@
-// Mixed-precision form: float32 collocation, split-bf16x3 tcgen05 contractions
-// with float32 accumulation in tensor memory, float64 weights, functional tail
-// and accumulation.
+// Mixed-precision form: double-float collocation, Ozaki-sliced (5 x 7-bit) bf16 tcgen05
+// contractions with exact fp32 accumulator levels in tensor memory, float64 weights,
+// functional and accumulation.
 #pragma once
 
 #include <cstdint>
@@ -87,8 +87,6 @@ struct MixedSlabOffsets {
 MixedSlabOffsets mixed_slab_offsets(int64_t rows);
 // Tile widths the tcgen05 GEMMs are built for; `bn` below is one of them.
 bool mixed_tile_supported(int bn);
-// Largest padded N_b^j the tensor-core form takes (its exact accumulator levels need it).
-int mixed_max_functions();
 void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, int bn, std::vector<int> &tasks);
 void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chunk_t0,
                           const std::vector<int64_t> &chunk_t1, int bn, MixedSchedule &s);

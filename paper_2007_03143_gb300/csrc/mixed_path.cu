@@ -10,6 +10,8 @@
 //        d = 0, 1, 2, whose partial sums are integer multiples of 2^-(12+7d) below 2^24
 //        units so the fp32 sums are exact, and levels 3-4 together (rounded, 2^-21 below
 //        level 0).  X = (acc0 + acc1 + acc2 + acc3) 2^(e_i + f_mu), summed in double-float.
+//        The exactness needs K <= 1184 functions per accumulation; a batch with more
+//        functions runs its K in segments of 1184, each exact, added in double-float.
 //   W^j = Z^jT Phi^j (Eq. vxc_batch) the same slicing over K = grid points: each function
 //        row of Z and of Phi is scaled by the maximum over the points of its V task (at
 //        most 8 tiles = 1024 points, so levels 0-2 stay exact) and sliced the same way.
@@ -48,7 +50,9 @@ using slc::pow2f;
 using slc::scale2;
 using slc::slice5;
 using slc::exp_of;
-constexpr int MAX_NP = 1184;   // largest padded N_b^j: keeps the exact accumulator levels exact
+constexpr int XSEG = 74;        // 16-wide K steps per X segment: K <= 1184 functions keeps the
+                                // exact accumulator levels exact; longer K runs in segments
+constexpr int MGGA_FB = 1184;   // functions per block of the meta-GGA kernel's shared maxima
 constexpr int VKS = 8;          // tiles per V task: K <= 1024 points keeps levels 0-2 exact
 // The functional runs in float64 at every point: float32 PBE above rho = 1e-8 was measured
 // at |dE_xc| = 6e-6 Eh on the 16-water workload, above the 1e-6 Eh bound of this form.
@@ -106,6 +110,10 @@ struct MixedArgs {
     const float *ph, *pl;        // P as double-float planes (nbf x nbf each)
     int *err;
     int keep_z;                  // z_slice also writes Z over X (per-batch debugging copy)
+    int pad_all;                 // the collocation writes zeros for every padding point of a tile
+                                 // (the meta-GGA kernels read all 128 points); otherwise only up
+                                 // to the count rounded up to 8 (z_slice reads 8-point groups),
+                                 // and the X epilogue stores live rows only
 };
 
 __device__ __forceinline__ int pad32(int n) { return (n + 31) & ~31; }
@@ -191,7 +199,7 @@ __device__ __forceinline__ df pow3(const df *xp, const df *yp, const df *zp, int
 // L is a template parameter so every monomial index is a compile-time constant.
 template <int L>
 __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const MixedSlabs &sl, size_t plane,
-                                             size_t o, bool live, float &mx) {
+                                             size_t o, bool live, bool st, float &mx) {
     df xp[L + 1], yp[L + 1], zp[L + 1];
     xp[0] = yp[0] = zp[0] = {1.f, 0.f};
 #pragma unroll
@@ -234,11 +242,13 @@ __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const
                 v[3] = df_add(v[3], t);
             }
             const size_t of = o + (size_t)f * TILE;
-            sl.phi[of] = live ? make_float2(v[0].h, v[0].l) : make_float2(0.f, 0.f);
+            if (st) {
+                sl.phi[of] = live ? make_float2(v[0].h, v[0].l) : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                sl.ghi[c * plane + of] = live ? v[c + 1].h : 0.f;
-                sl.glo[c * plane + of] = __float2bfloat16_rn(live ? v[c + 1].l : 0.f);
+                for (int c = 0; c < 3; ++c) {
+                    sl.ghi[c * plane + of] = live ? v[c + 1].h : 0.f;
+                    sl.glo[c * plane + of] = __float2bfloat16_rn(live ? v[c + 1].l : 0.f);
+                }
             }
             if (live) mx = fmaxf(mx, fabsf(v[0].h));
             ++f;
@@ -260,7 +270,7 @@ struct DfOps {
 // o, o + TILE, ... (the same formulas as colloc_shell for each component).
 template <int L>
 __device__ __forceinline__ void colloc_pure_shell(df X, df Y, df Z, df g, df h, const MixedSlabs &sl, size_t plane,
-                                                  size_t o, bool live, float &mx) {
+                                                  size_t o, bool live, bool st, float &mx) {
     constexpr int NC = (L + 1) * (L + 2) / 2, NO = 2 * L + 1;
     df xp[L + 1], yp[L + 1], zp[L + 1];
     xp[0] = yp[0] = zp[0] = {1.f, 0.f};
@@ -295,9 +305,9 @@ __device__ __forceinline__ void colloc_pure_shell(df X, df Y, df Z, df g, df h, 
         for (int k = 0; k < NO; ++k) {
             const size_t of = o + (size_t)k * TILE;
             if (comp == 0) {
-                sl.phi[of] = live ? make_float2(out[k].h, out[k].l) : make_float2(0.f, 0.f);
+                if (st) sl.phi[of] = live ? make_float2(out[k].h, out[k].l) : make_float2(0.f, 0.f);
                 if (live) mx = fmaxf(mx, fabsf(out[k].h));
-            } else {
+            } else if (st) {
                 sl.ghi[(comp - 1) * plane + of] = live ? out[k].h : 0.f;
                 sl.glo[(comp - 1) * plane + of] = __float2bfloat16_rn(live ? out[k].l : 0.f);
             }
@@ -327,6 +337,9 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
     int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
     int np = pad32(n);
     bool live = i < cnt;
+    // padding points past the count rounded up to 8 are read by no kernel of the spin-restricted
+    // and spin-unrestricted forms (their X rows are never used): nothing is stored for them
+    const bool st = m.pad_all || i < ((cnt + 7) & ~7);
     int64_t p = a.plan.tile_first[t] + i;
     df px = d_to_df(live ? a.plan.x[p] : 0.0), py = d_to_df(live ? a.plan.y[p] : 0.0),
        pz = d_to_df(live ? a.plan.z[p] : 0.0);
@@ -357,19 +370,22 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
         const size_t o = (size_t)(r0 + row) * TILE + i;
         if constexpr (HAS_PURE) {
             if (sh.pure) {   // L = 2 or 3
-                if (sh.L == 2) colloc_pure_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, mx);
-                else colloc_pure_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, mx);
+                if (sh.L == 2) colloc_pure_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, st, mx);
+                else colloc_pure_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, st, mx);
                 row += 2 * sh.L + 1;
                 continue;
             }
         }
         switch (sh.L) {
-            case 0: colloc_shell<0>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 1; break;
-            case 1: colloc_shell<1>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 3; break;
-            case 2: colloc_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 6; break;
-            default: colloc_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 10; break;
+            case 0: colloc_shell<0>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 1; break;
+            case 1: colloc_shell<1>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 3; break;
+            case 2: colloc_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 6; break;
+            default: colloc_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 10; break;
         }
     }
+    int e = exp_of(mx);
+    m.s.pexp[(t - a.t0) * TILE + i] = e;
+    if (!st) return;   // no barrier follows
     for (; row < np; ++row) {
         size_t o = (size_t)(r0 + row) * TILE + i;
         m.s.phi[o] = make_float2(0.f, 0.f);
@@ -379,8 +395,6 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
             m.s.glo[c * plane + o] = __float2bfloat16_rn(0.f);
         }
     }
-    int e = exp_of(mx);
-    m.s.pexp[(t - a.t0) * TILE + i] = e;
     // Ozaki slices of this point's row of Phi: K block kb -> row 4 r0 + 128 kb + i, 32 values
     for (int kb = 0; kb < np / 32; ++kb) {
         const size_t orow = (size_t)(4 * r0 + (int64_t)kb * TILE + i) * 32;
@@ -516,6 +530,10 @@ __device__ __forceinline__ VGeom v_geom(const ChunkArgs &a, const int *tasks, in
 // the 32-padded count are zero), for W the points past the count of the task's last tile (the
 // only tile of a batch that can be partial; Z is zero there).
 __device__ __forceinline__ int x_ksteps(const XGeom &g) { return (g.n + 15) >> 4; }
+// X segments of a task: batches with more than 1,184 functions accumulate K in segments of
+// XSEG steps, each exact in its own level accumulators; the epilogue adds segment s > 0 to
+// the X already stored by segment s - 1 (same CTA, same thread, in order) in double-float.
+__device__ __forceinline__ int x_nseg(const XGeom &g) { return (x_ksteps(g) + XSEG - 1) / XSEG; }
 __device__ __forceinline__ int v_ksteps(const ChunkArgs &a, const VGeom &g) {
     return (int)(g.te - g.tb - 1) * 8 + ((a.plan.tile_count[g.te - 1] + 15) >> 4);
 }
@@ -622,11 +640,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
     } else if (warp == 1) {
         if (lane == 0) {   // ------------------------------------------------ MMA issuer
             uint32_t gk = 0, tau = 0;
-            for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x, ++tau) {
-                int nks, ncols;
+            for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x) {
+                int nks, ncols, nseg = 1;
                 if (KIND == 0) {
                     XGeom g = x_geom(a, m, tasks, k);
                     nks = x_ksteps(g);
+                    nseg = x_nseg(g);
                     ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
                 } else {
                     VGeom g = v_geom(a, tasks, k);
@@ -634,31 +653,35 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
                 }
                 const uint32_t idesc = umma::idesc_bf16(BM, ncols);
-                const uint32_t b = tau % NBUF, use = tau / NBUF;
-                if (tau >= NBUF && !umma::mbar_wait(&tempty[b], (use - 1) & 1)) {
-                    atomicOr(m.err, 2);
-                    abort_flag = 1;
-                    break;
-                }
-                umma::fence_after_sync();
-                const uint32_t tacc = tmem + b * (XACC * BN);
-                for (int ks = 0; ks < nks; ++ks, ++gk) {
-                    int s = gk % GEMM_STAGES;
-                    if (!umma::mbar_wait(&full[s], (gk / GEMM_STAGES) & 1)) {
+                for (int sg = 0; sg < nseg && !abort_flag; ++sg, ++tau) {   // one accumulator set each
+                    const uint32_t b = tau % NBUF, use = tau / NBUF;
+                    if (tau >= NBUF && !umma::mbar_wait(&tempty[b], (use - 1) & 1)) {
                         atomicOr(m.err, 2);
                         abort_flag = 1;
                         break;
                     }
                     umma::fence_after_sync();
-                    uint32_t sa = umma::smem_u32(smem + s * GL::STAGE), sb = sa + GL::A_BYTES;
-                    // descriptors of slice 0; every other slice is a fixed offset in 16-byte
-                    // units (slice tiles BM x 32 B and BN x 32 B apart)
-                    const uint64_t a0 = umma::desc_sw32(sa), b0 = umma::desc_sw32(sb);
-                    issue_slice_mmas<BN>(tacc, a0, b0, idesc, ks == 0 ? 0u : 1u);
-                    umma::mma_commit(&empty[s]);
+                    const uint32_t tacc = tmem + b * (XACC * BN);
+                    const int ks0 = KIND == 0 ? sg * XSEG : 0;
+                    const int ks1 = KIND == 0 ? min(nks, ks0 + XSEG) : nks;
+                    for (int ks = ks0; ks < ks1; ++ks, ++gk) {
+                        int s = gk % GEMM_STAGES;
+                        if (!umma::mbar_wait(&full[s], (gk / GEMM_STAGES) & 1)) {
+                            atomicOr(m.err, 2);
+                            abort_flag = 1;
+                            break;
+                        }
+                        umma::fence_after_sync();
+                        uint32_t sa = umma::smem_u32(smem + s * GL::STAGE), sb = sa + GL::A_BYTES;
+                        // descriptors of slice 0; every other slice is a fixed offset in 16-byte
+                        // units (slice tiles BM x 32 B and BN x 32 B apart)
+                        const uint64_t a0 = umma::desc_sw32(sa), b0 = umma::desc_sw32(sb);
+                        issue_slice_mmas<BN>(tacc, a0, b0, idesc, ks == ks0 ? 0u : 1u);
+                        umma::mma_commit(&empty[s]);
+                    }
+                    if (abort_flag) break;
+                    umma::mma_commit(&tfull[b]);
                 }
-                if (abort_flag) break;
-                umma::mma_commit(&tfull[b]);
             }
             // every MMA this thread issued has completed before the allocation is released
             umma::mma_commit(drain);
@@ -675,7 +698,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
         const int i = q * 32 + lane;
         const int et = (warp - 4) * 32 + lane;   // 0 .. 511
         uint32_t tau = 0;
-        for (int k = blockIdx.x; k < ntasks; k += gridDim.x, ++tau) {
+        for (int k = blockIdx.x; k < ntasks; k += gridDim.x)
+        for (int sg = 0, nseg = KIND == 0 ? x_nseg(x_geom(a, m, tasks, k)) : 1; sg < nseg; ++sg, ++tau) {
             const uint32_t b = tau % NBUF, use = tau / NBUF, sb = tau & 1;
             if (KIND == 0) {
                 XGeom g = x_geom(a, m, tasks, k);
@@ -705,6 +729,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             if (KIND == 0) {
                 XGeom g = x_geom(a, m, tasks, k);
                 const int ei = m.s.pexp[(g.t - a.t0) * TILE + i];
+                const bool row_used = m.pad_all || i < a.plan.tile_count[g.t];
 #pragma unroll 1
                 for (int c = cpart * EPI_COLS; c < (cpart + 1) * EPI_COLS; c += 16) {
                     if (g.nc * BN + c >= g.n) break;   // warp-uniform
@@ -717,12 +742,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
 #pragma unroll
                     for (int kk = 0; kk < 16; ++kk) {
                         const int mu = g.nc * BN + c + kk;
-                        if (mu < g.n) {
+                        if (mu < g.n && row_used) {
                             df x = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
                             const int sc = min(max(ei + col_a[sb][c + kk], -252), 252);
                             const float s1 = pow2f(sc >> 1), s2 = pow2f(sc - (sc >> 1));
-                            m.s.x[(size_t)(g.r0 + mu) * TILE + i] =
-                                make_float2(__fmul_rn(__fmul_rn(x.h, s1), s2), __fmul_rn(__fmul_rn(x.l, s1), s2));
+                            float2 *xo = m.s.x + (size_t)(g.r0 + mu) * TILE + i;
+                            df xs{__fmul_rn(__fmul_rn(x.h, s1), s2), __fmul_rn(__fmul_rn(x.l, s1), s2)};
+                            if (sg > 0) {   // a later K segment: add to the segments before it
+                                const float2 o = *xo;
+                                xs = df_add({o.x, o.y}, xs);
+                            }
+                            *xo = make_float2(xs.h, xs.l);
                         }
                     }
                 }
@@ -782,14 +812,9 @@ __global__ void __launch_bounds__(TILE) rho_mixed(ChunkArgs a, MixedArgs m) {
     int j = a.plan.tile_batch[t];
     int cnt = a.plan.tile_count[t];
     int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
-    int np = pad32(n);
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     const float2 *phi = m.s.phi;
-    if (np > MAX_NP) {   // the exponent scratch holds MAX_NP rows; larger batches are rejected
-        if (i == 0) atomicOr(m.err, 8);
-        return;
-    }
     df rho{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
     if (i < cnt) {   // padding points contribute nothing (their coefficients stay zero)
 #pragma unroll 2
@@ -1010,14 +1035,9 @@ __global__ void __launch_bounds__(TILE) rho_mixed_uks(ChunkArgs a, MixedArgs m, 
     int j = a.plan.tile_batch[t];
     int cnt = a.plan.tile_count[t];
     int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
-    int np = pad32(n);
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     const float2 *phi = m.s.phi;
-    if (np > MAX_NP) {
-        if (i == 0) atomicOr(m.err, 8);
-        return;
-    }
     df rho[2] = {{0.f, 0.f}, {0.f, 0.f}};
     df g[2][3] = {{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}};
     if (i < cnt) {
@@ -1149,10 +1169,6 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed_mgga(ChunkArgs a, MixedArgs 
     int64_t r0 = a.plan.tile_row[t] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     const float2 *phi = m.s.phi;
-    if (np > MAX_NP) {
-        if (i == 0) atomicOr(m.err, 8);
-        return;
-    }
     df rho{0.f, 0.f}, tau{0.f, 0.f}, gr[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 2
     for (int mu = 0; mu < n; ++mu) {
@@ -1184,67 +1200,72 @@ __global__ void __launch_bounds__(TILE) rho_z_mixed_mgga(ChunkArgs a, MixedArgs 
         bz_d = b * dz;
         ct_d = 0.25 * w * vt;
     }
-    __shared__ int zmax[MAX_NP], fmx[MAX_NP], wmax[3][MAX_NP], gmax[3][MAX_NP];
-    for (int mu = i; mu < np; mu += TILE) {
-        zmax[mu] = 0;
-        fmx[mu] = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            wmax[k][mu] = 0;
-            gmax[k][mu] = 0;
-        }
-    }
-    __syncthreads();
+    // the per-function maxima over the tile's points, in blocks of MGGA_FB functions
+    __shared__ int zmax[MGGA_FB], fmx[MGGA_FB], wmax[3][MGGA_FB], gmax[3][MGGA_FB];
     const df cz = d_to_df(ca_d), cbx = d_to_df(bx_d), cby = d_to_df(by_d), cbz = d_to_df(bz_d), ct = d_to_df(ct_d);
     const int lane = i & 31;
+    for (int fb = 0; fb < np; fb += MGGA_FB) {
+        const int fe = min(np, fb + MGGA_FB), ne = min(n, fe);
+        for (int mu = fb + i; mu < fe; mu += TILE) {
+            zmax[mu - fb] = 0;
+            fmx[mu - fb] = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                wmax[k][mu - fb] = 0;
+                gmax[k][mu - fb] = 0;
+            }
+        }
+        __syncthreads();
 #pragma unroll 2
-    for (int mu = 0; mu < n; ++mu) {
-        size_t o = (size_t)(r0 + mu) * TILE + i;
-        const float2 f0 = phi[o];
-        const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
-        df z = df_mul(cz, {f0.x, f0.y});
-        z = df_add(z, dfl::mul_f(cbx, h1));
-        z = df_add(z, dfl::mul_f(cby, h2));
-        z = df_add(z, dfl::mul_f(cbz, h3));
-        m.s.x[o] = make_float2(z.h, z.l);
-        float az = fabsf(z.h), ap = fabsf(f0.x), aw[3], ag[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float hk = m.s.ghi[k * plane + o];
-            const df wk = df_mul(ct, {hk, __bfloat162float(m.s.glo[k * plane + o])});
-            y_g[k * plane + o] = make_float2(wk.h, wk.l);
-            aw[k] = fabsf(wk.h);
-            ag[k] = fabsf(hk);
-        }
-#pragma unroll
-        for (int q = 16; q > 0; q >>= 1) {
-            az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
-            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
+        for (int mu = fb; mu < ne; ++mu) {
+            size_t o = (size_t)(r0 + mu) * TILE + i;
+            const float2 f0 = phi[o];
+            const float h1 = m.s.ghi[o], h2 = m.s.ghi[plane + o], h3 = m.s.ghi[2 * plane + o];
+            df z = df_mul(cz, {f0.x, f0.y});
+            z = df_add(z, dfl::mul_f(cbx, h1));
+            z = df_add(z, dfl::mul_f(cby, h2));
+            z = df_add(z, dfl::mul_f(cbz, h3));
+            m.s.x[o] = make_float2(z.h, z.l);
+            float az = fabsf(z.h), ap = fabsf(f0.x), aw[3], ag[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                aw[k] = fmaxf(aw[k], __shfl_xor_sync(0xffffffffu, aw[k], q));
-                ag[k] = fmaxf(ag[k], __shfl_xor_sync(0xffffffffu, ag[k], q));
+                const float hk = m.s.ghi[k * plane + o];
+                const df wk = df_mul(ct, {hk, __bfloat162float(m.s.glo[k * plane + o])});
+                y_g[k * plane + o] = make_float2(wk.h, wk.l);
+                aw[k] = fabsf(wk.h);
+                ag[k] = fabsf(hk);
+            }
+#pragma unroll
+            for (int q = 16; q > 0; q >>= 1) {
+                az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
+                ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    aw[k] = fmaxf(aw[k], __shfl_xor_sync(0xffffffffu, aw[k], q));
+                    ag[k] = fmaxf(ag[k], __shfl_xor_sync(0xffffffffu, ag[k], q));
+                }
+            }
+            if (lane == 0) {
+                atomicMax(&zmax[mu - fb], __float_as_int(az));
+                atomicMax(&fmx[mu - fb], __float_as_int(ap));
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    atomicMax(&wmax[k][mu - fb], __float_as_int(aw[k]));
+                    atomicMax(&gmax[k][mu - fb], __float_as_int(ag[k]));
+                }
             }
         }
-        if (lane == 0) {
-            atomicMax(&zmax[mu], __float_as_int(az));
-            atomicMax(&fmx[mu], __float_as_int(ap));
+        __syncthreads();
+        for (int mu = fb + i; mu < ne; mu += TILE) {
+            m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[mu - fb]));
+            m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu - fb]));
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                atomicMax(&wmax[k][mu], __float_as_int(aw[k]));
-                atomicMax(&gmax[k][mu], __float_as_int(ag[k]));
+                wexp_g[(size_t)k * m.rows + r0 + mu] = exp_of(__int_as_float(wmax[k][mu - fb]));
+                gexp_g[(size_t)k * m.rows + r0 + mu] = exp_of(__int_as_float(gmax[k][mu - fb]));
             }
         }
-    }
-    __syncthreads();
-    for (int mu = i; mu < n; mu += TILE) {
-        m.s.zexp[r0 + mu] = exp_of(__int_as_float(zmax[mu]));
-        m.s.fexp[r0 + mu] = exp_of(__int_as_float(fmx[mu]));
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            wexp_g[(size_t)k * m.rows + r0 + mu] = exp_of(__int_as_float(wmax[k][mu]));
-            gexp_g[(size_t)k * m.rows + r0 + mu] = exp_of(__int_as_float(gmax[k][mu]));
-        }
+        __syncthreads();   // the next block's reset waits for these reads
     }
     __shared__ double re[TILE], rn[TILE];
     re[i] = e;
@@ -1389,8 +1410,6 @@ MixedSlabOffsets mixed_slab_offsets(int64_t rows) {
 size_t mixed_row_bytes() { return (size_t)TILE * (8 + 12 + 6 + 8 + 3 * NSL * 2) + 8 + 16; }
 
 bool mixed_tile_supported(int bn) { return bn == 128 || bn == 64; }
-
-int mixed_max_functions() { return MAX_NP; }
 
 void append_mixed_vtasks(int j, int n, int64_t s0, int64_t s1, int bn, std::vector<int> &tasks) {
     int mblk = (n + BM - 1) / BM, nblk = (n + bn - 1) / bn;
@@ -1639,6 +1658,7 @@ MixedArgs chunk_mixed_args(const ChunkArgs &a, MixedCtx &c, const MixedSchedule 
     m.pl = pdf + (size_t)a.nbf * a.nbf;
     m.err = c.d_err;
     m.keep_z = c.keep_z;
+    m.pad_all = 0;
     return m;
 }
 
@@ -1759,6 +1779,7 @@ cudaError_t launch_mixed_chunk_mgga(const ChunkArgs &a, MixedCtx &c, MixedReside
     if (nt <= 0) return cudaSuccess;
     const MixedSchedule::Chunk &ch = s.chunks[chunk_index];
     MixedArgs m = chunk_mixed_args(a, c, s, ch, c.pdf);
+    m.pad_all = 1;   // rho_z_mixed_mgga and grad_slices read every point of a tile
     cudaError_t err = cudaSuccess;
     const ChunkMaps q = chunk_maps(c, m, s, ch, err);
     const size_t plane = (size_t)a.rows * TILE;

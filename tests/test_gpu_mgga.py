@@ -67,6 +67,6 @@ def test_mgga_full_size_sampled_batches():
         # alpha = (tau - tau_W) / tau_unif cancels in the low-density tail, where vtau grows as
         # rho^(-1/3): the tensor-core form's 1e-10-relative densities move V by up to a few 1e-6
         # there (2.6e-6 on this workload), against 9.5e-8 for PBE
-        assert np.max(np.abs(Vm - V64)) <= 1e-5
+        assert np.max(np.abs(Vm - V64)) <= 5e-6
     finally:
         L.close()
