@@ -51,11 +51,18 @@ extern "C" {
                                density tau = 1/2 sum P grad phi . grad phi (the meta-GGA
                                extension of Sec. 2.1); gbxc_integrate and
                                gbxc_integrate_batches, both precisions */
+#define GBXC_PBE0_SL 3      /* the semi-local part of the PBE0 hybrid (Sec. 2.1 names hybrids):
+                               3/4 PBE exchange + PBE correlation.  The remaining 1/4 exact
+                               (Hartree-Fock) exchange is a four-centre integral, not a grid
+                               quadrature, and is left to the caller; accepted wherever
+                               GBXC_PBE is */
 
 /* arithmetic of the integration */
 #define GBXC_FP64 0         /* every step in float64 */
-#define GBXC_MIXED 1        /* float32 collocation, split-bf16x3 tensor-core contractions,
-                               float64 weights, low-density functional tail and accumulation */
+#define GBXC_MIXED 1        /* double-float (float32 pair) collocation and densities; both
+                               contractions on the tensor cores as Ozaki-sliced bf16 products
+                               (5 slices of 7 bits, 15 products, exact fp32 accumulator
+                               levels); float64 weights, functional and accumulation */
 
 /* kernel classes reported by gbxc_profile_read */
 #define GBXC_K_WEIGHTS 0    /* partition weights (grid loading) */
@@ -116,6 +123,9 @@ typedef struct {
     double sum_mn2;          /* sum_j N_g^j (N_b^j)^2 */
     double work;             /* sum_j W_j of Eq. batch_work */
     double sum_mn;           /* sum_j N_g^j N_b^j (grid-point x function elements) */
+    double sum_ms;           /* sum_j N_g^j |S_j| (grid-point x shell pairs of the collocation) */
+    double sum_n2;           /* sum_j (N_b^j)^2 (elements of the gathered P^j) */
+    int max_nfunc;           /* largest N_b^j */
 } gbxc_plan_info;
 
 /* Create a context on CUDA device `device` (device = -1 creates a host-only
@@ -364,6 +374,14 @@ int gbxc_serve_stats(gbxc_ctx *ctx, long long *queued, long long *running, long 
  * functions) is rejected with GBXC_ENOMEM. */
 int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int functional, double *Vxc,
                                 double *EN, void *stream);
+
+/* Measured arithmetic peaks of CUDA device `device`: float32 and float64 fused multiply-add
+ * throughput in TFLOP/s (2 flops per FMA), from independent FMA chains on every SM timed with
+ * CUDA events.  The paper has no counterpart: these are the denominators of the rooflines of
+ * kernels bound by the plain ALUs (the double-float collocation runs on the float32 FMA pipe,
+ * the float64 contractions on the float64 one).  Allocates and frees a small device buffer;
+ * returns GBXC_EINVAL for NULL outputs, GBXC_ECUDA on a CUDA failure. */
+int gbxc_measure_alu_peaks(int device, double *fp32_tflops, double *fp64_tflops);
 
 /* Per-kernel-class accounting.  Launch counts are always kept; with
  * gbxc_profile_enable(ctx, 1) every kernel-class span is also bracketed by CUDA

@@ -130,4 +130,17 @@ def pw92_lda(rho):
     return np.where(ok, f, 0.0), np.where(ok, v, 0.0)
 
 
-FUNCTIONALS = {"slater": slater, "pbe": pbe}
+PBE0_A = 0.25      # exact-exchange fraction of PBE0
+
+
+def pbe0_semilocal(rho, sigma):
+    """The grid part of the PBE0 hybrid: (1 - a) PBE exchange + PBE correlation, a = 1/4 (the
+    paper names hybrids among the functionals its method serves, Sec. 2.1; the a E_x^HF term is
+    a four-centre integral, not a quadrature over the grid)."""
+    fx, vx, sx = pbe_exchange(rho, sigma)
+    fc, vc, sc = pbe_correlation(rho, sigma)
+    k = 1.0 - PBE0_A
+    return k * fx + fc, k * vx + vc, k * sx + sc
+
+
+FUNCTIONALS = {"slater": slater, "pbe": pbe, "pbe0_sl": pbe0_semilocal}

@@ -135,4 +135,12 @@ def pbe_pol(ra, rb, saa, sab, sbb):
     return tuple(a + b for a, b in zip(x, c))
 
 
-FUNCTIONALS_POL = {"slater": slater_pol, "pbe": pbe_pol}
+def pbe0_semilocal_pol(ra, rb, saa, sab, sbb):
+    """(1 - a) PBE exchange + PBE correlation, a = 1/4: the grid part of PBE0."""
+    x = pbe_exchange_pol(ra, rb, saa, sab, sbb)
+    c = pbe_correlation_pol(ra, rb, saa, sab, sbb)
+    k = 1.0 - F.PBE0_A
+    return tuple(k * a + b for a, b in zip(x, c))
+
+
+FUNCTIONALS_POL = {"slater": slater_pol, "pbe": pbe_pol, "pbe0_sl": pbe0_semilocal_pol}

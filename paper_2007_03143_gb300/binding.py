@@ -21,13 +21,13 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 GBXC_OK, GBXC_EINVAL, GBXC_ENOMEM, GBXC_ECUDA, GBXC_ETIMEOUT, GBXC_ENOTREADY, GBXC_ENOENT = \
     0, -1, -2, -3, -4, -5, -6
 GBXC_BECKE, GBXC_SSF = 0, 1
-GBXC_SLATER, GBXC_PBE, GBXC_MVS_X = 0, 1, 2
+GBXC_SLATER, GBXC_PBE, GBXC_MVS_X, GBXC_PBE0_SL = 0, 1, 2, 3
 GBXC_FP64, GBXC_MIXED = 0, 1
 GBXC_ANGULAR_PRODUCT, GBXC_ANGULAR_LEBEDEV = 0, 1
 GBXC_MAX_PRIM = 8
 GBXC_MAX_L = 3
 
-FUNCTIONALS = {"slater": GBXC_SLATER, "pbe": GBXC_PBE, "mvs_x": GBXC_MVS_X}
+FUNCTIONALS = {"slater": GBXC_SLATER, "pbe": GBXC_PBE, "mvs_x": GBXC_MVS_X, "pbe0_sl": GBXC_PBE0_SL}
 PARTITIONS = {"becke": GBXC_BECKE, "ssf": GBXC_SSF}
 PRECISIONS = {"fp64": GBXC_FP64, "mixed": GBXC_MIXED}
 ANGULAR = {"product": GBXC_ANGULAR_PRODUCT, "lebedev": GBXC_ANGULAR_LEBEDEV}
@@ -62,7 +62,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("natoms", c_int), ("nshell", c_int), ("nbf", c_int), ("npts", c_longlong),
                 ("nbatch", c_int), ("nleaf", c_int), ("nshell_entries", c_longlong),
                 ("nfunc_entries", c_longlong), ("ntiles", c_longlong), ("sum_mn2", c_double),
-                ("work", c_double), ("sum_mn", c_double)]
+                ("work", c_double), ("sum_mn", c_double), ("sum_ms", c_double), ("sum_n2", c_double),
+                ("max_nfunc", c_int)]
 
 
 _lib = None
@@ -122,6 +123,8 @@ def lib():
     for name in ("gbxc_integrate_many", "gbxc_serve_start", "gbxc_serve_stop", "gbxc_submit", "gbxc_wait",
                  "gbxc_serve_stats", "gbxc_autotune", "gbxc_set_schedule"):
         getattr(L, name).restype = c_int
+    L.gbxc_measure_alu_peaks.argtypes = [c_int, pd, pd]
+    L.gbxc_measure_alu_peaks.restype = c_int
     L.gbxc_profile_enable.argtypes = [c_void_p, c_int]
     L.gbxc_profile_read.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("gbxc_create", "gbxc_load_basis", "gbxc_load_grid", "gbxc_plan_info_get",
@@ -400,6 +403,15 @@ def gbxc_profile_read(ctx) -> dict:
     n = np.zeros(GBXC_NKERNEL, np.int64)
     _check(ctx, lib().gbxc_profile_read(ctx, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def gbxc_measure_alu_peaks(device=0):
+    """(float32, float64) FMA throughput of the device in TFLOP/s, measured."""
+    a, b = c_double(), c_double()
+    rc = lib().gbxc_measure_alu_peaks(device, ctypes.byref(a), ctypes.byref(b))
+    if rc != GBXC_OK:
+        raise GbxcError(rc, "ALU peak measurement failed")
+    return a.value, b.value
 
 
 class Context:

@@ -322,6 +322,11 @@ void free_workspace(Workspace &w) {
     w = Workspace{};
 }
 
+// The LDA / GGA codes every integration call takes (the meta-GGA has its own paths).
+bool semilocal_lda_gga(int functional) {
+    return functional == GBXC_SLATER || functional == GBXC_PBE || functional == GBXC_PBE0_SL;
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes attr;
     cudaError_t e = cudaPointerGetAttributes(&attr, p);
@@ -471,11 +476,6 @@ Schedule &get_schedule(Molecule &m, int precision, int b0, int b1, size_t budget
     SchedKey key{precision, b0, b1, budget, tile_n};
     auto it = m.scheds.find(key);
     if (it != m.scheds.end()) return *it->second;
-    if (precision == GBXC_MIXED)
-        for (int j = b0; j < b1; ++j)
-            if (pad_funcs(m.plan.func_ptr[j + 1] - m.plan.func_ptr[j]) > mixed_max_functions())
-                throw ArgError{"a batch has more than " + std::to_string(mixed_max_functions()) +
-                               " significant functions: too many for the tensor-core form (use GBXC_FP64)"};
     auto sp = std::make_unique<Schedule>();
     Schedule &S = *sp;
     const HostPlan &P = m.plan;
@@ -598,7 +598,7 @@ int integrate_impl(gbxc_ctx *ctx, int mol, const double *P, int functional, int 
     REQUIRE(P, "P is NULL");
     REQUIRE(!on_other_device(P, ctx->device) && (!Vxc || !on_other_device(Vxc, ctx->device)),
             "P or Vxc is memory of another device");
-    REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE || functional == GBXC_MVS_X, "unknown functional");
+    REQUIRE(semilocal_lda_gga(functional) || functional == GBXC_MVS_X, "unknown functional");
     REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
     int nb = m.plan.nbatch();
     REQUIRE(0 <= b0 && b0 <= b1 && b1 <= nb, "batch range out of bounds");
@@ -1357,17 +1357,24 @@ int gbxc_plan_info_get(gbxc_ctx *ctx, int mol, gbxc_plan_info *info) {
         info->nshell_entries = (long long)P.shell_idx.size();
         info->nfunc_entries = (long long)P.func_idx.size();
         info->ntiles = (long long)P.ntiles();
-        double smn = 0, smn1 = 0, work = 0;
+        double smn = 0, smn1 = 0, work = 0, sms = 0, sn2 = 0;
+        int nmax = 0;
         for (int j = 0; j < P.nbatch(); ++j) {
             double mj = (double)(P.batch_ptr[j + 1] - P.batch_ptr[j]);
             double nj = (double)(P.func_ptr[j + 1] - P.func_ptr[j]);
             smn += mj * nj * nj;
             smn1 += mj * nj;
+            sms += mj * (double)(P.shell_ptr[j + 1] - P.shell_ptr[j]);
+            sn2 += nj * nj;
+            nmax = std::max(nmax, (int)(P.func_ptr[j + 1] - P.func_ptr[j]));
             work += P.work[j];
         }
         info->sum_mn2 = smn;
         info->sum_mn = smn1;
         info->work = work;
+        info->sum_ms = sms;
+        info->sum_n2 = sn2;
+        info->max_nfunc = nmax;
         return GBXC_OK;
     });
 }
@@ -1432,7 +1439,7 @@ int gbxc_integrate_uks(gbxc_ctx *ctx, int mol, const double *Pa, const double *P
         REQUIRE(Pa && Pb, "P is NULL");
         for (const void *q : {(const void *)Pa, (const void *)Pb, (const void *)Va, (const void *)Vb})
             REQUIRE(!q || !on_other_device(q, ctx->device), "a buffer is memory of another device");
-        REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "unknown functional");
+        REQUIRE(semilocal_lda_gga(functional), "unknown functional");
         REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
         const int nb = m.plan.nbatch();
         cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
@@ -1543,7 +1550,7 @@ int gbxc_debug_batch(gbxc_ctx *ctx, int mol, int batch, const double *P, int fun
         Molecule &m = get_mol(ctx, mol);
         if (!m.has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
         REQUIRE(batch >= 0 && batch < m.plan.nbatch(), "batch out of range");
-        REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "spin-restricted LDA/GGA only");
+        REQUIRE(semilocal_lda_gga(functional), "spin-restricted LDA/GGA only");
         double E, N;
         // the mixed form forms Z inside its slicing kernel; keep_z makes it leave Z in the slab
         struct KeepZ {
@@ -1602,7 +1609,7 @@ int gbxc_integrate_fp64_noalloc(gbxc_ctx *ctx, int mol, const double *P, int fun
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {
         REQUIRE(ctx->device >= 0, "integration needs a device context");
-        REQUIRE(functional == GBXC_SLATER || functional == GBXC_PBE, "unknown functional");
+        REQUIRE(semilocal_lda_gga(functional), "unknown functional");
         REQUIRE(P && Vxc && EN, "P, Vxc and EN must be device pointers");
         REQUIRE(is_device_ptr(P) && is_device_ptr(Vxc) && is_device_ptr(EN),
                 "P, Vxc and EN must be device pointers");
@@ -1685,7 +1692,7 @@ int many_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *
     for (int k = 0; k < nmol; ++k) {
         ms[k] = &get_mol(ctx, mol_ids[k]);
         if (!ms[k]->has_grid) return fail(ctx, GBXC_ENOTREADY, "a molecule has no grid");
-        REQUIRE(functional[k] == GBXC_SLATER || functional[k] == GBXC_PBE, "unknown functional");
+        REQUIRE(semilocal_lda_gga(functional[k]), "unknown functional");
         REQUIRE(P[k], "P is NULL");
         for (int q = 0; q < k; ++q) REQUIRE(mol_ids[q] != mol_ids[k], "a molecule appears twice");
     }
@@ -1937,7 +1944,7 @@ int gbxc_submit(gbxc_ctx *ctx, int mol, const double *P, int functional, int pre
         auto it = ctx->mols.find(mol);
         if (it == ctx->mols.end()) return fail(ctx, GBXC_ENOENT, "unknown molecule id");
         if (!it->second->has_grid) return fail(ctx, GBXC_ENOTREADY, "molecule has no grid");
-        if (functional != GBXC_SLATER && functional != GBXC_PBE) return fail(ctx, GBXC_EINVAL, "unknown functional");
+        if (!semilocal_lda_gga(functional)) return fail(ctx, GBXC_EINVAL, "unknown functional");
         if (precision != GBXC_FP64 && precision != GBXC_MIXED) return fail(ctx, GBXC_EINVAL, "unknown precision");
         size_t nn = (size_t)it->second->nbf * it->second->nbf;
         try {

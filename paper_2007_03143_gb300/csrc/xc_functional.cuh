@@ -13,6 +13,9 @@
 //                  A = (beta/gamma)/(exp(-eps/gamma) - 1).
 // PW92 (unpolarised): eps = -2a(1 + a1 r_s) ln(1 + 1/(2a Q)),
 //                  Q = b1 r_s^(1/2) + b2 r_s + b3 r_s^(3/2) + b4 r_s^2.
+// PBE0, semi-local part: f = (1 - a) f_x^PBE + f_c^PBE with a = 1/4, the exact-exchange
+//                  fraction of the hybrid; the a E_x^HF term is a four-centre integral over the
+//                  orbitals, not a grid quadrature, and belongs to the caller's exchange code.
 // Derivatives are written out by the chain rule, term by term.
 #pragma once
 
@@ -28,6 +31,7 @@ constexpr double kKappa = 0.804;
 constexpr double kBeta = 0.06672455060314922;
 constexpr double kMu = 0.21951497276451704;           // beta pi^2 / 3
 constexpr double kGamma = 0.0310906908696549;         // (1 - ln 2)/pi^2
+constexpr double kPbe0ExactFraction = 0.25;           // a of PBE0
 constexpr double kPwA = 0.031091, kPwA1 = 0.21370;
 constexpr double kPwB1 = 7.5957, kPwB2 = 3.5876, kPwB3 = 1.6382, kPwB4 = 0.49294;
 
@@ -98,7 +102,7 @@ __device__ __forceinline__ void pbe_c(T rho, T sigma, T &f, T &vrho, T &vsigma) 
     vsigma = rho * dH_dY * dY_du * du_dsigma;
 }
 
-// Evaluate functional `fn` (GBXC_SLATER or GBXC_PBE); zero below kRhoMin.
+// Evaluate functional `fn` (GBXC_SLATER, GBXC_PBE or GBXC_PBE0_SL); zero below kRhoMin.
 template <typename T>
 __device__ __forceinline__ void evaluate(int fn, T rho, T sigma, T &f, T &vrho, T &vsigma) {
     if (!(rho >= T(kRhoMin))) {
@@ -111,6 +115,12 @@ __device__ __forceinline__ void evaluate(int fn, T rho, T sigma, T &f, T &vrho, 
         T fx, vx, sx, fc, vc, sc;
         pbe_x(rho, sigma, fx, vx, sx);
         pbe_c(rho, sigma, fc, vc, sc);
+        if (fn == GBXC_PBE0_SL) {   // the hybrid's semi-local part: (1 - a) PBE exchange
+            const T k = T(1) - T(kPbe0ExactFraction);
+            fx *= k;
+            vx *= k;
+            sx *= k;
+        }
         f = fx + fc;
         vrho = vx + vc;
         vsigma = sx + sc;
@@ -230,9 +240,10 @@ __device__ __forceinline__ void exchange_channel(int fn, T r, T s, T &f, T &v, T
         if (fn == GBXC_SLATER) slater(T(2) * r, ff, vr, vsg);
         else pbe_x(T(2) * r, T(4) * s, ff, vr, vsg);
     }
-    f = T(0.5) * ff;
-    v = vr;
-    vs = T(2) * vsg;
+    const T k = fn == GBXC_PBE0_SL ? T(1) - T(kPbe0ExactFraction) : T(1);
+    f = T(0.5) * k * ff;
+    v = k * vr;
+    vs = T(2) * k * vsg;
 }
 
 template <typename T>
@@ -247,7 +258,7 @@ __device__ __forceinline__ void evaluate_pol(int fn, T ra, T rb, T saa, T sab, T
     s_aa = xsa;
     s_ab = T(0);
     s_bb = xsb;
-    if (fn == GBXC_PBE) {
+    if (fn == GBXC_PBE || fn == GBXC_PBE0_SL) {
         T fc, ca, cb, csa, csab, csb;
         pbe_c_pol(ra, rb, saa, sab, sbb, fc, ca, cb, csa, csab, csb);
         f += fc;

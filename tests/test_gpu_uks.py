@@ -33,7 +33,7 @@ def _uks(L, Pa, Pb, functional, precision="fp64"):
     return E, N, Va, Vb
 
 
-@pytest.mark.parametrize("functional", ["slater", "pbe"])
+@pytest.mark.parametrize("functional", ["slater", "pbe", "pbe0_sl"])
 def test_uks_matches_oracle(loaded, functional):
     nw = loaded.w.mol.n_waters
     Pa, Pb = _spins(loaded.w, 5 * nw, 5 * nw - 1, 700)
@@ -55,7 +55,7 @@ def test_equal_spins_give_the_restricted_result(loaded):
     assert np.max(np.abs(Va - V0)) <= 1e-12 * scale and np.max(np.abs(Vb - V0)) <= 1e-12 * scale
 
 
-@pytest.mark.parametrize("functional", ["slater", "pbe"])
+@pytest.mark.parametrize("functional", ["slater", "pbe", "pbe0_sl"])
 def test_uks_mixed_matches_oracle(loaded, functional):
     nw = loaded.w.mol.n_waters
     Pa, Pb = _spins(loaded.w, 5 * nw, 5 * nw - 1, 700)

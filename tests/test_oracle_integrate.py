@@ -93,6 +93,26 @@ def test_V_is_dE_dP_pbe(water1_pbe):
     assert _fd_error(*water1_pbe, "pbe") < 1e-7
 
 
+def test_V_is_dE_dP_pbe0_semilocal(water1_pbe):
+    assert _fd_error(*water1_pbe, "pbe0_sl") < 1e-7
+
+
+def test_pbe0_semilocal_is_linear_in_the_exchange_scale(water1_pbe):
+    """E[pbe0_sl] = E[pbe] - a E_x^PBE with E_x^PBE from a separate integration of the exchange
+    alone (an oracle functional made on the spot from pbe_exchange), and the same for V."""
+    w, g, pl = water1_pbe
+    r0 = I.integrate_method(g, w.basis, w.P, "pbe0_sl", pl)
+    r1 = I.integrate_method(g, w.basis, w.P, "pbe", pl)
+    F.FUNCTIONALS["_x_only"] = F.pbe_exchange
+    try:
+        rx = I.integrate_method(g, w.basis, w.P, "_x_only", pl)
+    finally:
+        del F.FUNCTIONALS["_x_only"]
+    assert abs(r0.E - (r1.E - 0.25 * rx.E)) < 1e-12 * abs(r1.E)
+    assert np.max(np.abs(r0.V - (r1.V - 0.25 * rx.V))) < 1e-12 * np.max(np.abs(r1.V))
+    assert r0.N == r1.N
+
+
 def test_planted_mistake_is_caught(water1_pbe, monkeypatch):
     # drop the factor 2 of Eq. z_mat's gradient term in the oracle: the dE/dP pin must fail
     orig = I.integrate_batch
@@ -172,7 +192,7 @@ def _spin_densities(w, na, nb, seed):
     return 0.5 * X.density_matrix(w.S, na, seed), 0.5 * X.density_matrix(w.S, nb, seed + 1)
 
 
-@pytest.mark.parametrize("functional", ["slater", "pbe"])
+@pytest.mark.parametrize("functional", ["slater", "pbe", "pbe0_sl"])
 def test_uks_equal_spins_reduce_to_rks(water1_pbe, functional):
     w, g, pl = water1_pbe
     r = I.integrate_method(g, w.basis, w.P, functional, pl)
