@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Throughput of XC integration (E_xc + V_xc + N_el) on one GB300, as one JSON line.
 
-Workload: the 16-water PBE cluster (48 atoms, 400 Cartesian functions, SSF partition,
-75 x 16 x 32 atomic grids = 1,843,200 points, batches <= 512, eta = 1e-10), seeded
-synthetic inputs from ``xcinputs``.  A step is one ``gbxc_integrate`` call over every
-batch of the resident plan: collocation, X = P^j Phi^j, rho/grad rho, PBE, Z, V^j and
-the scatter into V_xc, E_xc and N_el.
+Workload (default): the 64-water PBE cluster of the precision form (192 atoms, 1,600 Cartesian
+functions, SSF partition, 75 x 16 x 32 atomic grids = 7,372,800 points, batches <= 512,
+eta = 1e-10), seeded synthetic inputs from ``xcinputs``; the 16-water cluster (1,843,200
+points, 400 functions) is timed too and reported under ``extra``.  A step is one
+``gbxc_integrate`` call over every batch of the resident plan: collocation, P^j gather,
+X = P^j Phi^j, rho/grad rho, PBE, Z, V^j and the scatter into V_xc, E_xc and N_el.
 
-Forms: ``fp64`` (every step in float64) and ``mixed`` (float32 collocation, split-bf16x3
-tensor-core contractions, float64 accumulation).  The headline ``value`` is the fastest
-form whose |E_xc - E_xc(fp64)| <= 1e-6 Eh.
+Forms: ``fp64`` (every step in float64) and ``mixed`` (collocation and rho in double-float
+arithmetic on the float32 pipe; both contractions on the tcgen05 tensor cores as Ozaki-sliced
+bf16 products, 5 slices of 7 bits per operand and 15 slice products, accumulated exactly in
+fp32 levels; partition weights, functional and all E/N/V accumulation in float64).  The
+headline ``value`` is the fastest form whose |E_xc - E_xc(fp64)| <= 1e-6 Eh.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the stream the
 library runs on; between steps a 256 MiB buffer is written to flush L2 (outside the
@@ -23,6 +26,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -38,7 +42,8 @@ import xcinputs as X  # noqa: E402
 
 METRIC = "grid pts/s for E_xc+V_xc at |ΔE_xc|≤1e-6 Eh vs FP64 form; p50/p99 latency"
 UNIT = "grid pts/s"
-WORKLOAD = "water16_pbe"
+WORKLOAD = "water64_pbe"
+EXTRA_WORKLOAD = "water16_pbe"
 def describe(w):
     """The workload in words, from its own parameters."""
     g = w.grid
@@ -51,7 +56,6 @@ def describe(w):
             f"(O 3s2p1d, H 2s1p, 3 primitives), {w.functional.upper() if w.functional == 'pbe' else 'Slater'}, "
             f"{g.partition.upper() if g.partition == 'ssf' else 'Becke'} partition, Mura-Knowles {g.nrad} x {ang}, "
             f"batches <= {g.max_batch} points, eta = {g.eta:g}")
-FP64_PEAK_GFLOPS = 152 * 4 * 2.070   # 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (alu bound)
 
 
 def _rank_env():
@@ -165,45 +169,70 @@ def _traffic(kernel, form):
     return e.get("bytes_per_launch")
 
 
-# Per-unit work of each kernel class (the unit is one batch's (point, function) element, or
-# 2 m n^2 flops for a contraction).  Contractions: algorithmic flops 2 m n^2 each; the mixed
-# form issues 15 bf16 slice products per term, so its tensor work is 15 x 2 m n^2.
-# Streaming steps: the bytes of the step's inputs and outputs at the widths the form stores
-# them (float64 form: 8 B per value; mixed form: Phi as a float pair, 8 B, grad Phi as a float
-# hi word plus a bf16 lo word, 6 B per component, bf16 slices 2 B):
-#   colloc  writes Phi and grad Phi [+ 5 bf16 Phi slices in the mixed form]
-#   rho_z   float64: reads Phi, grad Phi, X, writes Z; mixed: reads Phi, grad Phi, X
-#           (Z is formed in the slicing kernel from per-point coefficients)
-#   vslice  mixed: reads Phi and the grad Phi hi words, writes 5 Z and 5 Phi bf16 slices
-STREAM_BYTES = {"fp64": {"colloc": 32, "rho_z": 48},
-                "mixed": {"colloc": 8 + 18 + 10, "rho_z": 8 + 18 + 8, "vslice": 8 + 12 + 20}}
+# Per-unit work of each kernel class, as the algorithmic work of the method (not the work the
+# implementation issues):
+#   xgemm, vgemm  X = P^j Phi^j and W = Z^T Phi: 2 m n^2 flops each per batch.  The mixed form
+#                 is bounded by the bf16 tensor peak at 3 x the algorithmic flops (a 3-term
+#                 split-bf16 contraction); it issues 15 slice products, reported as "issued".
+#                 The float64 form is bounded by the float64 FMA pipe.
+#   colloc        m |S_j| (3 exp + 25) operations per batch (3 primitives per shell), bounded
+#                 by the plain ALUs: the double-float arithmetic runs on the float32 FMA pipe,
+#                 whose measured peak is the denominator (an exp counted as one operation).
+#   pgather       the P^j gather: 8 B per element of P^j read, bounded by HBM/L2.
+#   rho_z, vslice Phi / X / Z round trips between kernels: implementation bytes, not algorithmic
+#                 ones; reported against the copy bandwidth at the widths the form stores them
+#                 (mixed: Phi 8 B, grad Phi 18 B, X 8 B, slices 2 B each; float64: 8 B values).
+COLLOC_OPS = 3 + 25
+STREAM_BYTES = {"fp64": {"rho_z": 48},
+                "mixed": {"rho_z": 8 + 18 + 8, "vslice": 8 + 12 + 20}}
 
 
-def roofline(kind, ms, form, info, peaks, peak_src):
+def roofline(kind, ms, form, info, peaks, peak_src, alu):
+    """Roofline of one kernel class from its per-call device time `ms`."""
     if ms <= 0:
         return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}
+    sec = ms / 1e3
     if kind in ("xgemm", "vgemm"):
         flops = 2.0 * info["sum_mn2"]
         if form == "fp64":
-            ach = flops / (ms / 1e3) / 1e12
-            r = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz",
+            r = {"bound": "alu", "achieved": flops / sec / 1e12, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                 "peak_source": alu["source"] + " float64 FMA",
                  "algorithmic_per_unit": "2 m n^2 flops per batch"}
         else:
-            ach = 15.0 * flops / (ms / 1e3) / 1e12
-            r = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            peak = peaks["bf16_tflops"]
+            r = {"bound": "tensor", "achieved": 3.0 * flops / sec / 1e12, "peak": peak, "unit": "TFLOP/s",
                  "peak_source": f"{peak_src} bf16 burst",
-                 "algorithmic_per_unit": "15 bf16 slice products x 2 m n^2 flops per batch"}
+                 "algorithmic_per_unit": "3 x 2 m n^2 flops per batch (split-bf16 count)",
+                 "issued": {"achieved": 15.0 * flops / sec / 1e12, "frac": 15.0 * flops / sec / 1e12 / peak,
+                            "per_unit": "15 bf16 slice products x 2 m n^2 flops per batch"}}
+    elif kind == "colloc":
+        ops = COLLOC_OPS * info["sum_ms"]
+        r = {"bound": "alu", "achieved": ops / sec / 1e12, "peak": alu["fp32_tflops"], "unit": "TFLOP/s",
+             "peak_source": alu["source"] + " float32 FMA",
+             "algorithmic_per_unit": f"{COLLOC_OPS} operations (3 exp + 25) per (point, shell) pair"}
+    elif kind == "pgather":
+        nbytes = 8.0 * info["sum_n2"]
+        r = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "peak_source": f"{peak_src} copy bandwidth", "algorithmic_per_unit": "8 B per element of P^j"}
     elif kind in STREAM_BYTES.get(form, {}):
         nbytes = STREAM_BYTES[form][kind] * info["sum_mn"]
-        ach = nbytes / (ms / 1e3) / 1e9
-        r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+        r = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
              "peak_source": f"{peak_src} copy bandwidth",
-             "algorithmic_per_unit": f"{STREAM_BYTES[form][kind]} B per (point, function) element"}
+             "algorithmic_per_unit": f"implementation bytes: {STREAM_BYTES[form][kind]} B per (point, function)"}
     else:
         return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}
     r["frac"] = r["achieved"] / r["peak"]
     return r
+
+
+def alu_peaks(G, device):
+    """Measured float32 / float64 FMA peaks (TFLOP/s); the nominal figures if that fails."""
+    try:
+        f32, f64 = G.gbxc_measure_alu_peaks(device)
+        return {"fp32_tflops": f32, "fp64_tflops": f64, "source": "measured (gbxc_measure_alu_peaks)"}
+    except Exception:
+        return {"fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
+                "source": "nominal (152 SMs, 2.07 GHz)"}
 
 
 def oracle_setup(w):
@@ -213,11 +242,8 @@ def oracle_setup(w):
     return g, pl
 
 
-def cpu_baseline(w, target_points, seed=0, setup=None):
-    """The oracle (method-equivalent mode, float64) on a seeded sample of the workload's batches."""
-    from oracle import integrate as I
-    from oracle import partition as PT
-    g, pl = setup if setup is not None else oracle_setup(w)
+def _sample(pl, target_points, seed):
+    """Seeded random batches of the plan holding at least target_points points."""
     rng = np.random.default_rng(seed)
     sel, n = [], 0
     for j in rng.permutation(len(pl.batch_points)):
@@ -225,31 +251,59 @@ def cpu_baseline(w, target_points, seed=0, setup=None):
         n += len(pl.batch_points[j])
         if n >= target_points:
             break
-    idx = np.concatenate([pl.batch_points[j] for j in sel])
+    return sel, n
+
+
+def _weights(w, g, pl, sels):
+    """Partition weights (oracle, float64) of the points of the sampled batches only."""
+    from oracle import partition as PT
+    idx = np.concatenate([pl.batch_points[j] for sel in sels for j in sel])
     g.w = np.zeros(len(g.x))
     g.w[idx] = g.wq[idx] * PT.partition_weights(g.x[idx], g.y[idx], g.z[idx], g.parent[idx], w.mol.xyz,
                                                 w.grid.partition)
+
+
+def cpu_baseline(w, target_points, seed=0, setup=None):
+    """The oracle (method-equivalent mode, float64) on a seeded sample of the workload's batches;
+    times the integrate step only (grid, plan and the sample's weights are prepared first)."""
+    from oracle import integrate as I
+    g, pl = setup if setup is not None else oracle_setup(w)
+    sel, n = _sample(pl, target_points, seed)
+    _weights(w, g, pl, [sel])
     t0 = time.perf_counter()
     I.integrate_method(g, w.basis, w.P, w.functional, pl, batches=sel)
     dt = time.perf_counter() - t0
     return n, dt, len(sel), len(pl.batch_points)
 
 
+def _default_points(w, small, large):
+    """Oracle sample size: fewer points for the large-basis workloads (their batches cost more
+    per point, and the oracle's SSF weights of the sample are prepared outside the timing)."""
+    return large if w.basis.nbf < 1000 else small
+
+
 def run_reference(args):
     rank, world, _ = _rank_env()
     if world > 1 and rank != 0:
         return 0
+    from oracle import integrate as I
     w = X.make_workload(args.workload)
-    setup = oracle_setup(w)
+    g, pl = oracle_setup(w)
+    target = args.ref_points or _default_points(w, 30000, 100000)
+    sels = [_sample(pl, target, s) for s in range(args.warmup + args.steps)]
+    _weights(w, g, pl, [sel for sel, _ in sels])
     times, pts = [], []
-    for s in range(args.warmup + args.steps):
-        n, dt, nsel, nb = cpu_baseline(w, args.ref_points, seed=s, setup=setup)
-        if s >= args.warmup:
+    for k, (sel, n) in enumerate(sels):
+        t0 = time.perf_counter()
+        I.integrate_method(g, w.basis, w.P, w.functional, pl, batches=sel)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
             times.append(dt)
             pts.append(n)
+    nb = len(pl.batch_points)
     value = sum(pts) / sum(times)
     cores = os.cpu_count()
-    sample = (f"{args.ref_points}+ points per step from seeded random batches of the "
+    sample = (f"{target}+ points per step from seeded random batches of the "
               f"{nb}-batch plan; integrate step only (grid, plan, weights precomputed)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
@@ -430,8 +484,9 @@ def main():
     ap.add_argument("--impl", default="gbxc", choices=["gbxc", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--forms", default="fp64,mixed")
-    ap.add_argument("--cpu-points", type=int, default=300000)
-    ap.add_argument("--ref-points", type=int, default=100000)
+    ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample points (0 = by workload)")
+    ap.add_argument("--ref-points", type=int, default=0, help="reference-arm points per step (0 = by workload)")
+    ap.add_argument("--extra-workload", default=EXTRA_WORKLOAD, help="also timed (mixed form); '' to skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scratch-mb", type=int, default=0, help="device scratch budget (0 = default)")
     ap.add_argument("--mode", default="single", choices=["single", "many", "serve"])
@@ -542,12 +597,13 @@ def main():
     compute = {k: v for k, v in prof.items() if k in ("colloc", "xgemm", "rho_z", "vgemm", "pgather", "vslice")}
     dom = max(compute, key=lambda k: compute[k][0])
     dom_ms, dom_launch = compute[dom]
-    roof = roofline(dom, dom_ms / args.steps, head, info, peaks, peak_src)
+    alu = alu_peaks(G, local)
+    roof = roofline(dom, dom_ms / args.steps, head, info, peaks, peak_src, alu)
     roof["kernel"] = dom
     roof["launches_per_step"] = dom_launch / args.steps
     roof["ms_per_step"] = dom_ms / args.steps
     roof["traffic"] = _traffic(dom, head)
-    roof["all_classes"] = {k: roofline(k, v[0] / args.steps, head, info, peaks, peak_src)
+    roof["all_classes"] = {k: roofline(k, v[0] / args.steps, head, info, peaks, peak_src, alu)
                            for k, v in compute.items() if v[0] > 0}
     launches = sum(v[1] for k, v in prof.items() if k != "weights")
 
@@ -566,23 +622,50 @@ def main():
     e2e = {"value": _job_rate(npts, world, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": nbf * nbf * 8, "d2h_bytes_per_step": nbf * nbf * 8 + 16}
 
+    extra = None
+    if args.extra_workload and args.extra_workload != args.workload:
+        we = X.make_workload(args.extra_workload)
+        mid_e = ctx.load_molecule(we.mol, we.basis, we.grid)
+        npts_e = G.gbxc_plan_info_get(ctx.h, mid_e)["npts"]
+        Pe = torch.tensor(we.P, device=dev)
+        Ve = torch.zeros((we.basis.nbf, we.basis.nbf), dtype=torch.float64, device=dev)
+        E64e, _ = G.gbxc_integrate(ctx.h, mid_e, Pe, we.functional, "fp64", Ve)
+        for _ in range(args.warmup):
+            G.gbxc_integrate(ctx.h, mid_e, Pe, we.functional, "mixed", Ve)
+        ms_e = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Eme, _ = G.gbxc_integrate(ctx.h, mid_e, Pe, we.functional, "mixed", Ve)
+            b.record(stream)
+            b.synchronize()
+            ms_e.append(a.elapsed_time(b))
+        extra = {"name": args.extra_workload, "workload": describe(we), "form": "mixed",
+                 "value": npts_e * len(ms_e) / (sum(ms_e) / 1e3), "unit": UNIT,
+                 "ms_per_step": sum(ms_e) / len(ms_e), "dE_xc_vs_fp64": abs(Eme - E64e)}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": R["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head == "fp64" else "bf16x3+f32+f64", "data": "synthetic",
+            "dtype": "f64" if head == "fp64" else "bf16(ozaki-5)+f32x2+f64", "data": "synthetic",
             "config": {"workload": describe(w), "name": args.workload, "npts": npts, "nbf": nbf,
-                       "nbatch": info["nbatch"], "sum_mn2": info["sum_mn2"], "form": head,
+                       "nbatch": info["nbatch"], "sum_mn2": info["sum_mn2"], "max_nfunc": info["max_nfunc"],
+                       "form": head, "host_arch": platform.machine(),
+                       "plan_note": "grid coordinates come from the host's libm (cos, log, sqrt), so nbatch "
+                                    "and sum_mn2 may differ in the last digits between host architectures",
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
+            "alu_peaks": alu,
             "p50_ms": p50, "p99_ms": p99, "e2e": e2e, "roofline": roof, "gpu_launches": launches,
-            "clocks": R["clocks"], "load_grid_s": load_s,
+            "clocks": R["clocks"], "load_grid_s": load_s, "extra": extra,
             "forms": {f: ({"value": npts * args.steps / (r["total_ms"] / 1e3), "ms_per_step":
                            r["total_ms"] / args.steps, **acc[f],
                            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in r["prof"].items()}}
                           if "error" not in r else r) for f, r in res.items()}}
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            n, dt, nsel, nb = cpu_baseline(w, args.cpu_points)
+            n, dt, nsel, nb = cpu_baseline(w, args.cpu_points or _default_points(w, 40000, 300000))
             line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"{n} points in {nsel} of {nb} batches (seeded), integrate "
                                               f"step only, numpy float64 with BLAS on all cores"}
