@@ -316,23 +316,25 @@ def run_reference(args):
     return 0
 
 
-def _water_pool(G, ctx, sizes, seed0, spec):
+def _water_pool(G, ctx, sizes, seed0, spec, device_planner=False):
     """Register seeded water clusters of the given sizes; returns [(mol id, nbf, npts, P)]."""
     out = []
+    load = G.gbxc_load_grid_device if device_planner else G.gbxc_load_grid
     for k, nw in enumerate(sizes):
         mol = X.water_cluster(nw, seed0 + k)
         b = X.make_basis(mol)
         S = X.overlap_matrix(b)
         P = X.density_matrix(S, 5 * nw, seed0 + 5000 + k)
         mid, nbf = G.gbxc_load_basis(ctx.h, mol.xyz, mol.Z, b.atom, b.L, b.nprim, b.alpha, b.coeff)
-        npts, _ = G.gbxc_load_grid(ctx.h, mid, spec.nrad, spec.ntheta, spec.nphi, spec.partition,
-                                   spec.max_batch, spec.eta, spec.mk_alpha)
+        npts, _ = load(ctx.h, mid, spec.nrad, spec.ntheta, spec.nphi, spec.partition, spec.max_batch, spec.eta,
+                       spec.mk_alpha)
         out.append((mid, nbf, npts, P))
     return out
 
 
 def run_many(args):
-    """Batching form: one CUDA-graph launch over many molecules of uneven size."""
+    """Batching form: one CUDA-graph launch over many molecules of uneven size (default: 256
+    seeded water clusters of 1-40 waters); the float64 form on a stated subsample."""
     import torch
     import paper_2007_03143_gb300 as G
     torch.cuda.set_device(0)
@@ -340,37 +342,48 @@ def run_many(args):
     sizes = [int(v) for v in rng.integers(args.min_waters, args.max_waters + 1, size=args.nmol)]
     spec = X.GridSpec(75, 16, 32, "ssf", 512)
     ctx = G.Context(0)
-    pool = _water_pool(G, ctx, sizes, 40000, spec)
-    ids = [p[0] for p in pool]
-    Ps = [torch.tensor(p[3], device="cuda") for p in pool]
+    t0 = time.perf_counter()
+    pool = _water_pool(G, ctx, sizes, 40000, spec, device_planner=True)
+    load_s = time.perf_counter() - t0
     fns = ["pbe"] * len(pool)
-    npts = sum(p[2] for p in pool)
-    res, tune = {}, {}
 
-    def timed(prec):
-        for _ in range(args.warmup):
-            G.gbxc_integrate_many(ctx.h, ids, Ps, fns, prec)
+    def timed(sub, prec, steps, warmup):
+        ids = [p[0] for p in sub]
+        Ps = [torch.tensor(p[3], device="cuda") for p in sub]
+        for _ in range(warmup):
+            G.gbxc_integrate_many(ctx.h, ids, Ps, fns[:len(sub)], prec)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            E, N = G.gbxc_integrate_many(ctx.h, ids, Ps, fns, prec)
-        return (time.perf_counter() - t0) / args.steps, E
+        ts = []
+        for _ in range(steps):
+            t = time.perf_counter()
+            E, N = G.gbxc_integrate_many(ctx.h, ids, Ps, fns[:len(sub)], prec)
+            ts.append(time.perf_counter() - t)
+        return ts, E
 
-    for prec in ("fp64", "mixed"):
-        dt0, _ = timed(prec)                       # default schedule: 8 branches, N tile 128
-        if args.no_autotune:
-            dt, E = dt0, _
-        else:
-            w, t, ms = G.gbxc_autotune(ctx.h, ids, Ps, fns, prec)
-            dt, E = timed(prec)
-            tune[prec] = {"branches": w, "tile_n": t, "tuned_device_ms": ms, "default_ms_per_step": dt0 * 1e3,
-                          "tuned_ms_per_step": dt * 1e3}
-        res[prec] = {"value": npts / dt, "ms_per_step": dt * 1e3, "E": E}
-    dE = float(np.max(np.abs(res["mixed"]["E"] - res["fp64"]["E"])))
+    tune = None
+    if not args.no_autotune:
+        ids = [p[0] for p in pool]
+        Ps = [torch.tensor(p[3], device="cuda") for p in pool]
+        w, t, ms = G.gbxc_autotune(ctx.h, ids, Ps, fns, "mixed")
+        tune = {"branches": w, "tile_n": t, "tuned_device_ms": ms, "grouped": w == 0}
+    ts, Em = timed(pool, "mixed", args.steps, args.warmup)
+    npts = sum(p[2] for p in pool)
+    lat = sorted(ts)
+    mixed = {"value": npts * len(ts) / sum(ts), "ms_per_step": 1e3 * sum(ts) / len(ts),
+             "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[-1]}
+    sub = pool[:args.fp64_subsample]
+    npts_sub = sum(p[2] for p in sub)
+    ts64, E64 = timed(sub, "fp64", 1, 1)
+    tsm, Ems = timed(sub, "mixed", 2, 1)
+    fp64 = {"value": npts_sub * len(ts64) / sum(ts64), "ms_per_step": 1e3 * sum(ts64) / len(ts64),
+            "subsample": f"the first {len(sub)} molecules ({sum(sizes[:len(sub)])} waters, {npts_sub} points)",
+            "mixed_on_subsample_value": npts_sub * len(tsm) / sum(tsm)}
+    dE = float(np.max(np.abs(np.asarray(Ems) - np.asarray(E64))))
     line = {"mode": "many", "metric": "grid pts/s, one CUDA-graph launch over many molecules", "unit": UNIT,
-            "value": res["mixed"]["value"], "ms_per_step": res["mixed"]["ms_per_step"],
-            "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"]},
-            "max_dE_xc_mixed_vs_fp64": dE, "autotune": tune, "n_molecules": len(pool), "waters": sizes, "npts": npts,
+            "value": mixed["value"], "ms_per_step": mixed["ms_per_step"], "p50_ms": mixed["p50_ms"],
+            "p99_ms": mixed["p99_ms"], "fp64": fp64, "max_dE_xc_mixed_vs_fp64_on_subsample": dE,
+            "schedule": tune if tune else "grouped launch (default)", "n_molecules": len(pool),
+            "waters": sizes, "total_waters": int(sum(sizes)), "npts": npts, "load_grid_s": load_s,
             "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
             "timing": "wall clock around the call (inputs resident on the device)"}
     print(json.dumps(line))
@@ -443,7 +456,7 @@ def run_serve(args):
     spec = X.GridSpec(75, 16, 32, "ssf", 512)
     ctx = G.Context(0)
     t0 = time.perf_counter()
-    pool = _water_pool(G, ctx, sizes, 50000, spec)
+    pool = _water_pool(G, ctx, sizes, 50000, spec, device_planner=True)
     load_s = time.perf_counter() - t0
     # float64 per-request path for comparison (one request per molecule, sequential)
     t0 = time.perf_counter()
@@ -463,7 +476,7 @@ def run_serve(args):
     G.gbxc_serve_start(ctx.h, args.slots, 0)
     sweep = [_stream(G, ctx, pool, r, args.requests, args.warmup_requests, 5100 + k) for k, r in enumerate(rates)]
     G.gbxc_serve_stop(ctx.h)
-    head = sweep[0]
+    head = next((x for x in sweep if x["offered_req_per_s"] == 200.0), sweep[-1])   # the configured mean rate
     line = {"mode": "serve", "metric": "p50/p99 latency and grid pts/s of a Poisson request stream",
             "unit": UNIT, **head, "sweep": sweep, "slots": args.slots, "pool_waters": sizes,
             "mean_points_per_request": float(np.mean([p[2] for p in pool])),
@@ -486,23 +499,28 @@ def main():
     ap.add_argument("--forms", default="fp64,mixed")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample points (0 = by workload)")
     ap.add_argument("--ref-points", type=int, default=0, help="reference-arm points per step (0 = by workload)")
-    ap.add_argument("--extra-workload", default=EXTRA_WORKLOAD, help="also timed (mixed form); '' to skip")
+    ap.add_argument("--extra-workload", default=EXTRA_WORKLOAD, help="also timed (mixed form); 'none' to skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scratch-mb", type=int, default=0, help="device scratch budget (0 = default)")
     ap.add_argument("--mode", default="single", choices=["single", "many", "serve"])
-    ap.add_argument("--nmol", type=int, default=64)
+    ap.add_argument("--nmol", type=int, default=256)
+    ap.add_argument("--fp64-subsample", type=int, default=16, help="batching: molecules timed in float64")
     ap.add_argument("--no-autotune", action="store_true", help="batching: keep the default schedule")
-    ap.add_argument("--min-waters", type=int, default=1)
-    ap.add_argument("--max-waters", type=int, default=8)
-    ap.add_argument("--pool", type=int, default=16)
+    ap.add_argument("--min-waters", type=int, default=None, help="default 1 (many) or 4 (serve)")
+    ap.add_argument("--max-waters", type=int, default=None, help="default 40 (many) or 100 (serve)")
+    ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--rate", type=float, default=40.0, help="serving: mean requests per second")
-    ap.add_argument("--rates", default="", help="serving: comma-separated sweep of offered rates")
-    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rates", default="25,50,100,200", help="serving: comma-separated sweep of offered rates")
+    ap.add_argument("--requests", type=int, default=100, help="serving: requests per offered rate")
     ap.add_argument("--warmup-requests", type=int, default=20)
     ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.min_waters is None:
+        args.min_waters = 4 if args.mode == "serve" else 1
+    if args.max_waters is None:
+        args.max_waters = 100 if args.mode == "serve" else 40
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "many":
@@ -623,7 +641,7 @@ def main():
            "h2d_bytes_per_step": nbf * nbf * 8, "d2h_bytes_per_step": nbf * nbf * 8 + 16}
 
     extra = None
-    if args.extra_workload and args.extra_workload != args.workload:
+    if args.extra_workload and args.extra_workload not in ("none", args.workload):
         we = X.make_workload(args.extra_workload)
         mid_e = ctx.load_molecule(we.mol, we.basis, we.grid)
         npts_e = G.gbxc_plan_info_get(ctx.h, mid_e)["npts"]

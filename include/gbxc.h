@@ -275,16 +275,21 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
                            void *stream);
 
 /* Batching form: integrate several resident molecules in ONE CUDA graph launch.
- * The molecules are spread over up to 8 parallel graph branches by the greedy
- * minimum-load rule of Algorithm 3 applied to the work estimate of Eq. batch_work,
- * each branch with its own stream and device workspace; every molecule's batches run
- * through the same batched kernels as gbxc_integrate.  The graph is captured on the
- * first call for a given (molecule list, functionals, precision) and replayed by later
- * calls with the same list (only P changes).
+ * Default (grouped) schedule: the molecules' plans are concatenated into one combined plan,
+ * so each kernel launch (collocation, P^j slicing, the two contractions, rho/functional, Z)
+ * covers the tiles of every molecule in a chunk of the device scratch, and a batch->molecule
+ * map gives each batch its molecule's P, V accumulator and functional (the paper's
+ * memory-saturating device subsets, Sec. 2.3, over all molecules at once).  The alternative
+ * schedule (gbxc_set_schedule / gbxc_autotune with branches >= 1) spreads the molecules over
+ * parallel graph branches by the greedy minimum-load rule of Algorithm 3 applied to the work
+ * estimate of Eq. batch_work, each branch with its own stream and workspace.  The graph is
+ * captured on the first call for a given (molecule list, precision, schedule) and replayed by
+ * later calls with the same list (P and the functionals may change).  A NaN or an infinity
+ * in any P returns GBXC_EINVAL.
  *   nmol          number of molecules (each id at most once)
  *   mol_ids[k]    molecule ids
  *   P[k]          nbf_k x nbf_k density matrices, host or device
- *   functional[k] GBXC_SLATER or GBXC_PBE per molecule
+ *   functional[k] GBXC_SLATER, GBXC_PBE or GBXC_PBE0_SL per molecule
  *   precision     GBXC_FP64 or GBXC_MIXED for all
  *   Exc, Nel      host arrays of nmol (may be NULL)
  *   Vxc[k]        outputs, host or device (Vxc or Vxc[k] may be NULL)
@@ -295,9 +300,10 @@ int gbxc_integrate_many(gbxc_ctx *ctx, int nmol, const int *mol_ids, const doubl
 
 /* Autotuner of the batching form (no counterpart in the paper, which uses MAGMA's fixed
  * kernels): times gbxc_integrate_many on this molecule list for every candidate schedule --
- * graph branch counts {1, 2, 4, 8, 16} (at most nmol) and, for GBXC_MIXED, the tcgen05 GEMM
- * N tile (128 functions with one TMEM accumulator set, or 64 with two, which lets a tile's
- * epilogue overlap the next tile's MMAs) -- by CUDA events around the graph launch (best of
+ * the grouped launch (branches 0) and graph branch counts {1, 2, 4, 8, 16} (at most nmol),
+ * and, for GBXC_MIXED, the tcgen05 GEMM N tile (128 functions with one TMEM accumulator set,
+ * or 64 with two, which lets a tile's epilogue overlap the next tile's MMAs) -- by CUDA
+ * events around the graph launch (best of
  * two replays after a capturing run), keeps the fastest for later gbxc_integrate_many calls
  * with the same (molecule list, precision) on this context, and returns it.
  *   arguments as gbxc_integrate_many (P is read; no results are returned)
@@ -310,8 +316,9 @@ int gbxc_autotune(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *con
                   double *ms_out);
 
 /* Sets the schedule gbxc_integrate_many uses for (molecule list, precision) on this context,
- * as gbxc_autotune would: `branches` graph branches (1..64, at most nmol are used) and GEMM
- * N tile `tile_n` (64 or 128; the float64 form ignores it).  GBXC_EINVAL otherwise. */
+ * as gbxc_autotune would: `branches` 0 for the grouped launch, else that many graph branches
+ * (1..64, at most nmol are used), and GEMM N tile `tile_n` (64 or 128; the float64 form
+ * ignores it).  GBXC_EINVAL otherwise. */
 int gbxc_set_schedule(gbxc_ctx *ctx, int nmol, const int *mol_ids, int precision, int branches, int tile_n);
 
 /* Serving form: continuous batching of integration requests.

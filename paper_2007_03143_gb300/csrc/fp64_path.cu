@@ -20,6 +20,7 @@
 
 #include "internal.h"
 #include "solid_harmonics.cuh"
+#include "group.cuh"
 #include "xc_functional.cuh"
 
 namespace gbxc {
@@ -147,6 +148,12 @@ __global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a, const double *__re
     int64_t t = a.t0 + blockIdx.x;
     int rb = blockIdx.y;
     int j = a.plan.tile_batch[t];
+    int nbf = a.nbf;
+    if (a.batch_mol) {   // grouped chunk: the batch's own molecule
+        const MolRef r = mol_of(a, j);
+        P = r.P;
+        nbf = r.nbf;
+    }
     int64_t f0 = a.plan.func_ptr[j];
     int n = (int)(a.plan.func_ptr[j + 1] - f0);
     int r0 = rb * XB_R;
@@ -175,7 +182,7 @@ __global__ void __launch_bounds__(256) xgemm_f64(ChunkArgs a, const double *__re
             int kk = e / XB_R, rr = e % XB_R;
             int k = k0 + kk;
             int fr = Frow[rr];
-            As[kk][rr] = (fr >= 0 && k < n) ? P[(size_t)fr * a.nbf + F[k]] : 0.0;
+            As[kk][rr] = (fr >= 0 && k < n) ? P[(size_t)fr * nbf + F[k]] : 0.0;
         }
         for (int e = tid; e < XB_K * TILE; e += 256) {
             int kk = e / TILE, c = e % TILE;
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(TILE) rho_xc_z_f64(ChunkArgs a) {
         double w = a.plan.w[a.plan.tile_first[t] + i];
         double sigma = gx * gx + gy * gy + gz * gz;
         double f, vr, vs;
-        xc::evaluate<double>(a.functional, rho, sigma, f, vr, vs);
+        xc::evaluate<double>(mol_of(a, j).functional, rho, sigma, f, vr, vs);
         e = w * f;
         nn = w * rho;
         ca = 0.5 * w * vr;
@@ -423,6 +430,12 @@ constexpr int VB = 64, VK = 16;
 __global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a, int zp, int pp, double *__restrict__ Vacc) {
     const int *task = a.vtasks + 5 * blockIdx.x;
     int j = task[0], mb = task[1], nb = task[2];
+    int nbf = a.nbf;
+    if (a.batch_mol) {   // grouped chunk: the batch's own molecule
+        const MolRef r = mol_of(a, j);
+        Vacc = r.Vacc;
+        nbf = r.nbf;
+    }
     int64_t tb = task[3], te = task[4];
     int64_t f0 = a.plan.func_ptr[j];
     int n = (int)(a.plan.func_ptr[j + 1] - f0);
@@ -471,7 +484,7 @@ __global__ void __launch_bounds__(256) vgemm_f64(ChunkArgs a, int zp, int pp, do
     for (int u = 0; u < 4; ++u) {
         int mr = m0 + ty * 4 + u;
         if (mr >= n) continue;
-        size_t rowg = (size_t)F[mr] * a.nbf;
+        size_t rowg = (size_t)F[mr] * nbf;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             int nr = n0 + tx * 4 + v;

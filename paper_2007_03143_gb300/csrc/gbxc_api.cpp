@@ -68,6 +68,8 @@ struct Molecule {
     MixedResident mixed_res;
     double work = 0.0;          // sum_j W_j, for balancing many molecules over graph branches
     double *many_P = nullptr, *many_V = nullptr, *many_tot = nullptr;   // gbxc_integrate_many
+    double *many_Vacc = nullptr;    // its V accumulator in the grouped launch
+    float *many_pdf = nullptr;      // and its P as double-float planes (tensor-core form)
     size_t many_cap = 0;
 };
 
@@ -183,6 +185,26 @@ struct ManyGraph {
     std::vector<cudaEvent_t> join;
 };
 
+// gbxc_integrate_many as one grouped launch per kernel and chunk: the molecules' plans are
+// concatenated into one combined plan (points copied; batches, shells and tiles renumbered;
+// function indices kept local to each molecule, since P and V are per molecule), so each
+// kernel launch of a chunk spans the tiles of every molecule in it.  batch_mol and the MolRef
+// table give each batch its molecule's P, V accumulator, nbf and functional.  The launches of
+// one call are captured once into a CUDA graph.
+struct Group {
+    std::vector<int> mols;
+    int precision = -1, tile_n = 0;
+    size_t budget = 0;
+    Molecule gm;                       // the combined plan; owns its device copies
+    std::vector<int> bofs;             // first combined batch of each molecule, then the total
+    int *d_batch_mol = nullptr;
+    MolRef *d_mols = nullptr;
+    std::vector<MolRef> h_mols;
+    Workspace ws;
+    cudaGraphExec_t exec = nullptr;
+    long long launches[GBXC_NKERNEL] = {};
+};
+
 }  // namespace
 
 struct gbxc_ctx {
@@ -192,6 +214,7 @@ struct gbxc_ctx {
     Workspace ws;                   // the default workspace (synchronous calls)
     std::vector<Workspace> branch_ws;   // gbxc_integrate_many branches
     ManyGraph many;
+    std::unique_ptr<Group> group;   // gbxc_integrate_many, grouped schedule
     // gbxc_autotune results: (molecule list, precision) -> {graph branches, GEMM N tile}
     std::map<std::pair<std::vector<int>, int>, std::pair<int, int>> tuned;
     std::string err;
@@ -301,7 +324,10 @@ void free_molecule(Molecule &m) {
     cudaFree(m.many_P);
     cudaFree(m.many_V);
     cudaFree(m.many_tot);
+    cudaFree(m.many_Vacc);
+    cudaFree(m.many_pdf);
 }
+
 
 void free_workspace(Workspace &w) {
     if (w.owns) {
@@ -320,6 +346,26 @@ void free_workspace(Workspace &w) {
         free_mixed_ctx(w.mixed);
     }
     w = Workspace{};
+}
+
+void free_group(std::unique_ptr<Group> &G);
+// The cached grouped launch holds copies of its molecules' plans and their buffers: drop it
+// when one of them is unloaded or gets a new grid.
+void drop_group_with(gbxc_ctx *ctx, int mol);
+
+void free_group(std::unique_ptr<Group> &G) {
+    if (!G) return;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    cudaFree(G->d_batch_mol);
+    cudaFree(G->d_mols);
+    free_workspace(G->ws);
+    free_molecule(G->gm);
+    G.reset();
+}
+
+void drop_group_with(gbxc_ctx *ctx, int mol) {
+    if (ctx->group && std::find(ctx->group->mols.begin(), ctx->group->mols.end(), mol) != ctx->group->mols.end())
+        free_group(ctx->group);
 }
 
 // The LDA / GGA codes every integration call takes (the meta-GGA has its own paths).
@@ -905,6 +951,7 @@ void gbxc_destroy(gbxc_ctx *ctx) {
         free_workspace(w);
     }
     ctx->branch_ws.clear();
+    free_group(ctx->group);
     if (ctx->many.exec) cudaGraphExecDestroy(ctx->many.exec);
     if (ctx->many.fork) cudaEventDestroy(ctx->many.fork);
     for (auto e : ctx->many.join) cudaEventDestroy(e);
@@ -1067,6 +1114,7 @@ int gbxc_load_plan(gbxc_ctx *ctx, int mol, const char *path, long long *npts_out
                 ctx->many.mols.clear();
             }
         }
+        drop_group_with(ctx, mol);
         free_grid(m);
         m.spec = h.spec;
         m.plan = std::move(P);
@@ -1089,6 +1137,7 @@ int gbxc_unload(gbxc_ctx *ctx, int mol) {
                 ctx->many.exec = nullptr;
                 ctx->many.mols.clear();
             }
+            drop_group_with(ctx, mol);
             for (auto t = ctx->tuned.begin(); t != ctx->tuned.end();) {
                 const std::vector<int> &ids = t->first.first;
                 t = std::find(ids.begin(), ids.end(), mol) != ids.end() ? ctx->tuned.erase(t) : std::next(t);
@@ -1314,6 +1363,7 @@ int load_grid_impl(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, long long
             ctx->many.mols.clear();
         }
         if (on_device) REQUIRE(!host_only, "the device planner needs a device context");
+        drop_group_with(ctx, mol);
         free_grid(m);
         m.spec = *spec;
         std::vector<double> x, y, z, wq;
@@ -1822,6 +1872,280 @@ int many_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *
     return GBXC_OK;
 }
 
+
+// The combined plan of a molecule list (host metadata, device copies, shell tables) and the
+// batch -> molecule map.
+void build_group(gbxc_ctx *ctx, Group &G, const std::vector<Molecule *> &ms) {
+    Molecule &g = G.gm;
+    HostPlan &H = g.plan;
+    cudaStream_t s = ctx->stream;
+    H = HostPlan{};
+    H.batch_ptr = {0};
+    H.shell_ptr = {0};
+    H.func_ptr = {0};
+    H.batch_tile = {0};
+    H.tile_row = {0};
+    std::vector<int> batch_mol;
+    int64_t pt = 0, t0 = 0, row = 0;
+    int sh0 = 0, b0 = 0;
+    G.bofs.clear();
+    g.shells.clear();
+    g.nbf = 0;
+    for (size_t k = 0; k < ms.size(); ++k) {
+        const Molecule &m = *ms[k];
+        const HostPlan &P = m.plan;
+        const int nb = P.nbatch();
+        const int64_t nt = P.ntiles();
+        G.bofs.push_back(b0);
+        for (int j = 0; j < nb; ++j) {
+            H.batch_ptr.push_back(P.batch_ptr[j + 1] + pt);
+            for (int64_t q = P.shell_ptr[j]; q < P.shell_ptr[j + 1]; ++q) H.shell_idx.push_back(P.shell_idx[q] + sh0);
+            H.shell_ptr.push_back((int64_t)H.shell_idx.size());
+            H.func_idx.insert(H.func_idx.end(), P.func_idx.begin() + P.func_ptr[j], P.func_idx.begin() + P.func_ptr[j + 1]);
+            H.func_ptr.push_back((int64_t)H.func_idx.size());
+            H.work.push_back(P.work[j]);
+            batch_mol.push_back((int)k);
+        }
+        for (int64_t t = 0; t < nt; ++t) {
+            H.tile_batch.push_back(P.tile_batch[t] + b0);
+            H.tile_first.push_back(P.tile_first[t] + pt);
+            H.tile_count.push_back(P.tile_count[t]);
+            H.tile_row.push_back(row + P.tile_row[t + 1]);
+        }
+        for (int j = 1; j <= nb; ++j) H.batch_tile.push_back(P.batch_tile[j] + t0);
+        g.shells.insert(g.shells.end(), m.shells.begin(), m.shells.end());
+        g.nbf = std::max(g.nbf, m.nbf);
+        H.nleaf += P.nleaf;
+        pt += P.npts;
+        t0 += nt;
+        row += P.tile_row[nt];
+        b0 += nb;
+        sh0 += (int)m.shells.size();
+    }
+    G.bofs.push_back(b0);
+    H.npts = pt;
+    g.nshell = sh0;
+    g.natoms = 0;
+    // device copies: the points (batch order) and weights of every molecule, the plan arrays
+    g.dev.x = dev_alloc<double>(g, pt);
+    g.dev.y = dev_alloc<double>(g, pt);
+    g.dev.z = dev_alloc<double>(g, pt);
+    g.dev.w = dev_alloc<double>(g, pt);
+    int64_t o = 0;
+    for (Molecule *m : ms) {
+        const size_t b = (size_t)m->plan.npts * 8;
+        check(cudaMemcpyAsync(g.dev.x + o, m->dev.x, b, cudaMemcpyDeviceToDevice, s), "copy x");
+        check(cudaMemcpyAsync(g.dev.y + o, m->dev.y, b, cudaMemcpyDeviceToDevice, s), "copy y");
+        check(cudaMemcpyAsync(g.dev.z + o, m->dev.z, b, cudaMemcpyDeviceToDevice, s), "copy z");
+        check(cudaMemcpyAsync(g.dev.w + o, m->dev.w, b, cudaMemcpyDeviceToDevice, s), "copy w");
+        o += m->plan.npts;
+    }
+    g.dev.wq = nullptr;
+    g.dev.parent = nullptr;
+    g.dev.shell_ptr = dev_upload(g, H.shell_ptr, s);
+    g.dev.shell_idx = dev_upload(g, H.shell_idx, s);
+    g.dev.func_ptr = dev_upload(g, H.func_ptr, s);
+    g.dev.func_idx = dev_upload(g, H.func_idx, s);
+    g.dev.tile_batch = dev_upload(g, H.tile_batch, s);
+    g.dev.tile_first = dev_upload(g, H.tile_first, s);
+    g.dev.tile_count = dev_upload(g, H.tile_count, s);
+    g.dev.tile_row = dev_upload(g, H.tile_row, s);
+    g.dev.batch_tile = dev_upload(g, H.batch_tile, s);
+    g.dev.batch_ptr = dev_upload(g, H.batch_ptr, s);
+    G.d_batch_mol = nullptr;
+    check(cudaMalloc(&G.d_batch_mol, std::max<size_t>(batch_mol.size(), 1) * sizeof(int)), "cudaMalloc batch map");
+    check(cudaMemcpyAsync(G.d_batch_mol, batch_mol.data(), batch_mol.size() * sizeof(int), cudaMemcpyHostToDevice, s),
+          "upload batch map");
+    check(cudaMalloc(&G.d_mols, ms.size() * sizeof(MolRef)), "cudaMalloc molecule table");
+    check(cudaMalloc(&g.d_shells, std::max<size_t>(g.shells.size(), 1) * sizeof(DevShell)), "cudaMalloc shells");
+    check(cudaMemcpyAsync(g.d_shells, g.shells.data(), g.shells.size() * sizeof(DevShell), cudaMemcpyHostToDevice, s),
+          "upload shells");
+    check(build_mixed_resident(g.shells, g.mixed_res), "mixed shells");
+    check(cudaStreamSynchronize(s), "build group");
+    g.has_grid = true;
+}
+
+// Queue one grouped integration: per molecule V_acc <- 0 (and P as double-float planes), the
+// chunks of the combined plan, then per molecule V = V_acc + V_acc^T and its E, N.
+void enqueue_group(Group &G, const std::vector<Molecule *> &ms, const Schedule &S, int precision, cudaStream_t s,
+                   Profiler *prof) {
+    Workspace &w = G.ws;
+    Molecule &g = G.gm;
+    for (Molecule *m : ms) {
+        check(cudaMemsetAsync(m->many_Vacc, 0, (size_t)m->nbf * m->nbf * 8, s), "zero V");
+        if (precision == GBXC_MIXED) check(mixed_p_to_df(m->many_P, m->many_pdf, m->nbf, s), "P planes");
+    }
+    if (precision == GBXC_MIXED) check(mixed_reset_error(w.mixed, s), "error word");
+    for (size_t ci = 0; ci < S.chunks.size(); ++ci) {
+        const auto &c = S.chunks[ci];
+        ChunkArgs a;
+        a.plan = g.dev;
+        a.shells = g.d_shells;
+        a.nbf = g.nbf;
+        a.t0 = c.t0;
+        a.t1 = c.t1;
+        a.row0 = c.row0;
+        a.rows = c.rows;
+        a.max_nfunc = c.max_nfunc;
+        a.functional = GBXC_PBE;   // unused: every batch takes its molecule's
+        a.P = nullptr;
+        a.Vacc = nullptr;
+        a.tileE = w.tileE;
+        a.tileN = w.tileN;
+        a.scratch = w.scratch;
+        a.vtasks = S.d_tasks ? S.d_tasks + 5 * c.task0 : nullptr;
+        a.nvtasks = (int)c.ntask;
+        a.prof = prof;
+        a.batch_mol = G.d_batch_mol;
+        a.mols = G.d_mols;
+        if (precision == GBXC_FP64)
+            check(launch_fp64_chunk(a, s), "fp64 chunk (grouped)");
+        else
+            check(launch_mixed_chunk(a, w.mixed, g.mixed_res, S.mixed, (int)ci, s), "mixed chunk (grouped)");
+    }
+    for (size_t k = 0; k < ms.size(); ++k) {
+        Molecule &m = *ms[k];
+        FinishArgs f;
+        f.Vacc = m.many_Vacc;
+        f.V = m.many_V;
+        f.nbf = m.nbf;
+        f.tileE = w.tileE;
+        f.tileN = w.tileN;
+        f.batch_tile = g.dev.batch_tile;
+        f.b0 = G.bofs[k];
+        f.b1 = G.bofs[k + 1];
+        f.Eb = w.Eb;
+        f.Nb = w.Nb;
+        f.tot = m.many_tot;
+        f.prof = prof;
+        check(launch_finish(f, s), "finish");
+    }
+}
+
+// gbxc_integrate_many with the grouped schedule (GEMM N tile `tile_n`).  Returns the device
+// time of the graph launch in *ms_out (CUDA events on the context stream).
+int group_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P, const int *functional,
+               int precision, int tile_n, double *Exc, double *const *Vxc, double *Nel, float *ms_out) {
+    REQUIRE(ctx->device >= 0, "integration needs a device context");
+    REQUIRE(nmol > 0 && mol_ids && P && functional, "bad molecule list");
+    REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
+    std::vector<Molecule *> ms(nmol);
+    for (int k = 0; k < nmol; ++k) {
+        ms[k] = &get_mol(ctx, mol_ids[k]);
+        if (!ms[k]->has_grid) return fail(ctx, GBXC_ENOTREADY, "a molecule has no grid");
+        REQUIRE(semilocal_lda_gga(functional[k]), "unknown functional");
+        REQUIRE(P[k], "P is NULL");
+        for (int q = 0; q < k; ++q) REQUIRE(mol_ids[q] != mol_ids[k], "a molecule appears twice");
+    }
+    if (precision == GBXC_FP64) tile_n = 128;
+    REQUIRE(mixed_tile_supported(tile_n), "unsupported GEMM tile");
+    const size_t budget = scratch_budget(ctx);
+    cudaStream_t o = ctx->stream;
+    std::vector<int> ids(mol_ids, mol_ids + nmol);
+    // per-molecule buffers: P, V_acc, V, {E, N} and the double-float P planes
+    for (int k = 0; k < nmol; ++k) {
+        Molecule &m = *ms[k];
+        size_t nn = (size_t)m.nbf * m.nbf;
+        if (nn > m.many_cap || !m.many_P || !m.many_Vacc || !m.many_pdf) {
+            size_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+            cudaFree(m.many_P);
+            cudaFree(m.many_V);
+            cudaFree(m.many_tot);
+            cudaFree(m.many_Vacc);
+            cudaFree(m.many_pdf);
+            m.many_P = m.many_V = m.many_tot = m.many_Vacc = nullptr;
+            m.many_pdf = nullptr;
+            grow_buf(m.many_P, c0, nn, "P");
+            grow_buf(m.many_V, c1, nn, "V");
+            grow_buf(m.many_tot, c2, 2, "totals");
+            grow_buf(m.many_Vacc, c3, nn, "V_acc");
+            grow_buf(m.many_pdf, c4, 2 * nn, "P planes");
+            m.many_cap = nn;
+            if (ctx->group) free_group(ctx->group);   // its graph holds the old buffers
+        }
+    }
+    Group *G = ctx->group.get();
+    if (!(G && G->mols == ids && G->precision == precision && G->tile_n == tile_n && G->budget == budget)) {
+        free_group(ctx->group);
+        ctx->group = std::make_unique<Group>();
+        G = ctx->group.get();
+        build_group(ctx, *G, ms);
+        G->mols = ids;
+        G->precision = precision;
+        G->tile_n = tile_n;
+        G->budget = budget;
+        Schedule &S = get_schedule(G->gm, precision, 0, G->gm.plan.nbatch(), budget, tile_n);
+        G->ws.stream = o;
+        reserve(G->ws, G->gm, S, precision);
+        G->h_mols.resize(nmol);
+        for (int k = 0; k < nmol; ++k) {
+            MolRef &r = G->h_mols[k];
+            r.P = ms[k]->many_P;
+            r.Vacc = ms[k]->many_Vacc;
+            r.ph = ms[k]->many_pdf;
+            r.pl = ms[k]->many_pdf + (size_t)ms[k]->nbf * ms[k]->nbf;
+            r.nbf = ms[k]->nbf;
+            r.functional = functional[k];
+        }
+        Profiler quiet;
+        cudaGraph_t graph = nullptr;
+        check(cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed), "begin capture");
+        try {
+            enqueue_group(*G, ms, S, precision, o, &quiet);
+        } catch (...) {
+            cudaStreamEndCapture(o, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            throw;
+        }
+        check(cudaStreamEndCapture(o, &graph), "end capture");
+        cudaError_t e = cudaGraphInstantiate(&G->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        check(e, "instantiate graph");
+        for (int c = 0; c < GBXC_NKERNEL; ++c) G->launches[c] = quiet.launches[c];
+    }
+    // this call's functionals and P (the graph reads both from device memory when it runs)
+    for (int k = 0; k < nmol; ++k) G->h_mols[k].functional = functional[k];
+    check(cudaMemcpyAsync(G->d_mols, G->h_mols.data(), nmol * sizeof(MolRef), cudaMemcpyHostToDevice, o),
+          "molecule table");
+    for (int k = 0; k < nmol; ++k) {
+        size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
+        check(cudaMemcpyAsync(ms[k]->many_P, P[k], nn * 8, cudaMemcpyDefault, o), "copy P");
+        check(launch_check_finite(ms[k]->many_P, (int64_t)nn, G->ws.d_tot + 2, k == 0, o), "check P");
+    }
+    for (int c = 0; c < GBXC_NKERNEL; ++c) ctx->prof.launches[c] += G->launches[c];
+    if (!ctx->ev0) {
+        check(cudaEventCreate(&ctx->ev0), "event");
+        check(cudaEventCreate(&ctx->ev1), "event");
+    }
+    ctx->prof.begin(GBXC_K_OTHER, o);
+    check(cudaEventRecord(ctx->ev0, o), "event");
+    check(cudaGraphLaunch(G->exec, o), "graph launch");
+    check(cudaEventRecord(ctx->ev1, o), "event");
+    ctx->prof.end(GBXC_K_OTHER, o, 0);
+    std::vector<double> tot(2 * (size_t)nmol);
+    double bad = 0.0;
+    check(cudaMemcpyAsync(&bad, G->ws.d_tot + 2, 8, cudaMemcpyDeviceToHost, o), "copy flag");
+    for (int k = 0; k < nmol; ++k) {
+        size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
+        check(cudaMemcpyAsync(&tot[2 * k], ms[k]->many_tot, 16, cudaMemcpyDeviceToHost, o), "copy E");
+        if (Vxc && Vxc[k]) check(cudaMemcpyAsync(Vxc[k], ms[k]->many_V, nn * 8, cudaMemcpyDefault, o), "copy V");
+    }
+    check(cudaStreamSynchronize(o), "integrate many");
+    if (bad != 0.0) return fail(ctx, GBXC_EINVAL, "a P contains a NaN or an infinity");
+    if (precision == GBXC_MIXED) {
+        int werr = 0;
+        check(mixed_read_error(G->ws.mixed, &werr, o), "status");
+        if (werr) return fail(ctx, GBXC_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
+    }
+    for (int k = 0; k < nmol; ++k) {
+        if (Exc) Exc[k] = tot[2 * k];
+        if (Nel) Nel[k] = tot[2 * k + 1];
+    }
+    if (ms_out) check(cudaEventElapsedTime(ms_out, ctx->ev0, ctx->ev1), "event time");
+    return GBXC_OK;
+}
+
 }  // namespace
 
 int gbxc_integrate_many(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *P,
@@ -1829,12 +2153,13 @@ int gbxc_integrate_many(gbxc_ctx *ctx, int nmol, const int *mol_ids, const doubl
     if (!ctx) return GBXC_EINVAL;
     return guarded(ctx, [&] {
         REQUIRE(nmol > 0 && mol_ids, "bad molecule list");
-        int W = std::min(nmol, 8), tile_n = 128;
+        int W = 0, tile_n = 128;   // default: the grouped launch
         auto it = ctx->tuned.find({std::vector<int>(mol_ids, mol_ids + nmol), precision});
         if (it != ctx->tuned.end()) {
             W = it->second.first;
             tile_n = it->second.second;
         }
+        if (W == 0) return group_impl(ctx, nmol, mol_ids, P, functional, precision, tile_n, Exc, Vxc, Nel, nullptr);
         return many_impl(ctx, nmol, mol_ids, P, functional, precision, W, tile_n, Exc, Vxc,
                          Nel, nullptr);
     });
@@ -1845,7 +2170,7 @@ int gbxc_set_schedule(gbxc_ctx *ctx, int nmol, const int *mol_ids, int precision
     return guarded(ctx, [&] {
         REQUIRE(nmol > 0 && mol_ids, "bad molecule list");
         REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
-        REQUIRE(branches >= 1 && branches <= 64, "branches must be in 1..64");
+        REQUIRE(branches >= 0 && branches <= 64, "branches must be 0 (grouped) or in 1..64");
         REQUIRE(mixed_tile_supported(tile_n), "tile_n must be 64 or 128");
         ctx->tuned[{std::vector<int>(mol_ids, mol_ids + nmol), precision}] = {branches, tile_n};
         return GBXC_OK;
@@ -1858,7 +2183,7 @@ int gbxc_autotune(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *con
     return guarded(ctx, [&] {
         REQUIRE(nmol > 0 && mol_ids, "bad molecule list");
         REQUIRE(precision == GBXC_FP64 || precision == GBXC_MIXED, "unknown precision");
-        std::vector<int> Ws;
+        std::vector<int> Ws = {0};   // 0: the grouped launch; then graph branch counts
         for (int w : {1, 2, 4, 8, 16})
             if (w <= nmol) Ws.push_back(w);
         if (Ws.back() < std::min(nmol, 16)) Ws.push_back(std::min(nmol, 16));
@@ -1868,12 +2193,17 @@ int gbxc_autotune(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *con
         for (int t : tiles)
             for (int w : Ws) {
                 float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-                int rc = many_impl(ctx, nmol, mol_ids, P, functional, precision, w, t, nullptr, nullptr, nullptr,
-                                   &m0);   // capture + first replay
+                auto run = [&](float *ms) {
+                    return w == 0 ? group_impl(ctx, nmol, mol_ids, P, functional, precision, t, nullptr, nullptr,
+                                               nullptr, ms)
+                                  : many_impl(ctx, nmol, mol_ids, P, functional, precision, w, t, nullptr, nullptr,
+                                              nullptr, ms);
+                };
+                int rc = run(&m0);   // capture + first replay
                 if (rc != GBXC_OK) return rc;
-                rc = many_impl(ctx, nmol, mol_ids, P, functional, precision, w, t, nullptr, nullptr, nullptr, &m1);
+                rc = run(&m1);
                 if (rc != GBXC_OK) return rc;
-                rc = many_impl(ctx, nmol, mol_ids, P, functional, precision, w, t, nullptr, nullptr, nullptr, &m2);
+                rc = run(&m2);
                 if (rc != GBXC_OK) return rc;
                 const double v = std::min(m1, m2);
                 if (v < best) {

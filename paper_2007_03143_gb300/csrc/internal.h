@@ -153,7 +153,19 @@ struct WeightsArgs {
 };
 cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s);
 
-// Tiles of one chunk are [t0, t1); slab rows are tile_row[t] - row0.
+// One molecule of a grouped launch over several molecules (gbxc_integrate_many): its P, its
+// V accumulator, its P as double-float planes (tensor-core form), function count and functional.
+struct MolRef {
+    const double *P;
+    double *Vacc;
+    const float *ph, *pl;
+    int nbf;
+    int functional;
+};
+
+// Tiles of one chunk are [t0, t1); slab rows are tile_row[t] - row0.  A grouped chunk spans the
+// batches of several molecules in one combined plan: batch_mol[j] names batch j's molecule in
+// mols[], whose P, V_acc, nbf and functional then replace the fields below.
 struct ChunkArgs {
     DevPlan plan;
     const DevShell *shells;
@@ -168,6 +180,8 @@ struct ChunkArgs {
     const int *vtasks;        // 5 ints per task: batch, mb, nb, t0, t1
     int nvtasks;
     Profiler *prof;
+    const int *batch_mol = nullptr;   // grouped chunks only (device)
+    const MolRef *mols = nullptr;     // grouped chunks only (device)
 };
 cudaError_t launch_fp64_chunk(const ChunkArgs &a, cudaStream_t s);
 // Spin-unrestricted chunk: a.P / a.Vacc carry spin a, Pb / Vacc_b spin b.

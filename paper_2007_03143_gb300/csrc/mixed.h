@@ -100,6 +100,10 @@ cudaError_t mixed_reserve(MixedCtx &c, const MixedSchedule &s, int nbf);
 size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf);
 // ... and its per-call preparation on `st` (P to double-float, error word reset).
 cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st);
+// Grouped chunks: each molecule's P as double-float planes (hi plane, then lo plane, nbf^2
+// floats each) and the reset of the error word, done by mixed_begin for a single molecule.
+cudaError_t mixed_p_to_df(const double *P, float *pdf, int nbf, cudaStream_t st);
+cudaError_t mixed_reset_error(MixedCtx &c, cudaStream_t st);
 cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
                                const MixedSchedule &s, int chunk_index, cudaStream_t st);
 // Spin-unrestricted form: buffers for chunks of up to max_rows slab rows, the per-call

@@ -37,6 +37,7 @@
 
 #include "mixed.h"
 #include "dfloat.cuh"
+#include "group.cuh"
 #include "slicing.cuh"
 #include "solid_harmonics.cuh"
 #include "umma.cuh"
@@ -152,10 +153,18 @@ __global__ void __launch_bounds__(32 * PS_ROWS) pslice_kernel(ChunkArgs a, Mixed
     const int mu = mu0 + warp;
     if (mu >= np) return;
     const int *F = a.plan.func_idx + f0;
-    const size_t rowoff = (mu < n) ? (size_t)F[mu] * a.nbf : 0;
+    const float *ph = m.ph, *pl = m.pl;
+    int nbf = a.nbf;
+    if (a.batch_mol) {   // grouped chunk: the batch's own molecule
+        const MolRef r = mol_of(a, j);
+        ph = r.ph;
+        pl = r.pl;
+        nbf = r.nbf;
+    }
+    const size_t rowoff = (mu < n) ? (size_t)F[mu] * nbf : 0;
     float mx = 0.f;
     if (mu < n)
-        for (int nu = lane; nu < n; nu += 32) mx = fmaxf(mx, fabsf(m.ph[rowoff + F[nu]]));
+        for (int nu = lane; nu < n; nu += 32) mx = fmaxf(mx, fabsf(ph[rowoff + F[nu]]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = exp_of(mx);
@@ -164,7 +173,7 @@ __global__ void __launch_bounds__(32 * PS_ROWS) pslice_kernel(ChunkArgs a, Mixed
     for (int kb = 0; kb < np / 32; ++kb) {
         const int nu = kb * 32 + lane;
         const bool in = mu < n && nu < n;
-        const float h = in ? m.ph[rowoff + F[nu]] : 0.f, l = in ? m.pl[rowoff + F[nu]] : 0.f;
+        const float h = in ? ph[rowoff + F[nu]] : 0.f, l = in ? pl[rowoff + F[nu]] : 0.f;
         float q[NSL];
         slice5(h, l, e, q);
         const size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + lane;
@@ -761,6 +770,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                 // V = V_acc + V_acc^T is unchanged, and the 32 lanes of a warp (consecutive
                 // mu) then update neighbouring words of one row of V_acc
                 VGeom g = v_geom(a, tasks, k);
+                const MolRef mr = mol_of(a, g.j);   // V_acc and nbf of the batch's molecule
                 const int mu = g.mc * BM + i;
                 const size_t colg = (mu < g.n) ? (size_t)a.plan.func_idx[a.plan.func_ptr[g.j] + mu] : 0;
                 const int64_t rg = a.plan.tile_row[g.tb] - a.row0;   // group exponents on the first tile
@@ -781,7 +791,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                             if (nu < g.n) {
                                 df w = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
                                 const int sc = ez + col_b[sb][c + kk];
-                                atomicAdd(&a.Vacc[(size_t)col_a[sb][c + kk] * a.nbf + colg],
+                                atomicAdd(&mr.Vacc[(size_t)col_a[sb][c + kk] * mr.nbf + colg],
                                           f2d_scaled(w.h, sc) + f2d_scaled(w.l, sc));
                             }
                         }
@@ -839,7 +849,7 @@ __global__ void __launch_bounds__(TILE) rho_mixed(ChunkArgs a, MixedArgs m) {
         double w = a.plan.w[a.plan.tile_first[t] + i];
         double sigma = dx * dx + dy * dy + dz * dz;
         double f, vr, vs;
-        xc::evaluate<double>(a.functional, r, sigma, f, vr, vs);
+        xc::evaluate<double>(mol_of(a, j).functional, r, sigma, f, vr, vs);
         e = w * f;
         nn = w * r;
         coef[0] = 0.5 * w * vr;
@@ -1600,6 +1610,14 @@ cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st) 
     if (e != cudaSuccess) return e;
     return cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
 }
+
+cudaError_t mixed_p_to_df(const double *P, float *pdf, int nbf, cudaStream_t st) {
+    int64_t nn = (int64_t)nbf * nbf;
+    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, pdf, pdf + nn, nn);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_reset_error(MixedCtx &c, cudaStream_t st) { return cudaMemsetAsync(c.d_err, 0, sizeof(int), st); }
 
 cudaError_t mixed_reserve_uks(MixedCtx &c, int64_t max_rows, int nbf) {
     const size_t rows = (size_t)std::max<int64_t>(max_rows, 1);

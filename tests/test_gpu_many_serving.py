@@ -36,7 +36,7 @@ def _alone(G, ctx, mid, nbf, P, fn, prec):
 def setup():
     G = need_gpu()
     ctx = G.Context(0)
-    mols = _molecules(G, ctx, [1, 3, 2, 4, 1, 2], 7000)
+    mols = _molecules(G, ctx, SIZES, SEED0)
     yield G, ctx, mols
     ctx.close()
 
@@ -61,7 +61,69 @@ def test_many_matches_single(setup, prec):
         assert abs(E2[k] - e) <= 1e-10
 
 
-@pytest.mark.parametrize("branches,tile_n", [(1, 64), (3, 64), (2, 128)])
+def _oracle(nw, seed, P, fn):
+    from oracle import integrate as I
+    mol = X.water_cluster(nw, seed)
+    b = X.make_basis(mol)
+    g = I.make_grid(mol.xyz, SPEC)
+    pl = I.make_plan(g, mol.xyz, b, SPEC)
+    return I.integrate_method(g, b, P, fn, pl)
+
+
+SIZES, SEED0 = [1, 3, 2, 4, 1, 2], 7000
+
+
+@pytest.mark.parametrize("prec,tol_e,tol_v", [("fp64", 1e-9, 1e-9), ("mixed", 1e-7, 1e-6)])
+def test_many_against_oracle(setup, prec, tol_e, tol_v):
+    """The default (grouped) launch over six molecules of 1-4 waters with LDA, PBE and the
+    PBE0 semi-local part mixed, each molecule against the oracle."""
+    G, ctx, mols = setup
+    fns = ["slater", "pbe", "pbe0_sl", "pbe", "pbe0_sl", "slater"]
+    Vs = [np.zeros((nbf, nbf)) for (_, nbf, _) in mols]
+    E, N = G.gbxc_integrate_many(ctx.h, [m[0] for m in mols], [m[2] for m in mols], fns, prec, Vs)
+    for k, (nw, (mid, nbf, P)) in enumerate(zip(SIZES, mols)):
+        ref = _oracle(nw, SEED0 + k, P, fns[k])
+        assert abs(E[k] - ref.E) <= tol_e, k
+        assert abs(N[k] - ref.N) <= tol_e, k
+        assert np.max(np.abs(Vs[k] - ref.V)) <= tol_v, k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grouped_launch_over_many_chunks(prec):
+    """A small scratch budget splits the combined plan into many chunks, several of which hold
+    tiles of more than one molecule: each result equals its single-molecule call.  Chunk
+    boundaries then split batches differently from the single calls; in the mixed form that
+    changes the V-side slicing groups (their exponents and so the rounding of V, whose error
+    against float64 is about 1e-7 either way), so the mixed V is held to the mixed form's
+    bound against the float64 call instead (E and N come from the X side and stay equal)."""
+    G = need_gpu()
+    ctx = G.Context(0, 6 << 20)
+    try:
+        mols = _molecules(G, ctx, [2, 1, 3, 1, 2], 7100)
+        fns = ["pbe", "slater", "pbe", "pbe0_sl", "pbe"]
+        ids = [m[0] for m in mols]
+        G.gbxc_set_schedule(ctx.h, ids, prec, 0, 128)
+        Vs = [np.zeros((nbf, nbf)) for (_, nbf, _) in mols]
+        E, N = G.gbxc_integrate_many(ctx.h, ids, [m[2] for m in mols], fns, prec, Vs)
+        for k, ((mid, nbf, P), fn) in enumerate(zip(mols, fns)):
+            e, n, V = _alone(G, ctx, mid, nbf, P, fn, prec)
+            assert abs(E[k] - e) <= 1e-10 and abs(N[k] - n) <= 1e-10, k
+            if prec == "mixed":
+                V = _alone(G, ctx, mid, nbf, P, fn, "fp64")[2]
+            assert np.max(np.abs(Vs[k] - V)) <= (1e-9 if prec == "fp64" else 1e-6), k
+    finally:
+        ctx.close()
+
+
+def test_grouped_launch_rejects_nonfinite_P(setup):
+    G, ctx, mols = setup
+    Ps = [m[2].copy() for m in mols]
+    Ps[2][1, 1] = float("nan")
+    with pytest.raises(G.GbxcError):
+        G.gbxc_integrate_many(ctx.h, [m[0] for m in mols], Ps, ["pbe"] * len(mols), "fp64")
+
+
+@pytest.mark.parametrize("branches,tile_n", [(1, 64), (3, 64), (2, 128), (0, 64), (0, 128)])
 def test_many_schedules(setup, branches, tile_n):
     # every schedule computes the same slice products in the same K order per element: only
     # the order of the float64 V atomics changes
@@ -85,13 +147,13 @@ def test_autotune(setup):
     ids = [m[0] for m in mols]
     Ps = [m[2] for m in mols]
     w, t, ms = G.gbxc_autotune(ctx.h, ids, Ps, fns, "mixed")
-    assert w in (1, 2, 4, 6) and t in (64, 128) and ms > 0.0
+    assert w in (0, 1, 2, 4, 6) and t in (64, 128) and ms > 0.0   # 0: the grouped launch
     E, _ = G.gbxc_integrate_many(ctx.h, ids, Ps, fns, "mixed")
     for k, (mid, nbf, P) in enumerate(mols):
         e, _, _ = _alone(G, ctx, mid, nbf, P, "pbe", "mixed")
         assert abs(E[k] - e) <= 1e-10
     w64, t64, ms64 = G.gbxc_autotune(ctx.h, ids, Ps, fns, "fp64")
-    assert w64 in (1, 2, 4, 6) and t64 == 128 and ms64 > 0.0
+    assert w64 in (0, 1, 2, 4, 6) and t64 == 128 and ms64 > 0.0
     with pytest.raises(G.GbxcError):
         G.gbxc_set_schedule(ctx.h, ids, "mixed", 2, 96)
 
@@ -127,6 +189,35 @@ def test_serving_alone_equals_in_the_mix(setup):
         assert e.value.code == G.GBXC_ENOENT
     finally:
         G.gbxc_serve_stop(ctx.h)
+
+
+def test_serving_large_request_overlaps_small_ones(setup):
+    """A 100-water request (the top of the serving pool's 4-100 water range; 11.5M points on the
+    75 x 16 x 32 grid, batches of up to about 1,600 functions) submitted between small ones:
+    every result equals its own gbxc_integrate (mixed form)."""
+    G, ctx, mols = setup
+    w = X.make_workload("water64_pbe", n_waters=100, seed=6000)
+    big = ctx.load_molecule(w.mol, w.basis, w.grid, device_planner=True)
+    try:
+        reqs = [(mols[1][0], mols[1][2], "pbe"), (big, w.P, "pbe"), (mols[3][0], mols[3][2], "slater"),
+                (mols[0][0], mols[0][2], "pbe0_sl"), (mols[5][0], mols[5][2], "pbe")]
+        alone = []
+        for mid, P, fn in reqs:
+            V = np.zeros(P.shape)
+            E, N = G.gbxc_integrate(ctx.h, mid, P, fn, "mixed", V)
+            alone.append((E, N, V))
+        G.gbxc_serve_start(ctx.h, 4, 0)
+        try:
+            tickets = [G.gbxc_submit(ctx.h, mid, P, fn, "mixed") for mid, P, fn in reqs]
+            for t, (mid, P, fn), ref in zip(tickets, reqs, alone):
+                V = np.zeros(P.shape)
+                E, N, lat = G.gbxc_wait(ctx.h, t, 300.0, V)
+                assert abs(E - ref[0]) <= 1e-10 and abs(N - ref[1]) <= 1e-10
+                assert np.max(np.abs(V - ref[2])) <= 1e-9
+        finally:
+            G.gbxc_serve_stop(ctx.h)
+    finally:
+        G.gbxc_unload(ctx.h, big)
 
 
 def test_serving_admission_by_footprint(setup):
