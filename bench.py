@@ -510,7 +510,7 @@ def main():
     ap.add_argument("--max-waters", type=int, default=None, help="default 40 (many) or 100 (serve)")
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--rate", type=float, default=40.0, help="serving: mean requests per second")
-    ap.add_argument("--rates", default="25,50,100,200", help="serving: comma-separated sweep of offered rates")
+    ap.add_argument("--rates", default="2,4,25,50,100,200", help="serving: comma-separated sweep of offered rates")
     ap.add_argument("--requests", type=int, default=100, help="serving: requests per offered rate")
     ap.add_argument("--warmup-requests", type=int, default=20)
     ap.add_argument("--slots", type=int, default=4)

@@ -2082,8 +2082,7 @@ int group_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const 
             MolRef &r = G->h_mols[k];
             r.P = ms[k]->many_P;
             r.Vacc = ms[k]->many_Vacc;
-            r.ph = ms[k]->many_pdf;
-            r.pl = ms[k]->many_pdf + (size_t)ms[k]->nbf * ms[k]->nbf;
+            r.pdf = reinterpret_cast<const float2 *>(ms[k]->many_pdf);
             r.nbf = ms[k]->nbf;
             r.functional = functional[k];
         }

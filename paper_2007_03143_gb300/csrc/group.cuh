@@ -12,8 +12,7 @@ __device__ __forceinline__ MolRef mol_of(const ChunkArgs &a, int j) {
     MolRef r;
     r.P = a.P;
     r.Vacc = a.Vacc;
-    r.ph = nullptr;
-    r.pl = nullptr;
+    r.pdf = nullptr;
     r.nbf = a.nbf;
     r.functional = a.functional;
     return r;

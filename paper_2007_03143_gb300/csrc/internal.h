@@ -158,7 +158,7 @@ cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s);
 struct MolRef {
     const double *P;
     double *Vacc;
-    const float *ph, *pl;
+    const float2 *pdf;                // (hi, lo) pairs, nbf x nbf
     int nbf;
     int functional;
 };

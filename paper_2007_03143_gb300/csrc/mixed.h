@@ -21,7 +21,7 @@ struct MixedCtx {
     int *pexp = nullptr;               // row exponents of the sliced P^j
     size_t pslice_rows = 0;            // capacity of pslices in elements
     size_t pexp_cap = 0;
-    float *pdf = nullptr;              // P as double-float planes (hi, lo)
+    float *pdf = nullptr;              // P as double-float (hi, lo) pairs, nbf x nbf
     size_t pdf_cap = 0;
     // spin-unrestricted form: P_b's planes, the second X/Z slab and its Z exponents
     float *pdf2 = nullptr;
@@ -100,8 +100,8 @@ cudaError_t mixed_reserve(MixedCtx &c, const MixedSchedule &s, int nbf);
 size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf);
 // ... and its per-call preparation on `st` (P to double-float, error word reset).
 cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st);
-// Grouped chunks: each molecule's P as double-float planes (hi plane, then lo plane, nbf^2
-// floats each) and the reset of the error word, done by mixed_begin for a single molecule.
+// Grouped chunks: each molecule's P as double-float (hi, lo) pairs (2 nbf^2 floats) and the
+// reset of the error word, done by mixed_begin for a single molecule.
 cudaError_t mixed_p_to_df(const double *P, float *pdf, int nbf, cudaStream_t st);
 cudaError_t mixed_reset_error(MixedCtx &c, cudaStream_t st);
 cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r,

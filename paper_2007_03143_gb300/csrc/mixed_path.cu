@@ -108,7 +108,7 @@ struct MixedArgs {
     __nv_bfloat16 *pslices;      // 5 planes, plane pitch pplane rows of 32
     int64_t pplane;
     int *pexp;                   // row exponents of P^j
-    const float *ph, *pl;        // P as double-float planes (nbf x nbf each)
+    const float2 *pdf;           // P as double-float (hi, lo) pairs, nbf x nbf
     int *err;
     int keep_z;                  // z_slice also writes Z over X (per-batch debugging copy)
     int pad_all;                 // the collocation writes zeros for every padding point of a tile
@@ -128,57 +128,61 @@ __device__ __forceinline__ double df_to_d(df a) { return dfl::to_double(a); }
 __device__ __forceinline__ df d_to_df(double d) { return dfl::from_double(d); }
 
 // ---------------------------------------------------------------- pslice
-// P as double-float planes, once per integration (the only float64 pass over P).
-__global__ void p_to_df(const double *__restrict__ P, float *__restrict__ ph, float *__restrict__ pl,
-                        int64_t nn) {
+// P as double-float pairs (hi, lo) once per integration (the only float64 pass over P).
+__global__ void p_to_df(const double *__restrict__ P, float2 *__restrict__ pdf, int64_t nn) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nn) return;
     df d = d_to_df(P[k]);
-    ph[k] = d.h;
-    pl[k] = d.l;
+    pdf[k] = make_float2(d.h, d.l);
 }
 
-// One warp per row mu of P^j, four rows per block (tasks: batch, first row of four): the row
-// exponent from the maximum over the row, then the 5 slices of P^j[mu][nu] for every K block
-// of 32 nu's, one nu per lane (gathers and stores coalesced over the lanes).  Rows and
+// Two rows mu of P^j per warp (lanes 0-15 the first, 16-31 the second), eight rows per block
+// (tasks: batch, first row of eight): the row exponent from the maximum over the row (a
+// reduction over the 16 lanes of the row), then the 5 slices of P^j[mu][nu] for every K block
+// of 32 nu's, two consecutive nu per lane, so that each slice plane of the two rows (two
+// consecutive 64-byte rows of the K-blocked layout) is one 128-byte store per warp.  Rows and
 // columns past N_b^j are written as zeros.
-constexpr int PS_ROWS = 4;
-__global__ void __launch_bounds__(32 * PS_ROWS) pslice_kernel(ChunkArgs a, MixedArgs m, const int *tasks) {
+constexpr int PS_WARPS = 4;
+constexpr int PS_ROWS = 2 * PS_WARPS;
+__global__ void __launch_bounds__(32 * PS_WARPS) pslice_kernel(ChunkArgs a, MixedArgs m, const int *tasks) {
     const int jl = tasks[2 * blockIdx.x], mu0 = tasks[2 * blockIdx.x + 1];
     const int j = m.j0 + jl;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int hl = lane & 15;
     const int64_t f0 = a.plan.func_ptr[j];
     const int n = (int)(a.plan.func_ptr[j + 1] - f0);
     const int np = pad32(n);
-    const int mu = mu0 + warp;
-    if (mu >= np) return;
+    const int mu = mu0 + 2 * warp + (lane >> 4);   // < np: np is a multiple of 32, mu0 of 8
     const int *F = a.plan.func_idx + f0;
-    const float *ph = m.ph, *pl = m.pl;
+    const float2 *pdf = m.pdf;
     int nbf = a.nbf;
     if (a.batch_mol) {   // grouped chunk: the batch's own molecule
         const MolRef r = mol_of(a, j);
-        ph = r.ph;
-        pl = r.pl;
+        pdf = r.pdf;
         nbf = r.nbf;
     }
     const size_t rowoff = (mu < n) ? (size_t)F[mu] * nbf : 0;
     float mx = 0.f;
     if (mu < n)
-        for (int nu = lane; nu < n; nu += 32) mx = fmaxf(mx, fabsf(ph[rowoff + F[nu]]));
+        for (int nu = hl; nu < n; nu += 16) mx = fmaxf(mx, fabsf(pdf[rowoff + F[nu]].x));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = exp_of(mx);
-    if (lane == 0) m.pexp[m.pexp_ofs[jl] + mu] = e;
+    if (hl == 0) m.pexp[m.pexp_ofs[jl] + mu] = e;
     const int64_t pofs = m.pofs[jl];
     for (int kb = 0; kb < np / 32; ++kb) {
-        const int nu = kb * 32 + lane;
-        const bool in = mu < n && nu < n;
-        const float h = in ? ph[rowoff + F[nu]] : 0.f, l = in ? pl[rowoff + F[nu]] : 0.f;
-        float q[NSL];
-        slice5(h, l, e, q);
-        const size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + lane;
+        const int nu = kb * 32 + 2 * hl;
+        const bool in0 = mu < n && nu < n, in1 = mu < n && nu + 1 < n;
+        const float2 p0 = in0 ? pdf[rowoff + F[nu]] : make_float2(0.f, 0.f);
+        const float2 p1 = in1 ? pdf[rowoff + F[nu + 1]] : make_float2(0.f, 0.f);
+        float q0[NSL], q1[NSL];
+        slice5(p0.x, p0.y, e, q0);
+        slice5(p1.x, p1.y, e, q1);
+        const size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + 2 * hl;
 #pragma unroll
-        for (int s = 0; s < NSL; ++s) m.pslices[(size_t)s * m.pplane * 32 + o] = __float2bfloat16_rn(q[s]);
+        for (int s = 0; s < NSL; ++s)
+            *reinterpret_cast<__nv_bfloat162 *>(m.pslices + (size_t)s * m.pplane * 32 + o) =
+                __floats2bfloat162_rn(q0[s], q1[s]);
     }
 }
 
@@ -208,7 +212,7 @@ __device__ __forceinline__ df pow3(const df *xp, const df *yp, const df *zp, int
 // L is a template parameter so every monomial index is a compile-time constant.
 template <int L>
 __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const MixedSlabs &sl, size_t plane,
-                                             size_t o, bool live, bool st, float &mx) {
+                                             size_t o, bool live, float &mx) {
     df xp[L + 1], yp[L + 1], zp[L + 1];
     xp[0] = yp[0] = zp[0] = {1.f, 0.f};
 #pragma unroll
@@ -251,13 +255,11 @@ __device__ __forceinline__ void colloc_shell(df X, df Y, df Z, df g, df h, const
                 v[3] = df_add(v[3], t);
             }
             const size_t of = o + (size_t)f * TILE;
-            if (st) {
-                sl.phi[of] = live ? make_float2(v[0].h, v[0].l) : make_float2(0.f, 0.f);
+            sl.phi[of] = live ? make_float2(v[0].h, v[0].l) : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    sl.ghi[c * plane + of] = live ? v[c + 1].h : 0.f;
-                    sl.glo[c * plane + of] = __float2bfloat16_rn(live ? v[c + 1].l : 0.f);
-                }
+            for (int c = 0; c < 3; ++c) {
+                sl.ghi[c * plane + of] = live ? v[c + 1].h : 0.f;
+                sl.glo[c * plane + of] = __float2bfloat16_rn(live ? v[c + 1].l : 0.f);
             }
             if (live) mx = fmaxf(mx, fabsf(v[0].h));
             ++f;
@@ -279,7 +281,7 @@ struct DfOps {
 // o, o + TILE, ... (the same formulas as colloc_shell for each component).
 template <int L>
 __device__ __forceinline__ void colloc_pure_shell(df X, df Y, df Z, df g, df h, const MixedSlabs &sl, size_t plane,
-                                                  size_t o, bool live, bool st, float &mx) {
+                                                  size_t o, bool live, float &mx) {
     constexpr int NC = (L + 1) * (L + 2) / 2, NO = 2 * L + 1;
     df xp[L + 1], yp[L + 1], zp[L + 1];
     xp[0] = yp[0] = zp[0] = {1.f, 0.f};
@@ -314,9 +316,9 @@ __device__ __forceinline__ void colloc_pure_shell(df X, df Y, df Z, df g, df h, 
         for (int k = 0; k < NO; ++k) {
             const size_t of = o + (size_t)k * TILE;
             if (comp == 0) {
-                if (st) sl.phi[of] = live ? make_float2(out[k].h, out[k].l) : make_float2(0.f, 0.f);
+                sl.phi[of] = live ? make_float2(out[k].h, out[k].l) : make_float2(0.f, 0.f);
                 if (live) mx = fmaxf(mx, fabsf(out[k].h));
-            } else if (st) {
+            } else {
                 sl.ghi[(comp - 1) * plane + of] = live ? out[k].h : 0.f;
                 sl.glo[(comp - 1) * plane + of] = __float2bfloat16_rn(live ? out[k].l : 0.f);
             }
@@ -347,8 +349,12 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
     int np = pad32(n);
     bool live = i < cnt;
     // padding points past the count rounded up to 8 are read by no kernel of the spin-restricted
-    // and spin-unrestricted forms (their X rows are never used): nothing is stored for them
-    const bool st = m.pad_all || i < ((cnt + 7) & ~7);
+    // and spin-unrestricted forms (their X rows are never used): nothing is computed or stored
+    // for them (no barrier follows)
+    if (!m.pad_all && i >= ((cnt + 7) & ~7)) {
+        m.s.pexp[(t - a.t0) * TILE + i] = 0;
+        return;
+    }
     int64_t p = a.plan.tile_first[t] + i;
     df px = d_to_df(live ? a.plan.x[p] : 0.0), py = d_to_df(live ? a.plan.y[p] : 0.0),
        pz = d_to_df(live ? a.plan.z[p] : 0.0);
@@ -379,22 +385,21 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
         const size_t o = (size_t)(r0 + row) * TILE + i;
         if constexpr (HAS_PURE) {
             if (sh.pure) {   // L = 2 or 3
-                if (sh.L == 2) colloc_pure_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, st, mx);
-                else colloc_pure_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, st, mx);
+                if (sh.L == 2) colloc_pure_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, mx);
+                else colloc_pure_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, mx);
                 row += 2 * sh.L + 1;
                 continue;
             }
         }
         switch (sh.L) {
-            case 0: colloc_shell<0>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 1; break;
-            case 1: colloc_shell<1>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 3; break;
-            case 2: colloc_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 6; break;
-            default: colloc_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, st, mx); row += 10; break;
+            case 0: colloc_shell<0>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 1; break;
+            case 1: colloc_shell<1>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 3; break;
+            case 2: colloc_shell<2>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 6; break;
+            default: colloc_shell<3>(X, Y, Z, g, h, m.s, plane, o, live, mx); row += 10; break;
         }
     }
     int e = exp_of(mx);
     m.s.pexp[(t - a.t0) * TILE + i] = e;
-    if (!st) return;   // no barrier follows
     for (; row < np; ++row) {
         size_t o = (size_t)(r0 + row) * TILE + i;
         m.s.phi[o] = make_float2(0.f, 0.f);
@@ -443,7 +448,8 @@ constexpr int GEMM_THREADS = 32 * (4 + EPI_WARPS);   // 4 control warps + the ep
 
 // Geometry of the persistent GEMM for an N tile of BN functions: one pipeline stage holds
 // one 16-wide K step of every slice of both operands (the global rows of 32 values are
-// fetched as two 32-byte halves with the 32-byte swizzle); tensor memory holds NBUF
+// fetched as two 32-byte halves with the 32-byte swizzle; the K step after it reads the
+// other halves of the same 64-byte rows, mostly from L2); tensor memory holds NBUF
 // accumulator sets of 4 x BN columns.
 template <int BN_>
 struct GemmCfg {
@@ -1605,7 +1611,7 @@ size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf) {
 
 cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st) {
     int64_t nn = (int64_t)nbf * nbf;
-    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, c.pdf, c.pdf + nn, nn);
+    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, reinterpret_cast<float2 *>(c.pdf), nn);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
@@ -1613,7 +1619,7 @@ cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st) 
 
 cudaError_t mixed_p_to_df(const double *P, float *pdf, int nbf, cudaStream_t st) {
     int64_t nn = (int64_t)nbf * nbf;
-    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, pdf, pdf + nn, nn);
+    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, reinterpret_cast<float2 *>(pdf), nn);
     return cudaGetLastError();
 }
 
@@ -1648,7 +1654,7 @@ cudaError_t mixed_begin_uks(MixedCtx &c, const double *Pa, const double *Pb, int
     cudaError_t e = mixed_begin(c, Pa, nbf, st);
     if (e != cudaSuccess) return e;
     int64_t nn = (int64_t)nbf * nbf;
-    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Pb, c.pdf2, c.pdf2 + nn, nn);
+    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Pb, reinterpret_cast<float2 *>(c.pdf2), nn);
     return cudaGetLastError();
 }
 
@@ -1672,8 +1678,7 @@ MixedArgs chunk_mixed_args(const ChunkArgs &a, MixedCtx &c, const MixedSchedule 
     m.pslices = reinterpret_cast<__nv_bfloat16 *>(c.pslices);
     m.pplane = std::max<int64_t>(s.max_prows, 1);
     m.pexp = c.pexp;
-    m.ph = pdf;
-    m.pl = pdf + (size_t)a.nbf * a.nbf;
+    m.pdf = reinterpret_cast<const float2 *>(pdf);
     m.err = c.d_err;
     m.keep_z = c.keep_z;
     m.pad_all = 0;
@@ -1699,7 +1704,7 @@ void run_pslice(const ChunkArgs &a, const MixedArgs &m, const MixedSchedule &s, 
     Profiler &P = *a.prof;
     P.begin(GBXC_K_PGATHER, st);
     if (ch.nptask > 0)
-        pslice_kernel<<<(unsigned)ch.nptask, 32 * PS_ROWS, 0, st>>>(a, m, s.d_ptasks + 2 * ch.ptask0);
+        pslice_kernel<<<(unsigned)ch.nptask, 32 * PS_WARPS, 0, st>>>(a, m, s.d_ptasks + 2 * ch.ptask0);
     P.end(GBXC_K_PGATHER, st);
 }
 
