@@ -670,8 +670,8 @@ def main():
             "config": {"workload": describe(w), "name": args.workload, "npts": npts, "nbf": nbf,
                        "nbatch": info["nbatch"], "sum_mn2": info["sum_mn2"], "max_nfunc": info["max_nfunc"],
                        "form": head, "host_arch": platform.machine(),
-                       "plan_note": "grid coordinates come from the host's libm (cos, log, sqrt), so nbatch "
-                                    "and sum_mn2 may differ in the last digits between host architectures",
+                       "plan_note": "geometry, exponents, grid and cutoffs use fixed-operation ln/exp/sin/cos "
+                                    "(no libm), so nbatch and sum_mn2 are the same on every host architecture",
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "alu_peaks": alu,

@@ -38,6 +38,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import elementary as el
+
 MAX_DEPTH = 16
 
 
@@ -45,7 +47,7 @@ def cutoff_radius(alphas, eta: float) -> float:
     """r_cut of one shell (Eq. rcut); natural logarithms."""
     rc = 0.0
     for a in alphas:
-        v = math.sqrt((math.log(a) / 2.0 - math.log(eta)) / a)
+        v = math.sqrt((el.ln(a) / 2.0 - el.ln(eta)) / a)
         if v > rc:
             rc = v
     return rc

@@ -7,17 +7,19 @@ every spherical harmonic of degree l <= 2*n_theta - 1 with |m| < n_phi / 2
 exactly.
 
 Floating-point contract: the coordinates produced here must be bit-identical
-to the library's host-side grid builder in the same process, because batch
-membership is decided by exact comparisons.  So every scalar transcendental
-goes through ``math`` (the platform libm), every combination is an explicit
-IEEE operation in a fixed order (no FMA, no pairwise sums), and the order of
-operations is spelled out in each docstring.
+to the library's host-side grid builder, because batch membership is decided by
+exact comparisons.  So every logarithm, sine and cosine is the fixed-operation
+version of ``elementary`` (not the platform libm, whose last bits differ between
+hosts), every combination is an explicit IEEE operation in a fixed order (no FMA,
+no pairwise sums), and the order of operations is spelled out in each docstring.
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
+
+from . import elementary as el
 
 
 def mura_knowles(n: int, alpha: float):
@@ -33,7 +35,7 @@ def mura_knowles(n: int, alpha: float):
     for k in range(1, n + 1):
         x = k / (n + 1.0)
         x3 = x * x * x
-        rk = -alpha * math.log(1.0 - x3)
+        rk = -alpha * el.ln(1.0 - x3)
         r[k - 1] = rk
         w[k - 1] = 3.0 * alpha * x * x / ((1.0 - x3) * (n + 1.0)) * rk * rk
     return r, w
@@ -50,7 +52,7 @@ def gauss_legendre(n: int):
     t_out = np.empty(n)
     w_out = np.empty(n)
     for i in range(n):
-        t = math.cos(math.pi * (i + 0.75) / (n + 0.5))
+        t = el.cos(math.pi * (i + 0.75) / (n + 0.5))
         for _ in range(100):
             p1, p2 = 1.0, 0.0
             for j in range(n):
@@ -83,8 +85,8 @@ def angular_product(ntheta: int, nphi: int):
     weight = w_a * ((2*pi)/n_phi).  Ordered theta-major.  Weights sum to 4*pi.
     """
     t, wt = gauss_legendre(ntheta)
-    cphi = np.array([math.cos(2.0 * math.pi * b / nphi) for b in range(nphi)])
-    sphi = np.array([math.sin(2.0 * math.pi * b / nphi) for b in range(nphi)])
+    cphi = np.array([el.cos(2.0 * math.pi * b / nphi) for b in range(nphi)])
+    sphi = np.array([el.sin(2.0 * math.pi * b / nphi) for b in range(nphi)])
     st = np.array([math.sqrt(1.0 - x * x) for x in t])
     ux = st[:, None] * cphi[None, :]
     uy = st[:, None] * sphi[None, :]

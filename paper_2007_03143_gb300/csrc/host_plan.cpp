@@ -3,8 +3,10 @@
 // Compiled with -ffp-contract=off: every expression below is evaluated as
 // written in IEEE double precision, so the coordinates and every comparison of
 // the batching are reproducible across compilers and across the host and the
-// reference CPU implementation (which uses the same libm calls in the same
-// order).
+// reference CPU implementation.  The logarithms, cosines and sines of the grid and
+// of the cutoffs are written out below with basic operations in a fixed order
+// instead of libm calls, whose last bits differ between host architectures, so a
+// seeded workload has the same coordinates and plan on every host.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -19,6 +21,58 @@ namespace {
 constexpr double kPi = 3.141592653589793;
 constexpr int kMaxDepth = 16;
 
+// ln x for finite x > 0: x = m 2^e with m in [1/sqrt 2, sqrt 2), ln m = 2 atanh(s),
+// s = (m - 1)/(m + 1), by the series s + s^3/3 + ... + s^25/25 (|s| <= 0.1716); ln 2 in
+// two parts, the high part with 32 significant bits so that e ln2_hi is exact.
+constexpr double kLn2Hi = 6.93147180369123816490e-01;
+constexpr double kLn2Lo = 1.90821492927058770002e-10;
+double ln_fixed(double x) {
+    int e = 0;
+    double m = std::frexp(x, &e);
+    if (m < 0.70710678118654752440) {
+        m = m * 2.0;
+        e = e - 1;
+    }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double s2 = s * s;
+    double t = s, acc = s;
+    for (int k = 1; k <= 12; ++k) {
+        t = t * s2;
+        acc = acc + t / (double)(2 * k + 1);
+    }
+    return (double)e * kLn2Hi + (2.0 * acc + (double)e * kLn2Lo);
+}
+
+// sin x and cos x for 0 <= x <= 8: x = q pi/2 + r with |r| <= pi/4 (pi/2 in two parts, the
+// high part with 33 significant bits so that q pi2_hi is exact), Taylor series of sin r and
+// cos r to r^23 and r^22, then the quadrant q mod 4.
+constexpr double kTwoOverPi = 0.63661977236758134308;
+constexpr double kPio2Hi = 1.57079632673412561417e+00;
+constexpr double kPio2Lo = 6.07710050650619224932e-11;
+void sincos_fixed(double x, double &sn, double &cs) {
+    const double q = std::floor(x * kTwoOverPi + 0.5);
+    const double r = (x - q * kPio2Hi) - q * kPio2Lo;
+    const double r2 = r * r;
+    double tc = 1.0, c = 1.0, ts = r, sv = r;
+    for (int k = 1; k <= 11; ++k) {
+        tc = tc * (-r2) / (double)((2 * k - 1) * (2 * k));
+        c = c + tc;
+        ts = ts * (-r2) / (double)((2 * k) * (2 * k + 1));
+        sv = sv + ts;
+    }
+    switch ((int)q & 3) {
+        case 0: sn = sv; cs = c; break;
+        case 1: sn = c; cs = -sv; break;
+        case 2: sn = -sv; cs = -c; break;
+        default: sn = -c; cs = sv; break;
+    }
+}
+double cos_fixed(double x) {
+    double s, c;
+    sincos_fixed(x, s, c);
+    return c;
+}
+
 // Mura-Knowles radial rule, r^2 Jacobian included:
 // x_k = k/(n+1), r_k = -alpha ln(1 - x_k^3), w_k = 3 alpha x_k^2 / ((1 - x_k^3)(n+1)) r_k^2.
 void mura_knowles(int n, double alpha, std::vector<double> &r, std::vector<double> &w) {
@@ -27,7 +81,7 @@ void mura_knowles(int n, double alpha, std::vector<double> &r, std::vector<doubl
     for (int k = 1; k <= n; ++k) {
         double x = k / (n + 1.0);
         double x3 = x * x * x;
-        double rk = -alpha * std::log(1.0 - x3);
+        double rk = -alpha * ln_fixed(1.0 - x3);
         r[k - 1] = rk;
         w[k - 1] = 3.0 * alpha * x * x / ((1.0 - x3) * (n + 1.0)) * rk * rk;
     }
@@ -48,7 +102,7 @@ void gauss_legendre(int n, std::vector<double> &t_out, std::vector<double> &w_ou
         }
     };
     for (int i = 0; i < n; ++i) {
-        double t = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double t = cos_fixed(kPi * (i + 0.75) / (n + 0.5));
         for (int it = 0; it < 100; ++it) {
             double p1, p2;
             legendre(t, p1, p2);
@@ -157,7 +211,7 @@ double shell_cutoff(const double *alpha, int nprim, double eta) {
     double rc = 0.0;
     for (int k = 0; k < nprim; ++k) {
         double a = alpha[k];
-        double v = std::sqrt((std::log(a) / 2.0 - std::log(eta)) / a);
+        double v = std::sqrt((ln_fixed(a) / 2.0 - ln_fixed(eta)) / a);
         if (v > rc) rc = v;
     }
     return rc;
@@ -232,8 +286,7 @@ void grid_tables(const gbxc_grid_spec &spec, GridTables &T) {
     T.wa.assign((size_t)nt * np, 0.0);
     std::vector<double> cphi(np), sphi(np);
     for (int b = 0; b < np; ++b) {
-        cphi[b] = std::cos(2.0 * kPi * b / np);
-        sphi[b] = std::sin(2.0 * kPi * b / np);
+        sincos_fixed(2.0 * kPi * b / np, sphi[b], cphi[b]);
     }
     double wphi = 2.0 * kPi / np;
     for (int a = 0; a < nt; ++a) {

@@ -67,7 +67,8 @@ struct DevPlan {
 
 // Grid generation and planning on the host (host_plan.cpp).  Bitwise contract:
 // the same coordinates and the same batches as the reference CPU planner in the
-// same process (plain IEEE double arithmetic, no contraction, platform libm).
+// same process (plain IEEE double arithmetic, no contraction; logarithms, sines and cosines
+// written out with basic operations instead of libm, so the plan is the same on every host).
 // 1-D factors of the atomic grid: Mura-Knowles radii and weights (r^2 included), and the
 // angular product rule's unit vectors and weights.
 struct GridTables {

@@ -27,6 +27,13 @@ Recipe (stated once, used everywhere):
 * Density: C ~ N(0, 1) of shape (N_b, 5 n_waters) from ``default_rng(seed)``,
   made S-orthonormal through a Cholesky factor of C^T S C, then P = 2 C C^T, so
   that Tr(P S) = 10 n_waters and P is symmetric positive semi-definite.
+
+Everything that decides a plan (atom positions, exponents) is computed with basic IEEE
+operations in a fixed order: the rotations' sines and cosines, the box edge's cube root and
+the exponents' powers by the fixed-operation functions below instead of the platform libm,
+and the rotation of each water as explicit sums, so a seed gives the same geometry and basis
+exponents, bit for bit, on every host architecture.  (Contraction coefficients and P, which
+change values only at rounding level, use numpy as is.)
 """
 from __future__ import annotations
 
@@ -36,6 +43,55 @@ from dataclasses import dataclass, field
 import numpy as np
 
 ANGSTROM_TO_BOHR = 1.0 / 0.529177210903
+
+# Fixed-operation elementary functions (see the module docstring): ln by 2 atanh((m-1)/(m+1))
+# on the frexp mantissa in [1/sqrt2, sqrt2); exp by exp(r) 2^k with r = y - k ln2 (ln 2 in two
+# parts) and the Taylor series of exp(r) to r^27; sin and cos by x = q pi/2 + r and the Taylor
+# series of sin r and cos r; cube root by Newton's iteration c <- (2c + x/c^2)/3.
+_LN2_HI, _LN2_LO = 6.93147180369123816490e-01, 1.90821492927058770002e-10
+_PIO2_HI, _PIO2_LO = 1.57079632673412561417e+00, 6.07710050650619224932e-11
+
+
+def _fixed_ln(x: float) -> float:
+    m, e = math.frexp(x)
+    if m < 0.70710678118654752440:
+        m, e = m * 2.0, e - 1
+    s = (m - 1.0) / (m + 1.0)
+    s2, t, acc = s * s, s, s
+    for k in range(1, 13):
+        t = t * s2
+        acc = acc + t / float(2 * k + 1)
+    return float(e) * _LN2_HI + (2.0 * acc + float(e) * _LN2_LO)
+
+
+def _fixed_exp(y: float) -> float:
+    k = math.floor(y / (_LN2_HI + _LN2_LO) + 0.5)
+    r = (y - float(k) * _LN2_HI) - float(k) * _LN2_LO
+    t, acc = 1.0, 1.0
+    for j in range(1, 28):
+        t = t * r / float(j)
+        acc = acc + t
+    return math.ldexp(acc, k)
+
+
+def _fixed_sincos(x: float):
+    q = float(math.floor(x * 0.63661977236758134308 + 0.5))
+    r = (x - q * _PIO2_HI) - q * _PIO2_LO
+    r2 = r * r
+    tc, c, ts, sn = 1.0, 1.0, r, r
+    for k in range(1, 12):
+        tc = tc * (-r2) / float((2 * k - 1) * (2 * k))
+        c = c + tc
+        ts = ts * (-r2) / float((2 * k) * (2 * k + 1))
+        sn = sn + ts
+    return [(sn, c), (c, -sn), (-sn, -c), (-c, sn)][int(q) & 3]
+
+
+def _fixed_cbrt(x: float) -> float:
+    c = 1.0
+    for _ in range(60):
+        c = (2.0 * c + x / (c * c)) / 3.0
+    return c
 
 # element -> list of (L, number of shells)
 _SHELL_RULES = {
@@ -140,10 +196,12 @@ def _rotation_from_uniform(u1: float, u2: float, u3: float) -> np.ndarray:
     """Uniform random rotation matrix from three U(0,1) numbers (Shoemake 1992)."""
     a = math.sqrt(1.0 - u1)
     b = math.sqrt(u1)
-    qx = a * math.sin(2.0 * math.pi * u2)
-    qy = a * math.cos(2.0 * math.pi * u2)
-    qz = b * math.sin(2.0 * math.pi * u3)
-    qw = b * math.cos(2.0 * math.pi * u3)
+    s2, c2 = _fixed_sincos(2.0 * math.pi * u2)
+    s3, c3 = _fixed_sincos(2.0 * math.pi * u3)
+    qx = a * s2
+    qy = a * c2
+    qz = b * s3
+    qw = b * c3
     return np.array([
         [1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qz * qw), 2 * (qx * qz + qy * qw)],
         [2 * (qx * qy + qz * qw), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qx * qw)],
@@ -159,7 +217,7 @@ def water_cluster(n_waters: int, seed: int, box_angstrom: float | None = None,
     """Seeded cluster of rigid waters in a cube (see module docstring)."""
     rng = np.random.default_rng(seed)
     if box_angstrom is None:
-        box_angstrom = 10.0 * (n_waters / 16.0) ** (1.0 / 3.0)
+        box_angstrom = 10.0 * _fixed_cbrt(n_waters / 16.0)
     if n_waters == 1:
         centers = [np.zeros(3)]
     else:
@@ -170,13 +228,16 @@ def water_cluster(n_waters: int, seed: int, box_angstrom: float | None = None,
             if tries > 200000:
                 raise RuntimeError("could not place waters; box too small")
             c = rng.uniform(0.0, box_angstrom, size=3)
-            if all(np.linalg.norm(c - o) >= min_oo_angstrom for o in centers):
+            if all(math.sqrt((c[0] - o[0]) * (c[0] - o[0]) + (c[1] - o[1]) * (c[1] - o[1])
+                             + (c[2] - o[2]) * (c[2] - o[2])) >= min_oo_angstrom for o in centers):
                 centers.append(c)
     xyz, Z = [], []
     for c in centers:
         R = _rotation_from_uniform(*rng.uniform(size=3)) if (rotate and n_waters > 1) else np.eye(3)
         for k, z in enumerate((8, 1, 1)):
-            xyz.append(c + R @ _WATER_LOCAL[k])
+            v = _WATER_LOCAL[k]
+            xyz.append([float(c[r]) + ((float(R[r, 0]) * v[0] + float(R[r, 1]) * v[1]) + float(R[r, 2]) * v[2])
+                        for r in range(3)])
             Z.append(z)
     return Molecule(Z=np.array(Z, dtype=np.int32),
                     xyz=np.array(xyz, dtype=np.float64) * ANGSTROM_TO_BOHR,
@@ -196,7 +257,8 @@ def _element_shells(Z: int):
         if nexp == 1:
             exps = np.array([1e3])
         else:
-            exps = 1e3 * (1e-4) ** (np.arange(nexp) / (nexp - 1))
+            l4 = _fixed_ln(1e-4)
+            exps = np.array([1e3 * _fixed_exp(l4 * (i / (nexp - 1))) for i in range(nexp)])
         for s in range(k):
             a = exps[3 * s:3 * s + 3].copy()
             d = rng.uniform(0.1, 1.0, size=3)
