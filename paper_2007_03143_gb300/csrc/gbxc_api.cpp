@@ -501,7 +501,7 @@ void carve(Workspace &w, char *base, const Molecule &m, const Schedule &S, int p
         w.mixed.pexp_cap = (size_t)std::max<int64_t>(ms.max_pexp, 1);
         w.mixed.pdf = reinterpret_cast<float *>(take(2 * nn * 4));
         w.mixed.pdf_cap = 2 * nn;
-        w.mixed.d_err = reinterpret_cast<int *>(take(4));
+        w.mixed.d_err = reinterpret_cast<int *>(take(16));   // error word and GEMM task counter
     }
 }
 

@@ -40,7 +40,7 @@ struct MixedCtx {
     int64_t mgga_rows = 0;
     int num_sms = 0;                   // persistent-GEMM grid size
     int keep_z = 0;                    // spin-restricted chunks also leave Z in the X plane
-    int *d_err = nullptr;
+    int *d_err = nullptr;              // [0] error word of the bounded waits, [1] GEMM task counter
 };
 // A shell with every constant split into a double-float pair (hi + lo).
 struct DfShell {

@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
 constexpr int XACC = 4;
 constexpr int BM = 128;                        // M extent of one MMA (points or functions)
 constexpr int EPI_WARPS = 16;
+constexpr int TQ = 8;                          // slots of the task ring (producer -> MMA and epilogue)
 constexpr int GEMM_THREADS = 32 * (4 + EPI_WARPS);   // 4 control warps + the epilogue warps
 
 // Geometry of the persistent GEMM for an N tile of BN functions: one pipeline stage holds
@@ -461,7 +462,7 @@ struct GemmCfg {
     static constexpr int A_BYTES = NSL * BM * 32;
     static constexpr int B_BYTES = NSL * BN * 32;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int TOTAL = 1024 + STAGES * STAGE + 256;
+    static constexpr int TOTAL = 1024 + STAGES * STAGE + 512;   // + barriers and the task ring
     static_assert(NBUF >= 1 && NBUF <= 2, "one or two accumulator sets");
     static_assert(TOTAL <= 227 * 1024, "shared memory");
 };
@@ -578,7 +579,7 @@ template <int KIND, int BN_>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_constant__ CUtensorMap ta,
                                                                    const __grid_constant__ CUtensorMap tb,
                                                                    ChunkArgs a, MixedArgs m, const int *tasks,
-                                                                   int ntasks) {
+                                                                   int ntasks, int *task_ctr) {
     using GL = GemmCfg<BN_>;
     constexpr int BN = GL::BN, NBUF = GL::NBUF, TMEM_COLS = GL::TMEM_COLS, GEMM_STAGES = GL::STAGES,
                   EPI_COLS = GL::EPI_COLS;
@@ -590,7 +591,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
     uint64_t *tfull = empty + GEMM_STAGES;   // [NBUF]
     uint64_t *tempty = tfull + NBUF;         // [NBUF]
     uint64_t *drain = tempty + NBUF;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *tqf = drain + 1;               // [TQ] producer -> consumers: the slot holds a task
+    uint64_t *tqe = tqf + TQ;                // [TQ] consumers -> producer: the slot was read
+    int *tq = reinterpret_cast<int *>(tqe + TQ);   // [TQ] task indices (-1: no more tasks)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tq + TQ);
     __shared__ volatile int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -604,6 +608,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             umma::mbar_init(&tempty[b], EPI_WARPS);
         }
         umma::mbar_init(drain, 1);
+        for (int q = 0; q < TQ; ++q) {
+            umma::mbar_init(&tqf[q], 1);
+            umma::mbar_init(&tqe[q], 1 + EPI_WARPS);   // the MMA thread and one lane per epilogue warp
+        }
         umma::fence_mbar_init();
         umma::prefetch_tmap(&ta);
         umma::prefetch_tmap(&tb);
@@ -615,8 +623,23 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
 
     if (warp == 0) {
         if (lane == 0) {   // ------------------------------------------------ producer
+            // Tasks are claimed from a global counter (dynamic scheduling: tasks that share an
+            // operand tile, e.g. the N chunks of one point tile, start at nearly the same time
+            // on neighbouring CTAs and find it in L2) and published to the MMA and epilogue warps
+            // through the ring; -1 ends the ring.
             uint32_t gk = 0;
-            for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x) {
+            for (uint32_t pt = 0;; ++pt) {
+                const uint32_t slot = pt % TQ;
+                if (pt >= TQ && !umma::mbar_wait(&tqe[slot], ((pt / TQ) - 1) & 1)) {
+                    atomicOr(m.err, 1);
+                    abort_flag = 1;
+                    break;   // the slot was not read: the consumers' waits on it expire
+                }
+                int k = abort_flag ? -1 : atomicAdd(task_ctr, 1);
+                if (k >= ntasks) k = -1;
+                tq[slot] = k;
+                umma::mbar_arrive(&tqf[slot]);
+                if (k < 0) break;
                 XGeom xg;
                 VGeom vg;
                 int nks;   // 16-wide K steps: two per stored block of 32
@@ -633,7 +656,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     if (gk >= GEMM_STAGES && !umma::mbar_wait(&empty[s], ((gk / GEMM_STAGES) - 1) & 1)) {
                         atomicOr(m.err, 1);
                         abort_flag = 1;
-                        break;
+                        break;   // the next ring slot then carries -1
                     }
                     int ay, by;
                     if (KIND == 0) {
@@ -655,7 +678,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
     } else if (warp == 1) {
         if (lane == 0) {   // ------------------------------------------------ MMA issuer
             uint32_t gk = 0, tau = 0;
-            for (int k = blockIdx.x; k < ntasks && !abort_flag; k += gridDim.x) {
+            for (uint32_t ct = 0;; ++ct) {
+                const uint32_t slot = ct % TQ;
+                if (!umma::mbar_wait(&tqf[slot], (ct / TQ) & 1)) {
+                    atomicOr(m.err, 2);
+                    abort_flag = 1;
+                    break;
+                }
+                const int k = tq[slot];
+                umma::mbar_arrive(&tqe[slot]);
+                if (k < 0) break;
+                if (abort_flag) continue;   // keep reading the ring until it ends, issue nothing
                 int nks, ncols, nseg = 1;
                 if (KIND == 0) {
                     XGeom g = x_geom(a, m, tasks, k);
@@ -703,35 +736,44 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             if (!umma::mbar_wait(drain, 0)) atomicOr(m.err, 4);
         }
     } else if (warp >= 4) {   // ---------------------------------------------- epilogue
-        // Per task, the epilogue warps first stage the column data of the task (X: P^j row
-        // exponents; V: global function indices and Phi group exponents) in shared memory,
-        // double-buffered by task parity, then meet at named barrier 1 (the 16 epilogue
-        // warps only).  Every epilogue warp visits every task and every barrier; after an
-        // abort the waits and the drain are skipped, never the barrier.
-        __shared__ int col_a[2][BN], col_b[2][BN];
-        const int q = warp & 3, cpart = (warp - 4) >> 2;
+        // Per task, each epilogue warp first stages the column data of its own EPI_COLS
+        // columns (X: P^j row exponents; V: global function indices and Phi group exponents) in
+        // its own shared-memory slots, one column per lane, then reads them back after a
+        // __syncwarp: no barrier spans the epilogue warps.
+        __shared__ int wcol_a[EPI_WARPS][EPI_COLS], wcol_b[EPI_WARPS][EPI_COLS];
+        const int q = warp & 3, cpart = (warp - 4) >> 2, ew = warp - 4;
         const int i = q * 32 + lane;
-        const int et = (warp - 4) * 32 + lane;   // 0 .. 511
+        int *col_a = wcol_a[ew], *col_b = wcol_b[ew];
         uint32_t tau = 0;
-        for (int k = blockIdx.x; k < ntasks; k += gridDim.x)
+        for (uint32_t ct = 0;; ++ct) {
+            const uint32_t slot = ct % TQ;
+            if (!umma::mbar_wait(&tqf[slot], (ct / TQ) & 1)) {
+                atomicOr(m.err, 4);
+                abort_flag = 1;
+                break;
+            }
+            const int k = tq[slot];
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&tqe[slot]);
+            if (k < 0) break;
+        // one pass per accumulator hand-over: the K segments of an X task, one pass for V
         for (int sg = 0, nseg = KIND == 0 ? x_nseg(x_geom(a, m, tasks, k)) : 1; sg < nseg; ++sg, ++tau) {
-            const uint32_t b = tau % NBUF, use = tau / NBUF, sb = tau & 1;
-            if (KIND == 0) {
-                XGeom g = x_geom(a, m, tasks, k);
-                if (et < BN) {
-                    const int mu = g.nc * BN + et;
-                    col_a[sb][et] = mu < g.n ? m.pexp[m.pexp_ofs[g.jl] + mu] : 0;
-                }
-            } else {
-                VGeom g = v_geom(a, tasks, k);
-                if (et < BN) {
-                    const int nu = g.nc * BN + et;
+            const uint32_t b = tau % NBUF, use = tau / NBUF;
+            if (lane < EPI_COLS) {
+                const int cc = cpart * EPI_COLS + lane;
+                if (KIND == 0) {
+                    XGeom g = x_geom(a, m, tasks, k);
+                    const int mu = g.nc * BN + cc;
+                    col_a[lane] = mu < g.n ? m.pexp[m.pexp_ofs[g.jl] + mu] : 0;
+                } else {
+                    VGeom g = v_geom(a, tasks, k);
+                    const int nu = g.nc * BN + cc;
                     const int64_t rg = a.plan.tile_row[g.tb] - a.row0;
-                    col_a[sb][et] = nu < g.n ? a.plan.func_idx[a.plan.func_ptr[g.j] + nu] : 0;
-                    col_b[sb][et] = nu < g.n ? m.s.fexp[rg + nu] : 0;
+                    col_a[lane] = nu < g.n ? a.plan.func_idx[a.plan.func_ptr[g.j] + nu] : 0;
+                    col_b[lane] = nu < g.n ? m.s.fexp[rg + nu] : 0;
                 }
             }
-            asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
+            __syncwarp();
             if (abort_flag) continue;
             if (!umma::mbar_wait(&tfull[b], use & 1)) {
                 atomicOr(m.err, 4);
@@ -759,7 +801,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                         const int mu = g.nc * BN + c + kk;
                         if (mu < g.n && row_used) {
                             df x = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
-                            const int sc = min(max(ei + col_a[sb][c + kk], -252), 252);
+                            const int sc = min(max(ei + col_a[c - cpart * EPI_COLS + kk], -252), 252);
                             const float s1 = pow2f(sc >> 1), s2 = pow2f(sc - (sc >> 1));
                             float2 *xo = m.s.x + (size_t)(g.r0 + mu) * TILE + i;
                             df xs{__fmul_rn(__fmul_rn(x.h, s1), s2), __fmul_rn(__fmul_rn(x.l, s1), s2)};
@@ -796,8 +838,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                             const int nu = g.nc * BN + c + kk;
                             if (nu < g.n) {
                                 df w = combine4(v0[kk], v1[kk], v2[kk], v3[kk]);
-                                const int sc = ez + col_b[sb][c + kk];
-                                atomicAdd(&mr.Vacc[(size_t)col_a[sb][c + kk] * mr.nbf + colg],
+                                const int lc = c - cpart * EPI_COLS + kk;
+                                const int sc = ez + col_b[lc];
+                                atomicAdd(&mr.Vacc[(size_t)col_a[lc] * mr.nbf + colg],
                                           f2d_scaled(w.h, sc) + f2d_scaled(w.l, sc));
                             }
                         }
@@ -807,6 +850,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             umma::fence_before_sync();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&tempty[b]);
+        }
         }
     }
     __syncthreads();
@@ -1593,8 +1637,8 @@ cudaError_t mixed_init(MixedCtx &c) {
 cudaError_t mixed_reserve(MixedCtx &c, const MixedSchedule &s, int nbf) {
     cudaError_t e0 = mixed_init(c);
     if (e0 != cudaSuccess) return e0;
-    if (!c.d_err) {
-        cudaError_t e = cudaMalloc(&c.d_err, sizeof(int));
+    if (!c.d_err) {   // [0] error word of the bounded waits, [1] task counter of the GEMM launches
+        cudaError_t e = cudaMalloc(&c.d_err, 4 * sizeof(int));
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = grow(c.pslices, c.pslice_rows, (size_t)std::max<int64_t>(s.max_prows, 1) * 32 * NSL);
@@ -1731,10 +1775,12 @@ void run_xgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, Mixed
     Profiler &P = *a.prof;
     P.begin(GBXC_K_XGEMM, st);
     const unsigned g = (unsigned)std::min(nx, c.num_sms);
+    int *ctr = c.d_err + 1;   // the launch's task counter, claimed by the CTAs' producers
+    cudaMemsetAsync(ctr, 0, sizeof(int), st);
     if (s.bn == 64)
-        gemm_persistent<0, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tax, q.tp, a, m, xtasks, nx);
+        gemm_persistent<0, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tax, q.tp, a, m, xtasks, nx, ctr);
     else
-        gemm_persistent<0, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(q.tax, q.tp, a, m, xtasks, nx);
+        gemm_persistent<0, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(q.tax, q.tp, a, m, xtasks, nx, ctr);
     P.end(GBXC_K_XGEMM, st);
 }
 
@@ -1756,11 +1802,14 @@ void run_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, Mixed
     if (a.nvtasks <= 0) return;
     P.begin(GBXC_K_VGEMM, st);
     const unsigned g = (unsigned)std::min(a.nvtasks, c.num_sms);
+    int *ctr = c.d_err + 1;
+    cudaMemsetAsync(ctr, 0, sizeof(int), st);
     if (s.bn == 64)
-        gemm_persistent<1, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tz, q.tph, a, m, a.vtasks, a.nvtasks);
+        gemm_persistent<1, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tz, q.tph, a, m, a.vtasks, a.nvtasks,
+                                                                             ctr);
     else
         gemm_persistent<1, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(q.tz, q.tph, a, m, a.vtasks,
-                                                                               a.nvtasks);
+                                                                               a.nvtasks, ctr);
     P.end(GBXC_K_VGEMM, st);
 }
 }  // namespace
