@@ -496,8 +496,9 @@ __device__ __forceinline__ void issue_slice_mmas(uint32_t tmem, uint64_t a0, uin
 }
 
 // ---------------------------------------------------------------- persistent GEMM
-// One CTA per SM walks tasks blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
-//   warp 0 lane 0  TMA producer; its stage ring runs across task boundaries
+// One CTA per SM; its producer claims tasks from a global counter in list order and hands
+// each to the MMA thread and the epilogue warps through a ring in shared memory.  Roles:
+//   warp 0 lane 0  task claims and TMA producer; its stage ring runs across task boundaries
 //   warp 1 lane 0  MMA issuer (15 slice products per 16-wide K step into 4 accumulators)
 //   warp 2         owns the tensor-memory allocation (all 512 columns)
 //   warps 4-19     epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one quarter of
