@@ -683,7 +683,7 @@ def main():
                           if "error" not in r else r) for f, r in res.items()}}
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            n, dt, nsel, nb = cpu_baseline(w, args.cpu_points or _default_points(w, 40000, 300000))
+            n, dt, nsel, nb = cpu_baseline(w, args.cpu_points or _default_points(w, 150000, 300000))
             line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"{n} points in {nsel} of {nb} batches (seeded), integrate "
                                               f"step only, numpy float64 with BLAS on all cores"}
