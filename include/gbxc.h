@@ -194,7 +194,7 @@ int gbxc_load_grid_device(gbxc_ctx *ctx, int mol, const gbxc_grid_spec *spec, lo
  * gbxc_export_plan / gbxc_plan_info_get): Phi and dPhi/dx, dPhi/dy, dPhi/dz as collocated
  * (Eq. gau_cart and its gradient), and Z (Eq. z_mat) as formed for the V contraction, in
  * float64 (double-float pairs summed for the mixed form).  Any output may be NULL.
- * functional GBXC_SLATER or GBXC_PBE; GBXC_EINVAL if the batch needs more than one chunk. */
+ * functional GBXC_SLATER, GBXC_PBE or GBXC_PBE0_SL; GBXC_EINVAL if the batch needs more than one chunk. */
 int gbxc_debug_batch(gbxc_ctx *ctx, int mol, int batch, const double *P, int functional, int precision,
                      double *phi, double *gx, double *gy, double *gz, double *z);
 
@@ -239,8 +239,9 @@ int gbxc_export_plan(gbxc_ctx *ctx, int mol, double *x, double *y, double *z, do
  * batch of the plan; Eqs. x_mat, eval_local_den, eval_local_den_grad,
  * eval_xc_batch, exc_batch, z_mat, vxc_batch, vxc_inc).
  *   P          nbf x nbf symmetric density matrix, host or device; read as given
- *   functional GBXC_SLATER, GBXC_PBE, or GBXC_MVS_X (meta-GGA)
- *   precision  GBXC_FP64 or GBXC_MIXED
+ *   functional GBXC_SLATER, GBXC_PBE, GBXC_PBE0_SL, or GBXC_MVS_X (meta-GGA)
+ *   precision  GBXC_FP64 or GBXC_MIXED (any batch size: batches with more than 1,184
+ *              significant functions run the X contraction in exact K segments)
  *   Exc, Nel   host scalars (may be NULL)
  *   Vxc        nbf x nbf output, host or device (may be NULL); exactly symmetric
  *   stream     cudaStream_t to run on (NULL = the context's own stream); the call
