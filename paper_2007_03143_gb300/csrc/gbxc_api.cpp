@@ -481,7 +481,7 @@ void carve(Workspace &w, char *base, const Molecule &m, const Schedule &S, int p
     w.d_P = reinterpret_cast<double *>(take(nn * 8));
     w.d_Vacc = reinterpret_cast<double *>(take(nn * 8));
     w.d_V = reinterpret_cast<double *>(take(nn * 8));
-    w.d_tot = reinterpret_cast<double *>(take(16));
+    w.d_tot = reinterpret_cast<double *>(take(24));   // E, N and the non-finite-P flag
     w.mat_cap = nn;
     w.tileE = reinterpret_cast<double *>(take((size_t)m.plan.ntiles() * 8));
     w.tileN = reinterpret_cast<double *>(take((size_t)m.plan.ntiles() * 8));
@@ -734,13 +734,13 @@ bool server_admit(gbxc_ctx *ctx) {
         size_t off = 0;
         if (!S.arena.alloc(fp, &off)) return false;       // wait for memory to free up
         size_t nn = (size_t)m.nbf * m.nbf;
-        if (2 * nn + 2 > S.pin_cap[slot]) {                // grow this (idle) slot's pinned staging
+        if (2 * nn + 3 > S.pin_cap[slot]) {                // grow this (idle) slot's pinned staging
             cudaStreamSynchronize(S.streams[slot]);
             cudaFreeHost(S.pin[slot]);
             S.pin[slot] = nullptr;
             S.pin_cap[slot] = 0;
-            check(cudaMallocHost(&S.pin[slot], (2 * nn + 2) * 8), "pinned staging");
-            S.pin_cap[slot] = 2 * nn + 2;
+            check(cudaMallocHost(&S.pin[slot], (2 * nn + 3) * 8), "pinned staging");
+            S.pin_cap[slot] = 2 * nn + 3;
         }
         double *pin = S.pin[slot];
         std::memcpy(pin, r->P.data(), nn * 8);
@@ -750,9 +750,10 @@ bool server_admit(gbxc_ctx *ctx) {
         carve(w, S.arena.base + off, m, Sch, r->precision, ctx->ws.mixed.encode_fn);
         cudaStream_t st = S.streams[slot];
         check(cudaMemcpyAsync(w.d_P, pin, nn * 8, cudaMemcpyHostToDevice, st), "copy P");
+        check(launch_check_finite(w.d_P, (int64_t)nn, w.d_tot + 2, true, st), "check P");
         enqueue(w, m, Sch, w.d_P, r->functional, r->precision, 0, m.plan.nbatch(), w.d_V, false, st, &ctx->prof);
         check(cudaMemcpyAsync(pin + nn, w.d_V, nn * 8, cudaMemcpyDeviceToHost, st), "copy V");
-        check(cudaMemcpyAsync(pin + 2 * nn, w.d_tot, 16, cudaMemcpyDeviceToHost, st), "copy E");
+        check(cudaMemcpyAsync(pin + 2 * nn, w.d_tot, 24, cudaMemcpyDeviceToHost, st), "copy E");
         check(cudaEventRecord(S.done_ev[slot], st), "record");
         std::lock_guard<std::mutex> q(S.qmu);
         S.queue.pop_front();
@@ -802,6 +803,10 @@ bool server_retire(gbxc_ctx *ctx) {
             }
         }
         double *pin = S.pin[k];
+        if (status == GBXC_OK && pin[2 * nn + 2] != 0.0) {
+            status = GBXC_EINVAL;
+            msg = "P contains a NaN or an infinity";
+        }
         if (status == GBXC_OK) {
             r->V.assign(pin + nn, pin + 2 * nn);
             r->E = pin[2 * nn];
@@ -1832,9 +1837,11 @@ int many_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *
         for (int c = 0; c < GBXC_NKERNEL; ++c) G.launches[c] = quiet.launches[c];
     }
     cudaStream_t o = ctx->stream;
+    double *bad_flag = ctx->branch_ws[0].d_tot + 2;
     for (int k = 0; k < nmol; ++k) {
         size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
         check(cudaMemcpyAsync(ms[k]->many_P, P[k], nn * 8, cudaMemcpyDefault, o), "copy P");
+        check(launch_check_finite(ms[k]->many_P, (int64_t)nn, bad_flag, k == 0, o), "check P");
     }
     long long total = 0;
     for (int c = 0; c < GBXC_NKERNEL; ++c) {
@@ -1851,6 +1858,8 @@ int many_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *
     check(cudaEventRecord(ctx->ev1, o), "event");
     ctx->prof.end(GBXC_K_OTHER, o, 0);
     std::vector<double> tot(2 * (size_t)nmol);
+    double bad = 0.0;
+    check(cudaMemcpyAsync(&bad, bad_flag, 8, cudaMemcpyDeviceToHost, o), "copy flag");
     for (int k = 0; k < nmol; ++k) {
         size_t nn = (size_t)ms[k]->nbf * ms[k]->nbf;
         check(cudaMemcpyAsync(&tot[2 * k], ms[k]->many_tot, 16, cudaMemcpyDeviceToHost, o), "copy E");
@@ -1858,6 +1867,7 @@ int many_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *
     }
     check(cudaStreamSynchronize(o), "integrate many");
     (void)total;
+    if (bad != 0.0) return fail(ctx, GBXC_EINVAL, "a P contains a NaN or an infinity");
     if (precision == GBXC_MIXED)
         for (int b = 0; b < W; ++b) {
             int werr = 0;

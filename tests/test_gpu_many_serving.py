@@ -115,12 +115,50 @@ def test_grouped_launch_over_many_chunks(prec):
         ctx.close()
 
 
-def test_grouped_launch_rejects_nonfinite_P(setup):
+@pytest.mark.parametrize("branches", [0, 2])
+def test_many_rejects_nonfinite_P(setup, branches):
+    """A NaN in one molecule's P fails the call with GBXC_EINVAL in the grouped launch and in
+    the branched schedule; the next call with clean densities is unaffected."""
     G, ctx, mols = setup
-    Ps = [m[2].copy() for m in mols]
-    Ps[2][1, 1] = float("nan")
-    with pytest.raises(G.GbxcError):
-        G.gbxc_integrate_many(ctx.h, [m[0] for m in mols], Ps, ["pbe"] * len(mols), "fp64")
+    ids = [m[0] for m in mols]
+    G.gbxc_set_schedule(ctx.h, ids, "fp64", branches, 128)
+    try:
+        Ps = [m[2].copy() for m in mols]
+        Ps[2][1, 1] = float("nan")
+        with pytest.raises(G.GbxcError) as e:
+            G.gbxc_integrate_many(ctx.h, ids, Ps, ["pbe"] * len(mols), "fp64")
+        assert e.value.code == G.GBXC_EINVAL
+        E, _ = G.gbxc_integrate_many(ctx.h, ids, [m[2] for m in mols], ["pbe"] * len(mols), "fp64")
+        e0, _, _ = _alone(G, ctx, mols[2][0], mols[2][1], mols[2][2], "pbe", "fp64")
+        assert abs(E[2] - e0) <= 1e-10
+    finally:
+        G.gbxc_set_schedule(ctx.h, ids, "fp64", 0, 128)
+
+
+def test_serving_against_oracle_and_nonfinite_P(setup):
+    """Requests served by the continuous-batching loop against the oracle (float64 at 1e-9, mixed
+    at the form's small-case bounds); a request whose P holds a NaN completes with GBXC_EINVAL
+    and leaves the others intact."""
+    G, ctx, mols = setup
+    picks = [(0, "slater", "fp64"), (2, "pbe", "fp64"), (1, "pbe0_sl", "mixed"), (4, "pbe", "mixed")]
+    bad = mols[3][2].copy()
+    bad[0, 0] = float("inf")
+    G.gbxc_serve_start(ctx.h, 3, 1 << 30)
+    try:
+        tickets = [G.gbxc_submit(ctx.h, mols[k][0], mols[k][2], fn, prec) for k, fn, prec in picks]
+        tbad = G.gbxc_submit(ctx.h, mols[3][0], bad, "pbe", "fp64")
+        for t, (k, fn, prec) in zip(tickets, picks):
+            V = np.zeros((mols[k][1], mols[k][1]))
+            E, N, lat = G.gbxc_wait(ctx.h, t, 120.0, V)
+            ref = _oracle(SIZES[k], SEED0 + k, mols[k][2], fn)
+            tol_e, tol_v = (1e-9, 1e-9) if prec == "fp64" else (1e-7, 1e-6)
+            assert abs(E - ref.E) <= tol_e and abs(N - ref.N) <= tol_e, k
+            assert np.max(np.abs(V - ref.V)) <= tol_v, k
+        with pytest.raises(G.GbxcError) as e:
+            G.gbxc_wait(ctx.h, tbad, 120.0)
+        assert e.value.code == G.GBXC_EINVAL
+    finally:
+        G.gbxc_serve_stop(ctx.h)
 
 
 @pytest.mark.parametrize("branches,tile_n", [(1, 64), (3, 64), (2, 128), (0, 64), (0, 128)])
