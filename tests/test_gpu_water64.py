@@ -69,6 +69,24 @@ def test_mixed_against_fp64_whole_grid(seed, w64):
             L.close()
 
 
+def test_segmented_x_with_n_tile_64():
+    """The 64-water cluster at seed 5064 (a batch of 1,187 functions: two K segments) through the
+    grouped many-molecule launch with the N tile 64, where two accumulator sets alternate, so a
+    segment's epilogue overlaps the next segment's MMAs: E_xc, N_el and V equal the single call's."""
+    L = Loaded("water64_pbe", seed=5064)
+    try:
+        G = L.G
+        nbf = L.w.basis.nbf
+        E1, N1, V1 = L.integrate("mixed")
+        G.gbxc_set_schedule(L.ctx.h, [L.mid], "mixed", 0, 64)
+        V = np.zeros((nbf, nbf))
+        E, N = G.gbxc_integrate_many(L.ctx.h, [L.mid], [L.w.P], ["pbe"], "mixed", [V])
+        assert abs(E[0] - E1) <= 1e-9 and abs(N[0] - N1) <= 1e-9
+        assert np.max(np.abs(V - V1)) <= 1e-6
+    finally:
+        L.close()
+
+
 def test_water100_mixed_against_fp64():
     L = Loaded("water64_pbe", n_waters=100, seed=6000)
     try:
