@@ -12,9 +12,11 @@
 //        level 0).  X = (acc0 + acc1 + acc2 + acc3) 2^(e_i + f_mu), summed in double-float.
 //        The exactness needs K <= 1184 functions per accumulation; a batch with more
 //        functions runs its K in segments of 1184, each exact, added in double-float.
-//   W^j = Z^jT Phi^j (Eq. vxc_batch) the same slicing over K = grid points: each function
-//        row of Z and of Phi is scaled by the maximum over the points of its V task (at
-//        most 8 tiles = 1024 points, so levels 0-2 stay exact) and sliced the same way.
+//   W^j = Z^jT Phi^j (Eq. vxc_batch) the same slicing over K = grid points (at most 8 tiles =
+//        1024 points per V task, so levels 0-2 stay exact).  Phi is taken from the X
+//        contraction's slices (Phi_i,nu 2^-e_i, one exponent per point), read MN-major, and
+//        Z_i,mu 2^e_i is sliced per function over the task's points, so the product needs
+//        only Z's exponents; the meta-GGA terms slice both operands per function.
 //
 // Everything that decides E_xc to 1e-9 stays above fp32 precision: collocation in
 // float64 written as double-float pairs, rho and grad rho summed in double-float, the
@@ -22,7 +24,7 @@
 //
 // Kernels per chunk of tiles: pslice (P^j row slices), colloc (Phi, grad Phi, Phi slices),
 // xgemm (tcgen05), rho (rho, grad rho, functional, E/N partials, per-point Z coefficients),
-// z_slice (Z in double-float, group exponent maxima, Z and Phi slices per V task), vgemm
+// z_slice (Z 2^e_i in double-float, group exponent maxima, Z slices per V task), vgemm
 // (tcgen05, scatter into V_acc with float64 atomics).  The spin-unrestricted form runs z_slice
 // once per spin; the meta-GGA form forms Z and W^k in its rho kernel (two passes over Phi) and
 // slices them with slice_v.
@@ -68,9 +70,11 @@ struct MixedSlabs {
     float2 *x;              // 1 plane [rows][128]: X (later Z) as (hi, lo)
     __nv_bfloat16 *ax;      // 5 planes [4 rows][32]: Phi slices, K-blocked per tile
     __nv_bfloat16 *vz;      // 5 planes [4 rows][32]: Z slices, point-blocked per tile
-    __nv_bfloat16 *vphi;    // 5 planes [4 rows][32]: Phi slices, point-blocked per tile
+    __nv_bfloat16 *vphi;    // 5 planes [4 rows][32]: Phi slices, point-blocked per tile (the
+                            // meta-GGA form; the others read Phi from ax)
     int *zexp, *fexp;       // [rows]: per tile and function, exponent of max |Z|, |Phi| over
-                            // the tile's points (group maxima on the group's first tile)
+                            // the tile's points (group maxima on the group's first tile; fexp
+                            // in the meta-GGA form only)
     int *pexp;              // [tiles][128] point exponents e_i
 };
 
@@ -349,10 +353,22 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
     int np = pad32(n);
     bool live = i < cnt;
     // padding points past the count rounded up to 8 are read by no kernel of the spin-restricted
-    // and spin-unrestricted forms (their X rows are never used): nothing is computed or stored
-    // for them (no barrier follows)
+    // and spin-unrestricted forms except the W contraction, whose 16-point K steps read their
+    // Phi slices up to the count rounded up to 16: those get zero slices, nothing else is
+    // computed or stored for them (no barrier follows)
     if (!m.pad_all && i >= ((cnt + 7) & ~7)) {
         m.s.pexp[(t - a.t0) * TILE + i] = 0;
+        if (i < ((cnt + 15) & ~15)) {
+            const size_t plane = (size_t)m.rows * TILE;
+            for (int kb = 0; kb < np / 32; ++kb) {
+                const size_t orow = (size_t)(4 * r0 + (int64_t)kb * TILE + i) * 32;
+#pragma unroll
+                for (int s = 0; s < NSL; ++s)
+#pragma unroll
+                    for (int c8 = 0; c8 < 32; c8 += 8)
+                        *reinterpret_cast<uint4 *>(m.s.ax + (size_t)s * plane + orow + c8) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
         return;
     }
     int64_t p = a.plan.tile_first[t] + i;
@@ -461,6 +477,10 @@ struct GemmCfg {
     static constexpr int EPI_COLS = BN / (EPI_WARPS / 4);  // columns per epilogue warp
     static constexpr int A_BYTES = NSL * BM * 32;
     static constexpr int B_BYTES = NSL * BN * 32;
+    // MN-major B (the V contraction's Phi from the X-side slices): BN / 32 boxes of 32
+    // functions x 16 points x NSL slices, rows of 64 B
+    static constexpr int MN_BOX = NSL * 16 * 64;
+    static_assert(B_BYTES == (BN / 32) * MN_BOX, "MN-major B fills the B stage");
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int TOTAL = 1024 + STAGES * STAGE + 512;   // + barriers and the task ring
     static_assert(NBUF >= 1 && NBUF <= 2, "one or two accumulator sets");
@@ -470,7 +490,7 @@ struct GemmCfg {
 // The 15 MMAs of one 16-wide K step with compile-time operand offsets.  `first` is 0 only
 // for the first K step of a task: then the first product into each accumulator overwrites
 // it (levels 0, 1, 2, 3 start at ops 0, 1, 3, 6).
-template <int BN, int Q>
+template <int BN, int BPL, int Q>   // BPL: B slice-plane stride in 16-byte units
 __device__ __forceinline__ void issue_op(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first) {
     constexpr int A[15] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
     constexpr int B[15] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
@@ -478,21 +498,21 @@ __device__ __forceinline__ void issue_op(uint32_t tmem, uint64_t a0, uint64_t b0
     constexpr bool LEAD[15] = {true, true, false, true, false, false, true, false, false, false,
                                false, false, false, false, false};
     const uint64_t ad = a0 + (uint64_t)(A[Q] * (BM * 32 / 16));
-    const uint64_t bd = b0 + (uint64_t)(B[Q] * (BN * 32 / 16));
+    const uint64_t bd = b0 + (uint64_t)(B[Q] * BPL);
     const uint32_t acc = LEAD[Q] ? first : 1u;
     umma::mma_bf16(tmem + C[Q] * BN, ad, bd, idesc, acc);
 }
 
-template <int BN, int... Q>
+template <int BN, int BPL, int... Q>
 __device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc, uint32_t first,
                                           std::integer_sequence<int, Q...>) {
-    (issue_op<BN, Q>(tmem, a0, b0, idesc, first), ...);
+    (issue_op<BN, BPL, Q>(tmem, a0, b0, idesc, first), ...);
 }
 
-template <int BN>
+template <int BN, int BPL>
 __device__ __forceinline__ void issue_slice_mmas(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc,
                                                  uint32_t first) {
-    issue_ops<BN>(tmem, a0, b0, idesc, first, std::make_integer_sequence<int, 15>{});
+    issue_ops<BN, BPL>(tmem, a0, b0, idesc, first, std::make_integer_sequence<int, 15>{});
 }
 
 // ---------------------------------------------------------------- persistent GEMM
@@ -575,7 +595,10 @@ __device__ __forceinline__ double f2d_scaled(float f, int k) {
 }
 
 // KIND 0: X^j = P^j Phi^j tiles (tasks: point tile, BN-function column chunk).
-// KIND 1: W^j = Z^T Phi tiles (tasks: batch, 128-row block, BN-column block, tile range).
+// KIND 1: W^j = Z^T Phi tiles (tasks: batch, 128-row block, BN-column block, tile range),
+//         Phi from slices cut per function over the task's points (the meta-GGA terms).
+// KIND 2: the same tiles with Z scaled by 2^e_i and Phi from the X contraction's slices (cut
+//         per point, read MN-major): the spin-restricted and spin-unrestricted forms.
 template <int KIND, int BN_>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_constant__ CUtensorMap ta,
                                                                    const __grid_constant__ CUtensorMap tb,
@@ -660,6 +683,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                         break;   // the next ring slot then carries -1
                     }
                     int ay, by;
+                    int64_t rx = 0;   // KIND 2: the X-side Phi slice rows of this 16-point step
                     if (KIND == 0) {
                         ay = (int)(4 * xg.r0 + (int64_t)kb * TILE);
                         by = (int)(xg.pofs + (int64_t)kb * xg.np + xg.nc * BN);
@@ -668,11 +692,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                         int64_t b0 = 4 * (a.plan.tile_row[t] - a.row0) + (int64_t)(kb % 4) * vg.np;
                         ay = (int)(b0 + vg.mc * BM);
                         by = (int)(b0 + vg.nc * BN);
+                        rx = 4 * (a.plan.tile_row[t] - a.row0) + (int64_t)(ks & 7) * 16 +
+                             (int64_t)vg.nc * (BN / 32) * TILE;
                     }
-                    umma::mbar_arrive_expect_tx(&full[s], GL::STAGE);
                     uint8_t *sa = smem + s * GL::STAGE;
-                    umma::tma_load_3d(sa, &ta, &full[s], kx, ay, 0);
-                    umma::tma_load_3d(sa + GL::A_BYTES, &tb, &full[s], kx, by, 0);
+                    if (KIND == 2) {
+                        // Phi_i,nu 2^-e_i from the X-side slices (rows: K block of 32 functions x
+                        // 128 points): one box of 32 functions x 16 points per 32 live columns,
+                        // MN-major in shared memory; columns past them are not read by the MMA
+                        const int nbox = (min(BN, vg.n - vg.nc * BN) + 31) / 32;
+                        umma::mbar_arrive_expect_tx(&full[s], GL::A_BYTES + nbox * GL::MN_BOX);
+                        umma::tma_load_3d(sa, &ta, &full[s], kx, ay, 0);
+                        for (int bx = 0; bx < nbox; ++bx)
+                            umma::tma_load_3d(sa + GL::A_BYTES + bx * GL::MN_BOX, &tb, &full[s], 0,
+                                              (int)(rx + (int64_t)bx * TILE), 0);
+                    } else {
+                        umma::mbar_arrive_expect_tx(&full[s], GL::STAGE);
+                        umma::tma_load_3d(sa, &ta, &full[s], kx, ay, 0);
+                        umma::tma_load_3d(sa + GL::A_BYTES, &tb, &full[s], kx, by, 0);
+                    }
                 }
             }
         }
@@ -701,7 +739,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     nks = v_ksteps(a, g);
                     ncols = min(BN, ((g.n - g.nc * BN) + 15) & ~15);
                 }
-                const uint32_t idesc = umma::idesc_bf16(BM, ncols);
+                const uint32_t idesc = umma::idesc_bf16(BM, ncols, KIND == 2);
                 for (int sg = 0; sg < nseg && !abort_flag; ++sg, ++tau) {   // one accumulator set each
                     const uint32_t b = tau % NBUF, use = tau / NBUF;
                     if (tau >= NBUF && !umma::mbar_wait(&tempty[b], (use - 1) & 1)) {
@@ -723,9 +761,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                         umma::fence_after_sync();
                         uint32_t sa = umma::smem_u32(smem + s * GL::STAGE), sb = sa + GL::A_BYTES;
                         // descriptors of slice 0; every other slice is a fixed offset in 16-byte
-                        // units (slice tiles BM x 32 B and BN x 32 B apart)
-                        const uint64_t a0 = umma::desc_sw32(sa), b0 = umma::desc_sw32(sb);
-                        issue_slice_mmas<BN>(tacc, a0, b0, idesc, ks == ks0 ? 0u : 1u);
+                        // units (slice tiles BM x 32 B and BN x 32 B apart; MN-major B: 1 KB
+                        // apart inside each box, boxes MN_BOX apart along N)
+                        const uint64_t a0 = umma::desc_sw32(sa);
+                        if (KIND == 2) {
+                            const uint64_t b0 = umma::desc_mn_sw64(sb, GL::MN_BOX, 512);
+                            issue_slice_mmas<BN, 1024 / 16>(tacc, a0, b0, idesc, ks == ks0 ? 0u : 1u);
+                        } else {
+                            const uint64_t b0 = umma::desc_sw32(sb);
+                            issue_slice_mmas<BN, BN * 32 / 16>(tacc, a0, b0, idesc, ks == ks0 ? 0u : 1u);
+                        }
                         umma::mma_commit(&empty[s]);
                     }
                     if (abort_flag) break;
@@ -771,7 +816,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                     const int nu = g.nc * BN + cc;
                     const int64_t rg = a.plan.tile_row[g.tb] - a.row0;
                     col_a[lane] = nu < g.n ? a.plan.func_idx[a.plan.func_ptr[g.j] + nu] : 0;
-                    col_b[lane] = nu < g.n ? m.s.fexp[rg + nu] : 0;
+                    col_b[lane] = (KIND == 1 && nu < g.n) ? m.s.fexp[rg + nu] : 0;
                 }
             }
             __syncwarp();
@@ -929,15 +974,17 @@ __global__ void __launch_bounds__(TILE) rho_mixed(ChunkArgs a, MixedArgs m) {
     }
 }
 
-// ---------------------------------------------------------------- Z and the V-side slices (spin-restricted)
+// ---------------------------------------------------------------- Z and its slices (spin-restricted)
 // Per K group (the up to VKS tiles of one batch that form one V task) and function row mu:
 // Z_i,mu = a_i Phi_i,mu + b_i . grad Phi_i,mu (Eq. z_mat, double-float, gradient hi words),
-// the exponents of max |Z| and max |Phi| per tile, their maximum over the group, and the bf16
-// slices of Z and Phi in the layout of slice_v; the group exponents go to the group's first
-// tile for the V epilogue.  The block's eight 16-thread slots cover G2 tiles (the group size
-// rounded up to a power of two) for 8 / G2 rows at a time, 8 points per thread, so Z and Phi
-// stay in registers while the slots exchange their tile exponents through shared memory (one
-// barrier per step, double-buffered): every element is read once.  The blocks of a group's
+// times 2^e_i, the exponent of point i's Phi slices: the W contraction takes Phi from the
+// slices the X contraction uses (Phi_i,nu 2^-e_i, cut per point), so
+// W_mu,nu = sum_i (Z_i,mu 2^e_i)(Phi_i,nu 2^-e_i) and only the scaled Z is sliced here, per
+// function over the group's points (the exponent of max |Z 2^e| per tile, their maximum over
+// the group, to the group's first tile for the V epilogue).  The block's eight 16-thread slots
+// cover G2 tiles (the group size rounded up to a power of two) for 8 / G2 rows at a time, 8
+// points per thread, so Z stays in registers while the slots exchange their tile exponents
+// through shared memory (one barrier per step, double-buffered): every element is read once.  The blocks of a group's
 // tiles share its rows (row step k to block k mod group size), so the grid keeps one block per
 // tile.  With keep_z the values of Z are also written over X for the per-batch debugging copy;
 // the group's first block then does every row, because those writes cover the coefficient rows
@@ -961,20 +1008,23 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
     const int64_t rg = a.plan.tile_row[g0] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
     // the group's per-point coefficients (a, b_x, b_y, b_z) as double-float pairs
-    __shared__ float2 cf[VKS][4][TILE];
+    __shared__ float2 cf[VKS][4][TILE];   // times 2^e_i, so that the products form Z 2^e_i
     __shared__ int64_t trow[VKS];
     __shared__ int tcnt[VKS];
-    __shared__ int red[2][8][2];   // per step parity and slot: tile exponents of |Z|, |Phi|
+    __shared__ int red[2][8];   // per step parity and slot: tile exponents of |Z 2^e|
     const double *cz = reinterpret_cast<const double *>(m.s.x);
     for (int u = 0; u < ng; ++u) {
         const int64_t ru = a.plan.tile_row[g0 + u] - a.row0;
+        const int cu = a.plan.tile_count[g0 + u];
         if (threadIdx.x == 0) {
             trow[u] = ru;
-            tcnt[u] = a.plan.tile_count[g0 + u];
+            tcnt[u] = cu;
         }
+        const int ep = threadIdx.x < cu ? m.s.pexp[(g0 + u - a.t0) * TILE + threadIdx.x] : 0;
+        const double pe = (double)pow2f(min(max(ep, -126), 127));
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const df c = d_to_df(cz[(size_t)(ru + q) * TILE + threadIdx.x]);
+            const df c = d_to_df(cz[(size_t)(ru + q) * TILE + threadIdx.x] * pe);
             cf[u][q][cf_slot(threadIdx.x)] = make_float2(c.h, c.l);
         }
     }
@@ -994,10 +1044,10 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
     for (int c = ub; c * R < n; c += nblk, par ^= 1) {
         const int mu = c * R + rr;
         const bool act = u < ng && mu < n;
-        float zh[8], zl[8], fh[8], fl[8];
+        float zh[8], zl[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) zh[e] = zl[e] = fh[e] = fl[e] = 0.f;
-        float az = 0.f, ap = 0.f;
+        for (int e = 0; e < 8; ++e) zh[e] = zl[e] = 0.f;
+        float az = 0.f;
         const size_t o = (size_t)(ru + mu) * TILE + 8 * pg;
         if (act && live8) {
             const float4 *fs = reinterpret_cast<const float4 *>(m.s.phi + o);
@@ -1011,76 +1061,59 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
                 const float gxs[2] = {(q & 1) ? a1.z : a1.x, (q & 1) ? a1.w : a1.y};
                 const float gys[2] = {(q & 1) ? a2.z : a2.x, (q & 1) ? a2.w : a2.y};
                 const float gzs[2] = {(q & 1) ? a3.z : a3.x, (q & 1) ? a3.w : a3.y};
-                fh[2 * q] = f4.x;
-                fl[2 * q] = f4.y;
-                fh[2 * q + 1] = f4.z;
-                fl[2 * q + 1] = f4.w;
+                const float fh[2] = {f4.x, f4.z}, fl[2] = {f4.y, f4.w};
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const int e = 2 * q + k, sp = cf_slot(8 * pg + e);
                     const float2 c0 = cf[u][0][sp], c1 = cf[u][1][sp], c2 = cf[u][2][sp], c3 = cf[u][3][sp];
-                    df z = df_mul({c0.x, c0.y}, {fh[e], fl[e]});
+                    df z = df_mul({c0.x, c0.y}, {fh[k], fl[k]});
                     z = df_add(z, dfl::mul_f({c1.x, c1.y}, gxs[k]));
                     z = df_add(z, dfl::mul_f({c2.x, c2.y}, gys[k]));
                     z = df_add(z, dfl::mul_f({c3.x, c3.y}, gzs[k]));
                     zh[e] = z.h;
                     zl[e] = z.l;
                     az = fmaxf(az, fabsf(z.h));
-                    ap = fmaxf(ap, fabsf(fh[e]));
                 }
             }
         }
 #pragma unroll
-        for (int q = 8; q > 0; q >>= 1) {   // over the 16 threads of the slot (one tile row)
+        for (int q = 8; q > 0; q >>= 1)   // over the 16 threads of the slot (one tile row)
             az = fmaxf(az, __shfl_xor_sync(0xffffffffu, az, q));
-            ap = fmaxf(ap, __shfl_xor_sync(0xffffffffu, ap, q));
-        }
-        if (pg == 0) {
-            red[par][slot][0] = act ? exp_of(az) : -1000;
-            red[par][slot][1] = act ? exp_of(ap) : -1000;
-        }
+        if (pg == 0) red[par][slot] = act ? exp_of(az) : -1000;
         __syncthreads();
-        int ez = -1000, ep = -1000;
-        for (int v = 0; v < (1 << lg); ++v) {
-            ez = max(ez, red[par][(rr << lg) + v][0]);
-            ep = max(ep, red[par][(rr << lg) + v][1]);
-        }
+        int ez = -1000;
+        for (int v = 0; v < (1 << lg); ++v) ez = max(ez, red[par][(rr << lg) + v]);
         if (!act) continue;
-        if (m.keep_z && live8) {
+        if (m.keep_z && live8) {   // Z itself: the scaling by 2^e_i undone (exact)
             float4 *zo = reinterpret_cast<float4 *>(m.s.x + o);
+            const int *pe = m.s.pexp + (g0 + u - a.t0) * TILE + 8 * pg;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) zo[q] = make_float4(zh[2 * q], zl[2 * q], zh[2 * q + 1], zl[2 * q + 1]);
+            for (int q = 0; q < 4; ++q) {
+                const int e0 = -min(max(pe[2 * q], -126), 127), e1 = -min(max(pe[2 * q + 1], -126), 127);
+                zo[q] = make_float4(scale2(zh[2 * q], e0), scale2(zl[2 * q], e0), scale2(zh[2 * q + 1], e1),
+                                    scale2(zl[2 * q + 1], e1));
+            }
         }
-        uint32_t wz[NSL][4], wp[NSL][4];
+        uint32_t wz[NSL][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {   // points 2q, 2q + 1
-            float a0[NSL], a1[NSL], b0[NSL], b1[NSL];
+            float a0[NSL], a1[NSL];
             slice5(zh[2 * q], zl[2 * q], ez, a0);
             slice5(zh[2 * q + 1], zl[2 * q + 1], ez, a1);
-            slice5(fh[2 * q], fl[2 * q], ep, b0);
-            slice5(fh[2 * q + 1], fl[2 * q + 1], ep, b1);
 #pragma unroll
             for (int sl = 0; sl < NSL; ++sl) {
                 __nv_bfloat162 bz = __floats2bfloat162_rn(a0[sl], a1[sl]);
-                __nv_bfloat162 bp = __floats2bfloat162_rn(b0[sl], b1[sl]);
                 wz[sl][q] = *reinterpret_cast<uint32_t *>(&bz);
-                wp[sl][q] = *reinterpret_cast<uint32_t *>(&bp);
             }
         }
         const size_t orow = (size_t)(4 * ru + (int64_t)pk * np + mu) * 32 + col;
         if (need8) {
 #pragma unroll
-            for (int sl = 0; sl < NSL; ++sl) {
+            for (int sl = 0; sl < NSL; ++sl)
                 *reinterpret_cast<uint4 *>(m.s.vz + (size_t)sl * plane + orow) =
                     make_uint4(wz[sl][0], wz[sl][1], wz[sl][2], wz[sl][3]);
-                *reinterpret_cast<uint4 *>(m.s.vphi + (size_t)sl * plane + orow) =
-                    make_uint4(wp[sl][0], wp[sl][1], wp[sl][2], wp[sl][3]);
-            }
         }
-        if (u == 0 && pg == 0) {
-            m.s.zexp[rg + mu] = ez;
-            m.s.fexp[rg + mu] = ep;
-        }
+        if (u == 0 && pg == 0) m.s.zexp[rg + mu] = ez;
     }
 }
 
@@ -1429,17 +1462,20 @@ __global__ void __launch_bounds__(TILE) slice_v(ChunkArgs a, MixedArgs m, const 
 }
 
 // ---------------------------------------------------------------- host helpers
+// Slabs of rows of 32 bf16 (64 B) in `planes` planes; K-major boxes of 16 values x box_rows
+// rows with the 32-byte swizzle, or (mn) boxes of all 32 values x 16 rows with the 64-byte
+// swizzle, the MN-major operand layout.
 CUtensorMap make_map(MixedCtx &c, void *ptr, int64_t rows, int64_t plane_rows, int planes, int box_rows,
-                     cudaError_t &err) {
+                     cudaError_t &err, bool mn = false) {
     CUtensorMap mp;
     std::memset(&mp, 0, sizeof(mp));
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(c.encode_fn);
     cuuint64_t dims[3] = {32, (cuuint64_t)std::max<int64_t>(rows, 1), (cuuint64_t)planes};
     cuuint64_t strides[2] = {64, (cuuint64_t)plane_rows * 64};
-    cuuint32_t box[3] = {16, (cuuint32_t)box_rows, (cuuint32_t)planes};
+    cuuint32_t box[3] = {mn ? 32u : 16u, (cuuint32_t)box_rows, (cuuint32_t)planes};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = encode(&mp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, mn ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) err = cudaErrorInvalidValue;
     return mp;
@@ -1623,6 +1659,8 @@ cudaError_t mixed_init(MixedCtx &c) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<1, 128>, smem, GemmCfg<128>::TOTAL);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<0, 64>, smem, GemmCfg<64>::TOTAL);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<1, 64>, smem, GemmCfg<64>::TOTAL);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<2, 128>, smem, GemmCfg<128>::TOTAL);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_persistent<2, 64>, smem, GemmCfg<64>::TOTAL);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -1731,7 +1769,7 @@ MixedArgs chunk_mixed_args(const ChunkArgs &a, MixedCtx &c, const MixedSchedule 
 }
 
 struct ChunkMaps {
-    CUtensorMap tax, tp, tz, tph;
+    CUtensorMap tax, tp, tz, tph, tax_mn;
 };
 
 ChunkMaps chunk_maps(MixedCtx &c, const MixedArgs &m, const MixedSchedule &s, const MixedSchedule::Chunk &ch,
@@ -1741,6 +1779,7 @@ ChunkMaps chunk_maps(MixedCtx &c, const MixedArgs &m, const MixedSchedule &s, co
     q.tp = make_map(c, m.pslices, ch.prows, m.pplane, NSL, s.bn, err);
     q.tz = make_map(c, m.s.vz, 4 * m.rows, 4 * m.rows, NSL, BM, err);
     q.tph = make_map(c, m.s.vphi, 4 * m.rows, 4 * m.rows, NSL, s.bn, err);
+    q.tax_mn = make_map(c, m.s.ax, 4 * m.rows, 4 * m.rows, NSL, 16, err, true);
     return q;
 }
 
@@ -1786,7 +1825,7 @@ void run_xgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, Mixed
 }
 
 void run_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c, const MixedSchedule &s,
-               cudaStream_t st);
+               cudaStream_t st, bool phi_v_side = false);
 
 void run_slice_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c,
                      const MixedSchedule &s, int64_t nt, cudaStream_t st) {
@@ -1794,22 +1833,30 @@ void run_slice_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q,
     P.begin(GBXC_K_SLICE, st);
     slice_v<false><<<(unsigned)nt, TILE, 0, st>>>(a, m, nullptr, nullptr);
     P.end(GBXC_K_SLICE, st);
-    run_vgemm(a, m, q, c, s, st);
+    run_vgemm(a, m, q, c, s, st, true);
 }
 
+// W^j and its scatter into V_acc: Phi from the V-side slices (slice_v; meta-GGA) or from the
+// X-side slices (z_slice's scaled Z; every other form)
 void run_vgemm(const ChunkArgs &a, const MixedArgs &m, const ChunkMaps &q, MixedCtx &c, const MixedSchedule &s,
-               cudaStream_t st) {
+               cudaStream_t st, bool phi_v_side) {
     Profiler &P = *a.prof;
     if (a.nvtasks <= 0) return;
     P.begin(GBXC_K_VGEMM, st);
     const unsigned g = (unsigned)std::min(a.nvtasks, c.num_sms);
     int *ctr = c.d_err + 1;
     cudaMemsetAsync(ctr, 0, sizeof(int), st);
-    if (s.bn == 64)
+    if (phi_v_side && s.bn == 64)
         gemm_persistent<1, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tz, q.tph, a, m, a.vtasks, a.nvtasks,
                                                                              ctr);
-    else
+    else if (phi_v_side)
         gemm_persistent<1, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(q.tz, q.tph, a, m, a.vtasks,
+                                                                               a.nvtasks, ctr);
+    else if (s.bn == 64)
+        gemm_persistent<2, 64><<<g, GEMM_THREADS, GemmCfg<64>::TOTAL, st>>>(q.tz, q.tax_mn, a, m, a.vtasks,
+                                                                             a.nvtasks, ctr);
+    else
+        gemm_persistent<2, 128><<<g, GEMM_THREADS, GemmCfg<128>::TOTAL, st>>>(q.tz, q.tax_mn, a, m, a.vtasks,
                                                                                a.nvtasks, ctr);
     P.end(GBXC_K_VGEMM, st);
 }
@@ -1888,7 +1935,7 @@ cudaError_t launch_mixed_chunk_mgga(const ChunkArgs &a, MixedCtx &c, MixedReside
         P.begin(GBXC_K_SLICE, st);
         slice_v<true><<<(unsigned)nt, TILE, 0, st>>>(a, mk, m.s.ghi + (size_t)k * plane, m.s.glo + (size_t)k * plane);
         P.end(GBXC_K_SLICE, st);
-        run_vgemm(a, mk, q, c, s, st);
+        run_vgemm(a, mk, q, c, s, st, true);
     }
     return cudaGetLastError();
 }

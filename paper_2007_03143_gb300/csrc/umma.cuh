@@ -3,7 +3,8 @@
 // cta_group::1), commits and tensor-memory loads.
 //
 // Operand layouts: K-major tiles with the 64-byte swizzle (rows of 32 bf16, 8-row groups
-// of 512 B) or the 32-byte swizzle (rows of 16 bf16, 8-row groups of 256 B).  A TMA box
+// of 512 B) or the 32-byte swizzle (rows of 16 bf16, 8-row groups of 256 B), and MN-major
+// tiles with the 64-byte swizzle (K-rows of 32 bf16 along M or N).  A TMA box
 // {k, rows, planes} lands as `planes` consecutive [rows x 2k B] tiles, each swizzled in
 // place; shared-memory descriptors address a 128-row (or N-row) tile.
 //
@@ -130,15 +131,30 @@ __device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
     return d;
 }
 
+// An MN-major operand with the 64-byte swizzle: 8 K-rows of 32 consecutive bf16 along M or N
+// (64 B each) form a 512-byte swizzle atom; K-groups of 8 rows are `sbo` bytes apart, the
+// next 32 values along M or N `lbo` bytes apart (both multiples of 16, below 256 KB).
+__device__ __forceinline__ uint64_t desc_mn_sw64(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(4) << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: fp32 accumulator (bits 4-5 = 1), bf16 A and B
-// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-           (static_cast<uint32_t>(M >> 4) << 24);
+// (bits 7-9 and 10-12 = 1), A K-major, B K-major (bit 16 = 0) or MN-major (bit 16 = 1),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major = false) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(b_mn_major) << 16) |
+           (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 // ---------------------------------------------------------------- MMA
-// D[tmem] (+)= A[smem] * B[smem]^T (both K-major); issued by a single thread.
+// D[tmem] (+)= A[smem] * B[smem]^T (operand majors as the instruction descriptor says);
+// issued by a single thread.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
