@@ -67,6 +67,7 @@ struct MixedSchedule {
         int max_np;
         int64_t xtask0, nxtask;        // X-contraction tasks (tile, N chunk) of the chunk
         int64_t ptask0, nptask;        // P^j slicing tasks (batch, group of 8 rows) of the chunk
+        int max_group = 8;             // tiles of the chunk's largest V task (z_slice's shared memory)
     };
     std::vector<Chunk> chunks;
     int *d_xtasks = nullptr;           // (tile, N chunk) pairs of every chunk

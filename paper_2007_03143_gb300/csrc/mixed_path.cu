@@ -994,7 +994,13 @@ __global__ void __launch_bounds__(TILE) rho_mixed(ChunkArgs a, MixedArgs m) {
 // instead of two.
 __device__ __forceinline__ int cf_slot(int p) { return p ^ ((p >> 4) & 7); }
 
-__global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
+// Dynamic shared memory: the coefficients of the chunk's largest group (4 KB per tile), so that
+// eight blocks fit an SM when the groups are short (batches of at most 512 points)
+__host__ __device__ constexpr size_t z_slice_smem(int max_group) {
+    return (size_t)max_group * 4 * TILE * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(TILE, 8) z_slice(ChunkArgs a, MixedArgs m) {
     const int64_t t = a.t0 + blockIdx.x;
     const int j = a.plan.tile_batch[t];
     const int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
@@ -1007,8 +1013,9 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
     if (ub >= nblk) return;   // block-uniform
     const int64_t rg = a.plan.tile_row[g0] - a.row0;
     const size_t plane = (size_t)m.rows * TILE;
-    // the group's per-point coefficients (a, b_x, b_y, b_z) as double-float pairs
-    __shared__ float2 cf[VKS][4][TILE];   // times 2^e_i, so that the products form Z 2^e_i
+    // the group's per-point coefficients (a, b_x, b_y, b_z) times 2^e_i as double-float pairs,
+    // [tile][4][TILE], so that the products form Z 2^e_i
+    extern __shared__ float2 cf[];
     __shared__ int64_t trow[VKS];
     __shared__ int tcnt[VKS];
     __shared__ int red[2][8];   // per step parity and slot: tile exponents of |Z 2^e|
@@ -1025,7 +1032,7 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const df c = d_to_df(cz[(size_t)(ru + q) * TILE + threadIdx.x] * pe);
-            cf[u][q][cf_slot(threadIdx.x)] = make_float2(c.h, c.l);
+            cf[(u * 4 + q) * TILE + cf_slot(threadIdx.x)] = make_float2(c.h, c.l);
         }
     }
     __syncthreads();
@@ -1065,7 +1072,8 @@ __global__ void __launch_bounds__(TILE) z_slice(ChunkArgs a, MixedArgs m) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const int e = 2 * q + k, sp = cf_slot(8 * pg + e);
-                    const float2 c0 = cf[u][0][sp], c1 = cf[u][1][sp], c2 = cf[u][2][sp], c3 = cf[u][3][sp];
+                    const float2 *cu4 = cf + u * 4 * TILE + sp;
+                    const float2 c0 = cu4[0], c1 = cu4[TILE], c2 = cu4[2 * TILE], c3 = cu4[3 * TILE];
                     df z = df_mul({c0.x, c0.y}, {fh[k], fl[k]});
                     z = df_add(z, dfl::mul_f({c1.x, c1.y}, gxs[k]));
                     z = df_add(z, dfl::mul_f({c2.x, c2.y}, gys[k]));
@@ -1566,6 +1574,12 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
         }
         ch.prows = rows;
         ch.pexp_rows = erows;
+        ch.max_group = 1;
+        for (int j = ch.j0; j <= ch.j1; ++j) {
+            const int64_t tb = std::max(plan.batch_tile[j], chunk_t0[c]);
+            const int64_t te = std::min(plan.batch_tile[j + 1], chunk_t1[c]);
+            ch.max_group = std::max<int>(ch.max_group, (int)std::min<int64_t>(VKS, te - tb));
+        }
         s.max_prows = std::max(s.max_prows, rows);
         s.max_pexp = std::max(s.max_pexp, erows);
         s.chunks.push_back(ch);
@@ -1880,7 +1894,7 @@ cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r
     rho_mixed<<<(unsigned)nt, TILE, 0, st>>>(a, m);
     P.end(GBXC_K_RHO_Z, st);
     P.begin(GBXC_K_SLICE, st);
-    z_slice<<<(unsigned)nt, TILE, 0, st>>>(a, m);
+    z_slice<<<(unsigned)nt, TILE, z_slice_smem(ch.max_group), st>>>(a, m);
     P.end(GBXC_K_SLICE, st);
     run_vgemm(a, m, q, c, s, st);
     return cudaGetLastError();
@@ -1969,13 +1983,13 @@ cudaError_t launch_mixed_chunk_uks(const ChunkArgs &a, MixedCtx &c, MixedResiden
     rho_mixed_uks<<<(unsigned)nt, TILE, 0, st>>>(a, ma, c.x2);
     P.end(GBXC_K_RHO_Z, st);
     P.begin(GBXC_K_SLICE, st);
-    z_slice<<<(unsigned)nt, TILE, 0, st>>>(a, ma);
+    z_slice<<<(unsigned)nt, TILE, z_slice_smem(ch.max_group), st>>>(a, ma);
     P.end(GBXC_K_SLICE, st);
     run_vgemm(a, ma, q, c, s, st);
     ChunkArgs ab = a;
     ab.Vacc = Vacc_b;
     P.begin(GBXC_K_SLICE, st);
-    z_slice<<<(unsigned)nt, TILE, 0, st>>>(ab, mb);
+    z_slice<<<(unsigned)nt, TILE, z_slice_smem(ch.max_group), st>>>(ab, mb);
     P.end(GBXC_K_SLICE, st);
     run_vgemm(ab, mb, q, c, s, st);
     return cudaGetLastError();
