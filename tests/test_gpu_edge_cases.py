@@ -67,7 +67,11 @@ def test_density_near_the_cut(scale):
     assert np.max(np.abs(V - ref.V)) <= 1e-9 * np.max(np.abs(ref.V)) + 1e-18
     Em, Nm, Vm = out["mixed"]
     assert abs(Em - ref.E) <= 1e-7 * abs(ref.E) + 1e-18
-    assert np.max(np.abs(Vm - ref.V)) <= 1e-6 * np.max(np.abs(ref.V)) + 1e-18
+    # V relative to its largest element: at scale 1e-12 the points whose density lies within
+    # the form's rounding of the cut are counted on one side or the other (measured 1.7e-9
+    # against max |V| of a few 1e-3)
+    dv = np.max(np.abs(Vm - ref.V))
+    assert dv <= 1e-6 * np.max(np.abs(ref.V)) + 1e-18, dv
 
 
 @pytest.mark.parametrize("Z,partition", [(8, "ssf"), (1, "becke"), (8, "becke")])
@@ -81,7 +85,8 @@ def test_single_atom(Z, partition):
     assert abs(E - ref.E) <= 1e-9 and abs(N - ref.N) <= 1e-9
     assert np.max(np.abs(V - ref.V)) <= 1e-9
     Em, Nm, Vm = out["mixed"]
-    assert abs(Em - ref.E) <= 1e-7 and np.max(np.abs(Vm - ref.V)) <= 1e-6
+    dv = np.max(np.abs(Vm - ref.V))
+    assert abs(Em - ref.E) <= 1e-7 and dv <= 1e-7, dv
 
 
 def test_tiny_batches():
@@ -94,7 +99,8 @@ def test_tiny_batches():
     E, N, V = out["fp64"]
     assert abs(E - ref.E) <= 1e-9 and np.max(np.abs(V - ref.V)) <= 1e-9
     Em, Nm, Vm = out["mixed"]
-    assert abs(Em - ref.E) <= 1e-7 and np.max(np.abs(Vm - ref.V)) <= 1e-6
+    dv = np.max(np.abs(Vm - ref.V))
+    assert abs(Em - ref.E) <= 1e-7 and dv <= 1e-7, dv
 
 
 def test_unload_releases_a_molecule_and_its_cached_graph():
@@ -136,7 +142,8 @@ def test_974_point_grid_mixed_against_float64():
         E64, N64 = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", "fp64", V64)
         Em, Nm = G.gbxc_integrate(ctx.h, mid, w.P, "pbe", "mixed", Vm)
         assert abs(Em - E64) <= 1e-7 and abs(Nm - N64) <= 1e-8
-        assert np.max(np.abs(Vm - V64)) <= 1e-6
+        dv = np.max(np.abs(Vm - V64))
+        assert dv <= 1e-7, dv
     finally:
         ctx.close()
 

@@ -19,7 +19,7 @@ def loaded(request):
     L.close()
 
 
-@pytest.mark.parametrize("precision,tol_e,tol_v", [("fp64", 1e-9, 1e-9), ("mixed", 1e-7, 1e-6)])
+@pytest.mark.parametrize("precision,tol_e,tol_v", [("fp64", 1e-9, 1e-9), ("mixed", 1e-7, 1e-7)])
 def test_pbe0_semilocal_matches_oracle(loaded, precision, tol_e, tol_v):
     g, pl = loaded.oracle()
     ref = I.integrate_method(g, loaded.w.basis, loaded.w.P, "pbe0_sl", pl)

@@ -73,7 +73,7 @@ def _oracle(nw, seed, P, fn):
 SIZES, SEED0 = [1, 3, 2, 4, 1, 2], 7000
 
 
-@pytest.mark.parametrize("prec,tol_e,tol_v", [("fp64", 1e-9, 1e-9), ("mixed", 1e-7, 1e-6)])
+@pytest.mark.parametrize("prec,tol_e,tol_v", [("fp64", 1e-9, 1e-9), ("mixed", 1e-7, 1e-7)])
 def test_many_against_oracle(setup, prec, tol_e, tol_v):
     """The default (grouped) launch over six molecules of 1-4 waters with LDA, PBE and the
     PBE0 semi-local part mixed, each molecule against the oracle."""
@@ -110,7 +110,7 @@ def test_grouped_launch_over_many_chunks(prec):
             assert abs(E[k] - e) <= 1e-10 and abs(N[k] - n) <= 1e-10, k
             if prec == "mixed":
                 V = _alone(G, ctx, mid, nbf, P, fn, "fp64")[2]
-            assert np.max(np.abs(Vs[k] - V)) <= (1e-9 if prec == "fp64" else 1e-6), k
+            assert np.max(np.abs(Vs[k] - V)) <= (1e-9 if prec == "fp64" else 1e-7), (k, np.max(np.abs(Vs[k] - V)))
     finally:
         ctx.close()
 
@@ -151,7 +151,7 @@ def test_serving_against_oracle_and_nonfinite_P(setup):
             V = np.zeros((mols[k][1], mols[k][1]))
             E, N, lat = G.gbxc_wait(ctx.h, t, 120.0, V)
             ref = _oracle(SIZES[k], SEED0 + k, mols[k][2], fn)
-            tol_e, tol_v = (1e-9, 1e-9) if prec == "fp64" else (1e-7, 1e-6)
+            tol_e, tol_v = (1e-9, 1e-9) if prec == "fp64" else (1e-7, 1e-7)
             assert abs(E - ref.E) <= tol_e and abs(N - ref.N) <= tol_e, k
             assert np.max(np.abs(V - ref.V)) <= tol_v, k
         with pytest.raises(G.GbxcError) as e:
@@ -176,7 +176,7 @@ def test_many_schedules(setup, branches, tile_n):
         assert abs(E[k] - e) <= 1e-10 and abs(N[k] - n) <= 1e-10, k
         assert np.max(np.abs(Vs[k] - V)) <= 1e-9, k
         e64, _, V64 = _alone(G, ctx, mid, nbf, P, fn, "fp64")
-        assert abs(E[k] - e64) <= 1e-7 and np.max(np.abs(Vs[k] - V64)) <= 1e-6, k
+        assert abs(E[k] - e64) <= 1e-7 and np.max(np.abs(Vs[k] - V64)) <= 1e-7, (k, np.max(np.abs(Vs[k] - V64)))
 
 
 def test_autotune(setup):

@@ -38,5 +38,5 @@ def test_spherical_mixed_against_fp64(sph):
     E64, N64, V64 = sph.integrate("fp64")
     Em, Nm, Vm = sph.integrate("mixed")
     assert abs(Em - E64) <= 1e-6 and abs(Nm - N64) <= 1e-6
-    assert np.max(np.abs(Vm - V64)) <= 1e-5
+    assert np.max(np.abs(Vm - V64)) <= 1e-7, np.max(np.abs(Vm - V64))
     assert np.array_equal(Vm, Vm.T)

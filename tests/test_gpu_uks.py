@@ -63,8 +63,8 @@ def test_uks_mixed_matches_oracle(loaded, functional):
     ref = I.integrate_method_uks(g, loaded.w.basis, Pa, Pb, functional, pl)
     E, N, Va, Vb = _uks(loaded, Pa, Pb, functional, "mixed")
     assert abs(E - ref.E) <= 1e-7 and abs(N - ref.N) <= 1e-8
-    assert np.max(np.abs(Va - ref.Va)) <= 1e-6
-    assert np.max(np.abs(Vb - ref.Vb)) <= 1e-6
+    assert np.max(np.abs(Va - ref.Va)) <= 1e-7, np.max(np.abs(Va - ref.Va))
+    assert np.max(np.abs(Vb - ref.Vb)) <= 1e-7, np.max(np.abs(Vb - ref.Vb))
     assert np.array_equal(Va, Va.T) and np.array_equal(Vb, Vb.T)
 
 
@@ -76,7 +76,7 @@ def test_uks_mixed_equal_spins_near_restricted_mixed(loaded):
     E0, N0, V0 = loaded.integrate("mixed", functional=fn)
     E, N, Va, Vb = _uks(loaded, 0.5 * loaded.w.P, 0.5 * loaded.w.P, fn, "mixed")
     assert abs(E - E0) <= 2e-7 and abs(N - N0) <= 1e-9
-    assert np.max(np.abs(Va - V0)) <= 1e-6 and np.max(np.abs(Vb - V0)) <= 1e-6
+    assert np.max(np.abs(Va - V0)) <= 1e-7 and np.max(np.abs(Vb - V0)) <= 1e-7, (np.max(np.abs(Va - V0)), np.max(np.abs(Vb - V0)))
 
 
 def test_uks_full_size_equal_spins():
@@ -99,6 +99,6 @@ def test_uks_mixed_full_size():
         E64, N64, Va64, Vb64 = _uks(L, Pa, Pb, "pbe", "fp64")
         E, N, Va, Vb = _uks(L, Pa, Pb, "pbe", "mixed")
         assert abs(E - E64) <= 1e-6 and abs(N - N64) <= 1e-7
-        assert np.max(np.abs(Va - Va64)) <= 1e-6 and np.max(np.abs(Vb - Vb64)) <= 1e-6
+        assert np.max(np.abs(Va - Va64)) <= 1e-7 and np.max(np.abs(Vb - Vb64)) <= 1e-7, (np.max(np.abs(Va - Va64)), np.max(np.abs(Vb - Vb64)))
     finally:
         L.close()
