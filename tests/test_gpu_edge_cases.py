@@ -68,8 +68,8 @@ def test_density_near_the_cut(scale):
     Em, Nm, Vm = out["mixed"]
     assert abs(Em - ref.E) <= 1e-7 * abs(ref.E) + 1e-18
     # V relative to its largest element: at scale 1e-12 the points whose density lies within
-    # the form's rounding of the cut are counted on one side or the other (measured 1.7e-9
-    # against max |V| of a few 1e-3)
+    # the form's rounding of the cut are counted on one side or the other (measured |dV| 1.7e-9,
+    # above 1e-7 of max |V|)
     dv = np.max(np.abs(Vm - ref.V))
     assert dv <= 1e-6 * np.max(np.abs(ref.V)) + 1e-18, dv
 
