@@ -69,7 +69,7 @@ struct Molecule {
     double work = 0.0;          // sum_j W_j, for balancing many molecules over graph branches
     double *many_P = nullptr, *many_V = nullptr, *many_tot = nullptr;   // gbxc_integrate_many
     double *many_Vacc = nullptr;    // its V accumulator in the grouped launch
-    float *many_pdf = nullptr;      // and its P as double-float planes (tensor-core form)
+    float *many_pdf = nullptr;      // and its P region (double-float pairs, slices; tensor-core form)
     size_t many_cap = 0;
 };
 
@@ -497,10 +497,8 @@ void carve(Workspace &w, char *base, const Molecule &m, const Schedule &S, int p
         check(mixed_init(w.mixed), "mixed init");
         w.mixed.pslices = reinterpret_cast<uint16_t *>(take((size_t)std::max<int64_t>(ms.max_prows, 1) * 32 * 5 * 2));
         w.mixed.pslice_rows = (size_t)std::max<int64_t>(ms.max_prows, 1) * 32 * 5;
-        w.mixed.pexp = reinterpret_cast<int *>(take((size_t)std::max<int64_t>(ms.max_pexp, 1) * 4));
-        w.mixed.pexp_cap = (size_t)std::max<int64_t>(ms.max_pexp, 1);
-        w.mixed.pdf = reinterpret_cast<float *>(take(2 * nn * 4));
-        w.mixed.pdf_cap = 2 * nn;
+        w.mixed.pdf = reinterpret_cast<float *>(take(mixed_pdf_floats(m.nbf) * 4));
+        w.mixed.pdf_cap = mixed_pdf_floats(m.nbf);
         w.mixed.d_err = reinterpret_cast<int *>(take(16));   // error word and GEMM task counter
     }
 }
@@ -1983,7 +1981,7 @@ void enqueue_group(Group &G, const std::vector<Molecule *> &ms, const Schedule &
     Molecule &g = G.gm;
     for (Molecule *m : ms) {
         check(cudaMemsetAsync(m->many_Vacc, 0, (size_t)m->nbf * m->nbf * 8, s), "zero V");
-        if (precision == GBXC_MIXED) check(mixed_p_to_df(m->many_P, m->many_pdf, m->nbf, s), "P planes");
+        if (precision == GBXC_MIXED) check(mixed_prepare_p(m->many_P, m->many_pdf, m->nbf, s), "P planes");
     }
     if (precision == GBXC_MIXED) check(mixed_reset_error(w.mixed, s), "error word");
     for (size_t ci = 0; ci < S.chunks.size(); ++ci) {
@@ -2069,7 +2067,7 @@ int group_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const 
             grow_buf(m.many_V, c1, nn, "V");
             grow_buf(m.many_tot, c2, 2, "totals");
             grow_buf(m.many_Vacc, c3, nn, "V_acc");
-            grow_buf(m.many_pdf, c4, 2 * nn, "P planes");
+            grow_buf(m.many_pdf, c4, mixed_pdf_floats(m.nbf), "P planes");
             m.many_cap = nn;
             if (ctx->group) free_group(ctx->group);   // its graph holds the old buffers
         }

@@ -159,7 +159,7 @@ cudaError_t launch_partition_weights(const WeightsArgs &a, cudaStream_t s);
 struct MolRef {
     const double *P;
     double *Vacc;
-    const float2 *pdf;                // (hi, lo) pairs, nbf x nbf
+    const float2 *pdf;                // P region of the tensor-core form (mixed.h: pdf_slices)
     int nbf;
     int functional;
 };

@@ -18,10 +18,8 @@ void append_fp64_vtasks(int j, int n, int64_t s0, int64_t s1, std::vector<int> &
 struct MixedCtx {
     void *encode_fn = nullptr;         // cuTensorMapEncodeTiled from the driver
     uint16_t *pslices = nullptr;       // 5 planes x rows x 32 bf16
-    int *pexp = nullptr;               // row exponents of the sliced P^j
     size_t pslice_rows = 0;            // capacity of pslices in elements
-    size_t pexp_cap = 0;
-    float *pdf = nullptr;              // P as double-float (hi, lo) pairs, nbf x nbf
+    float *pdf = nullptr;              // the P region (pdf_region_bytes): pairs, slices, exponents
     size_t pdf_cap = 0;
     // spin-unrestricted form: P_b's planes, the second X/Z slab and its Z exponents
     float *pdf2 = nullptr;
@@ -61,9 +59,8 @@ cudaError_t build_mixed_resident(const std::vector<DevShell> &shells, MixedResid
 struct MixedSchedule {
     struct Chunk {
         int j0, j1;                    // batches touched by the chunk (inclusive)
-        int64_t prow0;                 // offset of the chunk's entries in d_pofs / d_pexp_ofs
+        int64_t prow0;                 // offset of the chunk's entries in d_pofs
         int64_t prows;                 // rows of the sliced P^j blocks of the chunk
-        int64_t pexp_rows;             // sum of padded N_b^j over the chunk's batches
         int max_np;
         int64_t xtask0, nxtask;        // X-contraction tasks (tile, N chunk) of the chunk
         int64_t ptask0, nptask;        // P^j slicing tasks (batch, group of 8 rows) of the chunk
@@ -73,12 +70,20 @@ struct MixedSchedule {
     int *d_xtasks = nullptr;           // (tile, N chunk) pairs of every chunk
     int *d_ptasks = nullptr;           // (batch within the chunk, first row) pairs of every chunk
     int64_t *d_pofs = nullptr;         // per (chunk, batch): first P-slice row
-    int64_t *d_pexp_ofs = nullptr;     // per (chunk, batch): first row-exponent entry
-    int64_t max_prows = 0, max_pexp = 0;
+    int64_t max_prows = 0;
     int bn = 128;                      // N tile of the tcgen05 GEMMs: 128 or 64 functions
 };
 
 size_t mixed_row_bytes();
+// The P region of the tensor-core form, prepared once per integration from P (nbf x nbf):
+// the (hi, lo) double-float pair of every element (8 nbf^2 bytes), then the 5 bf16 slices of
+// every element with one exponent per row, as 16 bytes per element (slices 0-4, then three
+// zero halves; element (mu, nu) at 8 (mu nbf + nu) halves, 16-byte aligned), then the row
+// exponents (nbf ints).
+__host__ __device__ inline size_t pdf_slices_offset(int nbf) { return ((size_t)8 * nbf * nbf + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t pdf_exps_offset(int nbf) { return pdf_slices_offset(nbf) + (size_t)16 * nbf * nbf; }
+__host__ __device__ inline size_t pdf_region_bytes(int nbf) { return pdf_exps_offset(nbf) + (size_t)4 * nbf; }
+inline size_t mixed_pdf_floats(int nbf) { return (pdf_region_bytes(nbf) + 3) / 4; }
 // Byte offsets, within a chunk's scratch of `rows` slab rows, of the mixed form's planes that
 // hold per-point values: Phi (float2 hi/lo), grad Phi hi words (3 float planes), their lo words
 // (3 bf16 planes) and X / Z (float2 hi/lo); each plane is rows x 128 points.
@@ -99,11 +104,11 @@ cudaError_t mixed_init(MixedCtx &c);
 // Allocations of one in-flight mixed integration (call outside stream capture) ...
 cudaError_t mixed_reserve(MixedCtx &c, const MixedSchedule &s, int nbf);
 size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf);
-// ... and its per-call preparation on `st` (P to double-float, error word reset).
+// ... and its per-call preparation on `st` (the P region, error word reset).
 cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st);
-// Grouped chunks: each molecule's P as double-float (hi, lo) pairs (2 nbf^2 floats) and the
-// reset of the error word, done by mixed_begin for a single molecule.
-cudaError_t mixed_p_to_df(const double *P, float *pdf, int nbf, cudaStream_t st);
+// Grouped chunks: each molecule's P region (mixed_pdf_floats(nbf) floats) and the reset of the
+// error word, done by mixed_begin for a single molecule.
+cudaError_t mixed_prepare_p(const double *P, float *pdf, int nbf, cudaStream_t st);
 cudaError_t mixed_reset_error(MixedCtx &c, cudaStream_t st);
 cudaError_t launch_mixed_chunk(const ChunkArgs &a, MixedCtx &c, MixedResident &r,
                                const MixedSchedule &s, int chunk_index, cudaStream_t st);

@@ -108,11 +108,9 @@ struct MixedArgs {
     int64_t rows;
     int j0;                      // first batch of the chunk
     const int64_t *pofs;         // per batch of the chunk: first row of its P slices
-    const int64_t *pexp_ofs;     // per batch of the chunk: first entry of its row exponents
     __nv_bfloat16 *pslices;      // 5 planes, plane pitch pplane rows of 32
     int64_t pplane;
-    int *pexp;                   // row exponents of P^j
-    const float2 *pdf;           // P as double-float (hi, lo) pairs, nbf x nbf
+    const float2 *pdf;           // the P region (pairs, slices, row exponents)
     int *err;
     int keep_z;                  // z_slice also writes Z over X (per-batch debugging copy)
     int pad_all;                 // the collocation writes zeros for every padding point of a tile
@@ -132,20 +130,53 @@ __device__ __forceinline__ double df_to_d(df a) { return dfl::to_double(a); }
 __device__ __forceinline__ df d_to_df(double d) { return dfl::from_double(d); }
 
 // ---------------------------------------------------------------- pslice
-// P as double-float pairs (hi, lo) once per integration (the only float64 pass over P).
-__global__ void p_to_df(const double *__restrict__ P, float2 *__restrict__ pdf, int64_t nn) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nn) return;
-    df d = d_to_df(P[k]);
-    pdf[k] = make_float2(d.h, d.l);
+// The P region once per integration (the only float64 pass over P), one block per row mu:
+// the double-float pairs (hi, lo) of the row, the exponent of its largest |P_mu,nu| over all
+// nu, and the 5 slices of every element in that scale.  The X contraction gathers its P^j
+// operand from these planes: P^j's row maximum over a batch's functions is at most the row's
+// maximum over all functions, so a batch's slices lose only the bits of that ratio (none when
+// the row peaks inside the batch, as a density matrix's rows do near the diagonal).
+constexpr int PP_THREADS = 256;
+__global__ void __launch_bounds__(PP_THREADS) p_prepare(const double *__restrict__ P, float2 *__restrict__ pdf,
+                                                       int nbf) {
+    const int mu = blockIdx.x;
+    const double *row = P + (size_t)mu * nbf;
+    float2 *drow = pdf + (size_t)mu * nbf;
+    float mx = 0.f;
+    for (int nu = threadIdx.x; nu < nbf; nu += PP_THREADS) {
+        const df d = d_to_df(row[nu]);
+        drow[nu] = make_float2(d.h, d.l);
+        mx = fmaxf(mx, fabsf(d.h));
+    }
+    __shared__ float red[PP_THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+#pragma unroll
+    for (int w = 0; w < PP_THREADS / 32; ++w) mx = fmaxf(mx, red[w]);
+    const int e = exp_of(mx);
+    char *base = reinterpret_cast<char *>(pdf);
+    if (threadIdx.x == 0) reinterpret_cast<int *>(base + pdf_exps_offset(nbf))[mu] = e;
+    uint4 *sl = reinterpret_cast<uint4 *>(base + pdf_slices_offset(nbf)) + (size_t)mu * nbf;
+    for (int nu = threadIdx.x; nu < nbf; nu += PP_THREADS) {
+        const float2 v = drow[nu];
+        float q[NSL];
+        slice5(v.x, v.y, e, q);
+        __nv_bfloat162 b01 = __floats2bfloat162_rn(q[0], q[1]), b23 = __floats2bfloat162_rn(q[2], q[3]);
+        __nv_bfloat162 b4 = __floats2bfloat162_rn(q[4], 0.f);
+        sl[nu] = make_uint4(*reinterpret_cast<uint32_t *>(&b01), *reinterpret_cast<uint32_t *>(&b23),
+                            *reinterpret_cast<uint32_t *>(&b4), 0u);
+    }
 }
 
-// Two rows mu of P^j per warp (lanes 0-15 the first, 16-31 the second), eight rows per block
-// (tasks: batch, first row of eight): the row exponent from the maximum over the row (a
-// reduction over the 16 lanes of the row), then the 5 slices of P^j[mu][nu] for every K block
-// of 32 nu's, two consecutive nu per lane, so that each slice plane of the two rows (two
-// consecutive 64-byte rows of the K-blocked layout) is one 128-byte store per warp.  Rows and
-// columns past N_b^j are written as zeros.
+// P^j's slices for the X contraction's B operand, gathered from the P region (p_prepare): two
+// rows mu of P^j per warp (lanes 0-15 the first, 16-31 the second), eight rows per block
+// (tasks: batch, first row of eight), two consecutive nu per lane, so that each slice plane of
+// the two rows (two consecutive 64-byte rows of the K-blocked layout) is one 128-byte store
+// per warp.  The slices are P's own, cut with the row's exponent over all functions, so no
+// pass over the batch's row is needed first.  Rows and columns past N_b^j are zeros.
 constexpr int PS_WARPS = 4;
 constexpr int PS_ROWS = 2 * PS_WARPS;
 __global__ void __launch_bounds__(32 * PS_WARPS) pslice_kernel(ChunkArgs a, MixedArgs m, const int *tasks) {
@@ -165,28 +196,22 @@ __global__ void __launch_bounds__(32 * PS_WARPS) pslice_kernel(ChunkArgs a, Mixe
         pdf = r.pdf;
         nbf = r.nbf;
     }
-    const size_t rowoff = (mu < n) ? (size_t)F[mu] * nbf : 0;
-    float mx = 0.f;
-    if (mu < n)
-        for (int nu = hl; nu < n; nu += 16) mx = fmaxf(mx, fabsf(pdf[rowoff + F[nu]].x));
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = exp_of(mx);
-    if (hl == 0) m.pexp[m.pexp_ofs[jl] + mu] = e;
+    const uint4 *tab = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(pdf) + pdf_slices_offset(nbf));
+    const uint4 *row = tab + ((mu < n) ? (size_t)F[mu] * nbf : 0);
     const int64_t pofs = m.pofs[jl];
     for (int kb = 0; kb < np / 32; ++kb) {
         const int nu = kb * 32 + 2 * hl;
         const bool in0 = mu < n && nu < n, in1 = mu < n && nu + 1 < n;
-        const float2 p0 = in0 ? pdf[rowoff + F[nu]] : make_float2(0.f, 0.f);
-        const float2 p1 = in1 ? pdf[rowoff + F[nu + 1]] : make_float2(0.f, 0.f);
-        float q0[NSL], q1[NSL];
-        slice5(p0.x, p0.y, e, q0);
-        slice5(p1.x, p1.y, e, q1);
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        const uint4 p0 = in0 ? __ldg(row + F[nu]) : z;
+        const uint4 p1 = in1 ? __ldg(row + F[nu + 1]) : z;
+        // slice s of an element: half s of (x, y, z); the pair (nu, nu + 1) of each plane
+        const uint32_t w[NSL] = {__byte_perm(p0.x, p1.x, 0x5410), __byte_perm(p0.x, p1.x, 0x7632),
+                                 __byte_perm(p0.y, p1.y, 0x5410), __byte_perm(p0.y, p1.y, 0x7632),
+                                 __byte_perm(p0.z, p1.z, 0x5410)};
         const size_t o = (size_t)(pofs + (int64_t)kb * np + mu) * 32 + 2 * hl;
 #pragma unroll
-        for (int s = 0; s < NSL; ++s)
-            *reinterpret_cast<__nv_bfloat162 *>(m.pslices + (size_t)s * m.pplane * 32 + o) =
-                __floats2bfloat162_rn(q0[s], q1[s]);
+        for (int s = 0; s < NSL; ++s) *reinterpret_cast<uint32_t *>(m.pslices + (size_t)s * m.pplane * 32 + o) = w[s];
     }
 }
 
@@ -782,35 +807,48 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             if (!umma::mbar_wait(drain, 0)) atomicOr(m.err, 4);
         }
     } else if (warp >= 4) {   // ---------------------------------------------- epilogue
-        // Per task, each epilogue warp first stages the column data of its own EPI_COLS
-        // columns (X: P^j row exponents; V: global function indices and Phi group exponents) in
-        // its own shared-memory slots, one column per lane, then reads them back after a
-        // __syncwarp: no barrier spans the epilogue warps.
+        // Per accumulator hand-over, each epilogue warp first stages the column data of its own
+        // EPI_COLS columns (X: the row exponents of P; V: global function indices and Phi group
+        // exponents) in its own shared-memory slots, one column per lane, then reads them back
+        // after a __syncwarp: no barrier spans the epilogue warps.
         __shared__ int wcol_a[EPI_WARPS][EPI_COLS], wcol_b[EPI_WARPS][EPI_COLS];
         const int q = warp & 3, cpart = (warp - 4) >> 2, ew = warp - 4;
         const int i = q * 32 + lane;
         int *col_a = wcol_a[ew], *col_b = wcol_b[ew];
-        uint32_t tau = 0;
-        for (uint32_t ct = 0;; ++ct) {
+        uint32_t tau = 0, ct = 0;
+        // the next task of the ring (-1: no more tasks; -2: the wait expired)
+        auto ring_next = [&]() -> int {
             const uint32_t slot = ct % TQ;
             if (!umma::mbar_wait(&tqf[slot], (ct / TQ) & 1)) {
                 atomicOr(m.err, 4);
                 abort_flag = 1;
-                break;
+                return -2;
             }
+            ++ct;
             const int k = tq[slot];
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&tqe[slot]);
-            if (k < 0) break;
-        // one pass per accumulator hand-over: the K segments of an X task, one pass for V
-        for (int sg = 0, nseg = KIND == 0 ? x_nseg(x_geom(a, m, tasks, k)) : 1; sg < nseg; ++sg, ++tau) {
+            return k;
+        };
+        // one accumulator hand-over: segment sg of X task k, or V task k
+        auto epilogue = [&](int k, int sg) {
             const uint32_t b = tau % NBUF, use = tau / NBUF;
+            ++tau;
             if (lane < EPI_COLS) {
                 const int cc = cpart * EPI_COLS + lane;
                 if (KIND == 0) {
                     XGeom g = x_geom(a, m, tasks, k);
                     const int mu = g.nc * BN + cc;
-                    col_a[lane] = mu < g.n ? m.pexp[m.pexp_ofs[g.jl] + mu] : 0;
+                    const float2 *pdf = m.pdf;
+                    int nbf = a.nbf;
+                    if (a.batch_mol) {
+                        const MolRef r = mol_of(a, g.j);
+                        pdf = r.pdf;
+                        nbf = r.nbf;
+                    }
+                    const int *pe = reinterpret_cast<const int *>(reinterpret_cast<const char *>(pdf) +
+                                                                  pdf_exps_offset(nbf));
+                    col_a[lane] = mu < g.n ? pe[a.plan.func_idx[a.plan.func_ptr[g.j] + mu]] : 0;
                 } else {
                     VGeom g = v_geom(a, tasks, k);
                     const int nu = g.nc * BN + cc;
@@ -820,11 +858,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
                 }
             }
             __syncwarp();
-            if (abort_flag) continue;
+            if (abort_flag) return;
             if (!umma::mbar_wait(&tfull[b], use & 1)) {
                 atomicOr(m.err, 4);
                 abort_flag = 1;
-                continue;
+                return;
             }
             umma::fence_after_sync();
             __syncwarp();
@@ -896,7 +934,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_persistent(const __grid_
             umma::fence_before_sync();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&tempty[b]);
-        }
+        };
+        for (;;) {
+            const int k = ring_next();
+            if (k < 0) break;
+            // one pass per accumulator hand-over: the K segments of an X task, one pass for V
+            const int nseg = KIND == 0 ? x_nseg(x_geom(a, m, tasks, k)) : 1;
+            for (int sg = 0; sg < nseg; ++sg) epilogue(k, sg);
         }
     }
     __syncthreads();
@@ -1535,14 +1579,14 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
                           const std::vector<int64_t> &chunk_t1, int bn, MixedSchedule &s) {
     free_mixed_schedule(s);
     s.bn = bn;
-    std::vector<int64_t> pofs, pexp;
+    std::vector<int64_t> pofs;
     std::vector<int> xt, pt;
     for (size_t c = 0; c < chunk_t0.size(); ++c) {
         MixedSchedule::Chunk ch;
         ch.j0 = plan.tile_batch[chunk_t0[c]];
         ch.j1 = plan.tile_batch[chunk_t1[c] - 1];
         ch.prow0 = (int64_t)pofs.size();
-        int64_t rows = 0, erows = 0;
+        int64_t rows = 0;
         ch.max_np = 0;
         ch.xtask0 = (int64_t)xt.size() / 2;
         for (int64_t t = chunk_t0[c]; t < chunk_t1[c]; ++t) {
@@ -1567,13 +1611,10 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
             int64_t n = plan.func_ptr[j + 1] - plan.func_ptr[j];
             int64_t np = pad_funcs(n);
             pofs.push_back(rows);
-            pexp.push_back(erows);
             rows += (np / 32) * np;
-            erows += np;
             ch.max_np = std::max<int>(ch.max_np, (int)np);
         }
         ch.prows = rows;
-        ch.pexp_rows = erows;
         ch.max_group = 1;
         for (int j = ch.j0; j <= ch.j1; ++j) {
             const int64_t tb = std::max(plan.batch_tile[j], chunk_t0[c]);
@@ -1581,7 +1622,6 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
             ch.max_group = std::max<int>(ch.max_group, (int)std::min<int64_t>(VKS, te - tb));
         }
         s.max_prows = std::max(s.max_prows, rows);
-        s.max_pexp = std::max(s.max_pexp, erows);
         s.chunks.push_back(ch);
     }
     if (!xt.empty()) {
@@ -1595,8 +1635,6 @@ void build_mixed_schedule(const HostPlan &plan, const std::vector<int64_t> &chun
     if (!pofs.empty()) {
         cudaMalloc(&s.d_pofs, pofs.size() * sizeof(int64_t));
         cudaMemcpy(s.d_pofs, pofs.data(), pofs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-        cudaMalloc(&s.d_pexp_ofs, pexp.size() * sizeof(int64_t));
-        cudaMemcpy(s.d_pexp_ofs, pexp.data(), pexp.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     }
 }
 
@@ -1604,7 +1642,6 @@ void free_mixed_schedule(MixedSchedule &s) {
     cudaFree(s.d_xtasks);
     cudaFree(s.d_ptasks);
     cudaFree(s.d_pofs);
-    cudaFree(s.d_pexp_ofs);
     s = MixedSchedule{};
 }
 
@@ -1654,7 +1691,6 @@ void free_mixed_ctx(MixedCtx &c) {
     cudaFree(c.wexp_g);
     cudaFree(c.gexp_g);
     cudaFree(c.pslices);
-    cudaFree(c.pexp);
     cudaFree(c.d_err);
     c = MixedCtx{};
 }
@@ -1696,27 +1732,25 @@ cudaError_t mixed_reserve(MixedCtx &c, const MixedSchedule &s, int nbf) {
     }
     cudaError_t e = grow(c.pslices, c.pslice_rows, (size_t)std::max<int64_t>(s.max_prows, 1) * 32 * NSL);
     if (e != cudaSuccess) return e;
-    e = grow(c.pexp, c.pexp_cap, (size_t)std::max<int64_t>(s.max_pexp, 1));
-    if (e != cudaSuccess) return e;
-    return grow(c.pdf, c.pdf_cap, (size_t)std::max<int64_t>(2 * (int64_t)nbf * nbf, 1));
+    return grow(c.pdf, c.pdf_cap, std::max<size_t>(mixed_pdf_floats(nbf), 1));
 }
 
 size_t mixed_reserve_bytes(const MixedSchedule &s, int nbf) {
-    return (size_t)std::max<int64_t>(s.max_prows, 1) * 32 * NSL * 2 + (size_t)std::max<int64_t>(s.max_pexp, 1) * 4 +
-           (size_t)2 * nbf * nbf * 4;
+    return (size_t)std::max<int64_t>(s.max_prows, 1) * 32 * NSL * 2 +
+           mixed_pdf_floats(nbf) * 4;
 }
 
 cudaError_t mixed_begin(MixedCtx &c, const double *P, int nbf, cudaStream_t st) {
     int64_t nn = (int64_t)nbf * nbf;
-    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, reinterpret_cast<float2 *>(c.pdf), nn);
+    if (nn > 0) p_prepare<<<(unsigned)nbf, PP_THREADS, 0, st>>>(P, reinterpret_cast<float2 *>(c.pdf), nbf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemsetAsync(c.d_err, 0, sizeof(int), st);
 }
 
-cudaError_t mixed_p_to_df(const double *P, float *pdf, int nbf, cudaStream_t st) {
+cudaError_t mixed_prepare_p(const double *P, float *pdf, int nbf, cudaStream_t st) {
     int64_t nn = (int64_t)nbf * nbf;
-    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(P, reinterpret_cast<float2 *>(pdf), nn);
+    if (nn > 0) p_prepare<<<(unsigned)nbf, PP_THREADS, 0, st>>>(P, reinterpret_cast<float2 *>(pdf), nbf);
     return cudaGetLastError();
 }
 
@@ -1728,12 +1762,12 @@ cudaError_t mixed_reserve_uks(MixedCtx &c, int64_t max_rows, int nbf) {
     if (e != cudaSuccess) return e;
     e = grow(c.zexp2, c.zexp2_cap, rows);
     if (e != cudaSuccess) return e;
-    return grow(c.pdf2, c.pdf2_cap, (size_t)std::max<int64_t>(2 * (int64_t)nbf * nbf, 1));
+    return grow(c.pdf2, c.pdf2_cap, std::max<size_t>(mixed_pdf_floats(nbf), 1));
 }
 
 size_t mixed_reserve_uks_bytes(int64_t max_rows, int nbf) {
     const size_t rows = (size_t)std::max<int64_t>(max_rows, 1);
-    return rows * TILE * 8 + rows * 4 + (size_t)2 * nbf * nbf * 4;
+    return rows * TILE * 8 + rows * 4 + mixed_pdf_floats(nbf) * 4;
 }
 
 cudaError_t mixed_reserve_mgga(MixedCtx &c, int64_t max_rows) {
@@ -1751,7 +1785,7 @@ cudaError_t mixed_begin_uks(MixedCtx &c, const double *Pa, const double *Pb, int
     cudaError_t e = mixed_begin(c, Pa, nbf, st);
     if (e != cudaSuccess) return e;
     int64_t nn = (int64_t)nbf * nbf;
-    if (nn > 0) p_to_df<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Pb, reinterpret_cast<float2 *>(c.pdf2), nn);
+    if (nn > 0) p_prepare<<<(unsigned)nbf, PP_THREADS, 0, st>>>(Pb, reinterpret_cast<float2 *>(c.pdf2), nbf);
     return cudaGetLastError();
 }
 
@@ -1771,10 +1805,8 @@ MixedArgs chunk_mixed_args(const ChunkArgs &a, MixedCtx &c, const MixedSchedule 
     m.rows = a.rows;
     m.j0 = ch.j0;
     m.pofs = s.d_pofs + ch.prow0;
-    m.pexp_ofs = s.d_pexp_ofs + ch.prow0;
     m.pslices = reinterpret_cast<__nv_bfloat16 *>(c.pslices);
     m.pplane = std::max<int64_t>(s.max_prows, 1);
-    m.pexp = c.pexp;
     m.pdf = reinterpret_cast<const float2 *>(pdf);
     m.err = c.d_err;
     m.keep_z = c.keep_z;
