@@ -450,30 +450,40 @@ __global__ void __launch_bounds__(TILE, 7) colloc_mixed(ChunkArgs a, MixedArgs m
             m.s.glo[c * plane + o] = __float2bfloat16_rn(0.f);
         }
     }
-    // Ozaki slices of this point's row of Phi: K block kb -> row 4 r0 + 128 kb + i, 32 values
-    for (int kb = 0; kb < np / 32; ++kb) {
-        const size_t orow = (size_t)(4 * r0 + (int64_t)kb * TILE + i) * 32;
-#pragma unroll 1
-        for (int c8 = 0; c8 < 32; c8 += 8) {   // 8 functions -> one 16-byte store per slice
-            uint32_t w[NSL][4];
+    // Ozaki slices of this point's row of Phi: K block kb -> row 4 r0 + 128 kb + i, 32 values,
+    // eight functions per 16-byte store of each slice plane; the next eight values are loaded
+    // while the current ones are cut
+    const int ngr = np / 8;
+    float2 nx[8];
+    auto load8 = [&](int gi) {
+        if (gi < ngr) {
 #pragma unroll
-            for (int pr = 0; pr < 4; ++pr) {
-                size_t o = (size_t)(r0 + kb * 32 + c8 + 2 * pr) * TILE + i;
-                float2 f0 = phi[o], f1 = phi[o + TILE];
-                float q0[NSL], q1[NSL];
-                slice5(f0.x, f0.y, e, q0);
-                slice5(f1.x, f1.y, e, q1);
-#pragma unroll
-                for (int s = 0; s < NSL; ++s) {
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(q0[s], q1[s]);
-                    w[s][pr] = *reinterpret_cast<uint32_t *>(&b2);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < NSL; ++s)
-                *reinterpret_cast<uint4 *>(m.s.ax + (size_t)s * plane + orow + c8) =
-                    make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+            for (int k = 0; k < 8; ++k) nx[k] = phi[(size_t)(r0 + 8 * gi + k) * TILE + i];
         }
+    };
+    load8(0);
+#pragma unroll 1
+    for (int gi = 0; gi < ngr; ++gi) {
+        float2 cur[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cur[k] = nx[k];
+        load8(gi + 1);
+        uint32_t w[NSL][4];
+#pragma unroll
+        for (int pr = 0; pr < 4; ++pr) {
+            float q0[NSL], q1[NSL];
+            slice5(cur[2 * pr].x, cur[2 * pr].y, e, q0);
+            slice5(cur[2 * pr + 1].x, cur[2 * pr + 1].y, e, q1);
+#pragma unroll
+            for (int s = 0; s < NSL; ++s) {
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(q0[s], q1[s]);
+                w[s][pr] = *reinterpret_cast<uint32_t *>(&b2);
+            }
+        }
+        const size_t orow = (size_t)(4 * r0 + (int64_t)(gi >> 2) * TILE + i) * 32 + (gi & 3) * 8;
+#pragma unroll
+        for (int s = 0; s < NSL; ++s)
+            *reinterpret_cast<uint4 *>(m.s.ax + (size_t)s * plane + orow) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
     }
 }
 
@@ -1044,7 +1054,7 @@ __host__ __device__ constexpr size_t z_slice_smem(int max_group) {
     return (size_t)max_group * 4 * TILE * sizeof(float2);
 }
 
-__global__ void __launch_bounds__(TILE, 8) z_slice(ChunkArgs a, MixedArgs m) {
+__global__ void __launch_bounds__(TILE, 4) z_slice(ChunkArgs a, MixedArgs m) {
     const int64_t t = a.t0 + blockIdx.x;
     const int j = a.plan.tile_batch[t];
     const int n = (int)(a.plan.func_ptr[j + 1] - a.plan.func_ptr[j]);
@@ -1091,24 +1101,47 @@ __global__ void __launch_bounds__(TILE, 8) z_slice(ChunkArgs a, MixedArgs m) {
     // reads them, i.e. below the count rounded up to its 16-point K steps
     const int cu = u < ng ? tcnt[u] : 0;
     const bool live8 = 8 * pg < cu, need8 = 8 * pg < ((cu + 15) & ~15);
+    // the next step's Phi and grad Phi are loaded while this step's Z is formed and sliced
+    float4 nf[4], nh[3][2];
+    auto load = [&](int c2) {
+        const int mu2 = c2 * R + rr;
+        if (c2 * R < n && u < ng && mu2 < n && live8) {
+            const size_t o2 = (size_t)(ru + mu2) * TILE + 8 * pg;
+            const float4 *fs = reinterpret_cast<const float4 *>(m.s.phi + o2);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nf[q] = fs[q];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float4 *h = reinterpret_cast<const float4 *>(m.s.ghi + d * plane + o2);
+                nh[d][0] = h[0];
+                nh[d][1] = h[1];
+            }
+        }
+    };
+    load(ub);
     int par = 0;
     for (int c = ub; c * R < n; c += nblk, par ^= 1) {
         const int mu = c * R + rr;
         const bool act = u < ng && mu < n;
+        float4 cfs[4], ch[3][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfs[q] = nf[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ch[d][0] = nh[d][0];
+            ch[d][1] = nh[d][1];
+        }
+        load(c + nblk);
         float zh[8], zl[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) zh[e] = zl[e] = 0.f;
         float az = 0.f;
         const size_t o = (size_t)(ru + mu) * TILE + 8 * pg;
         if (act && live8) {
-            const float4 *fs = reinterpret_cast<const float4 *>(m.s.phi + o);
-            const float4 *h1 = reinterpret_cast<const float4 *>(m.s.ghi + o);
-            const float4 *h2 = reinterpret_cast<const float4 *>(m.s.ghi + plane + o);
-            const float4 *h3 = reinterpret_cast<const float4 *>(m.s.ghi + 2 * plane + o);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {   // points 2q, 2q + 1
-                const float4 f4 = fs[q];
-                const float4 a1 = h1[q >> 1], a2 = h2[q >> 1], a3 = h3[q >> 1];
+                const float4 f4 = cfs[q];
+                const float4 a1 = ch[0][q >> 1], a2 = ch[1][q >> 1], a3 = ch[2][q >> 1];
                 const float gxs[2] = {(q & 1) ? a1.z : a1.x, (q & 1) ? a1.w : a1.y};
                 const float gys[2] = {(q & 1) ? a2.z : a2.x, (q & 1) ? a2.w : a2.y};
                 const float gzs[2] = {(q & 1) ? a3.z : a3.x, (q & 1) ? a3.w : a3.y};
