@@ -132,7 +132,8 @@ typedef struct {
  * context: basis and grid loading build the plan on the host and
  * gbxc_export_plan returns it, except the partition weights; no CUDA call is
  * made and integration returns GBXC_EINVAL).  `scratch_bytes` bounds the device
- * scratch used per integration (0 = a default fraction of free memory); work
+ * scratch used per integration (0 = half the free device memory at the first integration,
+ * at most 128 GiB); work
  * that does not fit is processed in chunks of batches, like the paper's
  * device-memory-saturating subsets (Algorithm 2). */
 int gbxc_create(gbxc_ctx **out, int device, size_t scratch_bytes);
@@ -285,8 +286,10 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
  * parallel graph branches by the greedy minimum-load rule of Algorithm 3 applied to the work
  * estimate of Eq. batch_work, each branch with its own stream and workspace.  The graph is
  * captured on the first call for a given (molecule list, precision, schedule) and replayed by
- * later calls with the same list (P and the functionals may change).  A NaN or an infinity
- * in any P returns GBXC_EINVAL.
+ * later calls with the same list (P and the functionals may change).  The workspaces of these
+ * calls share one budget, fixed at the context's first such call: the scratch budget given to
+ * gbxc_create, or else the default one capped by half the device memory then free.  A NaN or
+ * an infinity in any P returns GBXC_EINVAL.
  *   nmol          number of molecules (each id at most once)
  *   mol_ids[k]    molecule ids
  *   P[k]          nbf_k x nbf_k density matrices, host or device
@@ -324,7 +327,8 @@ int gbxc_set_schedule(gbxc_ctx *ctx, int nmol, const int *mol_ids, int precision
 
 /* Serving form: continuous batching of integration requests.
  * gbxc_serve_start allocates one device arena of `arena_bytes` (0 = the context's
- * scratch budget), creates `nslots` streams and starts a scheduler thread.  Requests
+ * scratch budget, or, when gbxc_create was given none, at most half the device memory free at
+ * this call), creates `nslots` streams and starts a scheduler thread.  Requests
  * (gbxc_submit) queue in arrival order; the scheduler admits the head of the queue as
  * soon as a slot is free and a contiguous region of the arena can hold the request's
  * device footprint (scratch of its batch schedule, P, V, partial sums and, for

@@ -211,6 +211,8 @@ struct gbxc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     size_t scratch_budget = 0;
+    bool budget_given = false;      // gbxc_create's scratch_bytes (used as is everywhere)
+    size_t many_budget = 0;         // the many-molecule calls' budget, fixed at their first call
     Workspace ws;                   // the default workspace (synchronous calls)
     std::vector<Workspace> branch_ws;   // gbxc_integrate_many branches
     ManyGraph many;
@@ -503,15 +505,30 @@ void carve(Workspace &w, char *base, const Molecule &m, const Schedule &S, int p
     }
 }
 
-// The default budget is fixed at the first integration of the context (40% of the
-// free device memory then, at most 48 GiB), so schedules stay valid across calls.
+// The default budget is fixed at the first integration of the context (half the free device
+// memory then, at most 128 GiB), so schedules stay valid across calls.  Fewer, larger chunks
+// pay the ramp-up and tail of each kernel fewer times: the 64-water call runs in 2 chunks
+// instead of 5 at 48 GiB.
 size_t scratch_budget(gbxc_ctx *ctx) {
     if (ctx->scratch_budget) return ctx->scratch_budget;
     size_t fr = 0, tot = 0;
     check(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-    size_t b = (size_t)(0.4 * (double)fr);
-    ctx->scratch_budget = std::min<size_t>(b, (size_t)48 << 30);
+    size_t b = (size_t)(0.5 * (double)fr);
+    ctx->scratch_budget = std::min<size_t>(b, (size_t)128 << 30);
     return ctx->scratch_budget;
+}
+
+// Memory beside the single-call workspace (the many-molecule branches, the serving arena): a
+// default budget is capped by half the device memory free when it is first needed, since the
+// single-call workspace may already hold its own budget.
+size_t side_budget(gbxc_ctx *ctx, size_t &fixed) {
+    if (ctx->budget_given) return scratch_budget(ctx);
+    if (fixed) return fixed;
+    const size_t b = scratch_budget(ctx);
+    size_t fr = 0, tot = 0;
+    check(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+    fixed = std::min<size_t>(b, (size_t)(0.5 * (double)fr));
+    return fixed;
 }
 
 // Chunks of tiles whose slabs fit the budget, and the V-contraction tasks of each chunk.
@@ -924,6 +941,7 @@ int gbxc_create(gbxc_ctx **out, int device, size_t scratch_bytes) {
     if (!ctx) return GBXC_ENOMEM;
     ctx->device = device;
     ctx->scratch_budget = scratch_bytes;
+    ctx->budget_given = scratch_bytes != 0;
     int rc = guarded(ctx, [&] {
         check(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "stream");
         ctx->ws.stream = ctx->stream;
@@ -1752,7 +1770,7 @@ int many_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const *
     W = std::max(1, std::min(W, nmol));
     if (precision == GBXC_FP64) tile_n = 128;
     REQUIRE(mixed_tile_supported(tile_n), "unsupported GEMM tile");
-    const size_t budget = scratch_budget(ctx) / W;
+    const size_t budget = side_budget(ctx, ctx->many_budget) / W;
     // longest-processing-time assignment of molecules to graph branches by the work
     // estimate of Eq. batch_work (the paper's greedy minimum-load rule, Algorithm 3)
     std::vector<int> order(nmol);
@@ -2047,7 +2065,7 @@ int group_impl(gbxc_ctx *ctx, int nmol, const int *mol_ids, const double *const 
     }
     if (precision == GBXC_FP64) tile_n = 128;
     REQUIRE(mixed_tile_supported(tile_n), "unsupported GEMM tile");
-    const size_t budget = scratch_budget(ctx);
+    const size_t budget = side_budget(ctx, ctx->many_budget);
     cudaStream_t o = ctx->stream;
     std::vector<int> ids(mol_ids, mol_ids + nmol);
     // per-molecule buffers: P, V_acc, V, {E, N} and the double-float P planes
@@ -2234,7 +2252,8 @@ int gbxc_serve_start(gbxc_ctx *ctx, int nslots, size_t arena_bytes) {
         REQUIRE(nslots >= 1 && nslots <= 64, "nslots must be in 1..64");
         Server &S = ctx->srv;
         REQUIRE(!S.running, "the server is already running");
-        size_t cap = arena_bytes ? arena_bytes : scratch_budget(ctx);
+        size_t fixed = 0;
+        size_t cap = arena_bytes ? arena_bytes : side_budget(ctx, fixed);
         cudaError_t e = cudaMalloc(&S.arena_mem, cap);
         if (e != cudaSuccess) {
             cudaGetLastError();
