@@ -75,3 +75,35 @@ def test_mixed_device_pointers():
         assert np.max(np.abs(Vd.cpu().numpy() - V2)) <= 1e-12 * np.max(np.abs(V2))
     finally:
         L.close()
+
+
+def test_p_rows_peaking_outside_the_batch():
+    """P's slices are cut once per row with the row's largest element over all functions; a
+    batch whose P^j row peaks lower loses the bits of that ratio.  Here the most diffuse s
+    function of the first oxygen couples to the tightest s function of the second oxygen,
+    which the batches around the first water do not hold, above 5x its own diagonal (P stays
+    positive semidefinite: a rank-one term v v^T is added); the mixed form keeps its relative
+    accuracy."""
+    L = Loaded("water2_pbe_small")
+    try:
+        b = L.w.basis
+        sh0 = [s for s in range(len(b.L)) if b.atom[s] == 0 and b.L[s] == 0]
+        sh3 = [s for s in range(len(b.L)) if b.atom[s] == 3 and b.L[s] == 0]
+        mu = int(b.func_offset[sh0[-1]])   # most diffuse s of oxygen 0
+        nu = int(b.func_offset[sh3[0]])    # tightest s of oxygen 3
+        v = np.zeros(b.nbf)
+        v[mu], v[nu] = 1.0, 10.0
+        P = L.w.P + np.outer(v, v)
+        assert abs(P[mu, nu]) > 5 * abs(P[mu, mu])
+        g, pl = L.oracle()
+        ref = I.integrate_method(g, b, P, "pbe", pl)
+        E, N, V = L.integrate("mixed", P=P)
+        # positive semidefiniteness forces about 100 electrons into the tight function, so
+        # E_xc is near -4.4e3 Eh: the bounds are relative (measured |dE| 8.3e-11 |E|)
+        assert abs(E - ref.E) <= 1e-9 * abs(ref.E), abs(E - ref.E)
+        dv = np.max(np.abs(V - ref.V))
+        assert dv <= 1e-7 * np.max(np.abs(ref.V)), (dv, np.max(np.abs(ref.V)))
+        # some batch holds mu without nu, so the test reaches the case it is about
+        assert any(mu in set(f.tolist()) and nu not in set(f.tolist()) for f in pl.batch_funcs)
+    finally:
+        L.close()
