@@ -10,6 +10,7 @@ import math
 from fractions import Fraction
 
 import numpy as np
+import pytest
 
 from oracle import functionals as F
 from oracle import functionals_mgga as M
@@ -125,3 +126,23 @@ def test_becke_cell_function_has_three_iterations():
     assert abs(s(3) - 0.012350184590559365) < 1e-17
     assert abs(s(2) - 0.012350184590559365) > 0.05
     assert abs(PT._becke_s(np.array([0.5]))[0] - s(3)) < 1e-16
+
+
+@pytest.mark.parametrize("prm,A,c1", [
+    (FP.PW_E0, (1.0 - math.log(2.0)) / math.pi ** 2, 0.046644),
+    (FP.PW_E1, (1.0 - math.log(2.0)) / (2.0 * math.pi ** 2), 0.025599),
+    (FP.PW_AC, 1.0 / (6.0 * math.pi ** 2), 0.035475)])
+def test_pw92_high_density_expansion_of_every_parameter_set(prm, A, c1):
+    """PW92 builds beta_1 and beta_2 of each of its three sets (unpolarised, fully polarised,
+    spin stiffness -alpha_c) from the high-density expansion G(r_s) = A ln r_s - c1 + O(r_s ln r_s):
+    A is the random-phase coefficient ((1 - ln 2)/pi^2, half of it for the fully polarised gas,
+    1/(6 pi^2) for the stiffness), c1 the constant of the same expansion that PW92 takes from the
+    electron-gas literature (0.046644, 0.025599, 0.035475), and the expansion has no r_s^(1/2)
+    term, i.e. beta_2 = 2 A beta_1^2.  A beta_1 off by 0.5% moves the constant by 3e-4; a beta_2
+    off by 1% gives an r_s^(1/2) coefficient above 1e-4."""
+    assert abs(prm[0] - A) < 5e-7
+    rs = np.array([1e-16, 1e-14])
+    D = FP._G(rs, prm)[0] - prm[0] * np.log(rs)   # -c1 + a r_s^(1/2) + ...
+    assert abs(-D[0] - c1) < 3e-6
+    a_half = (D[1] - D[0]) / (np.sqrt(rs[1]) - np.sqrt(rs[0]))
+    assert abs(a_half) < 5e-6
