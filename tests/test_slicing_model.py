@@ -142,3 +142,41 @@ def test_contraction_against_float64_gemm(operands):
     assert np.max(err) <= 8.0 * K_MAX * 2.0 ** -34
     # and far below what a split-bf16 x 3 product (about 2^-16 per product) would leave
     assert np.max(err) < 1e-3 * K_MAX * 2.0 ** -16
+
+
+def test_w_contraction_with_phi_cut_per_point():
+    """The W contraction W = Z^T Phi over K points takes Phi's slices from the X contraction,
+    cut with one exponent e_i per point (Phi_i,nu 2^-e_i, |.| <= 1), and slices Z_i,mu 2^e_i with
+    one exponent per function over the points, so W_mu,nu = 2^(e_mu) sum_levels (Z-slices .
+    Phi-slices) needs only Z's exponents.  With K = 1,024 points (a V task's 8 tiles), levels
+    0-2 accumulate exactly in float32 and W lies within 8 K 2^-34 of the float64 product in units
+    of 2^(e_mu), even when the points' Phi maxima span nine decades."""
+    rng = np.random.default_rng(11)
+    K, M, N = 1024, 24, 20
+    point_scale = 10.0 ** rng.uniform(-6, 3, size=(K, 1))
+    Phi = rng.standard_normal((K, N)) * point_scale                    # points x functions
+    Z = rng.standard_normal((K, M)) * point_scale * 10.0 ** rng.uniform(-3, 0, size=(1, M))
+    hp, lp, ep = split_rows(Phi)                                       # one exponent per point
+    qp = slice5(hp, lp, ep)                                            # K x N slices, |.| <= 1
+    Zs = Z * np.ldexp(1.0, ep)                                         # Z_i,mu 2^e_i
+    hz, lz, ez = split_rows(Zs.T)                                      # one exponent per function
+    qz = slice5(hz, lz, ez)                                            # M x K slices
+    lv = {d: [] for d in range(5)}
+    for s in range(NSL):
+        for t in range(NSL - s):
+            lv[s + t].append((qz[s], qp[t]))
+    acc = []
+    for group in ((0,), (1,), (2,), (3, 4)):
+        a32 = np.zeros((M, N), dtype=F32)
+        for k in range(K):
+            for d in group:
+                for a, b in lv[d]:
+                    a32 = (a32 + np.outer(a[:, k], b[k, :]).astype(F32)).astype(F32)
+        acc.append(a32.astype(np.float64))
+    for d in range(3):   # the exact levels: the float32 sums equal the float64 ones
+        exact = sum(a.astype(np.float64) @ b.astype(np.float64) for a, b in lv[d])
+        assert np.array_equal(acc[d], exact), d
+    W = sum(acc) * np.ldexp(1.0, ez)
+    ref = Z.T @ Phi
+    err = np.abs(W - ref) / np.ldexp(1.0, ez)
+    assert np.max(err) <= 8.0 * K * 2.0 ** -34
