@@ -35,10 +35,11 @@ constants are pinned by closed forms and design conditions in
 cancellation of the second-order gradient terms, which fixes mu = beta pi^2/3 and the s and t
 normalisations, PW92's high-density coefficient against Gell-Mann-Brueckner's (1 - ln 2)/pi^2,
 the hydrogen atom's closed-form LSD exchange and exact exchange -5/16, which MVS reproduces,
-and PW92's high-density expansion for all three parameter sets: A, the constant c1 and no
-r_s^(1/2) term, which fix beta_1 and beta_2).
-Still "parity unpinned", because nothing in reach fixes them beyond those relations: the
-absolute value of beta, PW92's alpha_1, beta_3 and beta_4 (published values are used
+PW92's high-density expansion for all three parameter sets: A, the constant c1 and no
+r_s^(1/2) term, which fix beta_1 and beta_2; and PBE's beta against Ma and Brueckner's
+gradient coefficient through the small-t limit of H).
+Still "parity unpinned", because nothing in reach fixes them beyond those relations:
+PW92's alpha_1, beta_3 and beta_4 (published values are used
 verbatim; PBE's tabulated hydrogen values are checked to three decimals only), MVS's e1 and c1
 (they do not enter at alpha = 0), and the Mura-Knowles radial scale alpha = 5.0.
 """

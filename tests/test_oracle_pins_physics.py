@@ -146,3 +146,21 @@ def test_pw92_high_density_expansion_of_every_parameter_set(prm, A, c1):
     assert abs(-D[0] - c1) < 3e-6
     a_half = (D[1] - D[0]) / (np.sqrt(rs[1]) - np.sqrt(rs[0]))
     assert abs(a_half) < 5e-6
+
+
+def test_pbe_correlation_gradient_coefficient_is_ma_brueckner():
+    """For a slowly varying density PBE's correlation gradient term is n beta t^2, the
+    second-order gradient expansion of the high-density gas: beta = nu C_c(0) with
+    nu = (16/pi)(3 pi^2)^(1/3) and Ma and Brueckner's coefficient C_c(0) = 0.004235 (the
+    relation and value PW91 and PBE use; four digits, so 1e-4 relative).  t is built here from
+    its definition, t = |grad n| / (2 k_s n), k_s = (4 k_F / pi)^(1/2), k_F = (3 pi^2 n)^(1/3)."""
+    beta_mb = 16.0 / math.pi * (3.0 * math.pi ** 2) ** (1.0 / 3.0) * 0.004235
+    n = np.array([0.05, 0.5, 5.0])
+    kf = (3.0 * math.pi ** 2 * n) ** (1.0 / 3.0)
+    ks = np.sqrt(4.0 * kf / math.pi)
+    t2 = 1e-8
+    sigma = t2 * (2.0 * ks * n) ** 2
+    f1, _, _ = F.pbe_correlation(n, sigma)
+    f0, _, _ = F.pbe_correlation(n, np.zeros_like(n))
+    beta_eff = (f1 - f0) / (n * t2)
+    assert np.max(np.abs(beta_eff / beta_mb - 1.0)) < 1e-4
