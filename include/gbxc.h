@@ -288,7 +288,8 @@ int gbxc_integrate_batches(gbxc_ctx *ctx, int mol, const double *P, int function
  * captured on the first call for a given (molecule list, precision, schedule) and replayed by
  * later calls with the same list (P and the functionals may change).  The workspaces of these
  * calls share one budget, fixed at the context's first such call: the scratch budget given to
- * gbxc_create, or else the default one capped by half the device memory then free.  A NaN or
+ * gbxc_create, or else the default one capped by half the device memory then free after the part
+ * of the single-call budget not yet allocated.  A NaN or
  * an infinity in any P returns GBXC_EINVAL.
  *   nmol          number of molecules (each id at most once)
  *   mol_ids[k]    molecule ids
@@ -328,7 +329,8 @@ int gbxc_set_schedule(gbxc_ctx *ctx, int nmol, const int *mol_ids, int precision
 /* Serving form: continuous batching of integration requests.
  * gbxc_serve_start allocates one device arena of `arena_bytes` (0 = the context's
  * scratch budget, or, when gbxc_create was given none, at most half the device memory free at
- * this call), creates `nslots` streams and starts a scheduler thread.  Requests
+ * this call after the part of the single-call budget not yet allocated), creates `nslots`
+ * streams and starts a scheduler thread.  Requests
  * (gbxc_submit) queue in arrival order; the scheduler admits the head of the queue as
  * soon as a slot is free and a contiguous region of the arena can hold the request's
  * device footprint (scratch of its batch schedule, P, V, partial sums and, for

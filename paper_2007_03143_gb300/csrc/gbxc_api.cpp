@@ -519,15 +519,18 @@ size_t scratch_budget(gbxc_ctx *ctx) {
 }
 
 // Memory beside the single-call workspace (the many-molecule branches, the serving arena): a
-// default budget is capped by half the device memory free when it is first needed, since the
-// single-call workspace may already hold its own budget.
+// default budget is capped by half the device memory free when it is first needed, less the
+// part of the single-call budget that its workspace has not allocated yet, so that either
+// order of calls fits.
 size_t side_budget(gbxc_ctx *ctx, size_t &fixed) {
     if (ctx->budget_given) return scratch_budget(ctx);
     if (fixed) return fixed;
     const size_t b = scratch_budget(ctx);
     size_t fr = 0, tot = 0;
     check(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-    fixed = std::min<size_t>(b, (size_t)(0.5 * (double)fr));
+    const size_t pending = b > ctx->ws.scratch_cap ? b - ctx->ws.scratch_cap : 0;
+    const size_t room = fr > pending ? fr - pending : 0;
+    fixed = std::max<size_t>(std::min<size_t>(b, (size_t)(0.5 * (double)room)), (size_t)64 << 20);
     return fixed;
 }
 
