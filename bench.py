@@ -184,7 +184,7 @@ def _traffic(kernel, form):
 #                 (mixed: Phi 8 B, grad Phi 18 B, X 8 B, slices 2 B each; float64: 8 B values).
 COLLOC_OPS = 3 + 25
 STREAM_BYTES = {"fp64": {"rho_z": 48},
-                "mixed": {"rho_z": 8 + 18 + 8, "vslice": 8 + 12 + 20}}
+                "mixed": {"rho_z": 8 + 18 + 8, "vslice": 8 + 12 + 10}}   # vslice: Phi, grad Phi hi, Z slices
 
 
 def roofline(kind, ms, form, info, peaks, peak_src, alu):
