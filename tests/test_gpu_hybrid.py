@@ -1,7 +1,7 @@
 """The semi-local part of the PBE0 hybrid (3/4 PBE exchange + PBE correlation; Sec. 2.1 names
 hybrids among the functionals the method serves) through the C-ABI against the oracle, in both
 forms and through the many-molecule call: float64 |dE| <= 1e-9 Eh and max |dV| <= 1e-9; mixed
-|dE| <= 1e-7 Eh and max |dV| <= 1e-6 (the small-case bounds of the tensor-core form)."""
+|dE| <= 1e-7 Eh and max |dV| <= 1e-7 (the small-case bounds of the tensor-core form)."""
 import numpy as np
 import pytest
 

@@ -2,7 +2,7 @@
 
 The mixed form's bound is |dE_xc| <= 1e-6 Eh against the float64 result; its exact-level
 Ozaki slicing is expected to do far better, so the small cases are held to 1e-7 Eh and
-max |dV_ij| <= 1e-6, and per-batch energies at full size to 1e-8 Eh."""
+max |dV_ij| <= 1e-7, and per-batch energies at full size to 1e-8 Eh."""
 import numpy as np
 import pytest
 

@@ -1,7 +1,7 @@
 """Spin-unrestricted form (the extension of Sec. 2.1) through the C-ABI against the oracle:
 |dE| <= 1e-9 Eh, max |dV^s_ij| <= 1e-9 per spin (float64 form), and the spin-restricted result
 recovered exactly enough (1e-12 relative) when P^a = P^b = P/2.  The tensor-core (mixed) form
-takes the mixed form's small-case bounds: |dE| <= 1e-7 Eh, |dN| <= 1e-8, max |dV^s| <= 1e-6,
+takes the mixed form's small-case bounds: |dE| <= 1e-7 Eh, |dN| <= 1e-8, max |dV^s| <= 1e-7,
 and at full size |dE| <= 1e-6 Eh against its float64 form."""
 import numpy as np
 import pytest
